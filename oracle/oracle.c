@@ -1,0 +1,402 @@
+/*
+ * FP64 CPU oracle for the split-explicit barotropic subcycle of Banerjee, Scholz,
+ * Danilov, Klingbeil and Sidorenko, "Split-explicit external mode solver in finite
+ * volume sea ice ocean model FESOM2" (arXiv 2311.08241).
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain reference against which the
+ * CUDA path is checked. Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load it; the library never links or calls it, and it shares no code,
+ * header, table or helper with the library.
+ *
+ * What it computes (all in double precision, no FMA contraction: build with
+ * -ffp-contract=off):
+ *
+ *   Barotropic system, Eq. (4.5):  dU/dt + f e_z x U + g H grad(eta) = R,
+ *                                  deta/dt + div(U) = 0,   H = H0 + eta   (W = 0).
+ *   Substep of the dissipative forward-backward scheme, Eq. (4.10), dt = tau/M:
+ *       U^{m+1} = U^m - dt [ (f/2) e_z x (U^{m+1} + U^m) + g H^m grad(eta^m) - R ]
+ *       eta^{m+1} = eta^m - dt div[ (1+theta) U^{m+1} - theta U^m ]
+ *     (the bracket of Eq. 4.10 is printed with "- gH grad(eta) - R"; the signs
+ *      used here are the ones Eq. 4.5 fixes.)
+ *   After M substeps, Sect. 2.3: <eta>^{n+1} = eta^M, <U>^{n+1} = U^M, and the
+ *   time-mean transport of Eq. (4.12):
+ *       <<U>> = (1/M) sum_{m=1..M} U^m + (theta/M) (U^M - U^0).
+ *   U^0 of a baroclinic step is the U^M of the previous one (Sect. 2.3).
+ *
+ * Spatial discretisation (the paper defers it to Danilov et al. 2017): eta on
+ * vertices, U constant on triangles. The gradient of eta on a triangle is the
+ * Green-Gauss contour sum over its three edges (exact for the linear interpolant).
+ * The divergence at a vertex is the net flux out of its median-dual cell (the
+ * polygon joining edge midpoints and triangle centroids around the vertex) divided
+ * by that cell's area; it is evaluated edge by edge: for an edge (a,b) each
+ * adjacent triangle contributes the flux of its U through the segment from the
+ * edge midpoint to the triangle centroid, counted out of a's cell and into b's.
+ * A coast edge has one adjacent triangle and no flux through the coast itself.
+ * H on a triangle is the mean of H0 + eta over its corners (H0 alone when the
+ * linear option is chosen). Coriolis is taken at the triangle centroid.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct {
+    int nv, ne, ned;
+    int *tri;          /* ne*3 */
+    double *xy;        /* ne*6, element-frame corners */
+    double *depth_v;   /* nv */
+    double *f_e;       /* ne */
+    double *area_e;    /* ne, shoelace area of the triangle */
+    double *area_v;    /* nv, median-dual cell area */
+    int *edge_v;       /* ned*2, edge_v[2k] < edge_v[2k+1] */
+    int *edge_e;       /* ned*2, adjacent triangles, -1 where absent */
+    double *seg;       /* ned*2*2: (Nx,Ny) per side, the segment's normal times length,
+                          pointing from the cell of edge_v[2k] into that of edge_v[2k+1] */
+    int *vedge_off;    /* nv+1 */
+    int *vedge;        /* 2*ned, incident edges of each vertex in increasing edge order */
+} omesh;
+
+static void omesh_free(omesh *m)
+{
+    if (!m) return;
+    free(m->tri); free(m->xy); free(m->depth_v); free(m->f_e); free(m->area_e); free(m->area_v);
+    free(m->edge_v); free(m->edge_e); free(m->seg); free(m->vedge_off); free(m->vedge);
+    free(m);
+}
+
+typedef struct { long long key; int e; int k; } halfedge;
+
+static int cmp_half(const void *pa, const void *pb)
+{
+    const halfedge *a = (const halfedge *)pa, *b = (const halfedge *)pb;
+    if (a->key < b->key) return -1;
+    if (a->key > b->key) return 1;
+    if (a->e != b->e) return a->e < b->e ? -1 : 1;
+    return a->k - b->k;
+}
+
+/* Polygon area by the shoelace formula, vertices in order. */
+static double shoelace(const double *px, const double *py, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; i++) {
+        int j = (i + 1) % n;
+        s += px[i] * py[j] - px[j] * py[i];
+    }
+    return 0.5 * s;
+}
+
+/* Build the oracle's mesh. status: 0 ok, -1 bad index, -2 non-positive area,
+ * -3 an edge shared by more than two triangles, -4 allocation. */
+void *oracle_mesh_new(int nv, int ne, const int *tri, const double *xy,
+                      const double *depth_v, const double *f_e, int *status)
+{
+    *status = 0;
+    omesh *m = (omesh *)calloc(1, sizeof(omesh));
+    if (!m) { *status = -4; return NULL; }
+    m->nv = nv; m->ne = ne;
+    m->tri = (int *)malloc(sizeof(int) * 3 * (size_t)ne);
+    m->xy = (double *)malloc(sizeof(double) * 6 * (size_t)ne);
+    m->depth_v = (double *)malloc(sizeof(double) * (size_t)nv);
+    m->f_e = (double *)malloc(sizeof(double) * (size_t)ne);
+    m->area_e = (double *)malloc(sizeof(double) * (size_t)ne);
+    m->area_v = (double *)calloc((size_t)nv, sizeof(double));
+    if (!m->tri || !m->xy || !m->depth_v || !m->f_e || !m->area_e || !m->area_v) {
+        *status = -4; omesh_free(m); return NULL;
+    }
+    memcpy(m->tri, tri, sizeof(int) * 3 * (size_t)ne);
+    memcpy(m->xy, xy, sizeof(double) * 6 * (size_t)ne);
+    memcpy(m->depth_v, depth_v, sizeof(double) * (size_t)nv);
+    memcpy(m->f_e, f_e, sizeof(double) * (size_t)ne);
+
+    for (int e = 0; e < ne; e++)
+        for (int k = 0; k < 3; k++)
+            if (tri[3 * e + k] < 0 || tri[3 * e + k] >= nv) { *status = -1; omesh_free(m); return NULL; }
+
+    /* triangle areas and median-dual cell areas (sub-quad of each corner) */
+    for (int e = 0; e < ne; e++) {
+        const double *p = m->xy + 6 * e;
+        double px[3] = {p[0], p[2], p[4]}, py[3] = {p[1], p[3], p[5]};
+        double A = shoelace(px, py, 3);
+        if (!(A > 0.0)) { *status = -2; omesh_free(m); return NULL; }
+        m->area_e[e] = A;
+        double cx = (px[0] + px[1] + px[2]) / 3.0, cy = (py[0] + py[1] + py[2]) / 3.0;
+        for (int k = 0; k < 3; k++) {
+            int kn = (k + 1) % 3, kp = (k + 2) % 3;
+            double qx[4] = {px[k], 0.5 * (px[k] + px[kn]), cx, 0.5 * (px[k] + px[kp])};
+            double qy[4] = {py[k], 0.5 * (py[k] + py[kn]), cy, 0.5 * (py[k] + py[kp])};
+            m->area_v[tri[3 * e + k]] += shoelace(qx, qy, 4);
+        }
+    }
+
+    /* edges: group the 3*ne half-edges by their unordered vertex pair */
+    halfedge *h = (halfedge *)malloc(sizeof(halfedge) * 3 * (size_t)ne);
+    if (!h) { *status = -4; omesh_free(m); return NULL; }
+    for (int e = 0; e < ne; e++)
+        for (int k = 0; k < 3; k++) {
+            long long a = tri[3 * e + k], b = tri[3 * e + (k + 1) % 3];
+            long long lo = a < b ? a : b, hi = a < b ? b : a;
+            h[3 * e + k].key = lo * (long long)nv + hi;
+            h[3 * e + k].e = e;
+            h[3 * e + k].k = k;
+        }
+    qsort(h, 3 * (size_t)ne, sizeof(halfedge), cmp_half);
+    int ned = 0;
+    for (size_t i = 0; i < 3 * (size_t)ne;) {
+        size_t j = i;
+        while (j < 3 * (size_t)ne && h[j].key == h[i].key) j++;
+        if (j - i > 2) { free(h); *status = -3; omesh_free(m); return NULL; }
+        ned++;
+        i = j;
+    }
+    m->ned = ned;
+    m->edge_v = (int *)malloc(sizeof(int) * 2 * (size_t)ned);
+    m->edge_e = (int *)malloc(sizeof(int) * 2 * (size_t)ned);
+    m->seg = (double *)calloc(4 * (size_t)ned, sizeof(double));
+    if (!m->edge_v || !m->edge_e || !m->seg) { free(h); *status = -4; omesh_free(m); return NULL; }
+    int k = 0;
+    for (size_t i = 0; i < 3 * (size_t)ne;) {
+        size_t j = i;
+        while (j < 3 * (size_t)ne && h[j].key == h[i].key) j++;
+        int a = (int)(h[i].key / nv), b = (int)(h[i].key % nv);
+        m->edge_v[2 * k] = a;
+        m->edge_v[2 * k + 1] = b;
+        m->edge_e[2 * k] = -1;
+        m->edge_e[2 * k + 1] = -1;
+        for (size_t s = i; s < j; s++) {
+            int e = h[s].e;
+            int side = (int)(s - i);
+            m->edge_e[2 * k + side] = e;
+            /* corners of a and b inside e */
+            const double *p = m->xy + 6 * e;
+            int ka = -1, kb = -1;
+            for (int c = 0; c < 3; c++) {
+                if (tri[3 * e + c] == a) ka = c;
+                if (tri[3 * e + c] == b) kb = c;
+            }
+            double ax = p[2 * ka], ay = p[2 * ka + 1], bx = p[2 * kb], by = p[2 * kb + 1];
+            double cx = (p[0] + p[2] + p[4]) / 3.0, cy = (p[1] + p[3] + p[5]) / 3.0;
+            double mx = 0.5 * (ax + bx), my = 0.5 * (ay + by);
+            double dx = cx - mx, dy = cy - my;
+            double nx = dy, ny = -dx;               /* one of the two normals of length |d| */
+            if (nx * (bx - ax) + ny * (by - ay) < 0.0) { nx = -nx; ny = -ny; }
+            m->seg[4 * k + 2 * side] = nx;
+            m->seg[4 * k + 2 * side + 1] = ny;
+        }
+        k++;
+        i = j;
+    }
+    free(h);
+
+    /* incident edges per vertex, for an ordered per-vertex sum */
+    m->vedge_off = (int *)calloc((size_t)nv + 1, sizeof(int));
+    m->vedge = (int *)malloc(sizeof(int) * 2 * (size_t)ned);
+    if (!m->vedge_off || !m->vedge) { *status = -4; omesh_free(m); return NULL; }
+    for (int q = 0; q < ned; q++) {
+        m->vedge_off[m->edge_v[2 * q] + 1]++;
+        m->vedge_off[m->edge_v[2 * q + 1] + 1]++;
+    }
+    for (int v = 0; v < nv; v++) m->vedge_off[v + 1] += m->vedge_off[v];
+    int *fill = (int *)malloc(sizeof(int) * (size_t)nv);
+    if (!fill) { *status = -4; omesh_free(m); return NULL; }
+    memcpy(fill, m->vedge_off, sizeof(int) * (size_t)nv);
+    for (int q = 0; q < ned; q++) {
+        m->vedge[fill[m->edge_v[2 * q]]++] = q;
+        m->vedge[fill[m->edge_v[2 * q + 1]]++] = q;
+    }
+    free(fill);
+    return m;
+}
+
+void oracle_mesh_free(void *hm) { omesh_free((omesh *)hm); }
+
+int oracle_mesh_info(void *hm, int *ned, int *nbnd)
+{
+    omesh *m = (omesh *)hm;
+    int nb = 0;
+    for (int q = 0; q < m->ned; q++) nb += (m->edge_e[2 * q + 1] < 0);
+    *ned = m->ned;
+    *nbnd = nb;
+    return 0;
+}
+
+int oracle_areas(void *hm, double *area_v, double *area_e)
+{
+    omesh *m = (omesh *)hm;
+    if (area_v) memcpy(area_v, m->area_v, sizeof(double) * (size_t)m->nv);
+    if (area_e) memcpy(area_e, m->area_e, sizeof(double) * (size_t)m->ne);
+    return 0;
+}
+
+int oracle_edges(void *hm, int *edge_v, int *edge_e)
+{
+    omesh *m = (omesh *)hm;
+    memcpy(edge_v, m->edge_v, sizeof(int) * 2 * (size_t)m->ned);
+    memcpy(edge_e, m->edge_e, sizeof(int) * 2 * (size_t)m->ned);
+    return 0;
+}
+
+/* Green-Gauss gradient of the vertex field eta on triangle e. */
+static void gradient_e(const omesh *m, int e, const double *eta, double *gx, double *gy)
+{
+    const double *p = m->xy + 6 * e;
+    const int *t = m->tri + 3 * e;
+    double sx = 0.0, sy = 0.0;
+    for (int k = 0; k < 3; k++) {
+        int kn = (k + 1) % 3;
+        double dx = p[2 * kn] - p[2 * k], dy = p[2 * kn + 1] - p[2 * k + 1];
+        double etam = 0.5 * (eta[t[k]] + eta[t[kn]]);
+        /* outward normal times length of a counter-clockwise edge (dx,dy) is (dy,-dx) */
+        sx += etam * dy;
+        sy += etam * (-dx);
+    }
+    *gx = sx / m->area_e[e];
+    *gy = sy / m->area_e[e];
+}
+
+int oracle_gradient(void *hm, const double *eta, double *grad)
+{
+    omesh *m = (omesh *)hm;
+    for (int e = 0; e < m->ne; e++) gradient_e(m, e, eta, grad + 2 * e, grad + 2 * e + 1);
+    return 0;
+}
+
+/* Net outflow of F through the median-dual cell boundary of every vertex, per area. */
+static void divergence(const omesh *m, const double *F, double *edgeflux, double *div)
+{
+    int ned = m->ned, nv = m->nv;
+    #pragma omp parallel for schedule(static)
+    for (int q = 0; q < ned; q++) {
+        double s = 0.0;
+        for (int side = 0; side < 2; side++) {
+            int e = m->edge_e[2 * q + side];
+            if (e < 0) continue;
+            s += F[2 * e] * m->seg[4 * q + 2 * side] + F[2 * e + 1] * m->seg[4 * q + 2 * side + 1];
+        }
+        edgeflux[q] = s;     /* out of edge_v[2q], into edge_v[2q+1] */
+    }
+    #pragma omp parallel for schedule(static)
+    for (int v = 0; v < nv; v++) {
+        double s = 0.0;
+        for (int i = m->vedge_off[v]; i < m->vedge_off[v + 1]; i++) {
+            int q = m->vedge[i];
+            s += (m->edge_v[2 * q] == v) ? edgeflux[q] : -edgeflux[q];
+        }
+        div[v] = s / m->area_v[v];
+    }
+}
+
+int oracle_divergence(void *hm, const double *F, double *div)
+{
+    omesh *m = (omesh *)hm;
+    double *ef = (double *)malloc(sizeof(double) * (size_t)m->ned);
+    if (!ef) return -4;
+    divergence(m, F, ef, div);
+    free(ef);
+    return 0;
+}
+
+static double element_depth(const omesh *m, int e, const double *eta, int nonlinear_h)
+{
+    const int *t = m->tri + 3 * e;
+    double H = (m->depth_v[t[0]] + m->depth_v[t[1]] + m->depth_v[t[2]]) / 3.0;
+    if (nonlinear_h) H += (eta[t[0]] + eta[t[1]] + eta[t[2]]) / 3.0;
+    return H;
+}
+
+/* Volume sum A_v eta_v and energy sum A_v g eta^2/2 + sum A_e |U|^2/(2 H_e). */
+int oracle_diagnostics(void *hm, const double *eta, const double *U, double g, int nonlinear_h,
+                       double *volume, double *energy)
+{
+    omesh *m = (omesh *)hm;
+    double vol = 0.0, en = 0.0;
+    for (int v = 0; v < m->nv; v++) {
+        vol += m->area_v[v] * eta[v];
+        en += m->area_v[v] * 0.5 * g * eta[v] * eta[v];
+    }
+    for (int e = 0; e < m->ne; e++) {
+        double H = element_depth(m, e, eta, nonlinear_h);
+        en += m->area_e[e] * (U[2 * e] * U[2 * e] + U[2 * e + 1] * U[2 * e + 1]) / (2.0 * H);
+    }
+    *volume = vol;
+    *energy = en;
+    return 0;
+}
+
+/*
+ * Advance nsteps baroclinic steps of the SE subcycle.
+ *   R      ne*2 frozen forcing (element frame, m^2/s^2)
+ *   eta    nv, in: <eta>^n, out: <eta>^{n+nsteps}
+ *   U      ne*2, in: U^0 of the first step (the carried <U>^n), out: U^M of the last
+ *   Umean  ne*2, out: <<U>> of the last step (Eq. 4.12)
+ *   diag   NULL or nsteps*2: (volume, energy) after each step
+ * Returns 0, or -4 on allocation failure, -5 if M < 1.
+ */
+int oracle_advance(void *hm, const double *R, double g, double theta, double tau, int M,
+                   int nonlinear_h, int nsteps, double *eta, double *U, double *Umean, double *diag)
+{
+    omesh *m = (omesh *)hm;
+    if (M < 1) return -5;
+    int ne = m->ne, nv = m->nv;
+    double dt = tau / (double)M;
+    double *F = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
+    double *U0 = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
+    double *sumU = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
+    double *div = (double *)malloc(sizeof(double) * (size_t)nv);
+    double *ef = (double *)malloc(sizeof(double) * (size_t)m->ned);
+    if (!F || !U0 || !sumU || !div || !ef) {
+        free(F); free(U0); free(sumU); free(div); free(ef);
+        return -4;
+    }
+    for (int n = 0; n < nsteps; n++) {
+        memcpy(U0, U, sizeof(double) * 2 * (size_t)ne);
+        memset(sumU, 0, sizeof(double) * 2 * (size_t)ne);
+        for (int s = 0; s < M; s++) {
+            /* momentum: Crank-Nicolson Coriolis, pressure at eta^m with H^m, frozen R */
+            #pragma omp parallel for schedule(static)
+            for (int e = 0; e < ne; e++) {
+                double gx, gy;
+                gradient_e(m, e, eta, &gx, &gy);
+                double H = element_depth(m, e, eta, nonlinear_h);
+                double a = 0.5 * dt * m->f_e[e];
+                double ux = U[2 * e], uy = U[2 * e + 1];
+                /* (I + a J) U' = (I - a J) U + dt (-g H grad eta + R),  J = [[0,-1],[1,0]] */
+                double A11 = 1.0, A12 = -a, A21 = a, A22 = 1.0;
+                double bx = ux + a * uy + dt * (-g * H * gx + R[2 * e]);
+                double by = -a * ux + uy + dt * (-g * H * gy + R[2 * e + 1]);
+                double det = A11 * A22 - A12 * A21;
+                double nx = (bx * A22 - A12 * by) / det;
+                double ny = (A11 * by - A21 * bx) / det;
+                F[2 * e] = (1.0 + theta) * nx - theta * ux;
+                F[2 * e + 1] = (1.0 + theta) * ny - theta * uy;
+                U[2 * e] = nx;
+                U[2 * e + 1] = ny;
+                sumU[2 * e] += nx;
+                sumU[2 * e + 1] += ny;
+            }
+            /* continuity with the theta-weighted transport */
+            divergence(m, F, ef, div);
+            #pragma omp parallel for schedule(static)
+            for (int v = 0; v < nv; v++) eta[v] -= dt * div[v];
+        }
+        for (int e = 0; e < ne; e++)
+            for (int c = 0; c < 2; c++)
+                Umean[2 * e + c] = sumU[2 * e + c] / (double)M + theta / (double)M * (U[2 * e + c] - U0[2 * e + c]);
+        if (diag) oracle_diagnostics(m, eta, U, g, nonlinear_h, diag + 2 * n, diag + 2 * n + 1);
+    }
+    free(F); free(U0); free(sumU); free(div); free(ef);
+    return 0;
+}
+
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}

@@ -1,0 +1,305 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix (no GPU).
+
+Each test ties the oracle to something other than itself: the paper's printed
+characteristic matrix and polynomial (Sect. 3), exact invariants of Eqs. (4.10)-(4.12),
+closed-form solutions of special cases and a dense brute force built the
+finite-element way.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import brute, closed
+from oracle import runner as orc
+from paper_2311_08241_gb300 import inputs as I
+
+
+# ---------------------------------------------------------------- Sect. 3 closed forms
+
+def _same_roots(a, b, atol):
+    a = list(a)
+    for r in b:
+        i = int(np.argmin([abs(r - x) for x in a]))
+        if abs(r - a[i]) > atol:
+            return False
+        a.pop(i)
+    return True
+
+
+def _physical_root(c, theta):
+    lam = np.linalg.eigvals(closed.se_matrix(c, theta))
+    return lam[np.argmin(np.abs(lam - np.exp(1j * c)))]
+
+
+def test_se_matrix_roots_are_roots_of_printed_polynomial(golden_se):
+    th = golden_se["theta"]
+    for c in (0.01, 0.3, 1.0, 1.5):
+        ev = np.linalg.eigvals(closed.se_matrix(c, th))
+        rt = np.roots(closed.se_poly(c, th))
+        assert _same_roots(ev, rt, 1e-12)
+
+
+def test_small_courant_expansion_matches_printed_coefficients(golden_se):
+    """Eqs. (dp_2)-(dp_5): lambda = 1 + i c + n c^2 + q c^3 + O(c^4), |lambda| = 1 - chi c^2 + O(c^4)."""
+    th = golden_se["theta"]
+    assert golden_se["chi_fig1"] == pytest.approx(th / 2.0)          # 2 chi = theta
+    n, q = golden_se["n_se"], 1j * golden_se["q_se_imag"]
+    res = []
+    for c in (2e-2, 1e-2, 5e-3):
+        lam = _physical_root(c, th)
+        res.append(abs(lam - (1 + 1j * c + n * c * c + q * c ** 3)))
+        assert abs(abs(lam) - (1 - golden_se["chi_fig1"] * c * c)) < 2 * c ** 4
+    # the remainder is O(c^4) (for this scheme even O(c^5)): halving c divides it by >= ~16,
+    # while a wrong n or q would leave an O(c^2) or O(c^3) remainder (ratio 4 or 8)
+    assert res[0] / res[1] > 14 and res[1] / res[2] > 14
+
+
+def test_lattice_recurrence_has_the_printed_spectrum(golden_se):
+    """The per-mode recurrence of the mesh scheme has the eigenvalues of Eq. (3.7) with c^2 = gH kappa^2 dt^2."""
+    th = golden_se["theta"]
+    for kappa2, gH, dt in ((1e-9, 4e4, 20.0), (3e-8, 3e4, 12.0), (8e-8, 5e4, 5.0)):
+        c = math.sqrt(gH * kappa2) * dt
+        a = np.linalg.eigvals(closed.lattice_recurrence(kappa2, gH, dt, th))
+        b = np.linalg.eigvals(closed.se_matrix(c, th))
+        assert _same_roots(a, b, 1e-12)
+
+
+def test_phase_speed_tends_to_sqrt_gH():
+    """Long waves: arg(lambda) / (k dt) -> sqrt(gH) and damping per substep -> 1 as k dx -> 0."""
+    gH = 9.81 * 4000.0
+    th = 0.14
+    errs = []
+    for n in (32, 64, 128, 256):
+        dx = 1e6 / n
+        dt = 0.4 * dx / math.sqrt(gH)
+        k2 = closed.kappa2_square(n, dx, 1, 0)
+        lam = np.linalg.eigvals(closed.lattice_recurrence(k2, gH, dt, th))
+        lam = lam[np.argmax(lam.imag)]
+        k = 2 * math.pi / 1e6
+        errs.append(abs(np.angle(lam) / (k * dt) - math.sqrt(gH)) / math.sqrt(gH))
+    assert errs[-1] < 1e-3
+    assert all(errs[i + 1] < 0.3 * errs[i] for i in range(len(errs) - 1))  # second order
+
+
+# ---------------------------------------------------------------- oracle vs closed forms
+
+@pytest.mark.parametrize("kx,ky,theta", [(1, 0, 0.14), (3, 2, 0.14), (5, 7, 0.0), (2, 1, 0.5)])
+def test_oracle_periodic_wave_matches_closed_form(kx, ky, theta):
+    """P1: a cosine mode on the periodic right-triangle mesh evolves by the 2x2 recurrence exactly."""
+    case = I.periodic_wave_case(n=16, kx=kx, ky=ky, theta=theta, nsteps=3)
+    p = case.params
+    eta, U, Umean, _ = orc.run_case(case)
+    dt = p.tau / p.M
+    gH = p.g * 4000.0
+    k2 = closed.kappa2_square(16, 10e3, kx, ky)
+    u_e = closed.mode_amplitude(k2, gH, dt, p.theta, case.nsteps * p.M)
+    assert np.max(np.abs(eta - u_e[1] * case.eta0)) < 1e-11
+    assert abs(u_e[1]) < 1.0          # dissipative for theta > 0, neutral for theta = 0
+    if theta == 0.0:
+        assert abs(abs(u_e[1]) - 1.0) < 1.0 and np.max(np.abs(eta)) > 0.1
+
+
+def test_oracle_stability_boundary():
+    """P8: c = 2/sqrt(1+2 theta) separates bounded from growing runs (checkerboard mode)."""
+    n, dx, H, th = 8, 10e3, 4000.0, 0.14
+    gH = 9.81 * H
+    kappa_max = math.sqrt(closed.kappa2_square(n, dx, n // 2, n // 2))
+    out = {}
+    for frac in (0.97, 1.03):
+        dt = frac * closed.stability_limit(th) / (kappa_max * math.sqrt(gH))
+        case = I.periodic_wave_case(n=n, kx=n // 2, ky=n // 2, theta=th, M=40, tau=40 * dt, nsteps=5)
+        eta, *_ = orc.run_case(case)
+        out[frac] = np.max(np.abs(eta))
+    assert out[0.97] <= 1.0
+    assert out[1.03] > 10.0
+
+
+def test_oracle_inertial_oscillation():
+    """P4: uniform U on a periodic mesh turns clockwise by 2 atan(f dt/2) per substep, eta stays 0."""
+    mesh = I.periodic_square_mesh(8, 10e3, f=1e-4)
+    p = I.Params(tau=600.0, M=30, nonlinear_h=1)
+    U0 = np.tile([1.3, -0.4], (mesh.ne, 1))
+    eta, U, Umean, _ = orc.OracleMesh(mesh).advance(np.zeros((mesh.ne, 2)), p, 4, np.zeros(mesh.nv), U0)
+    dt = p.tau / p.M
+    phi = closed.inertial_rotation(1e-4, dt)
+
+    def rot(m):
+        c, s = math.cos(m * phi), math.sin(m * phi)
+        return np.array([c * 1.3 + s * -0.4, -s * 1.3 + c * -0.4])
+
+    assert np.max(np.abs(eta)) < 1e-12
+    assert np.max(np.abs(U - rot(4 * p.M))) < 1e-12
+    # time mean of the last step from the analytic sequence (Eq. 4.12)
+    m0 = 3 * p.M
+    want = sum(rot(m0 + m) for m in range(1, p.M + 1)) / p.M + p.theta / p.M * (rot(4 * p.M) - rot(m0))
+    assert np.max(np.abs(Umean - want)) < 1e-12
+
+
+def test_oracle_uniform_forcing_closed_form():
+    """P5: uniform R, f != 0: U^m = U* + Rot^m (U^0 - U*), with f e_z x U* = R."""
+    f = 1.2e-4
+    mesh = I.periodic_square_mesh(6, 10e3, f=f)
+    p = I.Params(tau=480.0, M=40, nonlinear_h=0)
+    R = np.tile([2e-4, -1e-4], (mesh.ne, 1))
+    eta, U, Umean, _ = orc.OracleMesh(mesh).advance(R, p, 3, np.zeros(mesh.nv), np.zeros((mesh.ne, 2)))
+    Ustar = np.array([R[0, 1] / f, -R[0, 0] / f])
+    phi = closed.inertial_rotation(f, p.tau / p.M)
+    m = 3 * p.M
+    d = -Ustar
+    c, s = math.cos(m * phi), math.sin(m * phi)
+    want = Ustar + np.array([c * d[0] + s * d[1], -s * d[0] + c * d[1]])
+    assert np.max(np.abs(U - want)) < 1e-10
+    assert np.max(np.abs(eta)) < 1e-12
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_oracle_volume_conservation_basin():
+    """P3: sum A_v eta_v is constant on the closed basin (20 steps, nonlinear H)."""
+    case = I.basin_case()
+    om = orc.OracleMesh(case.mesh)
+    av, ae = om.areas()
+    v0 = float(np.sum(av * case.eta0))
+    eta, U, Umean, diag = om.advance(case.R, case.params, case.nsteps, case.eta0, case.U0, want_diag=True)
+    scale = float(np.sum(av * np.abs(case.eta0)))
+    assert np.max(np.abs(diag[:, 0] - v0)) <= 1e-12 * scale
+    assert np.max(np.abs(eta - case.eta0)) > 1e-2       # the bump did move
+
+
+@pytest.mark.parametrize("nonlinear_h", [0, 1])
+def test_oracle_summation_identity(nonlinear_h):
+    """P2, Eqs. (4.11)-(4.12): eta^M - eta^0 = -tau D <<U>> at every vertex, to roundoff."""
+    case = I.tiny_jittered_case(nx=9, ny=7, seed=3, nonlinear_h=nonlinear_h, M=7, tau=70.0)
+    om = orc.OracleMesh(case.mesh)
+    eta1, U1, Um, _ = om.advance(case.R, case.params, 1, case.eta0, case.U0)
+    lhs = eta1 - case.eta0
+    rhs = -case.params.tau * om.divergence(Um)
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * max(1.0, np.max(np.abs(lhs)))
+    # a second step starts from the carried U^M
+    eta2, U2, Um2, _ = om.advance(case.R, case.params, 1, eta1, U1)
+    assert np.max(np.abs((eta2 - eta1) + case.params.tau * om.divergence(Um2))) < 1e-12
+
+
+def test_oracle_point_symmetry_basin():
+    """P7: the basin mesh and the centred bump are symmetric under a 180-degree turn."""
+    case = I.basin_case(nsteps=5)
+    eta, U, Umean, _ = orc.run_case(case)
+    nx, ny = 101, 51
+    e2 = eta.reshape(ny, nx)
+    assert np.max(np.abs(e2 - e2[::-1, ::-1])) < 1e-12 * np.max(np.abs(eta))
+
+
+def test_oracle_geometry_invariants():
+    """Median-dual cells tile the mesh; Green-Gauss is exact for linear fields; closed cells leak nothing."""
+    case = I.tiny_jittered_case(nx=10, ny=8, seed=5)
+    om = orc.OracleMesh(case.mesh)
+    av, ae = om.areas()
+    assert abs(av.sum() - ae.sum()) < 1e-9 * ae.sum()
+    P = case.mesh.pos[:, :2]
+    g = om.gradient(3e-6 * P[:, 0] - 7e-6 * P[:, 1] + 0.25)
+    assert np.max(np.abs(g - np.array([3e-6, -7e-6]))) < 1e-18
+    rng = np.random.default_rng(0)
+    F = rng.standard_normal((case.mesh.ne, 2))
+    assert abs(np.sum(av * om.divergence(F))) < 1e-9 * np.sum(av * np.abs(om.divergence(F)))
+    # a uniform field has zero divergence on a periodic mesh (every cell is closed)
+    pm = I.periodic_square_mesh(5, 1e3)
+    pom = orc.OracleMesh(pm)
+    assert np.max(np.abs(pom.divergence(np.tile([0.7, -0.2], (pm.ne, 1))))) < 1e-15
+    pav, _ = pom.areas()
+    assert np.allclose(pav, 1e3 ** 2, rtol=1e-13)
+
+
+def test_oracle_rejects_bad_meshes():
+    case = I.tiny_jittered_case()
+    m = case.mesh
+    bad = I.Mesh(m.name, m.tri.copy(), m.xy.copy(), m.pos, m.depth, m.coriolis)
+    bad.tri[0, 0] = m.nv
+    with pytest.raises(ValueError, match="-1"):
+        orc.OracleMesh(bad)
+    bad = I.Mesh(m.name, m.tri.copy(), m.xy.copy(), m.pos, m.depth, m.coriolis)
+    bad.xy[0, [1, 2]] = bad.xy[0, [2, 1]]
+    with pytest.raises(ValueError, match="-2"):
+        orc.OracleMesh(bad)
+    # an edge shared by three triangles
+    tri = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], dtype=np.int32)
+    xy = np.array([[[0, 0], [1, 0], [0, 1]], [[1, 0], [0, 0], [0, -1]], [[0, 0], [1, 0], [1, 1]]], float)
+    nm = I.Mesh("t", tri, xy, np.zeros((5, 3)), np.ones(5), np.zeros(3))
+    with pytest.raises(ValueError, match="-3"):
+        orc.OracleMesh(nm)
+
+
+# ---------------------------------------------------------------- brute force
+
+def _brute_meshes():
+    yield "jittered-nonlinear", I.tiny_jittered_case(nx=6, ny=5, seed=11, nonlinear_h=1)
+    yield "jittered-linear", I.tiny_jittered_case(nx=7, ny=5, seed=12, nonlinear_h=0)
+    X, F = I.icosphere(1)
+    xy, lat = I.sphere_element_frames(X * 6.371e6, F)
+    rng = np.random.default_rng(4)
+    sm = I.Mesh("sphere1", F, xy, X, 3000.0 + 1000.0 * rng.random(X.shape[0]), 2 * 7.292e-5 * np.sin(lat))
+    p = I.Params(tau=3000.0, M=6, nonlinear_h=1)
+    yield "sphere-level1", I.Case("s", sm, p, 1e-2 * rng.standard_normal((F.shape[0], 2)),
+                                  0.2 * rng.standard_normal(X.shape[0]),
+                                  20.0 * rng.standard_normal((F.shape[0], 2)), 2)
+
+
+@pytest.mark.parametrize("name,case", list(_brute_meshes()), ids=lambda x: x if isinstance(x, str) else "")
+def test_oracle_matches_brute_force(name, case):
+    """P6: the edge-form oracle equals the finite-element dense construction on tiny meshes."""
+    om = orc.OracleMesh(case.mesh)
+    e1, U1, M1, _ = om.advance(case.R, case.params, case.nsteps, case.eta0, case.U0)
+    e2, U2, M2 = brute.advance(case.mesh, case.R, case.params, case.nsteps, case.eta0, case.U0)
+    se = max(1.0, np.max(np.abs(e2)))
+    su = max(1.0, np.max(np.abs(U2)))
+    assert np.max(np.abs(e1 - e2)) < 1e-11 * se
+    assert np.max(np.abs(U1 - U2)) < 1e-11 * su
+    assert np.max(np.abs(M1 - M2)) < 1e-11 * su
+
+
+def test_oracle_operators_match_finite_element_adjoint():
+    """The edge-form divergence is minus the area-weighted adjoint of the P1 gradient."""
+    case = I.tiny_jittered_case(nx=8, ny=6, seed=21)
+    om = orc.OracleMesh(case.mesh)
+    G, D, Ae, Av = brute.p1_operators(case.mesh)
+    rng = np.random.default_rng(1)
+    eta = rng.standard_normal(case.mesh.nv)
+    F = rng.standard_normal((case.mesh.ne, 2))
+    assert np.allclose(om.gradient(eta).reshape(-1), G @ eta, rtol=1e-12, atol=1e-18)
+    assert np.allclose(om.divergence(F), D @ F.reshape(-1), rtol=1e-11, atol=1e-16)
+    av, ae = om.areas()
+    assert np.allclose(av, Av, rtol=1e-13) and np.allclose(ae, Ae, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- the pins catch planted mistakes
+
+PLANTS = {
+    # dropped theta weighting in the continuity flux
+    "drop_theta": ("F[2 * e] = (1.0 + theta) * nx - theta * ux;", "F[2 * e] = nx;"),
+    # wrong sign of the pressure gradient (the sign printed in the Eq. 4.10 bracket)
+    "pressure_sign": ("double bx = ux + a * uy + dt * (-g * H * gx + R[2 * e]);",
+                      "double bx = ux + a * uy + dt * (g * H * gx + R[2 * e]);"),
+    # Coriolis turned the wrong way
+    "coriolis_sign": ("double A11 = 1.0, A12 = -a, A21 = a, A22 = 1.0;",
+                      "double A11 = 1.0, A12 = a, A21 = -a, A22 = 1.0;"),
+    # mean without the theta correction of Eq. (4.12)
+    "mean_no_theta": ("+ theta / (double)M * (U[2 * e + c] - U0[2 * e + c]);", ";"),
+    # divergence counted into the wrong cell
+    "flux_side": ("s += (m->edge_v[2 * q] == v) ? edgeflux[q] : -edgeflux[q];",
+                  "s += (m->edge_v[2 * q] == v) ? -edgeflux[q] : edgeflux[q];"),
+}
+
+
+@pytest.mark.parametrize("plant", sorted(PLANTS))
+def test_pins_catch_planted_mistake(plant):
+    old, new = PLANTS[plant]
+    src = orc.source_text()
+    assert old in src
+    L = orc.build_variant(src.replace(old, new), plant)
+    case = I.tiny_jittered_case(nx=6, ny=5, seed=11, nonlinear_h=1)
+    om = orc.OracleMesh(case.mesh, L)
+    e1, U1, M1, _ = om.advance(case.R, case.params, case.nsteps, case.eta0, case.U0)
+    e2, U2, M2 = brute.advance(case.mesh, case.R, case.params, case.nsteps, case.eta0, case.U0)
+    err = max(np.max(np.abs(e1 - e2)), np.max(np.abs(U1 - U2)) / max(1.0, np.max(np.abs(U2))),
+              np.max(np.abs(M1 - M2)) / max(1.0, np.max(np.abs(M2))))
+    assert err > 1e-6, f"planted mistake {plant} went unnoticed"
