@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Throughput of the split-explicit barotropic subcycle on GB300.
+
+One benchmark step is one baroclinic step of the wind-driven zonal channel
+(4000 x 2000 km, jittered Delaunay mesh with 199,920 vertices and 398,664 triangles,
+beta plane, Gaussian ridge, M = 40 substeps of tau/M = 12 s): every row of the hot
+path (element pass, vertex pass, time-mean accumulation, step epilogue) runs once
+per substep. Metric: vertex-substeps per second, whole job.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank advances its own copy of the
+workload (independent ensemble members, no data exchange); the reported value is
+the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertex-substeps/s"
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--patch-vertices", type=int, default=512)
+    ap.add_argument("--e2e-steps", type=int, default=400)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-substeps", type=int, default=4,
+                    help="substeps of the channel per reference-arm step (a bounded sample)")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_2311_08241_gb300 import inputs as I
+
+    case = I.channel_case()
+    m = case.mesh
+    desc = {
+        "workload": "wind-driven zonal channel 4000x2000 km, jittered Delaunay lattice, beta plane, "
+                    "Gaussian ridge, tau=480 s, M=40",
+        "V": m.nv, "E": m.ne, "M": case.params.M, "tau_s": case.params.tau, "theta": case.params.theta,
+        "nonlinear_h": case.params.nonlinear_h,
+    }
+    return case, desc
+
+
+def algorithmic_bytes_per_substep(V, E):
+    """Bytes one substep must move at minimum with FP32 state and a compensated FP32-pair mean:
+    per element U r/w 16, mean pair r/w 32, corners 12, gradients 16, H0 and f 8, R 8 (92 B);
+    per vertex eta r/w 8, 1/A_v 4 (12 B)."""
+    return 12 * V + 92 * E
+
+
+def measured_hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", "sesw_kernels.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per substep launch from the committed ncu summary, if it matches this kernel source."""
+    p = os.path.join(ROOT, "profiles", "k_substep_channel.md")
+    try:
+        txt = open(p).read()
+    except OSError:
+        return None
+    m1 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not m1 or not m2 or m1.group(1) != kernel_source_hash():
+        return None
+    return float(m2.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(case, seconds, rank):
+    """The FP64 oracle, as it stands, on the host cores: whole baroclinic steps until `seconds` elapse."""
+    from oracle import runner as orc
+
+    om = orc.OracleMesh(case.mesh)
+    cores = orc.set_threads(0)
+    eta, U = case.eta0.copy(), case.U0.copy()
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        eta, U, _, _ = om.advance(case.R, case.params, 1, eta, U)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    om.close()
+    return {"value": case.mesh.nv * case.params.M * steps / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} baroclinic steps ({steps * case.params.M} substeps) of the benchmark workload "
+                      f"from rest, FP64, OpenMP over {cores} threads, {dt:.1f} s wall"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def whole_job_value(V, M, steps, world, slowest_ms):
+    """Vertex-substeps per second of all ranks together, timed by the slowest rank."""
+    return world * V * M * steps / (slowest_ms * 1e-3)
+
+
+def reduce_max(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def run_reference(args, world, rank):
+    """The oracle on the host cores, on bounded samples of the same workload."""
+    if rank != 0:
+        return
+    from oracle import runner as orc
+    from paper_2311_08241_gb300 import inputs as I
+
+    case, desc = workload()
+    S = max(1, args.ref_substeps)
+    p = case.params
+    sample = I.Params(g=p.g, theta=p.theta, tau=p.tau / p.M * S, M=S, nonlinear_h=p.nonlinear_h)
+    om = orc.OracleMesh(case.mesh)
+    cores = orc.set_threads(0)
+    eta, U = case.eta0.copy(), case.U0.copy()
+    for _ in range(args.warmup):
+        eta, U, _, _ = om.advance(case.R, sample, 1, eta, U)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        eta, U, _, _ = om.advance(case.R, sample, 1, eta, U)
+    dt = time.perf_counter() - t0
+    value = case.mesh.nv * S * args.steps / dt
+    sample_txt = (f"each step: {S} substeps (dt = tau/M = {p.tau / p.M:g} s) of the benchmark mesh, FP64 "
+                  f"oracle, OpenMP over {cores} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(desc, sample_substeps_per_step=S),
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": sample_txt},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2311_08241_gb300 import sesw as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case, desc = workload()
+    V, E, M = case.mesh.nv, case.mesh.ne, case.params.M
+    stream = torch.cuda.current_stream(dev)
+    sim = S.Subcycle(local, stream=stream)
+    sim.sesw_set_patch_vertices(args.patch_vertices)
+    sim.sesw_mesh_upload(case.mesh)
+    sim.sesw_set_params(case.params)
+    sim.sesw_set_forcing(case.R)
+    sim.sesw_set_state(case.eta0, case.U0)
+    info = sim.sesw_get_info()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        sim.sesw_advance(1)
+    torch.cuda.synchronize(dev)
+    if sim.sesw_status() != S.SESW_OK:
+        raise RuntimeError("warm-up went unstable")
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps
+        ev[k][0].record(stream)
+        sim.sesw_advance(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    rc = sim.sesw_status()
+    if rc != S.SESW_OK:
+        raise RuntimeError(f"timed run flagged status {rc}")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = reduce_max(sum(step_ms), world, dev)
+    ms_per_step = total_ms / args.steps
+    value = whole_job_value(V, M, args.steps, world, total_ms)
+
+    # roofline of the substep kernel: the step's event time over its M substep launches
+    # (the short epilogue launch is included, so this understates the kernel's rate)
+    b_alg = algorithmic_bytes_per_substep(V, E)
+    mean_step_s = statistics.mean(step_ms) * 1e-3
+    achieved = b_alg / (mean_step_s / M) / 1e9
+    peak, peak_src = measured_hbm_peak()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(), "peak_source": peak_src, "kernel": "k_substep",
+                "bytes_per_launch": b_alg}
+
+    # end to end through the public API with pinned host buffers: each step uploads
+    # its forcing, advances, and reads back eta and <<U>>
+    R_h = torch.from_numpy(np.ascontiguousarray(case.R)).pin_memory()
+    eta_h = torch.empty(V, dtype=torch.float64).pin_memory()
+    Um_h = torch.empty((E, 2), dtype=torch.float64).pin_memory()
+    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        sim.sesw_set_forcing(R_h)
+        sim.sesw_advance(1)
+        sim.sesw_get_state(eta_h, None, Um_h)
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * V * M * n_e2e / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(R_h.numel() * 8),
+           "d2h_bytes_per_step": int(eta_h.numel() * 8 + Um_h.numel() * 8), "steps": n_e2e}
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(desc, patch_vertices=info["patch_vertices"], npatch=info["npatch"],
+                           nslot=info["nslot"], l2="flushed between timed steps (256 MiB write)",
+                           parallelism=f"replicas{world}"),
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (M + 1), "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds, rank)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.gpus != world and world > 1:
+        print(f"warning: --gpus {args.gpus} but WORLD_SIZE {world}", file=sys.stderr)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * sesw — split-explicit shallow-water barotropic subcycle on an unstructured
+ * triangular mesh, for NVIDIA GB300 (sm_103a).
+ *
+ * The library advances the external (barotropic) mode of an ocean model over
+ * baroclinic steps. One baroclinic step of length tau is M substeps of the
+ * dissipative forward-backward scheme of Banerjee et al., "Split-explicit external
+ * mode solver in finite volume sea ice ocean model FESOM2" (arXiv 2311.08241),
+ * Sect. 2.2, Eq. (4.10), applied to the vertically integrated system of Eq. (4.5):
+ *
+ *   U^{m+1} = U^m - dt [ (f/2) e_z x (U^{m+1} + U^m) + g H^m grad(eta^m) - R ]
+ *   eta^{m+1} = eta^m - dt div[ (1+theta) U^{m+1} - theta U^m ],     dt = tau/M,
+ *
+ * with H = H0 + eta (or H0 alone when nonlinear_h = 0), the frozen forcing R of
+ * Eq. (4.4), and the time-mean transport of Eq. (4.12),
+ *
+ *   <<U>> = (1/M) sum_{m=1..M} U^m + (theta/M)(U^M - U^0),
+ *
+ * which satisfies eta^M - eta^0 = -tau div <<U>> exactly (Eq. 4.11). U^0 of each
+ * step is the U^M of the previous one (Sect. 2.3).
+ *
+ * Placement: eta on vertices, U on triangles ("elements"). The gradient of eta on a
+ * triangle is that of its linear interpolant; the divergence at a vertex is the net
+ * flux out of the vertex's median-dual cell divided by the cell's area
+ * (A_v = sum of A_e/3 over the incident triangles). Vectors are stored in each
+ * element's own planar frame (the frame of sesw_mesh.xy). The sign of the
+ * pressure-gradient term is the one Eq. (4.5) fixes (the bracket of Eq. 4.10 prints
+ * the opposite sign).
+ *
+ * Threading: a context is used by one host thread at a time. All device work is
+ * issued on the stream given to sesw_create (or sesw_set_stream).
+ *
+ * Errors: every int-returning call returns SESW_OK (0) or a negative status; the
+ * message of the last failure is available from sesw_last_error. No C++ exception
+ * crosses this interface.
+ */
+#ifndef SESW_H
+#define SESW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SESW_OK         0
+#define SESW_EINVAL    -1   /* bad argument, malformed mesh, unstable parameters */
+#define SESW_ECUDA     -2   /* a CUDA runtime call failed */
+#define SESW_ESTATE    -3   /* call out of order (e.g. advance before mesh upload) */
+#define SESW_ETIMEOUT  -4   /* a bounded device-side wait gave up */
+#define SESW_EUNSTABLE -5   /* non-finite or out-of-bound elevation detected on the device */
+#define SESW_ENOMEM    -6   /* device or host allocation failed */
+
+/* Location of a caller buffer. */
+#define SESW_HOST   0
+#define SESW_DEVICE 1
+
+typedef struct sesw_ctx sesw_ctx;
+
+/* Optional device allocator. alloc returns a device pointer of at least `bytes`
+ * bytes aligned to 256 B, or NULL; free releases it. `user` is passed back
+ * unchanged. When both are NULL the library uses cudaMalloc/cudaFree. */
+typedef void *(*sesw_alloc_fn)(size_t bytes, void *user);
+typedef void (*sesw_free_fn)(void *ptr, void *user);
+
+/* Mesh as supplied by the caller. All pointers are HOST pointers and are only read
+ * during sesw_mesh_upload (the library keeps its own copies).
+ *   nv, ne     number of vertices and triangles (>= 1 each)
+ *   tri        [ne][3] vertex indices in [0, nv); corners counter-clockwise in the
+ *              element's frame; an edge may be shared by at most two triangles,
+ *              traversed in opposite directions
+ *   xy         [ne][3][2] corner coordinates (m) in the element's own planar frame
+ *              (periodic meshes: unwrapped per element; sphere: the plane of the
+ *              flat triangle); the frame also defines the components of U and R
+ *   pos        [nv][3] vertex positions used only to order the mesh along a
+ *              space-filling curve (a 2-D curve when every z is 0, else 3-D);
+ *              NULL keeps the caller's order
+ *   depth      [nv] rest depth H0 (m), > 0; H0 on a triangle is the corner mean
+ *   coriolis   [ne] Coriolis parameter f (1/s) of each triangle */
+typedef struct sesw_mesh {
+    int32_t nv;
+    int32_t ne;
+    const int32_t *tri;
+    const double *xy;
+    const double *pos;
+    const double *depth;
+    const double *coriolis;
+} sesw_mesh;
+
+/* Scheme parameters (Eq. 4.10).
+ *   g            gravity (m/s^2), > 0
+ *   theta        dissipation parameter, >= 0 (the paper uses 0.14)
+ *   tau          baroclinic step (s), > 0; the substep is tau/M
+ *   M            substeps per baroclinic step, 1..65536
+ *   nonlinear_h  1: H = H0 + eta on each triangle (corner mean); 0: H = H0
+ *   scheme       0: dissipative forward-backward (Eq. 4.10); other values are rejected
+ *   flags        bit 0 (SESW_FLAG_NO_STABILITY_CHECK): accept parameters whose Courant
+ *                bound exceeds the stability limit (the bound is conservative)
+ *   eta_bound    |eta| above this (m) or a non-finite value sets SESW_EUNSTABLE; <= 0 means 1e4 */
+#define SESW_FLAG_NO_STABILITY_CHECK 1
+typedef struct sesw_params {
+    double g;
+    double theta;
+    double tau;
+    int32_t M;
+    int32_t nonlinear_h;
+    int32_t scheme;
+    int32_t flags;
+    double eta_bound;
+} sesw_params;
+
+/* Read-only facts about the uploaded mesh and its device layout. */
+typedef struct sesw_info {
+    int32_t nv, ne;
+    int32_t npatch;          /* vertex patches (one CTA each) */
+    int32_t nslot;           /* element slots: ne owned + guest copies on patch borders */
+    int32_t max_patch_slots; /* largest slot count of one patch */
+    int32_t patch_vertices;  /* target vertices per patch */
+    double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
+                                (0 until parameters are set) */
+    double courant_limit;    /* 2/sqrt(1+2 theta), the stability limit of the scheme */
+    int64_t device_bytes;    /* device memory held by the context */
+} sesw_info;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). alloc/free: see sesw_alloc_fn.
+ * On success *out owns the context until sesw_destroy. */
+int sesw_create(sesw_ctx **out, int device, void *cuda_stream,
+                sesw_alloc_fn alloc, sesw_free_fn free_fn, void *user);
+
+/* Replace the stream used for subsequent work. */
+int sesw_set_stream(sesw_ctx *ctx, void *cuda_stream);
+
+/* Set the target number of vertices per patch (>= 32) for the next mesh upload;
+ * default 512. */
+int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
+
+/* Validate, reorder and upload a mesh (mesh prep: geometry, space-filling-curve
+ * order, vertex patches with their boundary element copies, per-vertex incidence).
+ * Resets state and forcing to zero. Synchronises with the device.
+ * Errors: SESW_EINVAL (with a message naming the first bad item), SESW_ENOMEM,
+ * SESW_ECUDA. */
+int sesw_mesh_upload(sesw_ctx *ctx, const sesw_mesh *mesh);
+
+/* Set scheme parameters; requires an uploaded mesh. Rejects (SESW_EINVAL)
+ * parameters whose substep Courant number bound exceeds 2/sqrt(1+2 theta), the
+ * value beyond which the scheme's characteristic polynomial (Eq. dp_1, SE row) has a
+ * root outside the unit circle. The bound is element by element:
+ * c = dt sqrt(3 g max_e H0_e lambda_max(sum_k grad phi_k grad phi_k^T)), an upper
+ * bound of dt sqrt(lambda_max(-div g H0 grad)) for the lumped median-dual operator. */
+int sesw_set_params(sesw_ctx *ctx, const sesw_params *params);
+
+/* Set the state: eta [nv] (m) and U [ne][2] (m^2/s), in the caller's vertex and
+ * element order, as doubles at `where` (SESW_HOST or SESW_DEVICE). U is the U^0 of
+ * the next baroclinic step. Host buffers may be pageable or pinned. */
+int sesw_set_state(sesw_ctx *ctx, const double *eta, const double *U, int where);
+
+/* Set the frozen forcing R [ne][2] (m^2/s^2) of Eq. (4.4), caller order. */
+int sesw_set_forcing(sesw_ctx *ctx, const double *R, int where);
+
+/* Advance nsteps >= 0 baroclinic steps (nsteps*M substeps). Asynchronous on the
+ * context's stream; device-side instability is reported by sesw_status or
+ * sesw_get_state. Requires mesh and parameters. */
+int sesw_advance(sesw_ctx *ctx, int32_t nsteps);
+
+/* Copy out the state in caller order as doubles: eta [nv], U = U^M [ne][2] and
+ * Umean = <<U>> of the last step [ne][2] (Eq. 4.12; zero before the first step).
+ * Any pointer may be NULL. With SESW_HOST the call synchronises with the stream and
+ * returns SESW_EUNSTABLE if the device flagged instability; with SESW_DEVICE the
+ * copies are only enqueued. */
+int sesw_get_state(sesw_ctx *ctx, double *eta, double *U, double *Umean, int where);
+
+/* FP64 diagnostics of the current state: volume sum_v A_v eta_v (m^3) and energy
+ * sum_v A_v g eta_v^2/2 + sum_e A_e |U_e|^2 / (2 H_e) (m^5/s^2). Synchronises. */
+int sesw_diagnostics(sesw_ctx *ctx, double *volume, double *energy);
+
+/* Synchronise and return SESW_OK, SESW_EUNSTABLE or SESW_ETIMEOUT from the device
+ * status word; clears the word. */
+int sesw_status(sesw_ctx *ctx);
+
+/* Validate and lay out a mesh on the host only, with no device involved: the
+ * checks and the patch layout of sesw_mesh_upload for `patch_vertices` vertices per
+ * patch. On success fills info (courant fields and device_bytes 0). On failure
+ * returns SESW_EINVAL and copies the message into msg (NUL-terminated, at most
+ * msglen bytes; msg may be NULL). */
+int sesw_mesh_check(const sesw_mesh *mesh, int32_t patch_vertices, sesw_info *info,
+                    char *msg, size_t msglen);
+
+/* Mesh and layout facts; requires an uploaded mesh. */
+int sesw_get_info(sesw_ctx *ctx, sesw_info *info);
+
+/* Message of the last failed call on this context ("" if none). Valid until the
+ * next call on the context. */
+const char *sesw_last_error(sesw_ctx *ctx);
+
+/* Release all device and host resources. NULL is ignored. */
+void sesw_destroy(sesw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SESW_H */

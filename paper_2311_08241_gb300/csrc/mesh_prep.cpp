@@ -1,0 +1,334 @@
+// Host-side mesh preparation for libsesw: validation, P1 geometry, Hilbert
+// ordering, vertex patches with guest element copies, per-vertex incidence lists.
+//
+// Geometry (the paper defers the spatial discretisation to FESOM2's finite-volume
+// layout: scalars on vertices with median-dual control volumes, transports on
+// triangles): for a counter-clockwise triangle (a, b, c) with area A_e, the
+// gradient of the linear basis function of corner a is rot90(p_c - p_b) / (2 A_e),
+// rot90(x, y) = (-y, x). The median-dual area of a vertex is the sum of A_e/3 over
+// its triangles.
+#include <math.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "sesw_internal.h"
+
+namespace sesw {
+
+// Hilbert index of (x, y) on a 2^bits x 2^bits grid. At each level the quadrant
+// digit is read from the current bit of x and y, then the lower bits are rotated
+// or reflected so the sub-square is traversed in the curve's orientation.
+uint64_t hilbert2d(uint32_t x, uint32_t y, int bits)
+{
+    uint64_t d = 0;
+    for (int b = bits - 1; b >= 0; b--) {
+        uint32_t s = 1u << b;
+        uint32_t rx = (x & s) ? 1u : 0u;
+        uint32_t ry = (y & s) ? 1u : 0u;
+        d += (uint64_t)s * (uint64_t)s * (uint64_t)((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = ~x;
+                y = ~y;
+            }
+            uint32_t t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
+}
+
+// Hilbert index in 3-D, following Skilling's transpose formulation (J. Skilling,
+// "Programming the Hilbert curve", AIP Conf. Proc. 707, 2004): undo the excess
+// rotations level by level, Gray-encode, then interleave the bits of the three
+// transposed coordinates from the most significant level down.
+uint64_t hilbert3d(uint32_t x, uint32_t y, uint32_t z, int bits)
+{
+    uint32_t X[3] = {x, y, z};
+    const int n = 3;
+    uint32_t top = 1u << (bits - 1);
+    for (uint32_t q = top; q > 1; q >>= 1) {
+        uint32_t p = q - 1;
+        for (int i = 0; i < n; i++) {
+            if (X[i] & q) {
+                X[0] ^= p;
+            } else {
+                uint32_t t = (X[0] ^ X[i]) & p;
+                X[0] ^= t;
+                X[i] ^= t;
+            }
+        }
+    }
+    for (int i = 1; i < n; i++) X[i] ^= X[i - 1];
+    uint32_t t = 0;
+    for (uint32_t q = top; q > 1; q >>= 1)
+        if (X[n - 1] & q) t ^= q - 1;
+    for (int i = 0; i < n; i++) X[i] ^= t;
+    uint64_t key = 0;
+    for (int b = bits - 1; b >= 0; b--)
+        for (int i = 0; i < n; i++) key = (key << 1) | ((X[i] >> b) & 1u);
+    return key;
+}
+
+static bool finite(double v) { return std::isfinite(v); }
+
+static void fmt(std::string &err, const char *f, long long a, double b = 0.0)
+{
+    char buf[256];
+    snprintf(buf, sizeof buf, f, a, b);
+    err = buf;
+}
+
+int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::string &err)
+{
+    const int nv = m.nv, ne = m.ne;
+    if (nv < 1 || ne < 1) { err = "mesh needs nv >= 1 and ne >= 1"; return SESW_EINVAL; }
+    if (!m.tri || !m.xy || !m.depth || !m.coriolis) { err = "mesh has a NULL array"; return SESW_EINVAL; }
+    if ((long long)ne * 3 >= (1ll << 31) || (long long)nv >= (1ll << 30)) {
+        err = "mesh too large for 32-bit indexing";
+        return SESW_EINVAL;
+    }
+    if (patch_vertices < 32) patch_vertices = 32;
+
+    // ---- element checks and FP64 geometry (caller order)
+    std::vector<double> A(ne), gph(6 * (size_t)ne);
+    for (int e = 0; e < ne; e++) {
+        const int32_t *t = m.tri + 3 * (size_t)e;
+        for (int k = 0; k < 3; k++)
+            if (t[k] < 0 || t[k] >= nv) { fmt(err, "triangle %lld has a vertex index out of range", e); return SESW_EINVAL; }
+        if (t[0] == t[1] || t[1] == t[2] || t[0] == t[2]) { fmt(err, "triangle %lld repeats a vertex", e); return SESW_EINVAL; }
+        const double *p = m.xy + 6 * (size_t)e;
+        for (int k = 0; k < 6; k++)
+            if (!finite(p[k])) { fmt(err, "triangle %lld has a non-finite coordinate", e); return SESW_EINVAL; }
+        double twoA = (p[2] - p[0]) * (p[5] - p[1]) - (p[4] - p[0]) * (p[3] - p[1]);
+        if (!(twoA > 0.0)) { fmt(err, "triangle %lld is not counter-clockwise with positive area", e); return SESW_EINVAL; }
+        A[e] = 0.5 * twoA;
+        for (int k = 0; k < 3; k++) {
+            const double *pb = p + 2 * ((k + 1) % 3), *pc = p + 2 * ((k + 2) % 3);
+            gph[6 * (size_t)e + 2 * k] = -(pc[1] - pb[1]) / twoA;
+            gph[6 * (size_t)e + 2 * k + 1] = (pc[0] - pb[0]) / twoA;
+        }
+        if (!finite(m.coriolis[e])) { fmt(err, "triangle %lld has a non-finite Coriolis parameter", e); return SESW_EINVAL; }
+    }
+    for (int v = 0; v < nv; v++)
+        if (!(m.depth[v] > 0.0) || !finite(m.depth[v])) { fmt(err, "vertex %lld has a depth that is not positive and finite", v); return SESW_EINVAL; }
+
+    // ---- edges: each shared by at most two triangles, in opposite directions
+    {
+        std::vector<uint64_t> key(3 * (size_t)ne);
+        for (int e = 0; e < ne; e++)
+            for (int k = 0; k < 3; k++) {
+                uint32_t a = (uint32_t)m.tri[3 * (size_t)e + k], b = (uint32_t)m.tri[3 * (size_t)e + (k + 1) % 3];
+                uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
+                // low bit: direction (1 when traversed from the higher to the lower index)
+                key[3 * (size_t)e + k] = (((uint64_t)lo * (uint64_t)nv + hi) << 1) | (a > b ? 1u : 0u);
+            }
+        std::sort(key.begin(), key.end());
+        for (size_t i = 0; i < key.size();) {
+            size_t j = i;
+            while (j < key.size() && (key[j] >> 1) == (key[i] >> 1)) j++;
+            if (j - i > 2) { err = "an edge is shared by more than two triangles"; return SESW_EINVAL; }
+            if (j - i == 2 && (key[i] & 1u) == (key[i + 1] & 1u)) {
+                err = "two triangles traverse a shared edge in the same direction (inconsistent orientation)";
+                return SESW_EINVAL;
+            }
+            i = j;
+        }
+    }
+
+    // ---- median-dual areas; every vertex must be a corner of some triangle
+    std::vector<double> Av(nv, 0.0);
+    for (int e = 0; e < ne; e++)
+        for (int k = 0; k < 3; k++) Av[m.tri[3 * (size_t)e + k]] += A[e] / 3.0;
+    for (int v = 0; v < nv; v++)
+        if (!(Av[v] > 0.0)) { fmt(err, "vertex %lld is not a corner of any triangle", v); return SESW_EINVAL; }
+
+    // ---- vertex order along a Hilbert curve
+    std::vector<int> vperm(nv);
+    std::iota(vperm.begin(), vperm.end(), 0);
+    if (m.pos) {
+        bool flat = true;
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int v = 0; v < nv; v++)
+            for (int c = 0; c < 3; c++) {
+                double x = m.pos[3 * (size_t)v + c];
+                if (!finite(x)) { fmt(err, "vertex %lld has a non-finite position", v); return SESW_EINVAL; }
+                lo[c] = std::min(lo[c], x);
+                hi[c] = std::max(hi[c], x);
+            }
+        if (hi[2] - lo[2] > 0.0) flat = false;
+        double span = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        if (span <= 0.0) span = 1.0;
+        const int bits = 16;
+        const double scale = ((1u << bits) - 1) / span;
+        std::vector<uint64_t> key(nv);
+        for (int v = 0; v < nv; v++) {
+            uint32_t q[3];
+            for (int c = 0; c < 3; c++) q[c] = (uint32_t)((m.pos[3 * (size_t)v + c] - lo[c]) * scale);
+            key[v] = flat ? hilbert2d(q[0], q[1], bits) : hilbert3d(q[0], q[1], q[2], bits);
+        }
+        std::stable_sort(vperm.begin(), vperm.end(), [&](int a, int b) { return key[a] < key[b]; });
+    }
+    std::vector<int> vinv(nv);
+    for (int i = 0; i < nv; i++) vinv[vperm[i]] = i;
+
+    // ---- patches: balanced contiguous ranges of the ordered vertices
+    int npatch = (nv + patch_vertices - 1) / patch_vertices;
+    std::vector<int> patch_v(npatch + 1);
+    for (int p = 0; p <= npatch; p++) patch_v[p] = (int)((long long)p * nv / npatch);
+    std::vector<int> vpatch(nv);
+    int maxpv = 0;
+    for (int p = 0; p < npatch; p++) {
+        for (int v = patch_v[p]; v < patch_v[p + 1]; v++) vpatch[v] = p;
+        maxpv = std::max(maxpv, patch_v[p + 1] - patch_v[p]);
+    }
+
+    // ---- element order: by owner patch (patch of the lowest new corner), then corners
+    struct EK { int lo, mid, hi, e; };
+    std::vector<EK> ek(ne);
+    for (int e = 0; e < ne; e++) {
+        int c[3] = {vinv[m.tri[3 * (size_t)e]], vinv[m.tri[3 * (size_t)e + 1]], vinv[m.tri[3 * (size_t)e + 2]]};
+        std::sort(c, c + 3);
+        ek[e] = {c[0], c[1], c[2], e};
+    }
+    std::sort(ek.begin(), ek.end(), [](const EK &a, const EK &b) {
+        if (a.lo != b.lo) return a.lo < b.lo;
+        if (a.mid != b.mid) return a.mid < b.mid;
+        if (a.hi != b.hi) return a.hi < b.hi;
+        return a.e < b.e;
+    });
+    std::vector<int> eperm(ne), einv(ne);
+    for (int i = 0; i < ne; i++) { eperm[i] = ek[i].e; einv[ek[i].e] = i; }
+    std::vector<int> owner(ne);
+    for (int i = 0; i < ne; i++) owner[i] = vpatch[ek[i].lo];
+
+    // ---- guests: (patch, element) pairs for patches that touch but do not own an element
+    std::vector<std::pair<int, int>> guests;
+    guests.reserve((size_t)ne / 4);
+    for (int i = 0; i < ne; i++) {
+        int ps[3] = {vpatch[ek[i].lo], vpatch[ek[i].mid], vpatch[ek[i].hi]};
+        for (int k = 0; k < 3; k++) {
+            int q = ps[k];
+            if (q == owner[i]) continue;
+            bool dup = false;
+            for (int j = 0; j < k; j++) dup |= (ps[j] == q);
+            if (!dup) guests.push_back({q, i});
+        }
+    }
+    std::sort(guests.begin(), guests.end());
+
+    // ---- slots
+    std::vector<int> own_begin(npatch + 1, 0);
+    for (int i = 0; i < ne; i++) own_begin[owner[i] + 1]++;
+    for (int p = 0; p < npatch; p++) own_begin[p + 1] += own_begin[p];
+    std::vector<int> g_begin(npatch + 1, 0);
+    for (auto &g : guests) g_begin[g.first + 1]++;
+    for (int p = 0; p < npatch; p++) g_begin[p + 1] += g_begin[p];
+
+    const int nslot = ne + (int)guests.size();
+    std::vector<int> patch_slot(npatch + 1), patch_own(npatch);
+    patch_slot[0] = 0;
+    int maxslots = 0;
+    for (int p = 0; p < npatch; p++) {
+        patch_own[p] = own_begin[p + 1] - own_begin[p];
+        int n = patch_own[p] + (g_begin[p + 1] - g_begin[p]);
+        patch_slot[p + 1] = patch_slot[p] + n;
+        maxslots = std::max(maxslots, n);
+    }
+    if (maxslots >= (1 << 28)) { err = "a patch has too many element slots"; return SESW_EINVAL; }
+
+    std::vector<int> slot_elem(nslot);
+    std::vector<char> slot_guest(nslot, 0);
+    for (int p = 0; p < npatch; p++) {
+        int s = patch_slot[p];
+        for (int i = own_begin[p]; i < own_begin[p + 1]; i++) slot_elem[s++] = i;
+        for (int k = g_begin[p]; k < g_begin[p + 1]; k++) { slot_guest[s] = 1; slot_elem[s++] = guests[k].second; }
+    }
+
+    out = HostMesh();
+    out.nv = nv;
+    out.ne = ne;
+    out.npatch = npatch;
+    out.nslot = nslot;
+    out.max_patch_slots = maxslots;
+    out.max_patch_vertices = maxpv;
+    out.patch_vertices = patch_vertices;
+    out.vperm = vperm;
+    out.eperm = eperm;
+    out.patch_v = patch_v;
+    out.patch_slot = patch_slot;
+    out.patch_own = patch_own;
+    out.slot_v.resize(nslot);
+    out.slot_g.resize(nslot);
+    out.slot_c.resize(nslot);
+    for (int s = 0; s < nslot; s++) {
+        int i = slot_elem[s];
+        int e = eperm[i];
+        const int32_t *t = m.tri + 3 * (size_t)e;
+        const double *g = gph.data() + 6 * (size_t)e;
+        double h0 = (m.depth[t[0]] + m.depth[t[1]] + m.depth[t[2]]) / 3.0;
+        out.slot_v[s] = make_int4(vinv[t[0]], vinv[t[1]], vinv[t[2]], slot_guest[s] ? -1 - i : i);
+        out.slot_g[s] = make_float4((float)g[0], (float)g[1], (float)g[2], (float)g[3]);
+        out.slot_c[s] = make_float4((float)A[e], (float)h0, (float)m.coriolis[e], 0.0f);
+    }
+
+    // ---- per-vertex incidence (local slot, corner), ordered by vertex then slot
+    {
+        std::vector<int> cnt(nv + 1, 0);
+        for (int p = 0; p < npatch; p++)
+            for (int s = patch_slot[p]; s < patch_slot[p + 1]; s++) {
+                const int4 c = out.slot_v[s];
+                int cv[3] = {c.x, c.y, c.z};
+                for (int k = 0; k < 3; k++)
+                    if (vpatch[cv[k]] == p) cnt[cv[k] + 1]++;
+            }
+        for (int v = 0; v < nv; v++) cnt[v + 1] += cnt[v];
+        out.vcsr_off = cnt;
+        out.vcsr.resize(cnt[nv]);
+        std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+        for (int p = 0; p < npatch; p++)
+            for (int s = patch_slot[p]; s < patch_slot[p + 1]; s++) {
+                const int4 c = out.slot_v[s];
+                int cv[3] = {c.x, c.y, c.z};
+                for (int k = 0; k < 3; k++)
+                    if (vpatch[cv[k]] == p)
+                        out.vcsr[fill[cv[k]]++] = ((uint32_t)(s - patch_slot[p]) << 2) | (uint32_t)k;
+            }
+    }
+
+    out.inv_av.resize(nv);
+    out.area_v.resize(nv);
+    for (int i = 0; i < nv; i++) {
+        out.area_v[i] = Av[vperm[i]];
+        out.inv_av[i] = (float)(1.0 / Av[vperm[i]]);
+    }
+    out.area_e.resize(ne);
+    out.h0_e.resize(ne);
+    double gmax = 0.0;
+    for (int i = 0; i < ne; i++) {
+        int e = eperm[i];
+        const int32_t *t = m.tri + 3 * (size_t)e;
+        out.area_e[i] = A[e];
+        out.h0_e[i] = (m.depth[t[0]] + m.depth[t[1]] + m.depth[t[2]]) / 3.0;
+        // largest eigenvalue of the 2x2 matrix sum_k dphi_k dphi_k^T
+        const double *g = gph.data() + 6 * (size_t)e;
+        double sxx = 0, sxy = 0, syy = 0;
+        for (int k = 0; k < 3; k++) {
+            sxx += g[2 * k] * g[2 * k];
+            sxy += g[2 * k] * g[2 * k + 1];
+            syy += g[2 * k + 1] * g[2 * k + 1];
+        }
+        double tr = sxx + syy, det = sxx * syy - sxy * sxy;
+        double lmax = 0.5 * tr + sqrt(std::max(0.25 * tr * tr - det, 0.0));
+        gmax = std::max(gmax, out.h0_e[i] * lmax);
+    }
+    out.grad_gram_max_h = gmax;
+    return SESW_OK;
+}
+
+}  // namespace sesw

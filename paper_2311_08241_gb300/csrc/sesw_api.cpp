@@ -1,0 +1,500 @@
+// C-ABI of libsesw (declared in include/sesw.h): context, mesh upload, parameters,
+// state transfer, advance (a CUDA graph of one baroclinic step replayed per step),
+// diagnostics.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sesw_internal.h"
+
+struct sesw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    sesw_alloc_fn alloc = nullptr;
+    sesw_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    std::string err;
+    int patch_vertices = 512;
+    bool have_mesh = false, have_params = false;
+    sesw::DevMesh dm;
+    sesw::DevState ds;
+    std::vector<std::pair<void *, size_t>> allocs;
+    int64_t device_bytes = 0;
+    sesw_params params{};
+    sesw::StepArgs args{};
+    int parity = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int diag_blocks = 1;
+    double grad_gram_max_h = 0.0;
+    double courant_max = 0.0, courant_limit = 0.0;
+    int npatch = 0, nslot = 0, max_patch_slots = 0, patch_vertices_used = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int fail(sesw_ctx *c, int code, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+int fail_cuda(sesw_ctx *c, const char *what, cudaError_t e)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, SESW_ECUDA, m);
+}
+
+#define CK(ctx, call)                                         \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, #call, e_); \
+    } while (0)
+
+void *dalloc(sesw_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (c->alloc) {
+        p = c->alloc(bytes, c->user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        c->allocs.push_back({p, bytes});
+        c->device_bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+void free_all(sesw_ctx *c)
+{
+    for (auto &a : c->allocs) {
+        if (c->free_fn)
+            c->free_fn(a.first, c->user);
+        else
+            cudaFree(a.first);
+    }
+    c->allocs.clear();
+    c->device_bytes = 0;
+    c->dm = sesw::DevMesh();
+    c->ds = sesw::DevState();
+}
+
+void drop_graphs(sesw_ctx *c)
+{
+    for (auto &g : c->graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
+
+template <class T>
+int upload(sesw_ctx *c, T **dst, const std::vector<T> &src, const char *name)
+{
+    *dst = (T *)dalloc(c, sizeof(T) * std::max<size_t>(src.size(), 1));
+    if (!*dst) return fail(c, SESW_ENOMEM, std::string("device allocation failed for ") + name);
+    if (!src.empty()) CK(c, cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, c->stream));
+    return SESW_OK;
+}
+
+template <class T>
+int zalloc(sesw_ctx *c, T **dst, size_t n, const char *name)
+{
+    *dst = (T *)dalloc(c, sizeof(T) * std::max<size_t>(n, 1));
+    if (!*dst) return fail(c, SESW_ENOMEM, std::string("device allocation failed for ") + name);
+    CK(c, cudaMemsetAsync(*dst, 0, sizeof(T) * std::max<size_t>(n, 1), c->stream));
+    return SESW_OK;
+}
+
+#define TRY(x)                  \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != SESW_OK) return r_; \
+    } while (0)
+
+int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaSuccess;
+    int p = parity;
+    for (int m = 0; m < c->params.M && e == cudaSuccess; m++) {
+        e = sesw::launch_substep(c->dm, c->ds, c->args, p, 0, c->cap_stream);
+        p ^= 1;
+    }
+    if (e == cudaSuccess) e = sesw::launch_step_epilogue(c->dm, c->ds, c->args, c->cap_stream);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(c, "kernel launch during graph capture", e);
+    }
+    if (e2 != cudaSuccess) return fail_cuda(c, "cudaStreamEndCapture", e2);
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail_cuda(c, "cudaGraphInstantiate", e);
+    return SESW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sesw_create(sesw_ctx **out, int device, void *cuda_stream, sesw_alloc_fn alloc, sesw_free_fn free_fn,
+                void *user)
+{
+    if (!out) return SESW_EINVAL;
+    *out = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return SESW_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return SESW_ECUDA;
+    }
+    sesw_ctx *c = new (std::nothrow) sesw_ctx();
+    if (!c) return SESW_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = user;
+    DeviceGuard dg(device);
+    if (!dg.ok || cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return SESW_ECUDA;
+    }
+    *out = c;
+    return SESW_OK;
+}
+
+int sesw_set_stream(sesw_ctx *c, void *cuda_stream)
+{
+    if (!c) return SESW_EINVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return SESW_OK;
+}
+
+int sesw_set_patch_vertices(sesw_ctx *c, int32_t pv)
+{
+    if (!c) return SESW_EINVAL;
+    if (pv < 32 || pv > (1 << 20)) return fail(c, SESW_EINVAL, "patch_vertices must be in [32, 2^20]");
+    c->patch_vertices = pv;
+    return SESW_OK;
+}
+
+int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
+{
+    if (!c) return SESW_EINVAL;
+    if (!mesh) return fail(c, SESW_EINVAL, "mesh is NULL");
+    DeviceGuard dg(c->device);
+    if (!dg.ok) return fail(c, SESW_ECUDA, "cannot select the context's device");
+    sesw::HostMesh hm;
+    std::string err;
+    int rc;
+    try {
+        rc = sesw::prepare_mesh(*mesh, c->patch_vertices, hm, err);
+    } catch (const std::bad_alloc &) {
+        return fail(c, SESW_ENOMEM, "host allocation failed during mesh preparation");
+    }
+    if (rc != SESW_OK) return fail(c, rc, err);
+
+    // the substep kernel keeps 3 floats per slot of a patch in shared memory
+    int dev_smem = 0;
+    CK(c, cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if ((long long)hm.max_patch_slots * 3 * 4 > dev_smem)
+        return fail(c, SESW_EINVAL, "patches too large for shared memory; lower patch_vertices");
+
+    CK(c, cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    free_all(c);
+    c->have_mesh = c->have_params = false;
+
+    sesw::DevMesh &d = c->dm;
+    d.nv = hm.nv;
+    d.ne = hm.ne;
+    d.npatch = hm.npatch;
+    d.nslot = hm.nslot;
+    d.max_patch_slots = hm.max_patch_slots;
+    TRY(upload(c, &d.slot_v, hm.slot_v, "slot_v"));
+    TRY(upload(c, &d.slot_g, hm.slot_g, "slot_g"));
+    TRY(upload(c, &d.slot_c, hm.slot_c, "slot_c"));
+    TRY(upload(c, &d.patch_v, hm.patch_v, "patch_v"));
+    TRY(upload(c, &d.patch_slot, hm.patch_slot, "patch_slot"));
+    TRY(upload(c, &d.patch_own, hm.patch_own, "patch_own"));
+    TRY(upload(c, &d.vcsr_off, hm.vcsr_off, "vcsr_off"));
+    TRY(upload(c, &d.vcsr, hm.vcsr, "vcsr"));
+    TRY(upload(c, &d.inv_av, hm.inv_av, "inv_av"));
+    TRY(upload(c, &d.area_v, hm.area_v, "area_v"));
+    TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
+    TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
+
+    sesw::DevState &s = c->ds;
+    TRY(zalloc(c, &s.eta[0], hm.nv, "eta"));
+    TRY(zalloc(c, &s.eta[1], hm.nv, "eta"));
+    TRY(zalloc(c, &s.U, hm.nslot, "U"));
+    TRY(zalloc(c, &s.R, hm.nslot, "R"));
+    TRY(zalloc(c, &s.S_hi, hm.nslot, "S_hi"));
+    TRY(zalloc(c, &s.S_lo, hm.nslot, "S_lo"));
+    TRY(zalloc(c, &s.Umean, hm.ne, "Umean"));
+    TRY(zalloc(c, &s.status, 1, "status"));
+    c->diag_blocks = sesw::diagnostics_blocks(d);
+    TRY(zalloc(c, &s.diag_part, 2 * (size_t)c->diag_blocks, "diag_part"));
+    TRY(zalloc(c, &s.diag_out, 2, "diag_out"));
+    s.stage_elems = (size_t)hm.nv + 4 * (size_t)hm.ne;
+    TRY(zalloc(c, &s.stage, s.stage_elems, "stage"));
+    CK(c, sesw::substep_smem_attr(d));
+    CK(c, cudaStreamSynchronize(c->stream));
+
+    c->parity = 0;
+    c->grad_gram_max_h = hm.grad_gram_max_h;
+    c->npatch = hm.npatch;
+    c->nslot = hm.nslot;
+    c->max_patch_slots = hm.max_patch_slots;
+    c->patch_vertices_used = hm.patch_vertices;
+    c->courant_max = 0.0;
+    c->have_mesh = true;
+    return SESW_OK;
+}
+
+int sesw_set_params(sesw_ctx *c, const sesw_params *p)
+{
+    if (!c) return SESW_EINVAL;
+    if (!p) return fail(c, SESW_EINVAL, "params is NULL");
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting parameters");
+    if (!(p->g > 0.0) || !isfinite(p->g)) return fail(c, SESW_EINVAL, "g must be positive and finite");
+    if (!(p->theta >= 0.0) || !isfinite(p->theta)) return fail(c, SESW_EINVAL, "theta must be >= 0 and finite");
+    if (!(p->tau > 0.0) || !isfinite(p->tau)) return fail(c, SESW_EINVAL, "tau must be positive and finite");
+    if (p->M < 1 || p->M > 65536) return fail(c, SESW_EINVAL, "M must be in [1, 65536]");
+    if (p->nonlinear_h != 0 && p->nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
+    if (p->scheme != 0) return fail(c, SESW_EINVAL, "scheme must be 0 (dissipative forward-backward)");
+    const double dt = p->tau / p->M;
+    // Element-by-element bound on the largest eigenvalue of -div(g H0 grad):
+    // lambda_max <= max_e 3 g H0_e lambda_max(sum_k dphi_k dphi_k^T).
+    const double cmax = sqrt(3.0 * p->g * c->grad_gram_max_h) * dt;
+    const double limit = 2.0 / sqrt(1.0 + 2.0 * p->theta);
+    if (cmax > limit && !(p->flags & SESW_FLAG_NO_STABILITY_CHECK)) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "substep Courant number bound %.4f exceeds the stability limit 2/sqrt(1+2 theta) = %.4f; "
+                 "increase M",
+                 cmax, limit);
+        return fail(c, SESW_EINVAL, buf);
+    }
+    drop_graphs(c);
+    c->params = *p;
+    if (!(c->params.eta_bound > 0.0)) c->params.eta_bound = 1e4;
+    sesw::StepArgs &a = c->args;
+    a.g = (float)p->g;
+    a.g64 = p->g;
+    a.theta = (float)p->theta;
+    a.dt = (float)dt;
+    a.half_dt = (float)(0.5 * dt);
+    a.inv_M = (float)(1.0 / p->M);
+    a.eta_bound = (float)c->params.eta_bound;
+    a.nonlinear_h = p->nonlinear_h;
+    c->courant_max = cmax;
+    c->courant_limit = limit;
+    c->have_params = true;
+    return SESW_OK;
+}
+
+int sesw_set_state(sesw_ctx *c, const double *eta, const double *U, int where)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting the state");
+    if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    DeviceGuard dg(c->device);
+    const double *de = eta, *du = U;
+    if (where == SESW_HOST) {
+        double *st = c->ds.stage;
+        if (eta) {
+            CK(c, cudaMemcpyAsync(st, eta, sizeof(double) * c->dm.nv, cudaMemcpyHostToDevice, c->stream));
+            de = st;
+        }
+        if (U) {
+            CK(c, cudaMemcpyAsync(st + c->dm.nv, U, sizeof(double) * 2 * c->dm.ne, cudaMemcpyHostToDevice, c->stream));
+            du = st + c->dm.nv;
+        }
+    }
+    CK(c, sesw::launch_scatter_state(c->dm, c->ds, de, du, c->parity, c->stream));
+    return SESW_OK;
+}
+
+int sesw_set_forcing(sesw_ctx *c, const double *R, int where)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting the forcing");
+    if (!R) return fail(c, SESW_EINVAL, "R is NULL");
+    if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    DeviceGuard dg(c->device);
+    const double *dr = R;
+    if (where == SESW_HOST) {
+        // after the state slice of the staging buffer, so a pending state scatter is not overwritten
+        double *st = c->ds.stage + c->dm.nv + 2 * (size_t)c->dm.ne;
+        CK(c, cudaMemcpyAsync(st, R, sizeof(double) * 2 * c->dm.ne, cudaMemcpyHostToDevice, c->stream));
+        dr = st;
+    }
+    CK(c, sesw::launch_scatter_forcing(c->dm, c->ds, dr, c->stream));
+    return SESW_OK;
+}
+
+int sesw_advance(sesw_ctx *c, int32_t nsteps)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh || !c->have_params) return fail(c, SESW_ESTATE, "mesh and parameters must be set before advance");
+    if (nsteps < 0) return fail(c, SESW_EINVAL, "nsteps must be >= 0");
+    DeviceGuard dg(c->device);
+    for (int n = 0; n < nsteps; n++) {
+        cudaGraphExec_t &g = c->graph[c->parity];
+        if (!g) TRY(capture_step_graph(c, c->parity, &g));
+        CK(c, cudaGraphLaunch(g, c->stream));
+        c->parity ^= (c->params.M & 1);
+    }
+    return SESW_OK;
+}
+
+int sesw_get_state(sesw_ctx *c, double *eta, double *U, double *Umean, int where)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before reading the state");
+    if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    DeviceGuard dg(c->device);
+    const size_t nv = c->dm.nv, ne = c->dm.ne;
+    if (where == SESW_DEVICE) {
+        CK(c, sesw::launch_gather_state(c->dm, c->ds, c->parity, eta, U, Umean, c->stream));
+        return SESW_OK;
+    }
+    double *st = c->ds.stage;
+    double *se = eta ? st : nullptr, *su = U ? st + nv : nullptr, *sm = Umean ? st + nv + 2 * ne : nullptr;
+    CK(c, sesw::launch_gather_state(c->dm, c->ds, c->parity, se, su, sm, c->stream));
+    if (eta) CK(c, cudaMemcpyAsync(eta, se, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->stream));
+    if (U) CK(c, cudaMemcpyAsync(U, su, sizeof(double) * 2 * ne, cudaMemcpyDeviceToHost, c->stream));
+    if (Umean) CK(c, cudaMemcpyAsync(Umean, sm, sizeof(double) * 2 * ne, cudaMemcpyDeviceToHost, c->stream));
+    unsigned status = 0;
+    CK(c, cudaMemcpyAsync(&status, c->ds.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (status & 1u) return fail(c, SESW_EUNSTABLE, "non-finite or out-of-bound elevation detected");
+    return SESW_OK;
+}
+
+int sesw_diagnostics(sesw_ctx *c, double *volume, double *energy)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh || !c->have_params) return fail(c, SESW_ESTATE, "mesh and parameters must be set before diagnostics");
+    DeviceGuard dg(c->device);
+    CK(c, sesw::launch_diagnostics(c->dm, c->ds, c->args, c->parity, c->diag_blocks, c->stream));
+    double out[2] = {0.0, 0.0};
+    CK(c, cudaMemcpyAsync(out, c->ds.diag_out, sizeof out, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (volume) *volume = out[0];
+    if (energy) *energy = out[1];
+    return SESW_OK;
+}
+
+int sesw_status(sesw_ctx *c)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return SESW_OK;
+    DeviceGuard dg(c->device);
+    unsigned status = 0;
+    CK(c, cudaMemcpyAsync(&status, c->ds.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemsetAsync(c->ds.status, 0, sizeof(unsigned), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (status & 2u) return fail(c, SESW_ETIMEOUT, "a device-side wait gave up");
+    if (status & 1u) return fail(c, SESW_EUNSTABLE, "non-finite or out-of-bound elevation detected");
+    return SESW_OK;
+}
+
+int sesw_mesh_check(const sesw_mesh *mesh, int32_t patch_vertices, sesw_info *info, char *msg, size_t msglen)
+{
+    std::string err;
+    int rc;
+    sesw::HostMesh hm;
+    if (!mesh) {
+        err = "mesh is NULL";
+        rc = SESW_EINVAL;
+    } else {
+        try {
+            rc = sesw::prepare_mesh(*mesh, patch_vertices, hm, err);
+        } catch (const std::bad_alloc &) {
+            rc = SESW_ENOMEM;
+            err = "host allocation failed during mesh preparation";
+        }
+    }
+    if (msg && msglen) {
+        size_t n = std::min(err.size(), msglen - 1);
+        memcpy(msg, err.data(), n);
+        msg[n] = 0;
+    }
+    if (rc == SESW_OK && info) {
+        memset(info, 0, sizeof *info);
+        info->nv = hm.nv;
+        info->ne = hm.ne;
+        info->npatch = hm.npatch;
+        info->nslot = hm.nslot;
+        info->max_patch_slots = hm.max_patch_slots;
+        info->patch_vertices = hm.patch_vertices;
+    }
+    return rc;
+}
+
+int sesw_get_info(sesw_ctx *c, sesw_info *info)
+{
+    if (!c || !info) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "no mesh uploaded");
+    memset(info, 0, sizeof *info);
+    info->nv = c->dm.nv;
+    info->ne = c->dm.ne;
+    info->npatch = c->npatch;
+    info->nslot = c->nslot;
+    info->max_patch_slots = c->max_patch_slots;
+    info->patch_vertices = c->patch_vertices_used;
+    info->courant_max = c->courant_max;
+    info->courant_limit = c->have_params ? c->courant_limit : 0.0;
+    info->device_bytes = c->device_bytes;
+    return SESW_OK;
+}
+
+const char *sesw_last_error(sesw_ctx *c)
+{
+    if (!c) return "context is NULL";
+    return c->err.c_str();
+}
+
+void sesw_destroy(sesw_ctx *c)
+{
+    if (!c) return;
+    {
+        DeviceGuard dg(c->device);
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        drop_graphs(c);
+        free_all(c);
+        if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        cudaGetLastError();
+    }
+    delete c;
+}
+
+}  // extern "C"

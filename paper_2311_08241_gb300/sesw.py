@@ -1,0 +1,297 @@
+"""Python binding of libsesw (include/sesw.h) through ctypes.
+
+The functions below carry the C names and only marshal arguments: every step of
+the barotropic subcycle runs in the library's CUDA kernels. PyTorch supplies the
+device memory (its caching allocator, through the library's allocator callback)
+and the stream. There is no CPU fallback: if the library cannot be loaded, or no
+CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SESW_OK = 0
+SESW_EINVAL = -1
+SESW_ECUDA = -2
+SESW_ESTATE = -3
+SESW_ETIMEOUT = -4
+SESW_EUNSTABLE = -5
+SESW_ENOMEM = -6
+SESW_HOST = 0
+SESW_DEVICE = 1
+SESW_FLAG_NO_STABILITY_CHECK = 1
+
+_NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", -4: "SESW_ETIMEOUT",
+          -5: "SESW_EUNSTABLE", -6: "SESW_ENOMEM"}
+
+# every symbol include/sesw.h declares
+EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_patch_vertices", "sesw_mesh_upload",
+           "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
+           "sesw_diagnostics", "sesw_status", "sesw_mesh_check", "sesw_get_info", "sesw_last_error",
+           "sesw_destroy")
+
+
+class SeswError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class sesw_mesh(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("ne", ctypes.c_int32), ("tri", ctypes.c_void_p),
+                ("xy", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("depth", ctypes.c_void_p),
+                ("coriolis", ctypes.c_void_p)]
+
+
+class sesw_params(ctypes.Structure):
+    _fields_ = [("g", ctypes.c_double), ("theta", ctypes.c_double), ("tau", ctypes.c_double),
+                ("M", ctypes.c_int32), ("nonlinear_h", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("eta_bound", ctypes.c_double)]
+
+
+class sesw_info(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("ne", ctypes.c_int32), ("npatch", ctypes.c_int32),
+                ("nslot", ctypes.c_int32), ("max_patch_slots", ctypes.c_int32),
+                ("patch_vertices", ctypes.c_int32), ("courant_max", ctypes.c_double),
+                ("courant_limit", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsesw.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsesw not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.sesw_create.argtypes = [ctypes.POINTER(P), I, P, ALLOC_FN, FREE_FN, P]
+        L.sesw_set_stream.argtypes = [P, P]
+        L.sesw_set_patch_vertices.argtypes = [P, ctypes.c_int32]
+        L.sesw_mesh_upload.argtypes = [P, ctypes.POINTER(sesw_mesh)]
+        L.sesw_set_params.argtypes = [P, ctypes.POINTER(sesw_params)]
+        L.sesw_set_state.argtypes = [P, P, P, I]
+        L.sesw_set_forcing.argtypes = [P, P, I]
+        L.sesw_advance.argtypes = [P, ctypes.c_int32]
+        L.sesw_get_state.argtypes = [P, P, P, P, I]
+        L.sesw_diagnostics.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.sesw_status.argtypes = [P]
+        L.sesw_get_info.argtypes = [P, ctypes.POINTER(sesw_info)]
+        L.sesw_mesh_check.argtypes = [ctypes.POINTER(sesw_mesh), ctypes.c_int32, ctypes.POINTER(sesw_info),
+                                      ctypes.c_char_p, ctypes.c_size_t]
+        L.sesw_last_error.argtypes = [P]
+        L.sesw_last_error.restype = ctypes.c_char_p
+        L.sesw_destroy.argtypes = [P]
+        L.sesw_destroy.restype = None
+        for n in EXPORTS:
+            if n not in ("sesw_last_error", "sesw_destroy"):
+                getattr(L, n).restype = I
+        _lib = L
+        return L
+
+
+def _ptr(x):
+    """Address of a numpy array (host) or a torch tensor (device or host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _where(x):
+    if x is None or isinstance(x, np.ndarray):
+        return SESW_HOST
+    return SESW_DEVICE if x.is_cuda else SESW_HOST
+
+
+class Subcycle:
+    """One libsesw context: a mesh, parameters, forcing and state on one GPU.
+
+    Methods map one to one onto the C calls (sesw_mesh_upload, sesw_set_params, ...).
+    Host arrays are numpy float64 (int32 for indices); device arrays are torch
+    float64 CUDA tensors, passed by address.
+    """
+
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsesw needs a CUDA device; none is available")
+        self._L = load()
+        self.device = device
+        self._stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self._alloc_cb = ALLOC_FN(0)
+        self._free_cb = FREE_FN(0)
+        if use_torch_allocator:
+            dev, strm = device, self._stream
+
+            def _alloc(nbytes, _user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm)
+                except Exception:
+                    return None
+
+            def _free(ptr, _user):
+                try:
+                    torch.cuda.caching_allocator_delete(ptr)
+                except Exception:
+                    pass
+
+            self._alloc_cb = ALLOC_FN(_alloc)
+            self._free_cb = FREE_FN(_free)
+        h = ctypes.c_void_p()
+        rc = self._L.sesw_create(ctypes.byref(h), device, ctypes.c_void_p(self._stream.cuda_stream),
+                                 self._alloc_cb, self._free_cb, None)
+        if rc != SESW_OK:
+            raise SeswError(rc, "sesw_create failed")
+        self._h = h
+        self.nv = self.ne = 0
+        self.params = None
+
+    # -- helpers
+    def _check(self, rc):
+        if rc != SESW_OK:
+            raise SeswError(rc, self._L.sesw_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.sesw_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- the C calls
+    def sesw_set_patch_vertices(self, n: int):
+        return self._check(self._L.sesw_set_patch_vertices(self._h, int(n)))
+
+    def sesw_mesh_upload(self, mesh):
+        m, keep = _mesh_struct(mesh)
+        rc = self._check(self._L.sesw_mesh_upload(self._h, ctypes.byref(m)))
+        del keep
+        self.nv, self.ne = int(mesh.nv), int(mesh.ne)
+        return rc
+
+    def sesw_set_params(self, p, flags: int = 0, eta_bound: float = 0.0):
+        cp = sesw_params(float(p.g), float(p.theta), float(p.tau), int(p.M), int(p.nonlinear_h),
+                         int(getattr(p, "scheme", 0)), int(flags), float(eta_bound))
+        self.params = p
+        return self._check(self._L.sesw_set_params(self._h, ctypes.byref(cp)))
+
+    def sesw_set_state(self, eta, U):
+        eta = _as_f64(eta)
+        U = _as_f64(U)
+        return self._check(self._L.sesw_set_state(self._h, _ptr(eta), _ptr(U), _where(eta if eta is not None else U)))
+
+    def sesw_set_forcing(self, R):
+        R = _as_f64(R)
+        return self._check(self._L.sesw_set_forcing(self._h, _ptr(R), _where(R)))
+
+    def sesw_advance(self, nsteps: int):
+        return self._check(self._L.sesw_advance(self._h, int(nsteps)))
+
+    def sesw_get_state(self, eta=None, U=None, Umean=None):
+        """Fill the given buffers (numpy or torch float64); with no buffers, return new numpy arrays."""
+        if eta is None and U is None and Umean is None:
+            eta = np.empty(self.nv)
+            U = np.empty((self.ne, 2))
+            Umean = np.empty((self.ne, 2))
+        where = _where(next(x for x in (eta, U, Umean) if x is not None))
+        self._check(self._L.sesw_get_state(self._h, _ptr(eta), _ptr(U), _ptr(Umean), where))
+        return eta, U, Umean
+
+    def sesw_diagnostics(self):
+        v, e = ctypes.c_double(), ctypes.c_double()
+        self._check(self._L.sesw_diagnostics(self._h, ctypes.byref(v), ctypes.byref(e)))
+        return v.value, e.value
+
+    def sesw_status(self):
+        return self._L.sesw_status(self._h)
+
+    def sesw_get_info(self):
+        info = sesw_info()
+        self._check(self._L.sesw_get_info(self._h, ctypes.byref(info)))
+        return {k: getattr(info, k) for k, _ in sesw_info._fields_}
+
+
+def _mesh_struct(mesh):
+    keep = [np.ascontiguousarray(mesh.tri, dtype=np.int32),
+            np.ascontiguousarray(mesh.xy, dtype=np.float64),
+            None if mesh.pos is None else np.ascontiguousarray(mesh.pos, dtype=np.float64),
+            np.ascontiguousarray(mesh.depth, dtype=np.float64),
+            np.ascontiguousarray(mesh.coriolis, dtype=np.float64)]
+    t, xy, pos, d, f = keep
+    m = sesw_mesh(int(mesh.nv), int(t.shape[0]), _ptr(t), _ptr(xy), _ptr(pos), _ptr(d), _ptr(f))
+    return m, keep
+
+
+def sesw_mesh_check(mesh, patch_vertices: int = 512):
+    """Host-only validation and layout of a mesh (no GPU needed). Returns the layout facts."""
+    L = load()
+    m, keep = _mesh_struct(mesh)
+    info = sesw_info()
+    buf = ctypes.create_string_buffer(512)
+    rc = L.sesw_mesh_check(ctypes.byref(m), int(patch_vertices), ctypes.byref(info), buf, 512)
+    del keep
+    if rc != SESW_OK:
+        raise SeswError(rc, buf.value.decode())
+    return {k: getattr(info, k) for k, _ in sesw_info._fields_}
+
+
+def _as_f64(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return np.ascontiguousarray(x, dtype=np.float64)
+    import torch
+
+    if x.dtype != torch.float64 or not x.is_contiguous():
+        raise TypeError("device buffers must be contiguous torch.float64 tensors")
+    return x
+
+
+def run_case(case, nsteps=None, device=0, patch_vertices=None):
+    """Upload a case, advance it and return (eta, U, Umean) as numpy arrays."""
+    with Subcycle(device) as s:
+        if patch_vertices:
+            s.sesw_set_patch_vertices(patch_vertices)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_set_forcing(case.R)
+        s.sesw_set_state(case.eta0, case.U0)
+        s.sesw_advance(case.nsteps if nsteps is None else nsteps)
+        return s.sesw_get_state()

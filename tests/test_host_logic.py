@@ -1,0 +1,133 @@
+"""Host-side logic without a GPU: mesh validation and layout in libsesw, and the
+multi-rank aggregation of the benchmark (two gloo ranks on the CPU)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_2311_08241_gb300 import inputs as I
+from paper_2311_08241_gb300 import sesw as S
+
+
+def _check(mesh, pv=512):
+    return S.sesw_mesh_check(mesh, pv)
+
+
+@pytest.mark.parametrize("maker", [lambda: I.basin_case().mesh, lambda: I.channel_case().mesh,
+                                   lambda: I.sphere_mesh(5), lambda: I.tiny_jittered_case().mesh])
+def test_layout_of_valid_meshes(maker):
+    m = maker()
+    info = _check(m, 256)
+    assert info["nv"] == m.nv and info["ne"] == m.ne
+    assert info["npatch"] == -(-m.nv // 256)
+    assert info["ne"] <= info["nslot"] <= 3 * info["ne"]
+    assert info["max_patch_slots"] >= info["nslot"] / info["npatch"]
+
+
+def test_hilbert_order_keeps_patches_compact():
+    """Guest copies (elements on patch borders) are few with the space-filling-curve order and
+    many when patches are cut from the lattice's row-major order."""
+    m = I.channel_case().mesh
+    hil = _check(m, 512)
+    info_rm = S.sesw_mesh_check(_NoPos(m), 512)
+    g_hil = (hil["nslot"] - hil["ne"]) / hil["ne"]
+    g_rm = (info_rm["nslot"] - info_rm["ne"]) / info_rm["ne"]
+    assert g_hil < 0.4 and g_rm > 2 * g_hil
+    big = _check(m, 8192)
+    assert (big["nslot"] - big["ne"]) / big["ne"] < 0.5 * g_hil
+
+
+class _NoPos:
+    def __init__(self, m):
+        self.tri, self.xy, self.depth, self.coriolis = m.tri, m.xy, m.depth, m.coriolis
+        self.pos = None
+        self.nv, self.ne = m.nv, m.ne
+
+
+def _bad(mutate):
+    c = I.tiny_jittered_case()
+    m = c.mesh
+    b = I.Mesh(m.name, m.tri.copy(), m.xy.copy(), m.pos.copy(), m.depth.copy(), m.coriolis.copy())
+    mutate(b)
+    return b
+
+
+@pytest.mark.parametrize("mutate,needle", [
+    (lambda b: b.tri.__setitem__((2, 0), -1), "out of range"),
+    (lambda b: b.tri.__setitem__((2, 1), b.tri[2, 0]), "repeats a vertex"),
+    (lambda b: b.xy.__setitem__((0, 0, 0), np.nan), "non-finite coordinate"),
+    (lambda b: b.depth.__setitem__(3, 0.0), "depth"),
+    (lambda b: b.coriolis.__setitem__(1, np.inf), "Coriolis"),
+])
+def test_malformed_meshes_are_rejected(mutate, needle):
+    with pytest.raises(S.SeswError) as ei:
+        _check(_bad(mutate))
+    assert ei.value.code == S.SESW_EINVAL and needle in str(ei.value)
+
+
+def test_clockwise_triangle_rejected():
+    c = I.tiny_jittered_case()
+    m = c.mesh
+    xy = m.xy.copy()
+    xy[5, [1, 2]] = xy[5, [2, 1]]
+    tri = m.tri.copy()
+    b = I.Mesh(m.name, tri, xy, m.pos, m.depth, m.coriolis)
+    with pytest.raises(S.SeswError, match="counter-clockwise"):
+        _check(b)
+
+
+def test_topology_errors_rejected():
+    xy1 = np.array([[[0, 0], [1, 0], [0, 1]], [[1, 0], [0, 0], [0, -1]], [[0, 0], [1, 0], [1, 1]]], float) * 1e3
+    tri = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4]], dtype=np.int32)
+    m = I.Mesh("t", tri, xy1, np.zeros((5, 3)), np.ones(5), np.zeros(3))
+    with pytest.raises(S.SeswError, match="more than two"):
+        _check(m)
+    # two triangles walking a shared edge the same way
+    tri2 = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
+    xy2 = np.array([[[0, 0], [1, 0], [0, 1]], [[0, 0], [1, 0], [0.5, 2]]], float) * 1e3
+    m2 = I.Mesh("t", tri2, xy2, np.zeros((4, 3)), np.ones(4), np.zeros(2))
+    with pytest.raises(S.SeswError, match="same direction"):
+        _check(m2)
+    # a vertex that no triangle uses
+    m3 = I.Mesh("t", tri2[:1], xy2[:1], np.zeros((4, 3)), np.ones(4), np.zeros(1))
+    with pytest.raises(S.SeswError, match="not a corner"):
+        _check(m3)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+
+    slowest = bench.reduce_max(10.0 + rank, world, "cpu")
+    bench.barrier(world)
+    out.put((rank, slowest, bench.whole_job_value(1000, 40, 5, world, slowest)))
+    dist.destroy_process_group()
+
+
+def test_bench_aggregation_two_gloo_ranks():
+    import torch.multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [11.0, 11.0]
+    assert res[0][2] == pytest.approx(2 * 1000 * 40 * 5 / 11e-3)
