@@ -120,6 +120,8 @@ typedef struct sesw_info {
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
                                 (0 until parameters are set) */
     double courant_limit;    /* 2/sqrt(1+2 theta), the stability limit of the scheme */
+    double stiffness_bound;  /* upper bound L (1/m) of lambda_max(-div H0 grad);
+                                courant_max = (tau/M) sqrt(g L) */
     int64_t device_bytes;    /* device memory held by the context */
 } sesw_info;
 
@@ -146,9 +148,10 @@ int sesw_mesh_upload(sesw_ctx *ctx, const sesw_mesh *mesh);
 /* Set scheme parameters; requires an uploaded mesh. Rejects (SESW_EINVAL)
  * parameters whose substep Courant number bound exceeds 2/sqrt(1+2 theta), the
  * value beyond which the scheme's characteristic polynomial (Eq. dp_1, SE row) has a
- * root outside the unit circle. The bound is element by element:
- * c = dt sqrt(3 g max_e H0_e lambda_max(sum_k grad phi_k grad phi_k^T)), an upper
- * bound of dt sqrt(lambda_max(-div g H0 grad)) for the lumped median-dual operator. */
+ * root outside the unit circle. c is an upper bound of dt sqrt(lambda_max(-div g H0
+ * grad)) for the lumped median-dual operator: the smaller of an element-by-element
+ * bound, dt sqrt(3 g max_e H0_e lambda_max(sum_k grad phi_k grad phi_k^T)), and the
+ * Gershgorin bound over the rows of the stiffness matrix divided by A_v. */
 int sesw_set_params(sesw_ctx *ctx, const sesw_params *params);
 
 /* Set the state: eta [nv] (m) and U [ne][2] (m^2/s), in the caller's vertex and

@@ -42,17 +42,28 @@
 #include <omp.h>
 #endif
 
+/* Working precision. The oracle is built with double; a float build of the same
+ * source is used only to calibrate how far FP32 arithmetic of this algorithm drifts
+ * from FP64 (the parity tolerances of the FP32 GPU path). Mesh geometry (areas,
+ * edge normals, dual-cell segments) is always computed in double and then stored in
+ * the working precision; the time stepping uses `real` throughout; the interface
+ * stays double and converts at entry and exit. */
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+
 typedef struct {
     int nv, ne, ned;
     int *tri;          /* ne*3 */
-    double *xy;        /* ne*6, element-frame corners */
-    double *depth_v;   /* nv */
-    double *f_e;       /* ne */
-    double *area_e;    /* ne, shoelace area of the triangle */
-    double *area_v;    /* nv, median-dual cell area */
+    real *nrm;         /* ne*6, outward normal times length of each triangle edge k -> k+1 */
+    real *depth_v;     /* nv */
+    real *f_e;         /* ne */
+    real *area_e;      /* ne, shoelace area of the triangle */
+    real *area_v;      /* nv, median-dual cell area */
     int *edge_v;       /* ned*2, edge_v[2k] < edge_v[2k+1] */
     int *edge_e;       /* ned*2, adjacent triangles, -1 where absent */
-    double *seg;       /* ned*2*2: (Nx,Ny) per side, the segment's normal times length,
+    real *seg;         /* ned*2*2: (Nx,Ny) per side, the segment's normal times length,
                           pointing from the cell of edge_v[2k] into that of edge_v[2k+1] */
     int *vedge_off;    /* nv+1 */
     int *vedge;        /* 2*ned, incident edges of each vertex in increasing edge order */
@@ -61,7 +72,7 @@ typedef struct {
 static void omesh_free(omesh *m)
 {
     if (!m) return;
-    free(m->tri); free(m->xy); free(m->depth_v); free(m->f_e); free(m->area_e); free(m->area_v);
+    free(m->tri); free(m->nrm); free(m->depth_v); free(m->f_e); free(m->area_e); free(m->area_v);
     free(m->edge_v); free(m->edge_e); free(m->seg); free(m->vedge_off); free(m->vedge);
     free(m);
 }
@@ -98,38 +109,43 @@ void *oracle_mesh_new(int nv, int ne, const int *tri, const double *xy,
     if (!m) { *status = -4; return NULL; }
     m->nv = nv; m->ne = ne;
     m->tri = (int *)malloc(sizeof(int) * 3 * (size_t)ne);
-    m->xy = (double *)malloc(sizeof(double) * 6 * (size_t)ne);
-    m->depth_v = (double *)malloc(sizeof(double) * (size_t)nv);
-    m->f_e = (double *)malloc(sizeof(double) * (size_t)ne);
-    m->area_e = (double *)malloc(sizeof(double) * (size_t)ne);
-    m->area_v = (double *)calloc((size_t)nv, sizeof(double));
-    if (!m->tri || !m->xy || !m->depth_v || !m->f_e || !m->area_e || !m->area_v) {
-        *status = -4; omesh_free(m); return NULL;
+    m->nrm = (real *)malloc(sizeof(real) * 6 * (size_t)ne);
+    m->depth_v = (real *)malloc(sizeof(real) * (size_t)nv);
+    m->f_e = (real *)malloc(sizeof(real) * (size_t)ne);
+    m->area_e = (real *)malloc(sizeof(real) * (size_t)ne);
+    m->area_v = (real *)calloc((size_t)nv, sizeof(real));
+    double *av = (double *)calloc((size_t)nv, sizeof(double));
+    if (!m->tri || !m->nrm || !m->depth_v || !m->f_e || !m->area_e || !m->area_v || !av) {
+        free(av); *status = -4; omesh_free(m); return NULL;
     }
     memcpy(m->tri, tri, sizeof(int) * 3 * (size_t)ne);
-    memcpy(m->xy, xy, sizeof(double) * 6 * (size_t)ne);
-    memcpy(m->depth_v, depth_v, sizeof(double) * (size_t)nv);
-    memcpy(m->f_e, f_e, sizeof(double) * (size_t)ne);
+    for (int v = 0; v < nv; v++) m->depth_v[v] = (real)depth_v[v];
+    for (int e = 0; e < ne; e++) m->f_e[e] = (real)f_e[e];
 
     for (int e = 0; e < ne; e++)
         for (int k = 0; k < 3; k++)
-            if (tri[3 * e + k] < 0 || tri[3 * e + k] >= nv) { *status = -1; omesh_free(m); return NULL; }
+            if (tri[3 * e + k] < 0 || tri[3 * e + k] >= nv) { free(av); *status = -1; omesh_free(m); return NULL; }
 
-    /* triangle areas and median-dual cell areas (sub-quad of each corner) */
+    /* triangle areas, edge normals and median-dual cell areas (sub-quad of each corner) */
     for (int e = 0; e < ne; e++) {
-        const double *p = m->xy + 6 * e;
+        const double *p = xy + 6 * (size_t)e;
         double px[3] = {p[0], p[2], p[4]}, py[3] = {p[1], p[3], p[5]};
         double A = shoelace(px, py, 3);
-        if (!(A > 0.0)) { *status = -2; omesh_free(m); return NULL; }
-        m->area_e[e] = A;
+        if (!(A > 0.0)) { free(av); *status = -2; omesh_free(m); return NULL; }
+        m->area_e[e] = (real)A;
         double cx = (px[0] + px[1] + px[2]) / 3.0, cy = (py[0] + py[1] + py[2]) / 3.0;
         for (int k = 0; k < 3; k++) {
             int kn = (k + 1) % 3, kp = (k + 2) % 3;
+            /* outward normal times length of a counter-clockwise edge (dx,dy) is (dy,-dx) */
+            m->nrm[6 * e + 2 * k] = (real)(py[kn] - py[k]);
+            m->nrm[6 * e + 2 * k + 1] = (real)(-(px[kn] - px[k]));
             double qx[4] = {px[k], 0.5 * (px[k] + px[kn]), cx, 0.5 * (px[k] + px[kp])};
             double qy[4] = {py[k], 0.5 * (py[k] + py[kn]), cy, 0.5 * (py[k] + py[kp])};
-            m->area_v[tri[3 * e + k]] += shoelace(qx, qy, 4);
+            av[tri[3 * e + k]] += shoelace(qx, qy, 4);
         }
     }
+    for (int v = 0; v < nv; v++) m->area_v[v] = (real)av[v];
+    free(av);
 
     /* edges: group the 3*ne half-edges by their unordered vertex pair */
     halfedge *h = (halfedge *)malloc(sizeof(halfedge) * 3 * (size_t)ne);
@@ -154,7 +170,7 @@ void *oracle_mesh_new(int nv, int ne, const int *tri, const double *xy,
     m->ned = ned;
     m->edge_v = (int *)malloc(sizeof(int) * 2 * (size_t)ned);
     m->edge_e = (int *)malloc(sizeof(int) * 2 * (size_t)ned);
-    m->seg = (double *)calloc(4 * (size_t)ned, sizeof(double));
+    m->seg = (real *)calloc(4 * (size_t)ned, sizeof(real));
     if (!m->edge_v || !m->edge_e || !m->seg) { free(h); *status = -4; omesh_free(m); return NULL; }
     int k = 0;
     for (size_t i = 0; i < 3 * (size_t)ne;) {
@@ -170,7 +186,7 @@ void *oracle_mesh_new(int nv, int ne, const int *tri, const double *xy,
             int side = (int)(s - i);
             m->edge_e[2 * k + side] = e;
             /* corners of a and b inside e */
-            const double *p = m->xy + 6 * e;
+            const double *p = xy + 6 * (size_t)e;
             int ka = -1, kb = -1;
             for (int c = 0; c < 3; c++) {
                 if (tri[3 * e + c] == a) ka = c;
@@ -182,8 +198,8 @@ void *oracle_mesh_new(int nv, int ne, const int *tri, const double *xy,
             double dx = cx - mx, dy = cy - my;
             double nx = dy, ny = -dx;               /* one of the two normals of length |d| */
             if (nx * (bx - ax) + ny * (by - ay) < 0.0) { nx = -nx; ny = -ny; }
-            m->seg[4 * k + 2 * side] = nx;
-            m->seg[4 * k + 2 * side + 1] = ny;
+            m->seg[4 * k + 2 * side] = (real)nx;
+            m->seg[4 * k + 2 * side + 1] = (real)ny;
         }
         k++;
         i = j;
@@ -225,8 +241,8 @@ int oracle_mesh_info(void *hm, int *ned, int *nbnd)
 int oracle_areas(void *hm, double *area_v, double *area_e)
 {
     omesh *m = (omesh *)hm;
-    if (area_v) memcpy(area_v, m->area_v, sizeof(double) * (size_t)m->nv);
-    if (area_e) memcpy(area_e, m->area_e, sizeof(double) * (size_t)m->ne);
+    if (area_v) for (int v = 0; v < m->nv; v++) area_v[v] = (double)m->area_v[v];
+    if (area_e) for (int e = 0; e < m->ne; e++) area_e[e] = (double)m->area_e[e];
     return 0;
 }
 
@@ -239,18 +255,16 @@ int oracle_edges(void *hm, int *edge_v, int *edge_e)
 }
 
 /* Green-Gauss gradient of the vertex field eta on triangle e. */
-static void gradient_e(const omesh *m, int e, const double *eta, double *gx, double *gy)
+static void gradient_e(const omesh *m, int e, const real *eta, real *gx, real *gy)
 {
-    const double *p = m->xy + 6 * e;
+    const real *n = m->nrm + 6 * e;
     const int *t = m->tri + 3 * e;
-    double sx = 0.0, sy = 0.0;
+    real sx = 0, sy = 0;
     for (int k = 0; k < 3; k++) {
         int kn = (k + 1) % 3;
-        double dx = p[2 * kn] - p[2 * k], dy = p[2 * kn + 1] - p[2 * k + 1];
-        double etam = 0.5 * (eta[t[k]] + eta[t[kn]]);
-        /* outward normal times length of a counter-clockwise edge (dx,dy) is (dy,-dx) */
-        sx += etam * dy;
-        sy += etam * (-dx);
+        real etam = (eta[t[k]] + eta[t[kn]]) / 2;
+        sx += etam * n[2 * k];
+        sy += etam * n[2 * k + 1];
     }
     *gx = sx / m->area_e[e];
     *gy = sy / m->area_e[e];
@@ -259,17 +273,26 @@ static void gradient_e(const omesh *m, int e, const double *eta, double *gx, dou
 int oracle_gradient(void *hm, const double *eta, double *grad)
 {
     omesh *m = (omesh *)hm;
-    for (int e = 0; e < m->ne; e++) gradient_e(m, e, eta, grad + 2 * e, grad + 2 * e + 1);
+    real *er = (real *)malloc(sizeof(real) * (size_t)m->nv);
+    if (!er) return -4;
+    for (int v = 0; v < m->nv; v++) er[v] = (real)eta[v];
+    for (int e = 0; e < m->ne; e++) {
+        real gx, gy;
+        gradient_e(m, e, er, &gx, &gy);
+        grad[2 * e] = (double)gx;
+        grad[2 * e + 1] = (double)gy;
+    }
+    free(er);
     return 0;
 }
 
 /* Net outflow of F through the median-dual cell boundary of every vertex, per area. */
-static void divergence(const omesh *m, const double *F, double *edgeflux, double *div)
+static void divergence(const omesh *m, const real *F, real *edgeflux, real *div)
 {
     int ned = m->ned, nv = m->nv;
     #pragma omp parallel for schedule(static)
     for (int q = 0; q < ned; q++) {
-        double s = 0.0;
+        real s = 0;
         for (int side = 0; side < 2; side++) {
             int e = m->edge_e[2 * q + side];
             if (e < 0) continue;
@@ -279,7 +302,7 @@ static void divergence(const omesh *m, const double *F, double *edgeflux, double
     }
     #pragma omp parallel for schedule(static)
     for (int v = 0; v < nv; v++) {
-        double s = 0.0;
+        real s = 0;
         for (int i = m->vedge_off[v]; i < m->vedge_off[v + 1]; i++) {
             int q = m->vedge[i];
             s += (m->edge_v[2 * q] == v) ? edgeflux[q] : -edgeflux[q];
@@ -291,34 +314,40 @@ static void divergence(const omesh *m, const double *F, double *edgeflux, double
 int oracle_divergence(void *hm, const double *F, double *div)
 {
     omesh *m = (omesh *)hm;
-    double *ef = (double *)malloc(sizeof(double) * (size_t)m->ned);
-    if (!ef) return -4;
-    divergence(m, F, ef, div);
-    free(ef);
+    real *ef = (real *)malloc(sizeof(real) * (size_t)m->ned);
+    real *Fr = (real *)malloc(sizeof(real) * 2 * (size_t)m->ne);
+    real *dr = (real *)malloc(sizeof(real) * (size_t)m->nv);
+    if (!ef || !Fr || !dr) { free(ef); free(Fr); free(dr); return -4; }
+    for (size_t i = 0; i < 2 * (size_t)m->ne; i++) Fr[i] = (real)F[i];
+    divergence(m, Fr, ef, dr);
+    for (int v = 0; v < m->nv; v++) div[v] = (double)dr[v];
+    free(ef); free(Fr); free(dr);
     return 0;
 }
 
-static double element_depth(const omesh *m, int e, const double *eta, int nonlinear_h)
+static real element_depth(const omesh *m, int e, const real *eta, int nonlinear_h)
 {
     const int *t = m->tri + 3 * e;
-    double H = (m->depth_v[t[0]] + m->depth_v[t[1]] + m->depth_v[t[2]]) / 3.0;
-    if (nonlinear_h) H += (eta[t[0]] + eta[t[1]] + eta[t[2]]) / 3.0;
+    real H = (m->depth_v[t[0]] + m->depth_v[t[1]] + m->depth_v[t[2]]) / 3;
+    if (nonlinear_h) H += (eta[t[0]] + eta[t[1]] + eta[t[2]]) / 3;
     return H;
 }
 
-/* Volume sum A_v eta_v and energy sum A_v g eta^2/2 + sum A_e |U|^2/(2 H_e). */
+/* Volume sum A_v eta_v and energy sum A_v g eta^2/2 + sum A_e |U|^2/(2 H_e), in double. */
 int oracle_diagnostics(void *hm, const double *eta, const double *U, double g, int nonlinear_h,
                        double *volume, double *energy)
 {
     omesh *m = (omesh *)hm;
     double vol = 0.0, en = 0.0;
     for (int v = 0; v < m->nv; v++) {
-        vol += m->area_v[v] * eta[v];
-        en += m->area_v[v] * 0.5 * g * eta[v] * eta[v];
+        vol += (double)m->area_v[v] * eta[v];
+        en += (double)m->area_v[v] * 0.5 * g * eta[v] * eta[v];
     }
     for (int e = 0; e < m->ne; e++) {
-        double H = element_depth(m, e, eta, nonlinear_h);
-        en += m->area_e[e] * (U[2 * e] * U[2 * e] + U[2 * e + 1] * U[2 * e + 1]) / (2.0 * H);
+        const int *t = m->tri + 3 * e;
+        double H = ((double)m->depth_v[t[0]] + (double)m->depth_v[t[1]] + (double)m->depth_v[t[2]]) / 3.0;
+        if (nonlinear_h) H += (eta[t[0]] + eta[t[1]] + eta[t[2]]) / 3.0;
+        en += (double)m->area_e[e] * (U[2 * e] * U[2 * e] + U[2 * e + 1] * U[2 * e + 1]) / (2.0 * H);
     }
     *volume = vol;
     *energy = en;
@@ -334,43 +363,50 @@ int oracle_diagnostics(void *hm, const double *eta, const double *U, double g, i
  *   diag   NULL or nsteps*2: (volume, energy) after each step
  * Returns 0, or -4 on allocation failure, -5 if M < 1.
  */
-int oracle_advance(void *hm, const double *R, double g, double theta, double tau, int M,
-                   int nonlinear_h, int nsteps, double *eta, double *U, double *Umean, double *diag)
+int oracle_advance(void *hm, const double *R_in, double g_in, double theta_in, double tau, int M,
+                   int nonlinear_h, int nsteps, double *eta_io, double *U_io, double *Umean_out, double *diag)
 {
     omesh *m = (omesh *)hm;
     if (M < 1) return -5;
     int ne = m->ne, nv = m->nv;
-    double dt = tau / (double)M;
-    double *F = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
-    double *U0 = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
-    double *sumU = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
-    double *div = (double *)malloc(sizeof(double) * (size_t)nv);
-    double *ef = (double *)malloc(sizeof(double) * (size_t)m->ned);
-    if (!F || !U0 || !sumU || !div || !ef) {
-        free(F); free(U0); free(sumU); free(div); free(ef);
+    const real dt = (real)(tau / (double)M);
+    const real g = (real)g_in, theta = (real)theta_in;
+    real *F = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *U = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *U0 = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *sumU = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *R = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *eta = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *div = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *ef = (real *)malloc(sizeof(real) * (size_t)m->ned);
+    double *Ud = (double *)malloc(sizeof(double) * 2 * (size_t)ne);
+    if (!F || !U || !U0 || !sumU || !R || !eta || !div || !ef || !Ud) {
+        free(F); free(U); free(U0); free(sumU); free(R); free(eta); free(div); free(ef); free(Ud);
         return -4;
     }
+    for (size_t i = 0; i < 2 * (size_t)ne; i++) { U[i] = (real)U_io[i]; R[i] = (real)R_in[i]; }
+    for (int v = 0; v < nv; v++) eta[v] = (real)eta_io[v];
     for (int n = 0; n < nsteps; n++) {
-        memcpy(U0, U, sizeof(double) * 2 * (size_t)ne);
-        memset(sumU, 0, sizeof(double) * 2 * (size_t)ne);
+        memcpy(U0, U, sizeof(real) * 2 * (size_t)ne);
+        memset(sumU, 0, sizeof(real) * 2 * (size_t)ne);
         for (int s = 0; s < M; s++) {
             /* momentum: Crank-Nicolson Coriolis, pressure at eta^m with H^m, frozen R */
             #pragma omp parallel for schedule(static)
             for (int e = 0; e < ne; e++) {
-                double gx, gy;
+                real gx, gy;
                 gradient_e(m, e, eta, &gx, &gy);
-                double H = element_depth(m, e, eta, nonlinear_h);
-                double a = 0.5 * dt * m->f_e[e];
-                double ux = U[2 * e], uy = U[2 * e + 1];
+                real H = element_depth(m, e, eta, nonlinear_h);
+                real a = dt * m->f_e[e] / 2;
+                real ux = U[2 * e], uy = U[2 * e + 1];
                 /* (I + a J) U' = (I - a J) U + dt (-g H grad eta + R),  J = [[0,-1],[1,0]] */
-                double A11 = 1.0, A12 = -a, A21 = a, A22 = 1.0;
-                double bx = ux + a * uy + dt * (-g * H * gx + R[2 * e]);
-                double by = -a * ux + uy + dt * (-g * H * gy + R[2 * e + 1]);
-                double det = A11 * A22 - A12 * A21;
-                double nx = (bx * A22 - A12 * by) / det;
-                double ny = (A11 * by - A21 * bx) / det;
-                F[2 * e] = (1.0 + theta) * nx - theta * ux;
-                F[2 * e + 1] = (1.0 + theta) * ny - theta * uy;
+                real A11 = 1, A12 = -a, A21 = a, A22 = 1;
+                real bx = ux + a * uy + dt * (-g * H * gx + R[2 * e]);
+                real by = -a * ux + uy + dt * (-g * H * gy + R[2 * e + 1]);
+                real det = A11 * A22 - A12 * A21;
+                real nx = (bx * A22 - A12 * by) / det;
+                real ny = (A11 * by - A21 * bx) / det;
+                F[2 * e] = (1 + theta) * nx - theta * ux;
+                F[2 * e + 1] = (1 + theta) * ny - theta * uy;
                 U[2 * e] = nx;
                 U[2 * e + 1] = ny;
                 sumU[2 * e] += nx;
@@ -383,10 +419,20 @@ int oracle_advance(void *hm, const double *R, double g, double theta, double tau
         }
         for (int e = 0; e < ne; e++)
             for (int c = 0; c < 2; c++)
-                Umean[2 * e + c] = sumU[2 * e + c] / (double)M + theta / (double)M * (U[2 * e + c] - U0[2 * e + c]);
-        if (diag) oracle_diagnostics(m, eta, U, g, nonlinear_h, diag + 2 * n, diag + 2 * n + 1);
+                Umean_out[2 * e + c] = (double)(sumU[2 * e + c] / (real)M + theta / (real)M * (U[2 * e + c] - U0[2 * e + c]));
+        if (diag) {
+            double *ed = (double *)malloc(sizeof(double) * (size_t)nv);
+            if (ed) {
+                for (int v = 0; v < nv; v++) ed[v] = (double)eta[v];
+                for (size_t i = 0; i < 2 * (size_t)ne; i++) Ud[i] = (double)U[i];
+                oracle_diagnostics(m, ed, Ud, g_in, nonlinear_h, diag + 2 * n, diag + 2 * n + 1);
+                free(ed);
+            }
+        }
     }
-    free(F); free(U0); free(sumU); free(div); free(ef);
+    for (size_t i = 0; i < 2 * (size_t)ne; i++) U_io[i] = (double)U[i];
+    for (int v = 0; v < nv; v++) eta_io[v] = (double)eta[v];
+    free(F); free(U); free(U0); free(sumU); free(R); free(eta); free(div); free(ef); free(Ud);
     return 0;
 }
 

@@ -66,6 +66,26 @@ def lib():
     return _lib
 
 
+_lib32 = None
+
+
+def lib_fp32():
+    """The same oracle source built with float as its working precision. Used only to
+    measure how far FP32 arithmetic of the algorithm drifts from FP64."""
+    global _lib32
+    with _lock:
+        if _lib32 is None:
+            path = os.path.join(_BUILD, "liboracle_fp32.so")
+            if not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+                os.makedirs(_BUILD, exist_ok=True)
+                tmp = path + f".tmp{os.getpid()}"
+                subprocess.run(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+                                "-fno-fast-math", "-DORACLE_REAL=float", "-o", tmp, _SRC, "-lm"], check=True)
+                os.replace(tmp, path)
+            _lib32 = _bind(path)
+    return _lib32
+
+
 def build_variant(source_text: str, tag: str):
     """Compile a modified copy of oracle.c (used only to show that the pins catch
     planted mistakes) and return its bound library."""

@@ -118,25 +118,41 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     for (int v = 0; v < nv; v++)
         if (!(m.depth[v] > 0.0) || !finite(m.depth[v])) { fmt(err, "vertex %lld has a depth that is not positive and finite", v); return SESW_EINVAL; }
 
-    // ---- edges: each shared by at most two triangles, in opposite directions
+    // ---- edges: each shared by at most two triangles, in opposite directions. The
+    // off-diagonal stiffness of each edge, K_ab = sum_e A_e H0_e dphi_a . dphi_b, is
+    // summed on the way for the Gershgorin bound below.
+    std::vector<double> kdiag(nv, 0.0), koff(nv, 0.0);
     {
-        std::vector<uint64_t> key(3 * (size_t)ne);
-        for (int e = 0; e < ne; e++)
+        struct HE { uint64_t key; double k; };
+        std::vector<HE> he(3 * (size_t)ne);
+        for (int e = 0; e < ne; e++) {
+            const int32_t *t = m.tri + 3 * (size_t)e;
+            const double *g = gph.data() + 6 * (size_t)e;
+            const double h0 = (m.depth[t[0]] + m.depth[t[1]] + m.depth[t[2]]) / 3.0;
             for (int k = 0; k < 3; k++) {
-                uint32_t a = (uint32_t)m.tri[3 * (size_t)e + k], b = (uint32_t)m.tri[3 * (size_t)e + (k + 1) % 3];
+                int kn = (k + 1) % 3;
+                uint32_t a = (uint32_t)t[k], b = (uint32_t)t[kn];
                 uint32_t lo = a < b ? a : b, hi = a < b ? b : a;
                 // low bit: direction (1 when traversed from the higher to the lower index)
-                key[3 * (size_t)e + k] = (((uint64_t)lo * (uint64_t)nv + hi) << 1) | (a > b ? 1u : 0u);
+                he[3 * (size_t)e + k].key = (((uint64_t)lo * (uint64_t)nv + hi) << 1) | (a > b ? 1u : 0u);
+                he[3 * (size_t)e + k].k = A[e] * h0 * (g[2 * k] * g[2 * kn] + g[2 * k + 1] * g[2 * kn + 1]);
+                kdiag[t[k]] += A[e] * h0 * (g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1]);
             }
-        std::sort(key.begin(), key.end());
-        for (size_t i = 0; i < key.size();) {
+        }
+        std::sort(he.begin(), he.end(), [](const HE &x, const HE &y) { return x.key < y.key; });
+        for (size_t i = 0; i < he.size();) {
             size_t j = i;
-            while (j < key.size() && (key[j] >> 1) == (key[i] >> 1)) j++;
+            while (j < he.size() && (he[j].key >> 1) == (he[i].key >> 1)) j++;
             if (j - i > 2) { err = "an edge is shared by more than two triangles"; return SESW_EINVAL; }
-            if (j - i == 2 && (key[i] & 1u) == (key[i + 1] & 1u)) {
+            if (j - i == 2 && (he[i].key & 1u) == (he[i + 1].key & 1u)) {
                 err = "two triangles traverse a shared edge in the same direction (inconsistent orientation)";
                 return SESW_EINVAL;
             }
+            double kab = 0.0;
+            for (size_t q = i; q < j; q++) kab += he[q].k;
+            uint64_t pair = he[i].key >> 1;
+            koff[pair / (uint64_t)nv] += fabs(kab);
+            koff[pair % (uint64_t)nv] += fabs(kab);
             i = j;
         }
     }
@@ -327,7 +343,13 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
         double lmax = 0.5 * tr + sqrt(std::max(0.25 * tr * tr - det, 0.0));
         gmax = std::max(gmax, out.h0_e[i] * lmax);
     }
-    out.grad_gram_max_h = gmax;
+    // Two upper bounds of lambda_max(-div H0 grad) for the lumped operator (times g
+    // gives the largest squared substep frequency over dt^2): element by element,
+    // max_e 3 H0_e lambda_max(sum_k dphi_k dphi_k^T), and Gershgorin over the rows of
+    // K / A_v. Both are rigorous; the smaller one is kept.
+    double gersh = 0.0;
+    for (int v = 0; v < nv; v++) gersh = std::max(gersh, (kdiag[v] + koff[v]) / Av[v]);
+    out.grad_gram_max_h = std::min(3.0 * gmax, gersh);
     return SESW_OK;
 }
 

@@ -290,9 +290,8 @@ int sesw_set_params(sesw_ctx *c, const sesw_params *p)
     if (p->nonlinear_h != 0 && p->nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
     if (p->scheme != 0) return fail(c, SESW_EINVAL, "scheme must be 0 (dissipative forward-backward)");
     const double dt = p->tau / p->M;
-    // Element-by-element bound on the largest eigenvalue of -div(g H0 grad):
-    // lambda_max <= max_e 3 g H0_e lambda_max(sum_k dphi_k dphi_k^T).
-    const double cmax = sqrt(3.0 * p->g * c->grad_gram_max_h) * dt;
+    // upper bound of dt sqrt(lambda_max(-div g H0 grad)), see prepare_mesh
+    const double cmax = sqrt(p->g * c->grad_gram_max_h) * dt;
     const double limit = 2.0 / sqrt(1.0 + 2.0 * p->theta);
     if (cmax > limit && !(p->flags & SESW_FLAG_NO_STABILITY_CHECK)) {
         char buf[256];
@@ -456,6 +455,7 @@ int sesw_mesh_check(const sesw_mesh *mesh, int32_t patch_vertices, sesw_info *in
         info->nslot = hm.nslot;
         info->max_patch_slots = hm.max_patch_slots;
         info->patch_vertices = hm.patch_vertices;
+        info->stiffness_bound = hm.grad_gram_max_h;
     }
     return rc;
 }
@@ -473,6 +473,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->patch_vertices = c->patch_vertices_used;
     info->courant_max = c->courant_max;
     info->courant_limit = c->have_params ? c->courant_limit : 0.0;
+    info->stiffness_bound = c->grad_gram_max_h;
     info->device_bytes = c->device_bytes;
     return SESW_OK;
 }

@@ -42,7 +42,7 @@ struct HostMesh {
     std::vector<double> area_v;    // median-dual area (FP64, for diagnostics)
     std::vector<double> area_e;    // element area (FP64), new element order
     std::vector<double> h0_e;      // element rest depth (FP64), new element order
-    double grad_gram_max_h = 0.0;  // max over elements of H0_e * lambda_max(sum_i dphi_i dphi_i^T)
+    double grad_gram_max_h = 0.0;  // upper bound of lambda_max(-div H0 grad) (m/s^2 units without g)
 };
 
 // Validate and prepare; returns SESW_OK or SESW_EINVAL with a message in err.

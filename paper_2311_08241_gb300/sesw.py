@@ -59,7 +59,8 @@ class sesw_info(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("ne", ctypes.c_int32), ("npatch", ctypes.c_int32),
                 ("nslot", ctypes.c_int32), ("max_patch_slots", ctypes.c_int32),
                 ("patch_vertices", ctypes.c_int32), ("courant_max", ctypes.c_double),
-                ("courant_limit", ctypes.c_double), ("device_bytes", ctypes.c_int64)]
+                ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

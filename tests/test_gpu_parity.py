@@ -1,12 +1,17 @@
 """GPU path (through the C-ABI) against the FP64 oracle on the same seeded inputs.
 
-Tolerances (FP32 state on the GPU, FP64 in the oracle):
-  eta    max |d eta| <= ETA_TOL m. 1e-5 m after 100 channel steps (4000 substeps) is
-         the stated target; with FP32 rounding (2^-24 relative) per substep on
-         |eta| <~ 1 m, an unbiased random walk over 4000 substeps stays near
-         6e-8 * sqrt(4000) ~ 4e-6 m.
-  U, <<U>>  max |dU| <= U_REL * max |U_ref| (+ a floor of 1e-6 m^2/s for fields at rest),
-         the same per-substep rounding argument applied to the transport.
+Tolerances. The GPU keeps eta and U in FP32 (geometry derived in FP64, rounded
+once). Its drift from the FP64 oracle is compared with the drift of the same
+algorithm run in FP32 on the CPU: the oracle source built with float as its working
+precision (geometry still derived in double), on the same inputs. For every field,
+    max |GPU - FP64 oracle| <= ENVELOPE_FACTOR * max |FP32 oracle - FP64 oracle| + floor,
+with ENVELOPE_FACTOR = 2 (the two FP32 programs round in different orders, so their
+drifts differ by O(1) factors, not orders of magnitude) and a floor of a few FP32
+ulps of the field's scale. On top of that, eta must meet the absolute target
+max |d eta| <= 1e-5 m (after 100 baroclinic steps of the channel).
+The FP32 drift is large for U in the channel (~8e-5 relative after 4000 substeps):
+U is near geostrophic balance there, so FP32 rounding of eta and of the geometry
+(about 6e-8 relative) is amplified by g H / (f L).
 """
 import math
 
@@ -19,8 +24,9 @@ from paper_2311_08241_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-ETA_TOL = 1e-5
-U_REL = 2e-5
+ETA_ABS_TOL = 1e-5
+ENVELOPE_FACTOR = 2.0
+ULP_FLOOR = 8 * 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -35,40 +41,40 @@ def sesw():
     return S
 
 
-def _errs(ref, got):
-    e_ref, U_ref, M_ref = ref[:3]
-    e, U, Um = got
-    de = float(np.max(np.abs(e - e_ref)))
-    su = max(float(np.max(np.abs(U_ref))), 1e-300)
-    sm = max(float(np.max(np.abs(M_ref))), 1e-300)
-    du = float(np.max(np.abs(U - U_ref)))
-    dm = float(np.max(np.abs(Um - M_ref)))
-    return de, du, su, dm, sm
+def _maxabs(x):
+    return float(np.max(np.abs(x))) if np.size(x) else 0.0
 
 
-def _assert_close(ref, got, what, eta_tol=ETA_TOL, u_rel=U_REL):
-    de, du, su, dm, sm = _errs(ref, got)
-    print(f"{what}: max|d eta| = {de:.3e}, max|dU| = {du:.3e} (rel {du / su:.2e}), "
-          f"max|d<<U>>| = {dm:.3e} (rel {dm / sm:.2e})")
-    assert de <= eta_tol, f"{what}: eta error {de:.3e}"
-    assert du <= u_rel * su + 1e-6, f"{what}: U error {du:.3e} vs scale {su:.3e}"
-    assert dm <= u_rel * sm + 1e-6, f"{what}: <<U>> error {dm:.3e} vs scale {sm:.3e}"
+def _assert_close(case, got, what, nsteps=None):
+    """GPU result vs the FP64 oracle, within twice the FP32 oracle's drift (see module docstring)."""
+    ref = orc.run_case(case, nsteps=nsteps)
+    r32 = orc.run_case(case, nsteps=nsteps, L=orc.lib_fp32())
+    names = ("eta", "U", "<<U>>")
+    report = []
+    for k, name in enumerate(names):
+        scale = max(_maxabs(ref[k]), 1e-30)
+        err = _maxabs(got[k] - ref[k])
+        env = _maxabs(r32[k] - ref[k])
+        tol = ENVELOPE_FACTOR * env + ULP_FLOOR * scale
+        report.append(f"{name}: err {err:.3e} env32 {env:.3e} tol {tol:.3e} (scale {scale:.3e})")
+        assert err <= tol, f"{what}: {report[-1]}"
+    print(f"{what}: " + "; ".join(report))
+    assert _maxabs(got[0] - ref[0]) <= ETA_ABS_TOL, f"{what}: eta above the absolute target"
+    return ref
 
 
 def test_basin_matches_oracle(sesw):
     """Closed 1000x500 km basin, Gaussian bump, f-plane, 20 steps of 30 substeps."""
     case = I.basin_case()
-    ref = orc.run_case(case)
     got = sesw.run_case(case)
-    _assert_close(ref, got, "basin")
+    _assert_close(case, got, "basin")
 
 
 def test_channel_matches_oracle_100_steps(sesw):
     """Wind-driven channel (200k vertices) in the benchmark's launch configuration, 100 steps."""
     case = I.channel_case(nsteps=100)
-    ref = orc.run_case(case)
     got = sesw.run_case(case)
-    _assert_close(ref, got, "channel-100")
+    _assert_close(case, got, "channel-100")
 
 
 @pytest.mark.parametrize("pv", [32, 100, 777])
@@ -77,33 +83,29 @@ def test_tiny_meshes_many_patches(sesw, pv, seed):
     """Small jittered basins cut into many ragged patches (guest copies on every border)."""
     case = I.tiny_jittered_case(nx=23, ny=17, seed=seed, M=9, tau=90.0)
     case.nsteps = 4
-    ref = orc.run_case(case)
     got = sesw.run_case(case, patch_vertices=pv)
-    _assert_close(ref, got, f"tiny pv={pv} seed={seed}")
+    _assert_close(case, got, f"tiny pv={pv} seed={seed}")
 
 
 def test_linear_h_and_odd_M(sesw):
     case = I.tiny_jittered_case(nx=30, ny=20, seed=7, M=7, tau=70.0, nonlinear_h=0)
     case.nsteps = 5
-    ref = orc.run_case(case)
     got = sesw.run_case(case, patch_vertices=64)
-    _assert_close(ref, got, "linear-H odd M")
+    _assert_close(case, got, "linear-H odd M")
 
 
 def test_sphere_matches_oracle(sesw):
     """Icosahedral sphere (level 6 here; level 8 in the next test) with land, forcing and f = 2 Omega sin(lat)."""
     case = I.sphere_case(level=6, nsteps=10)
-    ref = orc.run_case(case)
     got = sesw.run_case(case)
-    _assert_close(ref, got, "sphere-l6")
+    _assert_close(case, got, "sphere-l6")
 
 
 def test_sphere_level8_full_size(sesw):
     """Global-like sphere at full size (level 8: ~460k wet vertices), 5 steps of 50 substeps."""
     case = I.sphere_case(level=8, nsteps=5)
-    ref = orc.run_case(case)
     got = sesw.run_case(case)
-    _assert_close(ref, got, "sphere-l8")
+    _assert_close(case, got, "sphere-l8")
 
 
 def test_periodic_wave_closed_form(sesw):
@@ -138,7 +140,7 @@ def test_summation_identity_and_volume(sesw):
             vols.append(s.sesw_diagnostics()[0])
     assert abs(v0 - float(np.sum(av * case.eta0))) < 1e-6 * float(np.sum(av * np.abs(case.eta0)))
     eps32 = 2.0 ** -24
-    bound = 4 * eps32 * math.sqrt(20 * case.params.M) * math.sqrt(float(np.sum((av * case.eta0) ** 2))) * 10
+    bound = 4 * eps32 * math.sqrt(20 * case.params.M) * math.sqrt(float(np.sum((av * case.eta0) ** 2)))
     drift = np.abs(np.array(vols) - v0)
     print("volume drift", drift.max(), "bound", bound)
     assert drift.max() <= bound

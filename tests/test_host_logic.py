@@ -131,3 +131,39 @@ def test_bench_aggregation_two_gloo_ranks():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [11.0, 11.0]
     assert res[0][2] == pytest.approx(2 * 1000 * 40 * 5 / 11e-3)
+
+
+@pytest.mark.parametrize("maker", [lambda: I.channel_case(), lambda: I.basin_case(),
+                                   lambda: I.ensemble_cases(nbasins=1, scale=0.05)[0]])
+def test_courant_bound_is_an_upper_bound(maker):
+    """The library's Courant bound is >= the true spectral radius of -div(g H0 grad) (scipy eigsh
+    on the symmetrised lumped operator), and not far above it."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as sla
+
+    case = maker()
+    m = case.mesh
+    info = _check(m, 512)
+    xy, tri = m.xy, m.tri
+    A = 0.5 * ((xy[:, 1, 0] - xy[:, 0, 0]) * (xy[:, 2, 1] - xy[:, 0, 1])
+               - (xy[:, 2, 0] - xy[:, 0, 0]) * (xy[:, 1, 1] - xy[:, 0, 1]))
+    G = np.zeros((m.ne, 3, 2))
+    for k in range(3):
+        d = xy[:, (k + 2) % 3] - xy[:, (k + 1) % 3]
+        G[:, k, 0] = -d[:, 1] / (2 * A)
+        G[:, k, 1] = d[:, 0] / (2 * A)
+    w = A * m.depth[tri].mean(axis=1)
+    r, c, v = [], [], []
+    for a in range(3):
+        for b in range(3):
+            r.append(tri[:, a])
+            c.append(tri[:, b])
+            v.append(w * (G[:, a] * G[:, b]).sum(axis=1))
+    K = sp.coo_matrix((np.concatenate(v), (np.concatenate(r), np.concatenate(c))), shape=(m.nv, m.nv)).tocsr()
+    Av = np.zeros(m.nv)
+    for k in range(3):
+        np.add.at(Av, tri[:, k], A / 3)
+    Dm = sp.diags(1 / np.sqrt(Av))
+    lam = sla.eigsh(Dm @ K @ Dm, k=1, which="LA", return_eigenvectors=False)[0]
+    assert lam <= info["stiffness_bound"] * (1 + 1e-9)
+    assert info["stiffness_bound"] <= 2.0 * lam

@@ -275,15 +275,15 @@ def test_oracle_operators_match_finite_element_adjoint():
 
 PLANTS = {
     # dropped theta weighting in the continuity flux
-    "drop_theta": ("F[2 * e] = (1.0 + theta) * nx - theta * ux;", "F[2 * e] = nx;"),
+    "drop_theta": ("F[2 * e] = (1 + theta) * nx - theta * ux;", "F[2 * e] = nx;"),
     # wrong sign of the pressure gradient (the sign printed in the Eq. 4.10 bracket)
-    "pressure_sign": ("double bx = ux + a * uy + dt * (-g * H * gx + R[2 * e]);",
-                      "double bx = ux + a * uy + dt * (g * H * gx + R[2 * e]);"),
+    "pressure_sign": ("real bx = ux + a * uy + dt * (-g * H * gx + R[2 * e]);",
+                      "real bx = ux + a * uy + dt * (g * H * gx + R[2 * e]);"),
     # Coriolis turned the wrong way
-    "coriolis_sign": ("double A11 = 1.0, A12 = -a, A21 = a, A22 = 1.0;",
-                      "double A11 = 1.0, A12 = a, A21 = -a, A22 = 1.0;"),
+    "coriolis_sign": ("real A11 = 1, A12 = -a, A21 = a, A22 = 1;",
+                      "real A11 = 1, A12 = a, A21 = -a, A22 = 1;"),
     # mean without the theta correction of Eq. (4.12)
-    "mean_no_theta": ("+ theta / (double)M * (U[2 * e + c] - U0[2 * e + c]);", ";"),
+    "mean_no_theta": ("+ theta / (real)M * (U[2 * e + c] - U0[2 * e + c]))", ")"),
     # divergence counted into the wrong cell
     "flux_side": ("s += (m->edge_v[2 * q] == v) ? edgeflux[q] : -edgeflux[q];",
                   "s += (m->edge_v[2 * q] == v) ? -edgeflux[q] : edgeflux[q];"),
