@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--patch-vertices", type=int, default=512)
+    ap.add_argument("--block-threads", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=400)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -259,6 +260,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
     sim = S.Subcycle(local, stream=stream)
     sim.sesw_set_patch_vertices(args.patch_vertices)
+    sim.sesw_set_block_threads(args.block_threads)
     sim.sesw_mesh_upload(case.mesh)
     sim.sesw_set_params(case.params)
     sim.sesw_set_forcing(case.R)
@@ -324,7 +326,8 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(desc, patch_vertices=info["patch_vertices"], npatch=info["npatch"],
+            "config": dict(desc, patch_vertices=info["patch_vertices"], block_threads=info["block_threads"],
+                           npatch=info["npatch"],
                            nslot=info["nslot"], l2="flushed between timed steps (256 MiB write)",
                            parallelism=f"replicas{world}"),
             "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (M + 1), "clocks": clk}

@@ -117,6 +117,8 @@ typedef struct sesw_info {
     int32_t nslot;           /* element slots: ne owned + guest copies on patch borders */
     int32_t max_patch_slots; /* largest slot count of one patch */
     int32_t patch_vertices;  /* target vertices per patch */
+    int32_t block_threads;   /* threads per block of the substep kernel */
+    int32_t reserved;
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
                                 (0 until parameters are set) */
     double courant_limit;    /* 2/sqrt(1+2 theta), the stability limit of the scheme */
@@ -137,6 +139,10 @@ int sesw_set_stream(sesw_ctx *ctx, void *cuda_stream);
 /* Set the target number of vertices per patch (>= 32) for the next mesh upload;
  * default 512. */
 int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
+
+/* Threads per block of the substep kernel (a multiple of 32 in [32, 1024]);
+ * default 256. Takes effect at the next advance. */
+int sesw_set_block_threads(sesw_ctx *ctx, int32_t threads);
 
 /* Validate, reorder and upload a mesh (mesh prep: geometry, space-filling-curve
  * order, vertex patches with their boundary element copies, per-vertex incidence).

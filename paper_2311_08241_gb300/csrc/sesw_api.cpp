@@ -22,6 +22,7 @@ struct sesw_ctx {
     void *user = nullptr;
     std::string err;
     int patch_vertices = 512;
+    int block_threads = 256;
     bool have_mesh = false, have_params = false;
     sesw::DevMesh dm;
     sesw::DevState ds;
@@ -141,7 +142,7 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     cudaError_t e = cudaSuccess;
     int p = parity;
     for (int m = 0; m < c->params.M && e == cudaSuccess; m++) {
-        e = sesw::launch_substep(c->dm, c->ds, c->args, p, 0, c->cap_stream);
+        e = sesw::launch_substep(c->dm, c->ds, c->args, p, c->block_threads, c->cap_stream);
         p ^= 1;
     }
     if (e == cudaSuccess) e = sesw::launch_step_epilogue(c->dm, c->ds, c->args, c->cap_stream);
@@ -201,6 +202,16 @@ int sesw_set_patch_vertices(sesw_ctx *c, int32_t pv)
     if (!c) return SESW_EINVAL;
     if (pv < 32 || pv > (1 << 20)) return fail(c, SESW_EINVAL, "patch_vertices must be in [32, 2^20]");
     c->patch_vertices = pv;
+    return SESW_OK;
+}
+
+int sesw_set_block_threads(sesw_ctx *c, int32_t threads)
+{
+    if (!c) return SESW_EINVAL;
+    if (threads < 32 || threads > 1024 || threads % 32)
+        return fail(c, SESW_EINVAL, "block_threads must be a multiple of 32 in [32, 1024]");
+    c->block_threads = threads;
+    drop_graphs(c);
     return SESW_OK;
 }
 
@@ -471,6 +482,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->nslot = c->nslot;
     info->max_patch_slots = c->max_patch_slots;
     info->patch_vertices = c->patch_vertices_used;
+    info->block_threads = c->block_threads;
     info->courant_max = c->courant_max;
     info->courant_limit = c->have_params ? c->courant_limit : 0.0;
     info->stiffness_bound = c->grad_gram_max_h;

@@ -19,7 +19,7 @@ namespace sesw {
 
 namespace {
 
-constexpr int kSubstepThreads = 256;
+constexpr int kSubstepMaxThreads = 1024;
 constexpr int kAuxThreads = 256;
 
 // Error-free accumulation of x into the pair (hi, lo): after the call hi + lo equals
@@ -47,7 +47,7 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
 //   c_k      = dt A_e F . g_k, k = 0, 1;  c_2 = -(c_0 + c_1)  flux into corner k's cell
 // Vertex part: eta' = eta + (sum of c over the vertex's incidences) / A_v.
 template <int NONLIN>
-__global__ void __launch_bounds__(kSubstepThreads)
+__global__ void __launch_bounds__(kSubstepMaxThreads)
 k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 *__restrict__ sc,
           const float2 *__restrict__ R, float2 *__restrict__ U, float2 *__restrict__ Shi,
           float2 *__restrict__ Slo, const int *__restrict__ patch_slot, const int *__restrict__ patch_own,
@@ -260,16 +260,16 @@ int grid_for(int n, int threads)
 cudaError_t launch_substep(const DevMesh &m, const DevState &s, const StepArgs &a, int parity, int block,
                            cudaStream_t stream)
 {
-    (void)block;
+    const int threads = block > 0 ? block : 256;
     const size_t smem = sizeof(float) * 3 * (size_t)m.max_patch_slots;
     const float *ein = s.eta[parity];
     float *eout = s.eta[parity ^ 1];
     if (a.nonlinear_h)
-        k_substep<1><<<m.npatch, kSubstepThreads, smem, stream>>>(
+        k_substep<1><<<m.npatch, threads, smem, stream>>>(
             m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
             m.vcsr_off, m.vcsr, m.inv_av, ein, eout, a, s.status);
     else
-        k_substep<0><<<m.npatch, kSubstepThreads, smem, stream>>>(
+        k_substep<0><<<m.npatch, threads, smem, stream>>>(
             m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
             m.vcsr_off, m.vcsr, m.inv_av, ein, eout, a, s.status);
     return cudaGetLastError();

@@ -31,10 +31,11 @@ _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", 
           -5: "SESW_EUNSTABLE", -6: "SESW_ENOMEM"}
 
 # every symbol include/sesw.h declares
-EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_patch_vertices", "sesw_mesh_upload",
+EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_patch_vertices", "sesw_set_block_threads",
+           "sesw_mesh_upload",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
-           "sesw_diagnostics", "sesw_status", "sesw_mesh_check", "sesw_get_info", "sesw_last_error",
-           "sesw_destroy")
+           "sesw_diagnostics", "sesw_status", "sesw_mesh_check",
+           "sesw_get_info", "sesw_last_error", "sesw_destroy")
 
 
 class SeswError(RuntimeError):
@@ -58,7 +59,8 @@ class sesw_params(ctypes.Structure):
 class sesw_info(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("ne", ctypes.c_int32), ("npatch", ctypes.c_int32),
                 ("nslot", ctypes.c_int32), ("max_patch_slots", ctypes.c_int32),
-                ("patch_vertices", ctypes.c_int32), ("courant_max", ctypes.c_double),
+                ("patch_vertices", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("courant_max", ctypes.c_double),
                 ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 
@@ -88,6 +90,7 @@ def load(build_if_missing: bool = True):
         L.sesw_create.argtypes = [ctypes.POINTER(P), I, P, ALLOC_FN, FREE_FN, P]
         L.sesw_set_stream.argtypes = [P, P]
         L.sesw_set_patch_vertices.argtypes = [P, ctypes.c_int32]
+        L.sesw_set_block_threads.argtypes = [P, ctypes.c_int32]
         L.sesw_mesh_upload.argtypes = [P, ctypes.POINTER(sesw_mesh)]
         L.sesw_set_params.argtypes = [P, ctypes.POINTER(sesw_params)]
         L.sesw_set_state.argtypes = [P, P, P, I]
@@ -199,6 +202,9 @@ class Subcycle:
     # -- the C calls
     def sesw_set_patch_vertices(self, n: int):
         return self._check(self._L.sesw_set_patch_vertices(self._h, int(n)))
+
+    def sesw_set_block_threads(self, n: int):
+        return self._check(self._L.sesw_set_block_threads(self._h, int(n)))
 
     def sesw_mesh_upload(self, mesh):
         m, keep = _mesh_struct(mesh)
