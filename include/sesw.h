@@ -184,6 +184,35 @@ int sesw_get_state(sesw_ctx *ctx, double *eta, double *U, double *Umean, int whe
  * sum_v A_v g eta_v^2/2 + sum_e A_e |U_e|^2 / (2 H_e) (m^5/s^2). Synchronises. */
 int sesw_diagnostics(sesw_ctx *ctx, double *volume, double *energy);
 
+/* Allocation-free volume and energy of a caller-held state. The paper has no
+ * counterpart: this serves callers that cannot allocate device memory where they need
+ * the numbers (code running inside another framework's memory pool or under its
+ * allocator lock, loops that must not enter the CUDA allocator, hosts that only hand
+ * over pre-allocated buffers). It needs no context and computes
+ *   out[0] = sum_v area_v[v] eta[v]
+ *   out[1] = sum_v area_v[v] g eta[v]^2 / 2 + sum_e area_e[e] |U[e]|^2 / (2 h_e[e]),
+ * the quantities of sesw_diagnostics, in FP64.
+ * Arguments: device pointers on the current device, caller order and caller-owned:
+ * area_v and eta [nv], area_e and h_e (water depth H of each triangle, > 0) [ne],
+ * U [ne][2], out [2]; g > 0; cuda_stream a cudaStream_t (NULL = legacy default).
+ * Work is enqueued on the stream and the call returns without waiting.
+ * Limits: 0 <= nv, ne <= SESW_NOALLOC_MAX_ITEMS (33,554,432); larger sizes and NULL
+ * pointers return SESW_EINVAL before anything is launched; a failed launch returns
+ * SESW_ECUDA.
+ * Scratch: one fixed 128 KiB array of partial sums (SESW_NOALLOC_MAX_CHUNKS pairs of
+ * doubles) that lives in the library's device memory on every GPU that loads the
+ * library, until the process exits. Nothing is allocated or freed by the call. Every
+ * call reuses the same array and overwrites the partials it needs (nothing has to
+ * start at zero); calls that overlap on the GPU (several streams or threads at once)
+ * race on it and must be ordered by the caller.
+ * The first call on a device looks up the array's device address with that device
+ * current (cudaGetSymbolAddress); make that first call before any stream capture. */
+#define SESW_NOALLOC_MAX_CHUNKS 8192
+#define SESW_NOALLOC_MAX_ITEMS (SESW_NOALLOC_MAX_CHUNKS * 4096)
+int sesw_diagnostics_noalloc(int64_t nv, int64_t ne, const double *area_v, const double *eta,
+                             const double *area_e, const double *h_e, const double *U, double g,
+                             double *out, void *cuda_stream);
+
 /* Synchronise and return SESW_OK, SESW_EUNSTABLE or SESW_ETIMEOUT from the device
  * status word; clears the word. */
 int sesw_status(sesw_ctx *ctx);

@@ -34,8 +34,10 @@ _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", 
 EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_patch_vertices", "sesw_set_block_threads",
            "sesw_mesh_upload",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
-           "sesw_diagnostics", "sesw_status", "sesw_mesh_check",
+           "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_status", "sesw_mesh_check",
            "sesw_get_info", "sesw_last_error", "sesw_destroy")
+SESW_NOALLOC_MAX_CHUNKS = 8192
+SESW_NOALLOC_MAX_ITEMS = SESW_NOALLOC_MAX_CHUNKS * 4096
 
 
 class SeswError(RuntimeError):
@@ -99,6 +101,7 @@ def load(build_if_missing: bool = True):
         L.sesw_get_state.argtypes = [P, P, P, P, I]
         L.sesw_diagnostics.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.sesw_status.argtypes = [P]
+        L.sesw_diagnostics_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, D, P, P]
         L.sesw_get_info.argtypes = [P, ctypes.POINTER(sesw_info)]
         L.sesw_mesh_check.argtypes = [ctypes.POINTER(sesw_mesh), ctypes.c_int32, ctypes.POINTER(sesw_info),
                                       ctypes.c_char_p, ctypes.c_size_t]
@@ -277,6 +280,15 @@ def sesw_mesh_check(mesh, patch_vertices: int = 512):
     if rc != SESW_OK:
         raise SeswError(rc, buf.value.decode())
     return {k: getattr(info, k) for k, _ in sesw_info._fields_}
+
+
+def sesw_diagnostics_noalloc(nv, ne, area_v, eta, area_e, h_e, U, g, out, stream=None):
+    """Allocation-free volume/energy of caller-held device arrays (torch float64 CUDA
+    tensors); writes out[0:2] on the stream and returns the status code."""
+    L = load()
+    sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
+    return L.sesw_diagnostics_noalloc(int(nv), int(ne), _ptr(area_v), _ptr(eta), _ptr(area_e), _ptr(h_e),
+                                      _ptr(U), float(g), _ptr(out), sp)
 
 
 def _as_f64(x):
