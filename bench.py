@@ -43,8 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--patch-vertices", type=int, default=512)
+    ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto")
+    ap.add_argument("--patch-vertices", type=int, default=256)
     ap.add_argument("--block-threads", type=int, default=256)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=400)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -91,9 +93,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per substep launch from the committed ncu summary, if it matches this kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_substep_channel.md")
+def profiled_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_channel.md")
     try:
         txt = open(p).read()
     except OSError:
@@ -259,8 +261,11 @@ def run_ours(args, world, rank, local):
     V, E, M = case.mesh.nv, case.mesh.ne, case.params.M
     stream = torch.cuda.current_stream(dev)
     sim = S.Subcycle(local, stream=stream)
+    sim.sesw_set_mode({"auto": S.SESW_MODE_AUTO, "graph": S.SESW_MODE_GRAPH,
+                       "persistent": S.SESW_MODE_PERSISTENT}[args.mode])
     sim.sesw_set_patch_vertices(args.patch_vertices)
     sim.sesw_set_block_threads(args.block_threads)
+    sim.sesw_set_blocks_per_sm(args.blocks_per_sm)
     sim.sesw_mesh_upload(case.mesh)
     sim.sesw_set_params(case.params)
     sim.sesw_set_forcing(case.R)
@@ -296,15 +301,21 @@ def run_ours(args, world, rank, local):
     ms_per_step = total_ms / args.steps
     value = whole_job_value(V, M, args.steps, world, total_ms)
 
-    # roofline of the substep kernel: the step's event time over its M substep launches
-    # (the short epilogue launch is included, so this understates the kernel's rate)
+    # Roofline of the dominant kernel. Persistent mode: one k_persistent launch per step
+    # does all M substeps, so a launch moves M * B_alg algorithmic bytes. Graph mode: M
+    # k_substep launches per step, each B_alg (the step's short epilogue launch is
+    # included in the event time, which understates the kernel's rate).
+    persistent = info["mode"] == S.SESW_MODE_PERSISTENT
     b_alg = algorithmic_bytes_per_substep(V, E)
     mean_step_s = statistics.mean(step_ms) * 1e-3
-    achieved = b_alg / (mean_step_s / M) / 1e9
+    per_launch = b_alg * M if persistent else b_alg
+    launch_s = mean_step_s if persistent else mean_step_s / M
+    achieved = per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
+    kname = "k_persistent" if persistent else "k_substep"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(), "peak_source": peak_src, "kernel": "k_substep",
-                "bytes_per_launch": b_alg}
+                "traffic": profiled_traffic(kname), "peak_source": peak_src, "kernel": kname,
+                "bytes_per_launch": per_launch}
 
     # end to end through the public API with pinned host buffers: each step uploads
     # its forcing, advances, and reads back eta and <<U>>
@@ -326,11 +337,15 @@ def run_ours(args, world, rank, local):
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(desc, patch_vertices=info["patch_vertices"], block_threads=info["block_threads"],
+            "config": dict(desc, mode="persistent" if persistent else "graph",
+                           patch_vertices=info["patch_vertices"], block_threads=info["block_threads"],
+                           blocks_per_sm=info["blocks_per_sm"], slots_per_thread=info["slots_per_thread"],
+                           smem_cached=info["cached"],
                            npatch=info["npatch"],
                            nslot=info["nslot"], l2="flushed between timed steps (256 MiB write)",
                            parallelism=f"replicas{world}"),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (M + 1), "clocks": clk}
+            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (1 if persistent else M + 1),
+            "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds, rank)
     sim.close()

@@ -96,9 +96,14 @@ typedef struct sesw_mesh {
  *   nonlinear_h  1: H = H0 + eta on each triangle (corner mean); 0: H = H0
  *   scheme       0: dissipative forward-backward (Eq. 4.10); other values are rejected
  *   flags        bit 0 (SESW_FLAG_NO_STABILITY_CHECK): accept parameters whose Courant
- *                bound exceeds the stability limit (the bound is conservative)
+ *                bound exceeds the stability limit (the bound is conservative);
+ *                bit 1 (SESW_FLAG_TEST_FORCE_TIMEOUT, for testing failure detection):
+ *                in SESW_MODE_PERSISTENT patch 0 never publishes its progress and each
+ *                bounded wait gives up after ~1e7 cycles instead of ~1 s, so the step
+ *                ends early and sesw_status reports SESW_ETIMEOUT
  *   eta_bound    |eta| above this (m) or a non-finite value sets SESW_EUNSTABLE; <= 0 means 1e4 */
 #define SESW_FLAG_NO_STABILITY_CHECK 1
+#define SESW_FLAG_TEST_FORCE_TIMEOUT 2
 typedef struct sesw_params {
     double g;
     double theta;
@@ -117,7 +122,11 @@ typedef struct sesw_info {
     int32_t nslot;           /* element slots: ne owned + guest copies on patch borders */
     int32_t max_patch_slots; /* largest slot count of one patch */
     int32_t patch_vertices;  /* target vertices per patch */
-    int32_t block_threads;   /* threads per block of the substep kernel */
+    int32_t block_threads;   /* threads per block of the substep (or persistent) kernel */
+    int32_t mode;            /* SESW_MODE_GRAPH or SESW_MODE_PERSISTENT (0 from sesw_mesh_check) */
+    int32_t blocks_per_sm;   /* persistent mode: resident blocks per SM */
+    int32_t slots_per_thread;/* persistent mode: element slots held in registers per thread */
+    int32_t cached;          /* persistent mode: 1 when static slot data lives in shared memory */
     int32_t reserved;
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
                                 (0 until parameters are set) */
@@ -136,9 +145,29 @@ int sesw_create(sesw_ctx **out, int device, void *cuda_stream,
 /* Replace the stream used for subsequent work. */
 int sesw_set_stream(sesw_ctx *ctx, void *cuda_stream);
 
-/* Set the target number of vertices per patch (>= 32) for the next mesh upload;
- * default 512. */
+/* Set the target number of vertices per patch (>= 32) of SESW_MODE_GRAPH for the
+ * next mesh upload; default 256. (The persistent mode uses one patch per SM.) */
 int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
+
+/* Execution modes of a baroclinic step.
+ *   SESW_MODE_GRAPH       M launches of the substep kernel (one block per patch of
+ *                         ~patch_vertices vertices) plus an epilogue, as one CUDA graph
+ *   SESW_MODE_PERSISTENT  one cooperative launch per step: one block per SM keeps its
+ *                         patch's elevation and fluxes in shared memory and its
+ *                         transports in registers for all M substeps, exchanging
+ *                         boundary elevation with neighbouring blocks through flags
+ *                         with bounded waits (a wait that gives up sets SESW_ETIMEOUT)
+ *   SESW_MODE_AUTO        persistent when the mesh fits it, else graph (default)
+ * Results are the same to FP32 rounding; the summation order per vertex depends on
+ * the patch layout. Takes effect at the next mesh upload. */
+#define SESW_MODE_AUTO       0
+#define SESW_MODE_GRAPH      1
+#define SESW_MODE_PERSISTENT 2
+int sesw_set_mode(sesw_ctx *ctx, int32_t mode);
+
+/* Persistent mode: resident blocks (patches) per SM, 1, 2 or 4; 0 (default) tries 2
+ * and falls back to 1. Takes effect at the next mesh upload. */
+int sesw_set_blocks_per_sm(sesw_ctx *ctx, int32_t blocks_per_sm);
 
 /* Threads per block of the substep kernel (a multiple of 32 in [32, 1024]);
  * default 256. Takes effect at the next advance. */

@@ -258,11 +258,23 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     }
     if (maxslots >= (1 << 28)) { err = "a patch has too many element slots"; return SESW_EINVAL; }
 
+    // Slot order inside a patch: owned elements whose corners are all the patch's own
+    // vertices ("interior"), then the other owned elements, then guests. Interior slots
+    // need no halo elevation, so the persistent kernel updates them while it waits for
+    // its neighbours.
     std::vector<int> slot_elem(nslot);
     std::vector<char> slot_guest(nslot, 0);
+    std::vector<int> patch_int(npatch, 0);
     for (int p = 0; p < npatch; p++) {
         int s = patch_slot[p];
-        for (int i = own_begin[p]; i < own_begin[p + 1]; i++) slot_elem[s++] = i;
+        for (int pass = 0; pass < 2; pass++)
+            for (int i = own_begin[p]; i < own_begin[p + 1]; i++) {
+                const bool interior = vpatch[ek[i].lo] == p && vpatch[ek[i].mid] == p && vpatch[ek[i].hi] == p;
+                if (interior == (pass == 0)) {
+                    slot_elem[s++] = i;
+                    if (interior) patch_int[p]++;
+                }
+            }
         for (int k = g_begin[p]; k < g_begin[p + 1]; k++) { slot_guest[s] = 1; slot_elem[s++] = guests[k].second; }
     }
 
@@ -279,6 +291,7 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     out.patch_v = patch_v;
     out.patch_slot = patch_slot;
     out.patch_own = patch_own;
+    out.patch_int = patch_int;
     out.slot_v.resize(nslot);
     out.slot_g.resize(nslot);
     out.slot_c.resize(nslot);
@@ -350,6 +363,66 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     double gersh = 0.0;
     for (int v = 0; v < nv; v++) gersh = std::max(gersh, (kdiag[v] + koff[v]) / Av[v]);
     out.grad_gram_max_h = std::min(3.0 * gmax, gersh);
+    return SESW_OK;
+}
+
+int build_halos(HostMesh &hm, std::string &err)
+{
+    const int np = hm.npatch;
+    hm.patch_halo.assign(np + 1, 0);
+    hm.patch_nbr.assign(np + 1, 0);
+    hm.halo_v.clear();
+    hm.nbr.clear();
+    hm.slot_l.assign(hm.nslot, make_ushort4(0, 0, 0, 0));
+    hm.max_patch_local = 0;
+    hm.max_nbr = 0;
+    hm.max_patch_halo = 0;
+    hm.max_patch_csr = 0;
+    std::vector<int> vpatch(hm.nv);
+    for (int p = 0; p < np; p++)
+        for (int v = hm.patch_v[p]; v < hm.patch_v[p + 1]; v++) vpatch[v] = p;
+    std::vector<int> halo, nb;
+    for (int p = 0; p < np; p++) {
+        const int vlo = hm.patch_v[p], vhi = hm.patch_v[p + 1], nown = vhi - vlo;
+        halo.clear();
+        for (int s = hm.patch_slot[p]; s < hm.patch_slot[p + 1]; s++) {
+            const int4 c = hm.slot_v[s];
+            const int cv[3] = {c.x, c.y, c.z};
+            for (int k = 0; k < 3; k++)
+                if (cv[k] < vlo || cv[k] >= vhi) halo.push_back(cv[k]);
+        }
+        std::sort(halo.begin(), halo.end());
+        halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+        const int nloc = nown + (int)halo.size();
+        if (nloc > 65535) {
+            err = "a patch has more than 65535 local vertices; the persistent kernel needs smaller patches";
+            return SESW_EINVAL;
+        }
+        for (int s = hm.patch_slot[p]; s < hm.patch_slot[p + 1]; s++) {
+            const int4 c = hm.slot_v[s];
+            const int cv[3] = {c.x, c.y, c.z};
+            unsigned short l[3];
+            for (int k = 0; k < 3; k++) {
+                if (cv[k] >= vlo && cv[k] < vhi)
+                    l[k] = (unsigned short)(cv[k] - vlo);
+                else
+                    l[k] = (unsigned short)(nown + (std::lower_bound(halo.begin(), halo.end(), cv[k]) - halo.begin()));
+            }
+            hm.slot_l[s] = make_ushort4(l[0], l[1], l[2], 0);
+        }
+        nb.clear();
+        for (int v : halo) nb.push_back(vpatch[v]);
+        std::sort(nb.begin(), nb.end());
+        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
+        hm.halo_v.insert(hm.halo_v.end(), halo.begin(), halo.end());
+        hm.nbr.insert(hm.nbr.end(), nb.begin(), nb.end());
+        hm.patch_halo[p + 1] = (int)hm.halo_v.size();
+        hm.patch_nbr[p + 1] = (int)hm.nbr.size();
+        hm.max_patch_local = std::max(hm.max_patch_local, nloc);
+        hm.max_nbr = std::max(hm.max_nbr, (int)nb.size());
+        hm.max_patch_halo = std::max(hm.max_patch_halo, (int)halo.size());
+        hm.max_patch_csr = std::max(hm.max_patch_csr, hm.vcsr_off[vhi] - hm.vcsr_off[vlo]);
+    }
     return SESW_OK;
 }
 

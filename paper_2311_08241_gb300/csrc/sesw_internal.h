@@ -33,6 +33,7 @@ struct HostMesh {
     std::vector<int> patch_v;      // [npatch+1] vertex ranges
     std::vector<int> patch_slot;   // [npatch+1] slot ranges
     std::vector<int> patch_own;    // [npatch] number of owned slots
+    std::vector<int> patch_int;    // [npatch] number of interior slots (the first ones)
     std::vector<int4> slot_v;      // corners (new vertex ids); .w = element id, or -1-element for guests
     std::vector<float4> slot_g;    // (dphi0/dx, dphi0/dy, dphi1/dx, dphi1/dy); dphi2 = -dphi0 - dphi1
     std::vector<float4> slot_c;    // (A_e, H0_e, f_e, 0)
@@ -43,7 +44,24 @@ struct HostMesh {
     std::vector<double> area_e;    // element area (FP64), new element order
     std::vector<double> h0_e;      // element rest depth (FP64), new element order
     double grad_gram_max_h = 0.0;  // upper bound of lambda_max(-div H0 grad) (m/s^2 units without g)
+
+    // Halo structure for the persistent kernel (filled by build_halos). A patch keeps
+    // its own vertices at local indices [0, n_own) and its halo vertices (corners of
+    // its slots owned by other patches) at [n_own, n_own + n_halo).
+    std::vector<int> patch_halo;   // [npatch+1] ranges into halo_v
+    std::vector<int> halo_v;       // halo vertex ids (new order), sorted per patch
+    std::vector<int> patch_nbr;    // [npatch+1] ranges into nbr
+    std::vector<int> nbr;          // neighbour patches (own a halo vertex; the relation is symmetric)
+    std::vector<ushort4> slot_l;   // local corner indices of each slot (.w unused)
+    int max_patch_local = 0;       // max n_own + n_halo
+    int max_nbr = 0;
+    int max_patch_halo = 0;        // max n_halo
+    int max_patch_csr = 0;         // max incidence entries of one patch's own vertices
 };
+
+// Fill the halo structure of a prepared mesh. Returns SESW_OK or SESW_EINVAL when a
+// patch needs local indices beyond 16 bits.
+int build_halos(HostMesh &hm, std::string &err);
 
 // Validate and prepare; returns SESW_OK or SESW_EINVAL with a message in err.
 int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::string &err);
@@ -61,6 +79,7 @@ struct DevMesh {
     int *patch_v = nullptr;
     int *patch_slot = nullptr;
     int *patch_own = nullptr;
+    int *patch_int = nullptr;
     int *vcsr_off = nullptr;
     uint32_t *vcsr = nullptr;
     float *inv_av = nullptr;
@@ -68,6 +87,13 @@ struct DevMesh {
     int *vperm = nullptr;
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
+    // persistent kernel
+    int *patch_halo = nullptr;
+    int *halo_v = nullptr;
+    int *patch_nbr = nullptr;
+    int *nbr = nullptr;
+    ushort4 *slot_l = nullptr;
+    int max_patch_local = 0, max_nbr = 0, max_patch_vertices = 0, max_patch_halo = 0, max_patch_csr = 0;
 };
 
 struct DevState {
@@ -82,11 +108,18 @@ struct DevState {
     double *diag_out = nullptr;           // [2] volume, energy
     double *stage = nullptr;              // FP64 staging for host/device transfers
     size_t stage_elems = 0;
+    // persistent kernel
+    float *xbuf[2] = {nullptr, nullptr};  // boundary elevation exchanged between patches, per substep parity
+    unsigned *flags = nullptr;            // substeps completed by each patch in the running step, one
+                                          // 128-byte line per patch, then the abort word
+    unsigned *abort_flag = nullptr;       // set by a block whose bounded wait gave up
 };
 
 struct StepArgs {
     float g, theta, dt, half_dt, inv_M, eta_bound;
     int nonlinear_h;
+    int silent_patch;          // persistent kernel: this patch never publishes progress (-1: none; test hook)
+    long long wait_cycles;     // persistent kernel: budget of one bounded wait, in SM clock cycles
     double g64;
 };
 
@@ -106,5 +139,19 @@ cudaError_t launch_gather_state(const DevMesh &m, const DevState &s, int parity,
 cudaError_t launch_diagnostics(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
                                int nblocks, cudaStream_t stream);
 int diagnostics_blocks(const DevMesh &m);
+
+// Persistent kernel: one launch per baroclinic step (see sesw_kernels.cu).
+struct PersistentPlan {
+    int slots_per_thread = 0;   // 0: not possible for this mesh
+    int threads = 0;
+    int cached = 0;             // 1: the patch's static data lives in shared memory
+    int blocks_per_sm = 1;
+    size_t smem = 0;
+};
+PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm);
+cudaError_t persistent_prepare(const PersistentPlan &plan);
+size_t persistent_flag_bytes(int npatch);
+cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                              const PersistentPlan &plan, cudaStream_t stream);
 
 }  // namespace sesw

@@ -26,12 +26,17 @@ SESW_ENOMEM = -6
 SESW_HOST = 0
 SESW_DEVICE = 1
 SESW_FLAG_NO_STABILITY_CHECK = 1
+SESW_FLAG_TEST_FORCE_TIMEOUT = 2
+SESW_MODE_AUTO = 0
+SESW_MODE_GRAPH = 1
+SESW_MODE_PERSISTENT = 2
 
 _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", -4: "SESW_ETIMEOUT",
           -5: "SESW_EUNSTABLE", -6: "SESW_ENOMEM"}
 
 # every symbol include/sesw.h declares
-EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_patch_vertices", "sesw_set_block_threads",
+EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_blocks_per_sm", "sesw_set_patch_vertices",
+           "sesw_set_block_threads",
            "sesw_mesh_upload",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
            "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_status", "sesw_mesh_check",
@@ -62,7 +67,8 @@ class sesw_info(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("ne", ctypes.c_int32), ("npatch", ctypes.c_int32),
                 ("nslot", ctypes.c_int32), ("max_patch_slots", ctypes.c_int32),
                 ("patch_vertices", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("courant_max", ctypes.c_double),
+                ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("slots_per_thread", ctypes.c_int32),
+                ("cached", ctypes.c_int32), ("reserved", ctypes.c_int32), ("courant_max", ctypes.c_double),
                 ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 
@@ -93,6 +99,8 @@ def load(build_if_missing: bool = True):
         L.sesw_set_stream.argtypes = [P, P]
         L.sesw_set_patch_vertices.argtypes = [P, ctypes.c_int32]
         L.sesw_set_block_threads.argtypes = [P, ctypes.c_int32]
+        L.sesw_set_mode.argtypes = [P, ctypes.c_int32]
+        L.sesw_set_blocks_per_sm.argtypes = [P, ctypes.c_int32]
         L.sesw_mesh_upload.argtypes = [P, ctypes.POINTER(sesw_mesh)]
         L.sesw_set_params.argtypes = [P, ctypes.POINTER(sesw_params)]
         L.sesw_set_state.argtypes = [P, P, P, I]
@@ -206,6 +214,12 @@ class Subcycle:
     def sesw_set_patch_vertices(self, n: int):
         return self._check(self._L.sesw_set_patch_vertices(self._h, int(n)))
 
+    def sesw_set_mode(self, mode: int):
+        return self._check(self._L.sesw_set_mode(self._h, int(mode)))
+
+    def sesw_set_blocks_per_sm(self, k: int):
+        return self._check(self._L.sesw_set_blocks_per_sm(self._h, int(k)))
+
     def sesw_set_block_threads(self, n: int):
         return self._check(self._L.sesw_set_block_threads(self._h, int(n)))
 
@@ -303,9 +317,11 @@ def _as_f64(x):
     return x
 
 
-def run_case(case, nsteps=None, device=0, patch_vertices=None):
+def run_case(case, nsteps=None, device=0, patch_vertices=None, mode=None):
     """Upload a case, advance it and return (eta, U, Umean) as numpy arrays."""
     with Subcycle(device) as s:
+        if mode is not None:
+            s.sesw_set_mode(mode)
         if patch_vertices:
             s.sesw_set_patch_vertices(patch_vertices)
         s.sesw_mesh_upload(case.mesh)

@@ -27,6 +27,8 @@ pytestmark = pytest.mark.gpu
 ETA_ABS_TOL = 1e-5
 ENVELOPE_FACTOR = 2.0
 ULP_FLOOR = 8 * 2.0 ** -24
+GRAPH, PERSISTENT = 1, 2          # SESW_MODE_GRAPH, SESW_MODE_PERSISTENT
+MODES = pytest.mark.parametrize("mode", [GRAPH, PERSISTENT], ids=["graph", "persistent"])
 
 
 @pytest.fixture(scope="module")
@@ -63,18 +65,21 @@ def _assert_close(case, got, what, nsteps=None):
     return ref
 
 
-def test_basin_matches_oracle(sesw):
+@MODES
+def test_basin_matches_oracle(sesw, mode):
     """Closed 1000x500 km basin, Gaussian bump, f-plane, 20 steps of 30 substeps."""
     case = I.basin_case()
-    got = sesw.run_case(case)
-    _assert_close(case, got, "basin")
+    got = sesw.run_case(case, mode=mode)
+    _assert_close(case, got, f"basin mode={mode}")
 
 
-def test_channel_matches_oracle_100_steps(sesw):
-    """Wind-driven channel (200k vertices) in the benchmark's launch configuration, 100 steps."""
+@MODES
+def test_channel_matches_oracle_100_steps(sesw, mode):
+    """Wind-driven channel (200k vertices), 100 steps; the persistent mode is the benchmark's launch
+    configuration."""
     case = I.channel_case(nsteps=100)
-    got = sesw.run_case(case)
-    _assert_close(case, got, "channel-100")
+    got = sesw.run_case(case, mode=mode)
+    _assert_close(case, got, f"channel-100 mode={mode}")
 
 
 @pytest.mark.parametrize("pv", [32, 100, 777])
@@ -83,29 +88,53 @@ def test_tiny_meshes_many_patches(sesw, pv, seed):
     """Small jittered basins cut into many ragged patches (guest copies on every border)."""
     case = I.tiny_jittered_case(nx=23, ny=17, seed=seed, M=9, tau=90.0)
     case.nsteps = 4
-    got = sesw.run_case(case, patch_vertices=pv)
+    got = sesw.run_case(case, patch_vertices=pv, mode=GRAPH)
     _assert_close(case, got, f"tiny pv={pv} seed={seed}")
 
 
-def test_linear_h_and_odd_M(sesw):
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_tiny_meshes_persistent(sesw, seed):
+    """Small meshes in the persistent kernel: few patches, ragged slot counts per block."""
+    case = I.tiny_jittered_case(nx=23 + seed, ny=17, seed=seed, M=9, tau=90.0)
+    case.nsteps = 4
+    got = sesw.run_case(case, mode=PERSISTENT)
+    _assert_close(case, got, f"tiny persistent seed={seed}")
+
+
+@MODES
+def test_linear_h_and_odd_M(sesw, mode):
     case = I.tiny_jittered_case(nx=30, ny=20, seed=7, M=7, tau=70.0, nonlinear_h=0)
     case.nsteps = 5
-    got = sesw.run_case(case, patch_vertices=64)
-    _assert_close(case, got, "linear-H odd M")
+    got = sesw.run_case(case, patch_vertices=64, mode=mode)
+    _assert_close(case, got, f"linear-H odd M mode={mode}")
 
 
-def test_sphere_matches_oracle(sesw):
+@MODES
+def test_sphere_matches_oracle(sesw, mode):
     """Icosahedral sphere (level 6 here; level 8 in the next test) with land, forcing and f = 2 Omega sin(lat)."""
     case = I.sphere_case(level=6, nsteps=10)
-    got = sesw.run_case(case)
-    _assert_close(case, got, "sphere-l6")
+    got = sesw.run_case(case, mode=mode)
+    _assert_close(case, got, f"sphere-l6 mode={mode}")
 
 
-def test_sphere_level8_full_size(sesw):
+@MODES
+def test_sphere_level8_full_size(sesw, mode):
     """Global-like sphere at full size (level 8: ~460k wet vertices), 5 steps of 50 substeps."""
     case = I.sphere_case(level=8, nsteps=5)
-    got = sesw.run_case(case)
-    _assert_close(case, got, "sphere-l8")
+    got = sesw.run_case(case, mode=mode)
+    _assert_close(case, got, f"sphere-l8 mode={mode}")
+
+
+def test_modes_agree(sesw):
+    """Graph and persistent execution differ only in the order of FP32 sums at each vertex."""
+    case = I.channel_case(nsteps=10)
+    a = sesw.run_case(case, mode=GRAPH)
+    b = sesw.run_case(case, mode=PERSISTENT)
+    r32 = orc.run_case(case, L=orc.lib_fp32())
+    ref = orc.run_case(case)
+    for k in range(3):
+        env = _maxabs(r32[k] - ref[k]) + ULP_FLOOR * _maxabs(ref[k])
+        assert _maxabs(a[k] - b[k]) <= 2 * ENVELOPE_FACTOR * env
 
 
 def test_periodic_wave_closed_form(sesw):
@@ -162,11 +191,13 @@ def test_diagnostics_match_oracle(sesw):
     assert abs(en - e_ref) <= 1e-5 * abs(e_ref)
 
 
-def test_resume_is_bitwise(sesw):
+@MODES
+def test_resume_is_bitwise(sesw, mode):
     """Checkpoint/resume: 3 steps, read back, restart in a new context, 2 steps == 5 straight steps."""
     case = I.tiny_jittered_case(nx=25, ny=18, seed=9, M=8, tau=80.0)
-    straight = sesw.run_case(case, nsteps=5)
+    straight = sesw.run_case(case, nsteps=5, mode=mode)
     with sesw.Subcycle() as s:
+        s.sesw_set_mode(mode)
         s.sesw_mesh_upload(case.mesh)
         s.sesw_set_params(case.params)
         s.sesw_set_forcing(case.R)
@@ -174,6 +205,7 @@ def test_resume_is_bitwise(sesw):
         s.sesw_advance(3)
         eta, U, _ = s.sesw_get_state()
     with sesw.Subcycle() as s:
+        s.sesw_set_mode(mode)
         s.sesw_mesh_upload(case.mesh)
         s.sesw_set_params(case.params)
         s.sesw_set_forcing(case.R)
@@ -184,10 +216,11 @@ def test_resume_is_bitwise(sesw):
         assert np.array_equal(a, b)
 
 
-def test_deterministic(sesw):
+@MODES
+def test_deterministic(sesw, mode):
     case = I.channel_case(nsteps=3)
-    a = sesw.run_case(case)
-    b = sesw.run_case(case)
+    a = sesw.run_case(case, mode=mode)
+    b = sesw.run_case(case, mode=mode)
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
 
@@ -239,3 +272,30 @@ def test_errors_are_reported(sesw):
         s.sesw_advance(1)
         assert s.sesw_status() == sesw.SESW_EUNSTABLE
         assert s.sesw_status() == sesw.SESW_OK        # cleared
+
+
+def test_persistent_wait_gives_up_and_context_stays_usable(sesw):
+    """Failure detection without a GPU fault: a patch that never publishes its progress makes
+    its neighbours' bounded waits give up (~10 ms budget under the test flag); the step ends,
+    the host reads SESW_ETIMEOUT, and the context then runs normal steps again."""
+    import time
+
+    case = I.basin_case(nsteps=1)
+    with sesw.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload(case.mesh)
+        assert s.sesw_get_info()["mode"] == PERSISTENT
+        s.sesw_set_params(case.params, flags=sesw.SESW_FLAG_TEST_FORCE_TIMEOUT)
+        s.sesw_set_state(case.eta0, case.U0)
+        t0 = time.perf_counter()
+        s.sesw_advance(1)
+        assert s.sesw_status() == sesw.SESW_ETIMEOUT
+        assert time.perf_counter() - t0 < 30.0
+        assert s.sesw_status() == sesw.SESW_OK
+        s.sesw_set_params(case.params)
+        s.sesw_set_state(case.eta0, case.U0)
+        s.sesw_advance(1)
+        assert s.sesw_status() == sesw.SESW_OK
+        got = s.sesw_get_state()
+    ref = orc.run_case(case)
+    assert _maxabs(got[0] - ref[0]) < 1e-5
