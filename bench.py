@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-substeps", type=int, default=4,
                     help="substeps of the channel per reference-arm step (a bounded sample)")
+    ap.add_argument("--workload", choices=["channel", "ensemble"], default="channel",
+                    help="channel: the headline workload; ensemble: 64 basins of uneven size, batched")
+    ap.add_argument("--ensemble-basins", type=int, default=64)
+    ap.add_argument("--ensemble-scale", type=float, default=1.0)
+    ap.add_argument("--sequential-steps", type=int, default=10)
     return ap.parse_args()
 
 
@@ -94,8 +99,12 @@ def kernel_source_hash():
 
 
 def profiled_traffic(kernel):
+    return profiled_traffic_for(kernel, "channel")
+
+
+def profiled_traffic_for(kernel, workload):
     """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
-    p = os.path.join(ROOT, "profiles", f"{kernel}_channel.md")
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     try:
         txt = open(p).read()
     except OSError:
@@ -215,6 +224,119 @@ def barrier(world):
         import torch.distributed as dist
 
         dist.barrier()
+
+
+def run_ensemble(args, world, rank, local):
+    """Batched ensemble: every basin in one upload and one advance per step (layout picked by the
+    autotuner), against advancing each basin in its own context one after another."""
+    import torch
+
+    from paper_2311_08241_gb300 import autotune as AT
+    from paper_2311_08241_gb300 import inputs as I
+    from paper_2311_08241_gb300 import sesw as S
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    cases = I.ensemble_cases(nbasins=args.ensemble_basins, scale=args.ensemble_scale, seed=20231118 + rank)
+    meshes = [c.mesh for c in cases]
+    params = [c.params for c in cases]
+    M = params[0].M
+    V = sum(m.nv for m in meshes)
+    E = sum(m.ne for m in meshes)
+    R = np.concatenate([c.R for c in cases])
+    eta0 = np.concatenate([c.eta0 for c in cases])
+    U0 = np.concatenate([c.U0 for c in cases])
+    best, table = AT.autotune(meshes, params, forcing=R, steps=3, warmup=1, device=local,
+                              graph_patches=(256, 1024), graph_threads=(256, 512))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(advance, nsteps):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            advance()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return [a.elapsed_time(b) for a, b in ev]
+
+    sim = S.Subcycle(local, stream=stream)
+    best.apply(sim)
+    sim.sesw_mesh_upload_batch(meshes)
+    sim.sesw_set_params_batch(params)
+    sim.sesw_set_forcing(R)
+    sim.sesw_set_state(eta0, U0)
+    info = sim.sesw_get_info()
+    for _ in range(args.warmup):
+        sim.sesw_advance(1)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    step_ms = timed(lambda: sim.sesw_advance(1), args.steps)
+    barrier(world)
+    clk = clocks.stop()
+    if sim.sesw_status() != S.SESW_OK:
+        raise RuntimeError("batched run flagged a device status")
+    total_ms = reduce_max(sum(step_ms), world, dev)
+    value = whole_job_value(V, M, args.steps, world, total_ms)
+
+    # the same basins advanced one context after another (each as the library runs a single mesh)
+    singles = []
+    for c in cases:
+        s1 = S.Subcycle(local, stream=stream)
+        s1.sesw_mesh_upload(c.mesh)
+        s1.sesw_set_params(c.params)
+        s1.sesw_set_forcing(c.R)
+        s1.sesw_set_state(c.eta0, c.U0)
+        singles.append(s1)
+    for s1 in singles:
+        s1.sesw_advance(1)
+    nseq = max(1, min(args.sequential_steps, args.steps))
+    seq_ms = timed(lambda: [s1.sesw_advance(1) for s1 in singles], nseq)
+    speedup = statistics.mean(seq_ms) / statistics.mean(step_ms)
+
+    # SSH agreement of the two forms after the same steps from the same start
+    nchk = 5
+    sim.sesw_set_state(eta0, U0)
+    sim.sesw_advance(nchk)
+    eta_b = sim.sesw_get_state()[0]
+    eta_s = []
+    for c, s1 in zip(cases, singles):
+        s1.sesw_set_state(c.eta0, c.U0)
+        s1.sesw_advance(nchk)
+        eta_s.append(s1.sesw_get_state()[0])
+        s1.close()
+    ssh_diff = float(np.max(np.abs(eta_b - np.concatenate(eta_s))))
+
+    persistent = info["mode"] == S.SESW_MODE_PERSISTENT
+    b_alg = algorithmic_bytes_per_substep(V, E)
+    mean_step_s = statistics.mean(step_ms) * 1e-3
+    per_launch = b_alg * M if persistent else b_alg
+    launch_s = mean_step_s if persistent else mean_step_s / M
+    achieved = per_launch / launch_s / 1e9
+    peak, peak_src = measured_hbm_peak()
+    kname = "k_persistent" if persistent else "k_substep"
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batched ensemble of {len(cases)} closed basins (jittered Delaunay, "
+                                   f"log-uniform 2e4-4e5 vertices x {args.ensemble_scale:g}), M={M}, per-basin dt",
+                       "V": V, "E": E, "M": M, "nbasin": len(cases), "layout": best.label(),
+                       "npatch": info["npatch"], "nslot": info["nslot"],
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "autotune_ms_per_step": {c.label(): t for c, t in table}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic_for(kname, "ensemble"),
+                         "peak_source": peak_src, "kernel": kname, "bytes_per_launch": per_launch},
+            "batched_vs_sequential": {"speedup": speedup, "sequential_ms_per_step": statistics.mean(seq_ms),
+                                      "batched_ms_per_step": statistics.mean(step_ms),
+                                      "max_ssh_difference_m": ssh_diff, "after_steps": nchk},
+            "gpu_launches": args.steps * (1 if persistent else M + 1), "clocks": clk}
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_reference(args, world, rank):
@@ -361,6 +483,8 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, world, rank)
+        elif args.workload == "ensemble":
+            run_ensemble(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

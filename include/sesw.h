@@ -127,7 +127,7 @@ typedef struct sesw_info {
     int32_t blocks_per_sm;   /* persistent mode: resident blocks per SM */
     int32_t slots_per_thread;/* persistent mode: element slots held in registers per thread */
     int32_t cached;          /* persistent mode: 1 when static slot data lives in shared memory */
-    int32_t reserved;
+    int32_t nbasin;          /* meshes in the uploaded batch (1 for sesw_mesh_upload) */
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
                                 (0 until parameters are set) */
     double courant_limit;    /* 2/sqrt(1+2 theta), the stability limit of the scheme */
@@ -180,6 +180,21 @@ int sesw_set_block_threads(sesw_ctx *ctx, int32_t threads);
  * SESW_ECUDA. */
 int sesw_mesh_upload(sesw_ctx *ctx, const sesw_mesh *mesh);
 
+/* Upload a batch of independent meshes ("basins", e.g. ensemble members of uneven
+ * size) that advance together in every sesw_advance. Each mesh is validated and
+ * prepared exactly as sesw_mesh_upload would prepare it alone (its own space-filling
+ * curve order and patches; the persistent mode picks one patch size for all), and the
+ * layouts are concatenated, so with SESW_MODE_GRAPH a basin's results are bitwise
+ * those of its own upload with the same patch size. Caller order of every state,
+ * forcing and output array is the concatenation of the meshes in order. Errors name
+ * the first bad basin. */
+int sesw_mesh_upload_batch(sesw_ctx *ctx, int32_t nmesh, const sesw_mesh *meshes);
+
+/* Parameters of a batch, one set per mesh (n = number of uploaded meshes). All sets
+ * must agree in g, theta, M, nonlinear_h, scheme, flags and eta_bound; tau (hence the
+ * substep dt = tau/M) may differ per mesh. Each mesh gets its own stability check. */
+int sesw_set_params_batch(sesw_ctx *ctx, int32_t n, const sesw_params *params);
+
 /* Set scheme parameters; requires an uploaded mesh. Rejects (SESW_EINVAL)
  * parameters whose substep Courant number bound exceeds 2/sqrt(1+2 theta), the
  * value beyond which the scheme's characteristic polynomial (Eq. dp_1, SE row) has a
@@ -212,6 +227,10 @@ int sesw_get_state(sesw_ctx *ctx, double *eta, double *U, double *Umean, int whe
 /* FP64 diagnostics of the current state: volume sum_v A_v eta_v (m^3) and energy
  * sum_v A_v g eta_v^2/2 + sum_e A_e |U_e|^2 / (2 H_e) (m^5/s^2). Synchronises. */
 int sesw_diagnostics(sesw_ctx *ctx, double *volume, double *energy);
+
+/* Per-mesh FP64 diagnostics of a batch: volume[b] and energy[b] for every uploaded
+ * mesh b (arrays of nbasin host doubles). Synchronises. */
+int sesw_diagnostics_batch(sesw_ctx *ctx, double *volume, double *energy);
 
 /* Allocation-free volume and energy of a caller-held state. The paper has no
  * counterpart: this serves callers that cannot allocate device memory where they need

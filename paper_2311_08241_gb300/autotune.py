@@ -1,0 +1,125 @@
+"""Pick the execution layout of a mesh (or batch) by timing it on the GPU.
+
+Candidates are the persistent kernel with 1, 2 or 4 resident blocks per SM and
+the per-substep graph with several patch sizes and block sizes. Each candidate is
+uploaded through the C-ABI and timed with CUDA events on a few baroclinic steps
+of the actual workload. A layout the mesh does not fit is skipped. The result
+is the fastest candidate, plus the whole table so callers can report it.
+"""
+from __future__ import annotations
+
+import dataclasses
+import statistics
+
+import numpy as np
+
+from . import sesw as S
+
+PERSISTENT_BLOCKS = (1, 2, 4)
+GRAPH_PATCHES = (128, 256, 512, 1024)
+GRAPH_THREADS = (128, 256, 512)
+
+
+@dataclasses.dataclass
+class Choice:
+    mode: int
+    blocks_per_sm: int = 0
+    patch_vertices: int = 256
+    block_threads: int = 256
+    ms_per_step: float = float("inf")
+
+    def apply(self, sim):
+        sim.sesw_set_mode(self.mode)
+        sim.sesw_set_blocks_per_sm(self.blocks_per_sm)
+        sim.sesw_set_patch_vertices(self.patch_vertices)
+        sim.sesw_set_block_threads(self.block_threads)
+
+    def label(self):
+        if self.mode == S.SESW_MODE_PERSISTENT:
+            return f"persistent bps={self.blocks_per_sm}"
+        return f"graph pv={self.patch_vertices} bt={self.block_threads}"
+
+
+def _time_steps(sim, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        sim.sesw_advance(1)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        a.record(stream)
+        sim.sesw_advance(1)
+        b.record(stream)
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in ev)
+
+
+def autotune(meshes, params, forcing=None, steps=5, warmup=2, device=0, include_graph=True, include_persistent=True,
+             graph_patches=GRAPH_PATCHES, graph_threads=GRAPH_THREADS, verbose=False):
+    """Time every candidate layout on the meshes (a list: one mesh, or the basins of a batch).
+
+    params: one Params per mesh. forcing: optional concatenated [sum E][2] array.
+    Returns (best Choice, list of (Choice, ms_per_step or None)).
+    """
+    import torch
+
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream(device)
+    nv = sum(m.nv for m in meshes)
+    ne = sum(m.ne for m in meshes)
+    eta0 = np.zeros(nv)
+    U0 = np.zeros((ne, 2))
+    table = []
+
+    def run(choice):
+        with S.Subcycle(device, stream=stream) as sim:
+            choice.apply(sim)
+            if len(meshes) == 1:
+                sim.sesw_mesh_upload(meshes[0])
+                sim.sesw_set_params(params[0])
+            else:
+                sim.sesw_mesh_upload_batch(meshes)
+                sim.sesw_set_params_batch(params)
+            info = sim.sesw_get_info()
+            if choice.mode == S.SESW_MODE_PERSISTENT and info["mode"] != S.SESW_MODE_PERSISTENT:
+                return None
+            if forcing is not None:
+                sim.sesw_set_forcing(forcing)
+            sim.sesw_set_state(eta0, U0)
+            if choice.mode == S.SESW_MODE_GRAPH:
+                # one upload serves every block size of this patch size
+                out = []
+                for bt in graph_threads:
+                    sim.sesw_set_block_threads(bt)
+                    out.append((bt, _time_steps(sim, steps, warmup, stream)))
+                return out
+            return _time_steps(sim, steps, warmup, stream)
+
+    if include_persistent:
+        for k in PERSISTENT_BLOCKS:
+            c = Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=k)
+            try:
+                t = run(c)
+            except S.SeswError:
+                t = None
+            c.ms_per_step = t if t is not None else float("inf")
+            table.append((c, t))
+            if verbose:
+                print(c.label(), t)
+    if include_graph:
+        for pv in graph_patches:
+            try:
+                res = run(Choice(S.SESW_MODE_GRAPH, patch_vertices=pv))
+            except S.SeswError:
+                res = None
+            for bt in graph_threads:
+                t = dict(res).get(bt) if res else None
+                c = Choice(S.SESW_MODE_GRAPH, patch_vertices=pv, block_threads=bt,
+                           ms_per_step=t if t is not None else float("inf"))
+                table.append((c, t))
+                if verbose:
+                    print(c.label(), t)
+    best = min((c for c, t in table if t is not None), key=lambda c: c.ms_per_step, default=None)
+    if best is None:
+        raise RuntimeError("no candidate layout ran on this mesh")
+    return best, table

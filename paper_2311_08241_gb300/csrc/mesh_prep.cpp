@@ -363,7 +363,79 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     double gersh = 0.0;
     for (int v = 0; v < nv; v++) gersh = std::max(gersh, (kdiag[v] + koff[v]) / Av[v]);
     out.grad_gram_max_h = std::min(3.0 * gmax, gersh);
+    out.nbasin = 1;
+    out.patch_basin.assign(npatch, 0);
+    out.basin_v = {0, nv};
+    out.basin_e = {0, ne};
+    out.basin_patch = {0, npatch};
+    out.basin_stiffness = {out.grad_gram_max_h};
     return SESW_OK;
+}
+
+void concat_meshes(std::vector<HostMesh> &parts, HostMesh &out)
+{
+    out = HostMesh();
+    int nv = 0, ne = 0, np = 0, ns = 0, ncsr = 0;
+    for (auto &h : parts) {
+        nv += h.nv;
+        ne += h.ne;
+        np += h.npatch;
+        ns += h.nslot;
+        ncsr += (int)h.vcsr.size();
+    }
+    out.nv = nv;
+    out.ne = ne;
+    out.npatch = np;
+    out.nslot = ns;
+    out.nbasin = (int)parts.size();
+    out.vperm.reserve(nv);
+    out.eperm.reserve(ne);
+    out.patch_v.assign(1, 0);
+    out.patch_slot.assign(1, 0);
+    out.vcsr_off.assign(1, 0);
+    out.basin_v.assign(1, 0);
+    out.basin_e.assign(1, 0);
+    out.basin_patch.assign(1, 0);
+    out.slot_v.reserve(ns);
+    out.slot_g.reserve(ns);
+    out.slot_c.reserve(ns);
+    out.vcsr.reserve(ncsr);
+    int vo = 0, eo = 0, po = 0, so = 0, co = 0;
+    for (size_t b = 0; b < parts.size(); b++) {
+        HostMesh &h = parts[b];
+        for (int v : h.vperm) out.vperm.push_back(v + vo);
+        for (int e : h.eperm) out.eperm.push_back(e + eo);
+        for (int p = 1; p <= h.npatch; p++) {
+            out.patch_v.push_back(h.patch_v[p] + vo);
+            out.patch_slot.push_back(h.patch_slot[p] + so);
+        }
+        out.patch_own.insert(out.patch_own.end(), h.patch_own.begin(), h.patch_own.end());
+        out.patch_int.insert(out.patch_int.end(), h.patch_int.begin(), h.patch_int.end());
+        for (int p = 0; p < h.npatch; p++) out.patch_basin.push_back((int)b);
+        for (const int4 &c : h.slot_v)
+            out.slot_v.push_back(make_int4(c.x + vo, c.y + vo, c.z + vo, c.w >= 0 ? c.w + eo : c.w - eo));
+        out.slot_g.insert(out.slot_g.end(), h.slot_g.begin(), h.slot_g.end());
+        out.slot_c.insert(out.slot_c.end(), h.slot_c.begin(), h.slot_c.end());
+        for (int v = 1; v <= h.nv; v++) out.vcsr_off.push_back(h.vcsr_off[v] + co);
+        out.vcsr.insert(out.vcsr.end(), h.vcsr.begin(), h.vcsr.end());
+        out.inv_av.insert(out.inv_av.end(), h.inv_av.begin(), h.inv_av.end());
+        out.area_v.insert(out.area_v.end(), h.area_v.begin(), h.area_v.end());
+        out.area_e.insert(out.area_e.end(), h.area_e.begin(), h.area_e.end());
+        out.h0_e.insert(out.h0_e.end(), h.h0_e.begin(), h.h0_e.end());
+        out.max_patch_slots = std::max(out.max_patch_slots, h.max_patch_slots);
+        out.max_patch_vertices = std::max(out.max_patch_vertices, h.max_patch_vertices);
+        out.patch_vertices = std::max(out.patch_vertices, h.patch_vertices);
+        out.grad_gram_max_h = std::max(out.grad_gram_max_h, h.grad_gram_max_h);
+        out.basin_stiffness.push_back(h.grad_gram_max_h);
+        vo += h.nv;
+        eo += h.ne;
+        po += h.npatch;
+        so += h.nslot;
+        co += (int)h.vcsr.size();
+        out.basin_v.push_back(vo);
+        out.basin_e.push_back(eo);
+        out.basin_patch.push_back(po);
+    }
 }
 
 int build_halos(HostMesh &hm, std::string &err)

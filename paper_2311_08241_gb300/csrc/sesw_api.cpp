@@ -40,6 +40,10 @@ struct sesw_ctx {
     double grad_gram_max_h = 0.0;
     double courant_max = 0.0, courant_limit = 0.0;
     int npatch = 0, nslot = 0, max_patch_slots = 0, patch_vertices_used = 0;
+    int nbasin = 1;
+    std::vector<int> patch_basin;
+    std::vector<double> basin_stiffness;
+    std::vector<float> patch_dt_host;
 };
 
 namespace {
@@ -271,28 +275,63 @@ int sesw_set_mode(sesw_ctx *c, int32_t mode)
     return SESW_OK;
 }
 
-int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
+static int prepare_parts(sesw_ctx *c, const sesw_mesh *meshes, int n, int pv, sesw::HostMesh &hm, std::string &err)
+{
+    std::vector<sesw::HostMesh> parts(n);
+    for (int b = 0; b < n; b++) {
+        int rc = sesw::prepare_mesh(meshes[b], pv, parts[b], err);
+        if (rc != SESW_OK) {
+            if (n > 1) err = "basin " + std::to_string(b) + ": " + err;
+            return rc;
+        }
+    }
+    if (n == 1)
+        hm = std::move(parts[0]);
+    else
+        sesw::concat_meshes(parts, hm);
+    (void)c;
+    return SESW_OK;
+}
+
+static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
 {
     if (!c) return SESW_EINVAL;
-    if (!mesh) return fail(c, SESW_EINVAL, "mesh is NULL");
+    if (!meshes || n < 1) return fail(c, SESW_EINVAL, "need at least one mesh");
     DeviceGuard dg(c->device);
     if (!dg.ok) return fail(c, SESW_ECUDA, "cannot select the context's device");
+    long long nv_total = 0;
+    for (int b = 0; b < n; b++) {
+        if (meshes[b].nv < 1 || meshes[b].ne < 1) return fail(c, SESW_EINVAL, "every mesh needs nv >= 1 and ne >= 1");
+        nv_total += meshes[b].nv;
+    }
+    if (nv_total >= (1ll << 30)) return fail(c, SESW_EINVAL, "meshes too large for 32-bit indexing");
     sesw::HostMesh hm;
     std::string err;
     int rc;
     int mode = SESW_MODE_GRAPH;
     sesw::PersistentPlan plan;
     try {
-        if (c->mode_req != SESW_MODE_GRAPH && mesh->nv > 0) {
+        if (c->mode_req != SESW_MODE_GRAPH) {
             // persistent: blocks_per_sm patches per SM, all resident
             int nsm = 0;
             CK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
             const int tries[2] = {c->blocks_per_sm > 0 ? c->blocks_per_sm : 2, c->blocks_per_sm > 0 ? 0 : 1};
             for (int bps : tries) {
                 if (bps <= 0 || plan.slots_per_thread > 0) continue;
-                const int nblk = nsm * bps;
-                const int pv = std::max(32, (int)(((long long)mesh->nv + nblk - 1) / nblk));
-                rc = sesw::prepare_mesh(*mesh, pv, hm, err);
+                const long long nblk = (long long)nsm * bps;
+                if (n > nblk) continue;
+                // smallest patch size (>= 32) whose patch count over all meshes fits the grid
+                auto count = [&](long long pv) {
+                    long long t = 0;
+                    for (int b = 0; b < n; b++) t += (meshes[b].nv + pv - 1) / pv;
+                    return t;
+                };
+                long long lo = std::max<long long>(32, (nv_total + nblk - 1) / nblk), hi = std::max<long long>(lo, nv_total);
+                while (lo < hi) {
+                    const long long mid = (lo + hi) / 2;
+                    if (count(mid) <= nblk) hi = mid; else lo = mid + 1;
+                }
+                rc = prepare_parts(c, meshes, n, (int)lo, hm, err);
                 if (rc != SESW_OK) return fail(c, rc, err);
                 rc = sesw::build_halos(hm, err);
                 if (rc == SESW_OK && hm.npatch <= nblk) {
@@ -314,7 +353,7 @@ int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
             }
         }
         if (mode == SESW_MODE_GRAPH) {
-            rc = sesw::prepare_mesh(*mesh, c->patch_vertices, hm, err);
+            rc = prepare_parts(c, meshes, n, c->patch_vertices, hm, err);
             if (rc != SESW_OK) return fail(c, rc, err);
         }
     } catch (const std::bad_alloc &) {
@@ -351,6 +390,14 @@ int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
     TRY(upload(c, &d.area_v, hm.area_v, "area_v"));
     TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
+    TRY(zalloc(c, &d.patch_dt, hm.npatch, "patch_dt"));
+    {
+        std::vector<int> bslot(hm.nbasin + 1);
+        for (int b = 0; b <= hm.nbasin; b++) bslot[b] = hm.patch_slot[hm.basin_patch[b]];
+        TRY(upload(c, &d.basin_v, hm.basin_v, "basin_v"));
+        TRY(upload(c, &d.basin_slot, bslot, "basin_slot"));
+        d.nbasin = hm.nbasin;
+    }
     if (mode == SESW_MODE_PERSISTENT) {
         TRY(upload(c, &d.patch_halo, hm.patch_halo, "patch_halo"));
         TRY(upload(c, &d.halo_v, hm.halo_v, "halo_v"));
@@ -393,6 +440,9 @@ int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
     c->plan = plan;
     c->persist_graph_ok = true;
     c->grad_gram_max_h = hm.grad_gram_max_h;
+    c->nbasin = hm.nbasin;
+    c->patch_basin = hm.patch_basin;
+    c->basin_stiffness = hm.basin_stiffness;
     c->npatch = hm.npatch;
     c->nslot = hm.nslot;
     c->max_patch_slots = hm.max_patch_slots;
@@ -402,28 +452,68 @@ int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
     return SESW_OK;
 }
 
+int sesw_mesh_upload(sesw_ctx *c, const sesw_mesh *mesh)
+{
+    if (!c) return SESW_EINVAL;
+    if (!mesh) return fail(c, SESW_EINVAL, "mesh is NULL");
+    return upload_batch(c, mesh, 1);
+}
+
+int sesw_mesh_upload_batch(sesw_ctx *c, int32_t nmesh, const sesw_mesh *meshes)
+{
+    if (!c) return SESW_EINVAL;
+    return upload_batch(c, meshes, nmesh);
+}
+
+static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps);
+
 int sesw_set_params(sesw_ctx *c, const sesw_params *p)
 {
     if (!c) return SESW_EINVAL;
     if (!p) return fail(c, SESW_EINVAL, "params is NULL");
     if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting parameters");
-    if (!(p->g > 0.0) || !isfinite(p->g)) return fail(c, SESW_EINVAL, "g must be positive and finite");
-    if (!(p->theta >= 0.0) || !isfinite(p->theta)) return fail(c, SESW_EINVAL, "theta must be >= 0 and finite");
-    if (!(p->tau > 0.0) || !isfinite(p->tau)) return fail(c, SESW_EINVAL, "tau must be positive and finite");
-    if (p->M < 1 || p->M > 65536) return fail(c, SESW_EINVAL, "M must be in [1, 65536]");
-    if (p->nonlinear_h != 0 && p->nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
-    if (p->scheme != 0) return fail(c, SESW_EINVAL, "scheme must be 0 (dissipative forward-backward)");
-    const double dt = p->tau / p->M;
-    // upper bound of dt sqrt(lambda_max(-div g H0 grad)), see prepare_mesh
-    const double cmax = sqrt(p->g * c->grad_gram_max_h) * dt;
-    const double limit = 2.0 / sqrt(1.0 + 2.0 * p->theta);
-    if (cmax > limit && !(p->flags & SESW_FLAG_NO_STABILITY_CHECK)) {
-        char buf[256];
-        snprintf(buf, sizeof buf,
-                 "substep Courant number bound %.4f exceeds the stability limit 2/sqrt(1+2 theta) = %.4f; "
-                 "increase M",
-                 cmax, limit);
-        return fail(c, SESW_EINVAL, buf);
+    std::vector<sesw_params> all(c->nbasin, *p);
+    return set_params_impl(c, c->nbasin, all.data());
+}
+
+int sesw_set_params_batch(sesw_ctx *c, int32_t n, const sesw_params *ps)
+{
+    if (!c) return SESW_EINVAL;
+    if (!ps) return fail(c, SESW_EINVAL, "params is NULL");
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting parameters");
+    if (n != c->nbasin) return fail(c, SESW_EINVAL, "need one parameter set per uploaded mesh");
+    return set_params_impl(c, n, ps);
+}
+
+static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
+{
+    DeviceGuard dg(c->device);
+    const sesw_params *p = &ps[0];
+    double cmax_all = 0.0, limit = 0.0;
+    for (int b = 0; b < n; b++) {
+        const sesw_params &q = ps[b];
+        if (!(q.g > 0.0) || !isfinite(q.g)) return fail(c, SESW_EINVAL, "g must be positive and finite");
+        if (!(q.theta >= 0.0) || !isfinite(q.theta)) return fail(c, SESW_EINVAL, "theta must be >= 0 and finite");
+        if (!(q.tau > 0.0) || !isfinite(q.tau)) return fail(c, SESW_EINVAL, "tau must be positive and finite");
+        if (q.M < 1 || q.M > 65536) return fail(c, SESW_EINVAL, "M must be in [1, 65536]");
+        if (q.nonlinear_h != 0 && q.nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
+        if (q.scheme != 0) return fail(c, SESW_EINVAL, "scheme must be 0 (dissipative forward-backward)");
+        if (q.g != p->g || q.theta != p->theta || q.M != p->M || q.nonlinear_h != p->nonlinear_h ||
+            q.flags != p->flags || q.eta_bound != p->eta_bound)
+            return fail(c, SESW_EINVAL, "meshes of one batch may differ only in tau");
+        const double dt = q.tau / q.M;
+        // upper bound of dt sqrt(lambda_max(-div g H0 grad)), see prepare_mesh
+        const double cmax = sqrt(q.g * c->basin_stiffness[b]) * dt;
+        limit = 2.0 / sqrt(1.0 + 2.0 * q.theta);
+        if (cmax > limit && !(q.flags & SESW_FLAG_NO_STABILITY_CHECK)) {
+            char buf[320];
+            snprintf(buf, sizeof buf,
+                     "%s%ssubstep Courant number bound %.4f exceeds the stability limit 2/sqrt(1+2 theta) = %.4f; "
+                     "increase M",
+                     n > 1 ? "basin " : "", n > 1 ? (std::to_string(b) + ": ").c_str() : "", cmax, limit);
+            return fail(c, SESW_EINVAL, buf);
+        }
+        cmax_all = std::max(cmax_all, cmax);
     }
     drop_graphs(c);
     c->params = *p;
@@ -432,8 +522,6 @@ int sesw_set_params(sesw_ctx *c, const sesw_params *p)
     a.g = (float)p->g;
     a.g64 = p->g;
     a.theta = (float)p->theta;
-    a.dt = (float)dt;
-    a.half_dt = (float)(0.5 * dt);
     a.inv_M = (float)(1.0 / p->M);
     a.eta_bound = (float)c->params.eta_bound;
     a.nonlinear_h = p->nonlinear_h;
@@ -442,7 +530,13 @@ int sesw_set_params(sesw_ctx *c, const sesw_params *p)
     const bool test_timeout = (p->flags & SESW_FLAG_TEST_FORCE_TIMEOUT) != 0;
     a.silent_patch = test_timeout ? 0 : -1;
     a.wait_cycles = test_timeout ? 20000000ll : 2000000000ll;
-    c->courant_max = cmax;
+    c->patch_dt_host.resize(c->patch_basin.size());
+    for (size_t q = 0; q < c->patch_basin.size(); q++)
+        c->patch_dt_host[q] = (float)(ps[c->patch_basin[q]].tau / ps[c->patch_basin[q]].M);
+    CK(c, cudaMemcpyAsync(c->dm.patch_dt, c->patch_dt_host.data(), sizeof(float) * c->patch_dt_host.size(),
+                          cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->courant_max = cmax_all;
     c->courant_limit = limit;
     c->have_params = true;
     return SESW_OK;
@@ -536,6 +630,24 @@ int sesw_diagnostics(sesw_ctx *c, double *volume, double *energy)
     return SESW_OK;
 }
 
+int sesw_diagnostics_batch(sesw_ctx *c, double *volume, double *energy)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh || !c->have_params) return fail(c, SESW_ESTATE, "mesh and parameters must be set before diagnostics");
+    if (!volume || !energy) return fail(c, SESW_EINVAL, "volume and energy must not be NULL");
+    DeviceGuard dg(c->device);
+    double *out = c->ds.stage;   // 2 * nbasin doubles; the staging buffer holds nv + 4 ne >= that
+    CK(c, sesw::launch_diagnostics_basins(c->dm, c->ds, c->args, c->parity, out, c->stream));
+    std::vector<double> h(2 * (size_t)c->nbasin);
+    CK(c, cudaMemcpyAsync(h.data(), out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->nbasin; b++) {
+        volume[b] = h[2 * b];
+        energy[b] = h[2 * b + 1];
+    }
+    return SESW_OK;
+}
+
 int sesw_status(sesw_ctx *c)
 {
     if (!c) return SESW_EINVAL;
@@ -604,6 +716,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->courant_limit = c->have_params ? c->courant_limit : 0.0;
     info->stiffness_bound = c->grad_gram_max_h;
     info->device_bytes = c->device_bytes;
+    info->nbasin = c->nbasin;
     return SESW_OK;
 }
 

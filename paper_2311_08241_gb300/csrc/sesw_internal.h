@@ -45,6 +45,15 @@ struct HostMesh {
     std::vector<double> h0_e;      // element rest depth (FP64), new element order
     double grad_gram_max_h = 0.0;  // upper bound of lambda_max(-div H0 grad) (m/s^2 units without g)
 
+    // Batches: a layout may hold several independent meshes ("basins"), each prepared
+    // on its own and concatenated; patches never straddle basins.
+    int nbasin = 1;
+    std::vector<int> patch_basin;      // [npatch]
+    std::vector<int> basin_v;          // [nbasin+1] caller vertex ranges
+    std::vector<int> basin_e;          // [nbasin+1] caller element ranges
+    std::vector<int> basin_patch;      // [nbasin+1] patch ranges
+    std::vector<double> basin_stiffness;   // per basin, as grad_gram_max_h
+
     // Halo structure for the persistent kernel (filled by build_halos). A patch keeps
     // its own vertices at local indices [0, n_own) and its halo vertices (corners of
     // its slots owned by other patches) at [n_own, n_own + n_halo).
@@ -58,6 +67,10 @@ struct HostMesh {
     int max_patch_halo = 0;        // max n_halo
     int max_patch_csr = 0;         // max incidence entries of one patch's own vertices
 };
+
+// Concatenate independently prepared meshes (each with patch_basin all 0) into one
+// layout; caller order of the result is the concatenation of the inputs' caller orders.
+void concat_meshes(std::vector<HostMesh> &parts, HostMesh &out);
 
 // Fill the halo structure of a prepared mesh. Returns SESW_OK or SESW_EINVAL when a
 // patch needs local indices beyond 16 bits.
@@ -87,6 +100,10 @@ struct DevMesh {
     int *vperm = nullptr;
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
+    float *patch_dt = nullptr;     // [npatch] substep length tau/M of the patch's basin
+    int nbasin = 1;
+    int *basin_v = nullptr;        // [nbasin+1] vertex ranges (new order = caller order per basin)
+    int *basin_slot = nullptr;     // [nbasin+1] slot ranges
     // persistent kernel
     int *patch_halo = nullptr;
     int *halo_v = nullptr;
@@ -115,8 +132,9 @@ struct DevState {
     unsigned *abort_flag = nullptr;       // set by a block whose bounded wait gave up
 };
 
+// Scheme constants shared by all patches (the substep dt is per patch, DevMesh::patch_dt).
 struct StepArgs {
-    float g, theta, dt, half_dt, inv_M, eta_bound;
+    float g, theta, inv_M, eta_bound;
     int nonlinear_h;
     int silent_patch;          // persistent kernel: this patch never publishes progress (-1: none; test hook)
     long long wait_cycles;     // persistent kernel: budget of one bounded wait, in SM clock cycles
@@ -139,6 +157,9 @@ cudaError_t launch_gather_state(const DevMesh &m, const DevState &s, int parity,
 cudaError_t launch_diagnostics(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
                                int nblocks, cudaStream_t stream);
 int diagnostics_blocks(const DevMesh &m);
+// Per-basin volume and energy into out[2 * nbasin] (device).
+cudaError_t launch_diagnostics_basins(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
+                                      double *out, cudaStream_t stream);
 
 // Persistent kernel: one launch per baroclinic step (see sesw_kernels.cu).
 struct PersistentPlan {

@@ -55,11 +55,12 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
           float2 *__restrict__ Slo, const int *__restrict__ patch_slot, const int *__restrict__ patch_own,
           const int *__restrict__ patch_v, const int *__restrict__ vcsr_off,
           const uint32_t *__restrict__ vcsr, const float *__restrict__ inv_av,
-          const float *__restrict__ eta_in, float *__restrict__ eta_out, StepArgs a,
-          unsigned *__restrict__ status)
+          const float *__restrict__ eta_in, float *__restrict__ eta_out, const float *__restrict__ patch_dt,
+          StepArgs a, unsigned *__restrict__ status)
 {
     extern __shared__ float sflux[];
     const int p = blockIdx.x;
+    const float dt = patch_dt[p], half_dt = 0.5f * dt;
     const int s0 = patch_slot[p];
     const int n = patch_slot[p + 1] - s0;
     const int nown = patch_own[p];
@@ -79,9 +80,9 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
         float H = c.y;
         if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
         const float gH = a.g * H;
-        const float aa = c.z * a.half_dt;
-        const float rx = u.x + aa * u.y + a.dt * (r.x - gH * gx);
-        const float ry = u.y - aa * u.x + a.dt * (r.y - gH * gy);
+        const float aa = c.z * half_dt;
+        const float rx = u.x + aa * u.y + dt * (r.x - gH * gx);
+        const float ry = u.y - aa * u.x + dt * (r.y - gH * gy);
         const float inv = 1.0f / (1.0f + aa * aa);
         const float nx = (rx + aa * ry) * inv;
         const float ny = (ry - aa * rx) * inv;
@@ -95,7 +96,7 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
             Shi[s] = hi;
             Slo[s] = lo;
         }
-        const float w = a.dt * c.x;
+        const float w = dt * c.x;
         const float c0 = w * (fx * g.x + fy * g.y);
         const float c1 = w * (fx * g.z + fy * g.w);
         sflux[3 * i + 0] = c0;
@@ -233,6 +234,36 @@ k_diag_partial(const int4 *__restrict__ sv, const float4 *__restrict__ sc, const
     }
 }
 
+// One block per basin: volume and energy of its vertex and owned-slot ranges.
+__global__ void __launch_bounds__(kAuxThreads)
+k_diag_basins(const int *__restrict__ basin_v, const int *__restrict__ basin_slot, const int4 *__restrict__ sv,
+              const float4 *__restrict__ sc, const float2 *__restrict__ U, const double *__restrict__ area_v,
+              const float *__restrict__ eta, double g, int nonlinear_h, double *__restrict__ out)
+{
+    __shared__ double sh[2][32];
+    const int b = blockIdx.x;
+    double vol = 0.0, en = 0.0;
+    for (int v = basin_v[b] + threadIdx.x; v < basin_v[b + 1]; v += blockDim.x) {
+        const double e = (double)eta[v];
+        vol += area_v[v] * e;
+        en += area_v[v] * 0.5 * g * e * e;
+    }
+    for (int s = basin_slot[b] + threadIdx.x; s < basin_slot[b + 1]; s += blockDim.x) {
+        const int4 c = sv[s];
+        if (c.w < 0) continue;
+        const float4 k = sc[s];
+        double H = (double)k.y;
+        if (nonlinear_h) H += ((double)eta[c.x] + (double)eta[c.y] + (double)eta[c.z]) / 3.0;
+        const float2 u = U[s];
+        en += (double)k.x * ((double)u.x * u.x + (double)u.y * u.y) / (2.0 * H);
+    }
+    block_sum2<32>(vol, en, sh);
+    if (threadIdx.x == 0) {
+        out[2 * b] = vol;
+        out[2 * b + 1] = en;
+    }
+}
+
 __global__ void __launch_bounds__(kAuxThreads)
 k_diag_final(const double *__restrict__ part, int nparts, double *__restrict__ out)
 {
@@ -273,6 +304,7 @@ struct PArgs {
     const float2 *R;
     float2 *U, *Umean;
     const float *inv_av;
+    const float *patch_dt;
     const float *eta_in;
     float *eta_out;
     float *xb[2];
@@ -367,10 +399,10 @@ __device__ __forceinline__ void element_update(const float e0, const float e1, c
     flux3[2] = -(c0 + c1);
 }
 
-__device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a)
+__device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a, float dt)
 {
-    const float aa = c.z * a.half_dt;
-    return make_float4(a.dt * c.x, a.g * c.y, aa, 1.0f / (1.0f + aa * aa));
+    const float aa = c.z * (0.5f * dt);
+    return make_float4(dt * c.x, a.g * c.y, aa, 1.0f / (1.0f + aa * aa));
 }
 
 template <int SPT, int NONLIN, int CACHED>
@@ -386,6 +418,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
     const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
     const StepArgs a = P.a;
+    const float dt = P.patch_dt[p];
 
     float *seta = reinterpret_cast<float *>(smem_raw);
     float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
@@ -403,7 +436,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     if (CACHED) {
         for (int i = threadIdx.x; i < ns; i += T) {
             s_g[i] = P.sg[s0 + i];
-            s_c[i] = slot_coef(P.sc[s0 + i], a);
+            s_c[i] = slot_coef(P.sc[s0 + i], a, dt);
             s_r[i] = P.R[s0 + i];
             s_l[i] = P.sl[s0 + i];
         }
@@ -445,7 +478,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                     l = s_l[i];
                 } else {
                     g = P.sg[s0 + i];
-                    coef = slot_coef(P.sc[s0 + i], a);
+                    coef = slot_coef(P.sc[s0 + i], a, dt);
                     r = P.R[s0 + i];
                     l = P.sl[s0 + i];
                 }
@@ -461,7 +494,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                     e2 = seta[l.z];
                 }
                 element_update<NONLIN>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
-                                       a.theta, one_p_theta, a.dt, a.g);
+                                       a.theta, one_p_theta, dt, a.g);
             }
         }
     };
@@ -612,20 +645,53 @@ cudaError_t launch_substep(const DevMesh &m, const DevState &s, const StepArgs &
     if (a.nonlinear_h)
         k_substep<1><<<m.npatch, threads, smem, stream>>>(
             m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
-            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, a, s.status);
+            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, a, s.status);
     else
         k_substep<0><<<m.npatch, threads, smem, stream>>>(
             m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
-            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, a, s.status);
+            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, a, s.status);
     return cudaGetLastError();
+}
+
+// The dynamic shared-memory limit is a process-wide attribute of each kernel, shared by
+// every context of the process; it is always raised to the device's opt-in maximum
+// (a permission, nothing is reserved) so that contexts with different patch sizes
+// never lower it under each other's launches.
+int optin_smem()
+{
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+
+// Raise a kernel's dynamic shared-memory limit to the most the device allows it (the
+// opt-in maximum less the kernel's static shared memory); returns that limit or -1.
+int raise_smem_limit(const void *fn)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    const int limit = optin_smem() - (int)fa.sharedSizeBytes;
+    if (limit <= 0 || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    return limit;
 }
 
 cudaError_t substep_smem_attr(const DevMesh &m)
 {
-    const size_t smem = sizeof(float) * 3 * (size_t)m.max_patch_slots;
-    cudaError_t e = cudaFuncSetAttribute(k_substep<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_substep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t need = sizeof(float) * 3 * (size_t)m.max_patch_slots;
+    const int l0 = raise_smem_limit((const void *)k_substep<0>);
+    const int l1 = raise_smem_limit((const void *)k_substep<1>);
+    if (l0 < 0 || l1 < 0 || (size_t)l0 < need || (size_t)l1 < need) return cudaErrorInvalidValue;
+    return cudaSuccess;
 }
 
 cudaError_t launch_step_epilogue(const DevMesh &m, const DevState &s, const StepArgs &a, cudaStream_t stream)
@@ -702,7 +768,7 @@ PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm)
     if (smem > budget) return plan;
     void *fn = persistent_kernel(spt, 1, cached);
     int occ = 0;
-    if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+    if (!fn || raise_smem_limit(fn) < (int)smem ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, smem) != cudaSuccess || occ < blocks_per_sm) {
         cudaGetLastError();
         return plan;
@@ -719,9 +785,9 @@ cudaError_t persistent_prepare(const PersistentPlan &plan)
     void *fn0 = persistent_kernel(plan.slots_per_thread, 0, plan.cached);
     void *fn1 = persistent_kernel(plan.slots_per_thread, 1, plan.cached);
     if (!fn0 || !fn1) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fn1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plan.smem);
+    const int l0 = raise_smem_limit(fn0), l1 = raise_smem_limit(fn1);
+    if (l0 < (int)plan.smem || l1 < (int)plan.smem) return cudaErrorInvalidValue;
+    return cudaSuccess;
 }
 
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
@@ -746,6 +812,7 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     P.U = s.U;
     P.Umean = s.Umean;
     P.inv_av = m.inv_av;
+    P.patch_dt = m.patch_dt;
     P.eta_in = s.eta[parity];
     P.eta_out = s.eta[parity ^ 1];
     P.xb[0] = s.xbuf[0];
@@ -772,6 +839,14 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     if (e != cudaSuccess) return e;
     // flags and the abort word start from zero in the next step
     return cudaMemsetAsync(s.flags, 0, flag_bytes(m.npatch), stream);
+}
+
+cudaError_t launch_diagnostics_basins(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
+                                      double *out, cudaStream_t stream)
+{
+    k_diag_basins<<<m.nbasin, kAuxThreads, 0, stream>>>(m.basin_v, m.basin_slot, m.slot_v, m.slot_c, s.U, m.area_v,
+                                                       s.eta[parity], a.g64, a.nonlinear_h, out);
+    return cudaGetLastError();
 }
 
 int diagnostics_blocks(const DevMesh &m)

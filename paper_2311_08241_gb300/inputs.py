@@ -501,7 +501,10 @@ def ensemble_cases(nbasins=64, vmin=2e4, vmax=4e5, h=5e3, M=40, nsteps=50, seed=
         Xn = np.stack([P[:, 0] / max(Lx, 1.0), P[:, 1] / max(Lx, 1.0), np.full(V, 0.37 * b)], axis=1)
         d = dn.fractal(Xn, octaves=3, base_freq=2.0)
         d = (d - d.min()) / max(d.max() - d.min(), 1e-12)
-        depth = 1000.0 + 4000.0 * d
+        # each basin spans its own seeded sub-range of 1000-5000 m
+        dlo = rng.uniform(1000.0, 2500.0)
+        dhi = rng.uniform(max(dlo + 500.0, 3000.0), 5000.0)
+        depth = dlo + (dhi - dlo) * d
         width = min(Lx, Ly)
         eta0 = np.zeros(V)
         for _ in range(4):

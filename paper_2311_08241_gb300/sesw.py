@@ -37,7 +37,7 @@ _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", 
 # every symbol include/sesw.h declares
 EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_blocks_per_sm", "sesw_set_patch_vertices",
            "sesw_set_block_threads",
-           "sesw_mesh_upload",
+           "sesw_mesh_upload", "sesw_mesh_upload_batch", "sesw_set_params_batch", "sesw_diagnostics_batch",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
            "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_status", "sesw_mesh_check",
            "sesw_get_info", "sesw_last_error", "sesw_destroy")
@@ -68,7 +68,7 @@ class sesw_info(ctypes.Structure):
                 ("nslot", ctypes.c_int32), ("max_patch_slots", ctypes.c_int32),
                 ("patch_vertices", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("slots_per_thread", ctypes.c_int32),
-                ("cached", ctypes.c_int32), ("reserved", ctypes.c_int32), ("courant_max", ctypes.c_double),
+                ("cached", ctypes.c_int32), ("nbasin", ctypes.c_int32), ("courant_max", ctypes.c_double),
                 ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64)]
 
@@ -103,6 +103,9 @@ def load(build_if_missing: bool = True):
         L.sesw_set_blocks_per_sm.argtypes = [P, ctypes.c_int32]
         L.sesw_mesh_upload.argtypes = [P, ctypes.POINTER(sesw_mesh)]
         L.sesw_set_params.argtypes = [P, ctypes.POINTER(sesw_params)]
+        L.sesw_mesh_upload_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(sesw_mesh)]
+        L.sesw_set_params_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(sesw_params)]
+        L.sesw_diagnostics_batch.argtypes = [P, P, P]
         L.sesw_set_state.argtypes = [P, P, P, I]
         L.sesw_set_forcing.argtypes = [P, P, I]
         L.sesw_advance.argtypes = [P, ctypes.c_int32]
@@ -231,10 +234,31 @@ class Subcycle:
         return rc
 
     def sesw_set_params(self, p, flags: int = 0, eta_bound: float = 0.0):
-        cp = sesw_params(float(p.g), float(p.theta), float(p.tau), int(p.M), int(p.nonlinear_h),
-                         int(getattr(p, "scheme", 0)), int(flags), float(eta_bound))
+        cp = _params_struct(p, flags, eta_bound)
         self.params = p
         return self._check(self._L.sesw_set_params(self._h, ctypes.byref(cp)))
+
+    def sesw_mesh_upload_batch(self, meshes):
+        structs, keeps = zip(*[_mesh_struct(m) for m in meshes])
+        arr = (sesw_mesh * len(structs))(*structs)
+        rc = self._check(self._L.sesw_mesh_upload_batch(self._h, len(structs), arr))
+        del keeps
+        self.nv = sum(int(m.nv) for m in meshes)
+        self.ne = sum(int(m.ne) for m in meshes)
+        self.nbasin = len(structs)
+        return rc
+
+    def sesw_set_params_batch(self, params, flags: int = 0, eta_bound: float = 0.0):
+        arr = (sesw_params * len(params))(*[_params_struct(p, flags, eta_bound) for p in params])
+        self.params = params[0]
+        return self._check(self._L.sesw_set_params_batch(self._h, len(params), arr))
+
+    def sesw_diagnostics_batch(self):
+        n = self.sesw_get_info()["nbasin"]
+        vol = np.empty(n)
+        en = np.empty(n)
+        self._check(self._L.sesw_diagnostics_batch(self._h, _ptr(vol), _ptr(en)))
+        return vol, en
 
     def sesw_set_state(self, eta, U):
         eta = _as_f64(eta)
@@ -270,6 +294,11 @@ class Subcycle:
         info = sesw_info()
         self._check(self._L.sesw_get_info(self._h, ctypes.byref(info)))
         return {k: getattr(info, k) for k, _ in sesw_info._fields_}
+
+
+def _params_struct(p, flags=0, eta_bound=0.0):
+    return sesw_params(float(p.g), float(p.theta), float(p.tau), int(p.M), int(p.nonlinear_h),
+                       int(getattr(p, "scheme", 0)), int(flags), float(eta_bound))
 
 
 def _mesh_struct(mesh):

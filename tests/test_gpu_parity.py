@@ -24,11 +24,8 @@ from paper_2311_08241_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-ETA_ABS_TOL = 1e-5
-ENVELOPE_FACTOR = 2.0
-ULP_FLOOR = 8 * 2.0 ** -24
-GRAPH, PERSISTENT = 1, 2          # SESW_MODE_GRAPH, SESW_MODE_PERSISTENT
-MODES = pytest.mark.parametrize("mode", [GRAPH, PERSISTENT], ids=["graph", "persistent"])
+from parity_util import (ENVELOPE_FACTOR, ETA_ABS_TOL, GRAPH, MODES, PERSISTENT, ULP_FLOOR, _assert_close,
+                         _maxabs)
 
 
 @pytest.fixture(scope="module")
@@ -41,28 +38,6 @@ def sesw():
 
     S.load()
     return S
-
-
-def _maxabs(x):
-    return float(np.max(np.abs(x))) if np.size(x) else 0.0
-
-
-def _assert_close(case, got, what, nsteps=None):
-    """GPU result vs the FP64 oracle, within twice the FP32 oracle's drift (see module docstring)."""
-    ref = orc.run_case(case, nsteps=nsteps)
-    r32 = orc.run_case(case, nsteps=nsteps, L=orc.lib_fp32())
-    names = ("eta", "U", "<<U>>")
-    report = []
-    for k, name in enumerate(names):
-        scale = max(_maxabs(ref[k]), 1e-30)
-        err = _maxabs(got[k] - ref[k])
-        env = _maxabs(r32[k] - ref[k])
-        tol = ENVELOPE_FACTOR * env + ULP_FLOOR * scale
-        report.append(f"{name}: err {err:.3e} env32 {env:.3e} tol {tol:.3e} (scale {scale:.3e})")
-        assert err <= tol, f"{what}: {report[-1]}"
-    print(f"{what}: " + "; ".join(report))
-    assert _maxabs(got[0] - ref[0]) <= ETA_ABS_TOL, f"{what}: eta above the absolute target"
-    return ref
 
 
 @MODES
@@ -299,3 +274,22 @@ def test_persistent_wait_gives_up_and_context_stays_usable(sesw):
         got = s.sesw_get_state()
     ref = orc.run_case(case)
     assert _maxabs(got[0] - ref[0]) < 1e-5
+
+
+def test_contexts_with_different_layouts_coexist(sesw):
+    """Kernel attributes are process-wide: a context with large patches keeps working after a
+    context with small patches has been set up (and the other way round)."""
+    big = I.channel_case(nsteps=2)
+    small = I.tiny_jittered_case(nx=20, ny=14, seed=3)
+    with sesw.Subcycle() as a, sesw.Subcycle() as b:
+        for s, c in ((a, big), (b, small)):
+            s.sesw_set_mode(PERSISTENT)
+            s.sesw_mesh_upload(c.mesh)
+            s.sesw_set_params(c.params)
+            s.sesw_set_forcing(c.R)
+            s.sesw_set_state(c.eta0, c.U0)
+        a.sesw_advance(2)
+        b.sesw_advance(2)
+        ra, rb = a.sesw_get_state(), b.sesw_get_state()
+    assert np.array_equal(ra[0], sesw.run_case(big, nsteps=2, mode=PERSISTENT)[0])
+    assert np.array_equal(rb[0], sesw.run_case(small, nsteps=2, mode=PERSISTENT)[0])
