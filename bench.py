@@ -313,8 +313,11 @@ def run_ensemble(args, world, rank, local):
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
     b_alg = algorithmic_bytes_per_substep(V, E)
     mean_step_s = statistics.mean(step_ms) * 1e-3
-    per_launch = b_alg * M if persistent else b_alg
-    launch_s = mean_step_s if persistent else mean_step_s / M
+    # persistent: a step is one launch per pack, each doing M substeps of its basins
+    # (averaged over packs); graph: M substep launches of the whole batch
+    launches_per_step = max(1, info["npack"]) if persistent else M + 1
+    per_launch = b_alg * M / launches_per_step if persistent else b_alg
+    launch_s = mean_step_s / launches_per_step if persistent else mean_step_s / M
     achieved = per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
     kname = "k_persistent" if persistent else "k_substep"
@@ -324,7 +327,7 @@ def run_ensemble(args, world, rank, local):
             "config": {"workload": f"batched ensemble of {len(cases)} closed basins (jittered Delaunay, "
                                    f"log-uniform 2e4-4e5 vertices x {args.ensemble_scale:g}), M={M}, per-basin dt",
                        "V": V, "E": E, "M": M, "nbasin": len(cases), "layout": best.label(),
-                       "npatch": info["npatch"], "nslot": info["nslot"],
+                       "npatch": info["npatch"], "nslot": info["nslot"], "npack": info["npack"],
                        "l2": "flushed between timed steps (256 MiB write)",
                        "autotune_ms_per_step": {c.label(): t for c, t in table}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -333,7 +336,7 @@ def run_ensemble(args, world, rank, local):
             "batched_vs_sequential": {"speedup": speedup, "sequential_ms_per_step": statistics.mean(seq_ms),
                                       "batched_ms_per_step": statistics.mean(step_ms),
                                       "max_ssh_difference_m": ssh_diff, "after_steps": nchk},
-            "gpu_launches": args.steps * (1 if persistent else M + 1), "clocks": clk}
+            "gpu_launches": args.steps * launches_per_step, "clocks": clk}
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -134,6 +134,9 @@ typedef struct sesw_info {
     double stiffness_bound;  /* upper bound L (1/m) of lambda_max(-div H0 grad);
                                 courant_max = (tau/M) sqrt(g L) */
     int64_t device_bytes;    /* device memory held by the context */
+    int32_t npack;           /* persistent mode: cooperative launches per step (packs of meshes
+                                that together fit the resident grid) */
+    int32_t reserved2;
 } sesw_info;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a
@@ -183,9 +186,12 @@ int sesw_mesh_upload(sesw_ctx *ctx, const sesw_mesh *mesh);
 /* Upload a batch of independent meshes ("basins", e.g. ensemble members of uneven
  * size) that advance together in every sesw_advance. Each mesh is validated and
  * prepared exactly as sesw_mesh_upload would prepare it alone (its own space-filling
- * curve order and patches; the persistent mode picks one patch size for all), and the
- * layouts are concatenated, so with SESW_MODE_GRAPH a basin's results are bitwise
- * those of its own upload with the same patch size. Caller order of every state,
+ * curve order and patches), and the layouts are concatenated, so with SESW_MODE_GRAPH a
+ * basin's results are bitwise those of its own upload with the same patch size. In
+ * SESW_MODE_PERSISTENT one patch size is used for all meshes (the smallest that puts
+ * the largest mesh into one grid of resident blocks); the meshes are packed, largest
+ * first, into packs that each fill at most that grid, and a step runs one cooperative
+ * launch per pack. Caller order of every state,
  * forcing and output array is the concatenation of the meshes in order. Errors name
  * the first bad basin. */
 int sesw_mesh_upload_batch(sesw_ctx *ctx, int32_t nmesh, const sesw_mesh *meshes);

@@ -319,22 +319,16 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
             for (int bps : tries) {
                 if (bps <= 0 || plan.slots_per_thread > 0) continue;
                 const long long nblk = (long long)nsm * bps;
-                if (n > nblk) continue;
-                // smallest patch size (>= 32) whose patch count over all meshes fits the grid
-                auto count = [&](long long pv) {
-                    long long t = 0;
-                    for (int b = 0; b < n; b++) t += (meshes[b].nv + pv - 1) / pv;
-                    return t;
-                };
-                long long lo = std::max<long long>(32, (nv_total + nblk - 1) / nblk), hi = std::max<long long>(lo, nv_total);
-                while (lo < hi) {
-                    const long long mid = (lo + hi) / 2;
-                    if (count(mid) <= nblk) hi = mid; else lo = mid + 1;
-                }
+                // Patch size: the smallest (>= 32) that puts the largest mesh into one grid
+                // of resident blocks; meshes are then packed, largest first, into packs of
+                // at most nblk patches, and a step launches the packs one after another.
+                long long vmax = 0;
+                for (int b = 0; b < n; b++) vmax = std::max<long long>(vmax, meshes[b].nv);
+                const long long lo = std::max<long long>(32, (vmax + nblk - 1) / nblk);
                 rc = prepare_parts(c, meshes, n, (int)lo, hm, err);
                 if (rc != SESW_OK) return fail(c, rc, err);
                 rc = sesw::build_halos(hm, err);
-                if (rc == SESW_OK && hm.npatch <= nblk) {
+                if (rc == SESW_OK) {
                     sesw::DevMesh probe;
                     probe.max_patch_slots = hm.max_patch_slots;
                     probe.max_patch_local = hm.max_patch_local;
@@ -391,6 +385,38 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
     TRY(zalloc(c, &d.patch_dt, hm.npatch, "patch_dt"));
+    if (mode == SESW_MODE_PERSISTENT) {
+        // first-fit decreasing packing of whole meshes into packs of at most nblk patches
+        int nsm = 0;
+        CK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+        const int nblk = nsm * plan.blocks_per_sm;
+        std::vector<int> order(hm.nbasin);
+        for (int b = 0; b < hm.nbasin; b++) order[b] = b;
+        auto np_of = [&](int b) { return hm.basin_patch[b + 1] - hm.basin_patch[b]; };
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return np_of(x) > np_of(y); });
+        std::vector<std::vector<int>> packs;
+        std::vector<int> fill;
+        for (int b : order) {
+            if (np_of(b) > nblk) return fail(c, SESW_EINVAL, "a mesh needs more patches than resident blocks");
+            size_t k = 0;
+            while (k < packs.size() && fill[k] + np_of(b) > nblk) k++;
+            if (k == packs.size()) {
+                packs.emplace_back();
+                fill.push_back(0);
+            }
+            packs[k].push_back(b);
+            fill[k] += np_of(b);
+        }
+        std::vector<int> pp;
+        d.pack_off.assign(1, 0);
+        for (auto &pk : packs) {
+            std::sort(pk.begin(), pk.end());
+            for (int b : pk)
+                for (int q = hm.basin_patch[b]; q < hm.basin_patch[b + 1]; q++) pp.push_back(q);
+            d.pack_off.push_back((int)pp.size());
+        }
+        TRY(upload(c, &d.pack_patch, pp, "pack_patch"));
+    }
     {
         std::vector<int> bslot(hm.nbasin + 1);
         for (int b = 0; b <= hm.nbasin; b++) bslot[b] = hm.patch_slot[hm.basin_patch[b]];
@@ -717,6 +743,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->stiffness_bound = c->grad_gram_max_h;
     info->device_bytes = c->device_bytes;
     info->nbasin = c->nbasin;
+    info->npack = c->mode == SESW_MODE_PERSISTENT ? (int32_t)c->dm.pack_off.size() - 1 : 0;
     return SESW_OK;
 }
 

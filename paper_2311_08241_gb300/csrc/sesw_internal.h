@@ -104,6 +104,10 @@ struct DevMesh {
     int nbasin = 1;
     int *basin_v = nullptr;        // [nbasin+1] vertex ranges (new order = caller order per basin)
     int *basin_slot = nullptr;     // [nbasin+1] slot ranges
+    // persistent mode: patches grouped into packs that each fit the resident grid; a
+    // step launches the packs one after another
+    int *pack_patch = nullptr;     // [npatch] patch ids, pack by pack
+    std::vector<int> pack_off;     // [npack+1] ranges into pack_patch (host)
     // persistent kernel
     int *patch_halo = nullptr;
     int *halo_v = nullptr;

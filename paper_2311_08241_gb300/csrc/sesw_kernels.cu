@@ -310,6 +310,8 @@ struct PArgs {
     float *xb[2];
     unsigned *flags;        // [npatch], then the abort word
     unsigned *status;
+    const int *pack_patch;  // patch of each block: pack_patch[pack_base + blockIdx.x]
+    int pack_base;
     StepArgs a;
     int M, npatch;
     // shared-memory carve-up (CACHED), in bytes from the dynamic shared base
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_ok;
-    const int p = blockIdx.x;
+    const int p = P.pack_patch[P.pack_base + blockIdx.x];
     const int T = blockDim.x;
     const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
     const int nown_s = P.patch_own[p], nint = P.patch_int[p];
@@ -832,11 +834,17 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     P.off_csr = L.off_csr;
     P.off_inv = L.off_inv;
     P.off_halo = L.off_halo;
+    P.pack_patch = m.pack_patch;
     void *fn = persistent_kernel(plan.slots_per_thread, a.nonlinear_h, plan.cached);
     if (!fn) return cudaErrorInvalidValue;
-    void *args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(m.npatch), dim3(plan.threads), args, plan.smem, stream);
-    if (e != cudaSuccess) return e;
+    // one cooperative launch per pack; all packs of a step use the same elevation parity
+    for (size_t k = 0; k + 1 < m.pack_off.size(); k++) {
+        P.pack_base = m.pack_off[k];
+        const int nblocks = m.pack_off[k + 1] - m.pack_off[k];
+        void *args[] = {&P};
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(plan.threads), args, plan.smem, stream);
+        if (e != cudaSuccess) return e;
+    }
     // flags and the abort word start from zero in the next step
     return cudaMemsetAsync(s.flags, 0, flag_bytes(m.npatch), stream);
 }

@@ -76,6 +76,15 @@ def test_batch_matches_oracle_per_basin(S, mode):
         assert abs(v - v0) <= 1e-5 * float(np.sum(av * np.abs(c.eta0)))
 
 
+def test_batch_persistent_packs(S):
+    """More patches than resident blocks: the batch runs as several cooperative launches per step."""
+    cases = I.ensemble_cases(nbasins=14, scale=0.04, seed=11, nsteps=2)
+    (eta, U, Um), info, _ = _run_batch(S, cases, PERSISTENT, 2)
+    assert info["mode"] == PERSISTENT and info["npack"] > 1, info
+    for c, e, u, um in zip(cases, _split(cases, eta, "v"), _split(cases, U, "e"), _split(cases, Um, "e")):
+        _assert_close(c, (e, u, um), f"{c.name} packs={info['npack']}", nsteps=2)
+
+
 def test_batch_parameter_rules(S):
     cases = _ensemble(n=3)
     with S.Subcycle() as s:
