@@ -100,3 +100,37 @@ def advance(mesh, R, params, nsteps, eta, U):
             S += U
         Umean = S / params.M + params.theta / params.M * (U - U0)
     return eta, U, Umean
+
+
+def advance_sesm(mesh, R, params, coef, nsteps, eta, U):
+    """SESM steps (Eqs. 4.7-4.8) with the dense finite-element operators; levels before the start of a
+    subcycle equal level 0. Returns (eta, U, Umean)."""
+    beta, delta, gamma, zeta = coef
+    G, D, A, Av = p1_operators(mesh)
+    E, V = mesh.ne, mesh.nv
+    tri = np.asarray(mesh.tri)
+    H0e = np.asarray(mesh.depth)[tri].mean(axis=1)
+    f = np.asarray(mesh.coriolis)
+    dt = params.tau / params.M
+    eta = np.array(eta, dtype=np.float64)
+    U = np.array(U, dtype=np.float64).reshape(E, 2)
+    Rv = np.asarray(R, dtype=np.float64).reshape(E, 2)
+    Umean = np.zeros((E, 2))
+    for _ in range(nsteps):
+        Uh = [U.copy(), U.copy(), U.copy()]            # U^m, U^{m-1}, U^{m-2}
+        Eh = [eta.copy(), eta.copy(), eta.copy()]      # eta^m, eta^{m-1}, eta^{m-2}
+        S = np.zeros((E, 2))
+        for _m in range(params.M):
+            UAB = (1.5 + beta) * Uh[0] - (0.5 + 2 * beta) * Uh[1] + beta * Uh[2]
+            S += UAB
+            enew = Eh[0] - dt * (D @ UAB.reshape(-1))
+            eAM = delta * enew + (1 - delta - gamma - zeta) * Eh[0] + gamma * Eh[1] + zeta * Eh[2]
+            H = H0e + (eAM[tri].mean(axis=1) if params.nonlinear_h else 0.0)
+            grad = (G @ eAM).reshape(E, 2)
+            cor = np.stack([f * UAB[:, 1], -f * UAB[:, 0]], axis=1)
+            Unew = Uh[0] + dt * (cor - params.g * H[:, None] * grad + Rv)
+            Uh = [Unew, Uh[0], Uh[1]]
+            Eh = [enew, Eh[0], Eh[1]]
+        U, eta = Uh[0], Eh[0]
+        Umean = S / params.M
+    return eta, U, Umean

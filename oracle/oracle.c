@@ -436,6 +436,95 @@ int oracle_advance(void *hm, const double *R_in, double g_in, double theta_in, d
     return 0;
 }
 
+/*
+ * Advance nsteps baroclinic steps of the AB3-AM4 substep with dissipative coefficients
+ * (SESM), Eqs. (4.7)-(4.8), W = 0:
+ *     U_AB   = (3/2 + beta) U^m - (1/2 + 2 beta) U^{m-1} + beta U^{m-2}
+ *     eta^{m+1} = eta^m - dt div(U_AB)
+ *     eta_AM = delta eta^{m+1} + (1 - delta - gamma - zeta) eta^m + gamma eta^{m-1} + zeta eta^{m-2}
+ *     U^{m+1} = U^m + dt ( -f e_z x U_AB - g H_AM grad(eta_AM) + R ),  H_AM = H0 + eta_AM
+ *                                                    (H0 alone when nonlinear_h = 0)
+ * Levels before the start of the subcycle (m - k < 0) are taken equal to level 0.
+ * The time-mean transport is the mean of the transports the continuity equation used,
+ *     <<U>> = (1/M) sum_{m=0..M-1} U_AB^m,
+ * which makes eta^M - eta^0 = -tau div <<U>> exact (Eq. 4.11).
+ */
+int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_in, double delta_in,
+                        double gamma_in, double zeta_in, double tau, int M, int nonlinear_h, int nsteps,
+                        double *eta_io, double *U_io, double *Umean_out)
+{
+    omesh *m = (omesh *)hm;
+    if (M < 1) return -5;
+    const int ne = m->ne, nv = m->nv;
+    const real dt = (real)(tau / (double)M);
+    const real g = (real)g_in, beta = (real)beta_in, delta = (real)delta_in, gam = (real)gamma_in,
+               zeta = (real)zeta_in;
+    const real ab0 = (real)1.5 + beta, ab1 = -((real)0.5 + 2 * beta), ab2 = beta;
+    const real am0 = delta, am1 = 1 - delta - gam - zeta, am2 = gam, am3 = zeta;
+    real *U[3], *E[4];
+    for (int k = 0; k < 3; k++) U[k] = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    for (int k = 0; k < 4; k++) E[k] = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *UAB = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *sumF = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *R = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *eAM = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *div = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *ef = (real *)malloc(sizeof(real) * (size_t)m->ned);
+    int ok = UAB && sumF && R && eAM && div && ef;
+    for (int k = 0; k < 3; k++) ok = ok && U[k];
+    for (int k = 0; k < 4; k++) ok = ok && E[k];
+    if (!ok) {
+        for (int k = 0; k < 3; k++) free(U[k]);
+        for (int k = 0; k < 4; k++) free(E[k]);
+        free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef);
+        return -4;
+    }
+    for (size_t i = 0; i < 2 * (size_t)ne; i++) { U[0][i] = (real)U_io[i]; R[i] = (real)R_in[i]; }
+    for (int v = 0; v < nv; v++) E[0][v] = (real)eta_io[v];
+    for (int n = 0; n < nsteps; n++) {
+        /* U[0] = U^m, U[1] = U^{m-1}, U[2] = U^{m-2}; E[0] = eta^m, E[1..3] older levels */
+        memcpy(U[1], U[0], sizeof(real) * 2 * (size_t)ne);
+        memcpy(U[2], U[0], sizeof(real) * 2 * (size_t)ne);
+        for (int k = 1; k < 4; k++) memcpy(E[k], E[0], sizeof(real) * (size_t)nv);
+        memset(sumF, 0, sizeof(real) * 2 * (size_t)ne);
+        for (int s = 0; s < M; s++) {
+            for (size_t i = 0; i < 2 * (size_t)ne; i++) {
+                UAB[i] = ab0 * U[0][i] + ab1 * U[1][i] + ab2 * U[2][i];
+                sumF[i] += UAB[i];
+            }
+            /* continuity with the AB3 transport: eta^{m+1} into the oldest level's array */
+            divergence(m, UAB, ef, div);
+            real *enew = E[3];
+            for (int v = 0; v < nv; v++) enew[v] = E[0][v] - dt * div[v];
+            /* AM4 elevation: eta^{m+1}, eta^m, eta^{m-1}, eta^{m-2} */
+            for (int v = 0; v < nv; v++) eAM[v] = am0 * enew[v] + am1 * E[0][v] + am2 * E[1][v] + am3 * E[2][v];
+            /* momentum with explicit Coriolis on U_AB and the AM4 pressure gradient; U^{m+1}
+               goes into the array of U^{m-2}, which is no longer needed */
+            real *unew = U[2];
+            #pragma omp parallel for schedule(static)
+            for (int e = 0; e < ne; e++) {
+                real gx, gy;
+                gradient_e(m, e, eAM, &gx, &gy);
+                real H = element_depth(m, e, eAM, nonlinear_h);
+                real ux = UAB[2 * e], uy = UAB[2 * e + 1];
+                /* -f e_z x U_AB = (f U_AB_y, -f U_AB_x) */
+                unew[2 * e] = U[0][2 * e] + dt * (m->f_e[e] * uy - g * H * gx + R[2 * e]);
+                unew[2 * e + 1] = U[0][2 * e + 1] + dt * (-m->f_e[e] * ux - g * H * gy + R[2 * e + 1]);
+            }
+            /* rotate the levels */
+            real *t = U[2]; U[2] = U[1]; U[1] = U[0]; U[0] = t;
+            real *te = E[3]; E[3] = E[2]; E[2] = E[1]; E[1] = E[0]; E[0] = te;
+        }
+        for (size_t i = 0; i < 2 * (size_t)ne; i++) Umean_out[i] = (double)(sumF[i] / (real)M);
+    }
+    for (size_t i = 0; i < 2 * (size_t)ne; i++) U_io[i] = (double)U[0][i];
+    for (int v = 0; v < nv; v++) eta_io[v] = (double)E[0][v];
+    for (int k = 0; k < 3; k++) free(U[k]);
+    for (int k = 0; k < 4; k++) free(E[k]);
+    free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef);
+    return 0;
+}
+
 int oracle_set_threads(int n)
 {
 #ifdef _OPENMP

@@ -51,6 +51,8 @@ def _bind(path):
     L.oracle_diagnostics.argtypes = [P, P, P, D, I, ctypes.POINTER(D), ctypes.POINTER(D)]
     L.oracle_advance.argtypes = [P, P, D, D, D, I, I, I, P, P, P, P]
     L.oracle_set_threads.argtypes = [I]
+    L.oracle_advance_sesm.argtypes = [P, P, D, D, D, D, D, D, I, I, I, P, P, P]
+    L.oracle_advance_sesm.restype = I
     for f in ("oracle_mesh_info", "oracle_areas", "oracle_edges", "oracle_gradient",
               "oracle_divergence", "oracle_diagnostics", "oracle_advance",
               "oracle_set_threads"):
@@ -197,6 +199,21 @@ class OracleMesh:
         if rc:
             raise RuntimeError(f"oracle_advance failed ({rc})")
         return eta, U, Umean, diag
+
+
+    def advance_sesm(self, R, params, coef, nsteps, eta, U):
+        """SESM steps (Eqs. 4.7-4.8); coef = (beta, delta, gamma, zeta). Returns (eta, U, Umean)."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        eta = np.array(eta, dtype=np.float64, copy=True)
+        U = np.array(U, dtype=np.float64, copy=True)
+        Umean = np.zeros((self.ne, 2))
+        b, d, g, z = (float(x) for x in coef)
+        rc = self._L.oracle_advance_sesm(self._h, _p(R), float(params.g), b, d, g, z, float(params.tau),
+                                         int(params.M), int(params.nonlinear_h), int(nsteps), _p(eta), _p(U),
+                                         _p(Umean))
+        if rc:
+            raise RuntimeError(f"oracle_advance_sesm failed ({rc})")
+        return eta, U, Umean
 
 
 def run_case(case, nsteps=None, want_diag=False, L=None):

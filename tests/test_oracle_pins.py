@@ -303,3 +303,114 @@ def test_pins_catch_planted_mistake(plant):
     err = max(np.max(np.abs(e1 - e2)), np.max(np.abs(U1 - U2)) / max(1.0, np.max(np.abs(U2))),
               np.max(np.abs(M1 - M2)) / max(1.0, np.max(np.abs(M2))))
     assert err > 1e-6, f"planted mistake {plant} went unnoticed"
+
+
+# ---------------------------------------------------------------- SESM (Eqs. 4.7-4.8, Sect. 3)
+
+def _sesm_coef(golden_se):
+    chi = golden_se["chi_fig1"]
+    b = golden_se["beta_sesm"]
+    z = golden_se["zeta_c0"] + golden_se["zeta_c1"] * chi
+    g = golden_se["gamma_c0"] + golden_se["gamma_c1"] * chi
+    d = 2 * chi + g + 2 * z + 0.5
+    return b, d, g, z
+
+
+def test_sesm_parameters_follow_printed_rules(golden_se):
+    b, d, g, z = _sesm_coef(golden_se)
+    assert (b, d, g, z) == pytest.approx(closed.sesm_params(golden_se["chi_fig1"]))
+    chi, n, q = closed.sesm_small_c(b, d, g, z)
+    assert chi == pytest.approx(golden_se["chi_fig1"])
+
+
+def test_sesm_matrix_roots_are_roots_of_printed_polynomial(golden_se):
+    coef = _sesm_coef(golden_se)
+    for c in (0.05, 0.3, 0.9, 1.3):
+        ev = np.linalg.eigvals(closed.sesm_matrix(c, *coef))
+        rt = np.roots(closed.sesm_poly(c, *coef))
+        assert _same_roots(ev, rt, 1e-9)
+
+
+def test_sesm_small_courant_expansion(golden_se):
+    """The physical root of Eq. (3.5) follows lambda = 1 + i c + n c^2 + q c^3 + O(c^4) with the printed
+    SESM n and q (Eq. dp_5), and |lambda| = 1 - chi c^2 + O(c^4) (Eq. dp_3)."""
+    coef = _sesm_coef(golden_se)
+    chi, n, q = closed.sesm_small_c(*coef)
+    res = []
+    for c in (2e-2, 1e-2, 5e-3):
+        lam = np.linalg.eigvals(closed.sesm_matrix(c, *coef))
+        lam = lam[np.argmin(np.abs(lam - np.exp(1j * c)))]
+        res.append(abs(lam - (1 + 1j * c + n * c * c + q * c ** 3)))
+        assert abs(abs(lam) - (1 - chi * c * c)) < 5 * c ** 4
+    assert res[0] / res[1] > 12 and res[1] / res[2] > 12
+
+
+def test_sesm_lattice_recurrence_has_the_printed_spectrum(golden_se):
+    coef = _sesm_coef(golden_se)
+    for kappa2, gH, dt in ((1e-9, 4e4, 20.0), (3e-8, 3e4, 12.0), (6e-8, 5e4, 5.0)):
+        c = math.sqrt(gH * kappa2) * dt
+        a = np.linalg.eigvals(closed.sesm_lattice_matrix(kappa2, gH, dt, *coef))
+        b = np.linalg.eigvals(closed.sesm_matrix(c, *coef))
+        assert _same_roots(a, b, 1e-9)
+
+
+@pytest.mark.parametrize("kx,ky", [(1, 0), (3, 2), (5, 7)])
+def test_oracle_sesm_periodic_wave_matches_closed_form(golden_se, kx, ky):
+    coef = _sesm_coef(golden_se)
+    case = I.periodic_wave_case(n=16, kx=kx, ky=ky, nsteps=3, M=30, tau=450.0)
+    p = case.params
+    om = orc.OracleMesh(case.mesh)
+    eta, U, Um = om.advance_sesm(case.R, p, coef, case.nsteps, case.eta0, case.U0)
+    k2 = closed.kappa2_square(16, 10e3, kx, ky)
+    u, e = closed.sesm_mode_amplitude(k2, p.g * 4000.0, p.tau / p.M, coef, p.M, case.nsteps)
+    assert np.max(np.abs(eta - e * case.eta0)) < 1e-11
+    assert abs(e) < 1.0
+
+
+@pytest.mark.parametrize("nonlinear_h", [0, 1])
+def test_oracle_sesm_summation_identity_and_volume(golden_se, nonlinear_h):
+    coef = _sesm_coef(golden_se)
+    case = I.tiny_jittered_case(nx=9, ny=7, seed=3, nonlinear_h=nonlinear_h, M=7, tau=70.0)
+    om = orc.OracleMesh(case.mesh)
+    eta1, U1, Um = om.advance_sesm(case.R, case.params, coef, 1, case.eta0, case.U0)
+    assert np.max(np.abs((eta1 - case.eta0) + case.params.tau * om.divergence(Um))) < 1e-12
+    av, _ = om.areas()
+    eta3, _, _ = om.advance_sesm(case.R, case.params, coef, 3, case.eta0, case.U0)
+    assert abs(np.sum(av * eta3) - np.sum(av * case.eta0)) < 1e-12 * np.sum(av * np.abs(case.eta0))
+
+
+def test_oracle_sesm_matches_brute_force(golden_se):
+    coef = _sesm_coef(golden_se)
+    for nl in (0, 1):
+        case = I.tiny_jittered_case(nx=6, ny=5, seed=13, nonlinear_h=nl)
+        om = orc.OracleMesh(case.mesh)
+        e1, U1, M1 = om.advance_sesm(case.R, case.params, coef, case.nsteps, case.eta0, case.U0)
+        e2, U2, M2 = brute.advance_sesm(case.mesh, case.R, case.params, coef, case.nsteps, case.eta0, case.U0)
+        assert np.max(np.abs(e1 - e2)) < 1e-11 * max(1.0, np.max(np.abs(e2)))
+        assert np.max(np.abs(U1 - U2)) < 1e-11 * max(1.0, np.max(np.abs(U2)))
+        assert np.max(np.abs(M1 - M2)) < 1e-11 * max(1.0, np.max(np.abs(M2)))
+
+
+SESM_PLANTS = {
+    "ab3_weights": ("const real ab0 = (real)1.5 + beta, ab1 = -((real)0.5 + 2 * beta), ab2 = beta;",
+                    "const real ab0 = (real)1.5, ab1 = -((real)0.5), ab2 = 0;"),
+    "am4_order": ("eAM[v] = am0 * enew[v] + am1 * E[0][v] + am2 * E[1][v] + am3 * E[2][v];",
+                  "eAM[v] = am1 * enew[v] + am0 * E[0][v] + am2 * E[1][v] + am3 * E[2][v];"),
+    "coriolis_sign": ("unew[2 * e] = U[0][2 * e] + dt * (m->f_e[e] * uy - g * H * gx + R[2 * e]);",
+                      "unew[2 * e] = U[0][2 * e] + dt * (-m->f_e[e] * uy - g * H * gx + R[2 * e]);"),
+}
+
+
+@pytest.mark.parametrize("plant", sorted(SESM_PLANTS))
+def test_sesm_pins_catch_planted_mistake(golden_se, plant):
+    old, new = SESM_PLANTS[plant]
+    src = orc.source_text()
+    assert old in src
+    L = orc.build_variant(src.replace(old, new), "sesm_" + plant)
+    coef = _sesm_coef(golden_se)
+    case = I.tiny_jittered_case(nx=6, ny=5, seed=13, nonlinear_h=1)
+    om = orc.OracleMesh(case.mesh, L)
+    e1, U1, M1 = om.advance_sesm(case.R, case.params, coef, case.nsteps, case.eta0, case.U0)
+    e2, U2, M2 = brute.advance_sesm(case.mesh, case.R, case.params, coef, case.nsteps, case.eta0, case.U0)
+    err = max(np.max(np.abs(e1 - e2)), np.max(np.abs(U1 - U2)) / max(1.0, np.max(np.abs(U2))))
+    assert err > 1e-6, f"planted mistake {plant} went unnoticed"
