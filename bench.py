@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto")
+    ap.add_argument("--scheme", choices=["se", "sesm"], default="se",
+                    help="se: dissipative forward-backward (Eq. 4.10); sesm: AB3-AM4 (Eqs. 4.7-4.8, graph mode)")
     ap.add_argument("--patch-vertices", type=int, default=256)
     ap.add_argument("--block-threads", type=int, default=256)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -383,6 +385,13 @@ def run_ours(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     case, desc = workload()
+    if args.scheme == "sesm":
+        from paper_2311_08241_gb300 import inputs as I
+
+        p = case.params
+        case.params = I.Params(g=p.g, theta=p.theta, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h, scheme=1)
+        args.mode = "graph"
+        desc = dict(desc, scheme="SESM (AB3-AM4, Eqs. 4.7-4.8)")
     V, E, M = case.mesh.nv, case.mesh.ne, case.params.M
     stream = torch.cuda.current_stream(dev)
     sim = S.Subcycle(local, stream=stream)
@@ -437,7 +446,7 @@ def run_ours(args, world, rank, local):
     launch_s = mean_step_s if persistent else mean_step_s / M
     achieved = per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
-    kname = "k_persistent" if persistent else "k_substep"
+    kname = "k_persistent" if persistent else ("k_sesm" if args.scheme == "sesm" else "k_substep")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(kname), "peak_source": peak_src, "kernel": kname,
                 "bytes_per_launch": per_launch}

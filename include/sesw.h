@@ -94,14 +94,21 @@ typedef struct sesw_mesh {
  *   tau          baroclinic step (s), > 0; the substep is tau/M
  *   M            substeps per baroclinic step, 1..65536
  *   nonlinear_h  1: H = H0 + eta on each triangle (corner mean); 0: H = H0
- *   scheme       0: dissipative forward-backward (Eq. 4.10); other values are rejected
+ *   scheme       0: dissipative forward-backward (Eq. 4.10, "SE");
+ *                1: AB3-AM4 with dissipative coefficients (Eqs. 4.7-4.8, "SESM"), SESW_MODE_GRAPH
+ *                   only; levels before the start of a subcycle are taken equal to level 0 and
+ *                   <<U>> is the mean of the AB3 transports, which keeps Eq. 4.11 exact
  *   flags        bit 0 (SESW_FLAG_NO_STABILITY_CHECK): accept parameters whose Courant
  *                bound exceeds the stability limit (the bound is conservative);
  *                bit 1 (SESW_FLAG_TEST_FORCE_TIMEOUT, for testing failure detection):
  *                in SESW_MODE_PERSISTENT patch 0 never publishes its progress and each
  *                bounded wait gives up after ~1e7 cycles instead of ~1 s, so the step
  *                ends early and sesw_status reports SESW_ETIMEOUT
- *   eta_bound    |eta| above this (m) or a non-finite value sets SESW_EUNSTABLE; <= 0 means 1e4 */
+ *   eta_bound    |eta| above this (m) or a non-finite value sets SESW_EUNSTABLE; <= 0 means 1e4
+ *   sesm_beta, sesm_delta, sesm_gamma, sesm_zeta
+ *                SESM coefficients of Eq. (4.7); all zero selects beta = 0.281105 and, with
+ *                chi = theta/2, gamma = 0.083 - 0.514 chi, zeta = 0.010 - 0.135 chi,
+ *                delta = 2 chi + gamma + 2 zeta + 1/2 (Eqs. dp_4, dp_6) */
 #define SESW_FLAG_NO_STABILITY_CHECK 1
 #define SESW_FLAG_TEST_FORCE_TIMEOUT 2
 typedef struct sesw_params {
@@ -113,6 +120,10 @@ typedef struct sesw_params {
     int32_t scheme;
     int32_t flags;
     double eta_bound;
+    double sesm_beta;
+    double sesm_delta;
+    double sesm_gamma;
+    double sesm_zeta;
 } sesw_params;
 
 /* Read-only facts about the uploaded mesh and its device layout. */
@@ -204,7 +215,8 @@ int sesw_set_params_batch(sesw_ctx *ctx, int32_t n, const sesw_params *params);
 /* Set scheme parameters; requires an uploaded mesh. Rejects (SESW_EINVAL)
  * parameters whose substep Courant number bound exceeds 2/sqrt(1+2 theta), the
  * value beyond which the scheme's characteristic polynomial (Eq. dp_1, SE row) has a
- * root outside the unit circle. c is an upper bound of dt sqrt(lambda_max(-div g H0
+ * root outside the unit circle (for SESM the limit of its coefficients, found
+ * numerically from the spectral radius of the per-mode substep matrix). c is an upper bound of dt sqrt(lambda_max(-div g H0
  * grad)) for the lumped median-dual operator: the smaller of an element-by-element
  * bound, dt sqrt(3 g max_e H0_e lambda_max(sum_k grad phi_k grad phi_k^T)), and the
  * Gershgorin bound over the rows of the stiffness matrix divided by A_v. */

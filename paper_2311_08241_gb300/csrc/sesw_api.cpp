@@ -150,6 +150,38 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     cudaError_t e = cudaSuccess;
     if (c->mode == SESW_MODE_PERSISTENT) {
         e = sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->plan, c->cap_stream);
+    } else if (c->params.scheme == 1) {
+        // SESM: level rings, U^m in B[m % 3] (B[0] holds U^0 and, at the end, U^M) and
+        // eta^m in Er[m % 5] (Er[0] holds eta^0 and, at the end, eta^M); levels before
+        // the start of the subcycle alias level 0
+        const int M = c->params.M;
+        float2 *B[3] = {c->ds.U, c->ds.U_x[0], c->ds.U_x[1]};
+        float *Er[5] = {c->ds.eta[0], c->ds.eta[1], c->ds.eta_x[0], c->ds.eta_x[1], c->ds.eta_x[2]};
+        auto ul = [&](int j) { return B[j < 0 ? 0 : j % 3]; };
+        auto el = [&](int j) { return Er[j < 0 ? 0 : j % 5]; };
+        for (int m = 0; m <= M && e == cudaSuccess; m++) {
+            sesw::SesmPtrs q;
+            q.update = m > 0;
+            q.vertex = m < M;
+            q.u0 = m < M ? B[m % 3] : B[0];
+            q.u1 = ul(m - 1);
+            q.u2 = ul(m - 2);
+            q.u3 = ul(m - 3);
+            if (m == 0) {      // U_AB^0 = ab0 U^0 + ab1 U^{-1} + ab2 U^{-2} with both aliases of U^0
+                q.u1 = B[0];
+                q.u2 = B[0];
+            }
+            q.e0 = el(m);
+            q.e1 = el(m - 1);
+            q.e2 = el(m - 2);
+            q.e3 = el(m - 3);
+            q.enew = el(m + 1);
+            e = sesw::launch_sesm(c->dm, c->ds, c->args, q, c->block_threads, c->cap_stream);
+        }
+        if (e == cudaSuccess) e = sesw::launch_step_epilogue(c->dm, c->ds, c->args, c->cap_stream);
+        if (e == cudaSuccess && M % 5 != 0)
+            e = cudaMemcpyAsync(Er[0], Er[M % 5], sizeof(float) * (size_t)c->dm.nv, cudaMemcpyDeviceToDevice,
+                                c->cap_stream);
     } else {
         int p = parity;
         for (int m = 0; m < c->params.M && e == cudaSuccess; m++) {
@@ -197,8 +229,52 @@ int enqueue_step(sesw_ctx *c)
         }
     }
     CK(c, cudaGraphLaunch(g, c->stream));
-    c->parity ^= (c->mode == SESW_MODE_PERSISTENT) ? 1 : (c->params.M & 1);
+    if (c->mode == SESW_MODE_PERSISTENT)
+        c->parity ^= 1;
+    else if (c->params.scheme == 0)
+        c->parity ^= (c->params.M & 1);      // SESM ends every step with eta^M in eta[0]
     return SESW_OK;
+}
+
+// Largest substep Courant number c for which the SESM substep (AB3 weights ab, AM4
+// weights am) is stable: bisection on the spectral radius of the per-mode 6x6 matrix,
+// estimated from the growth of ||A^4096|| by repeated squaring. The eigenvalues depend
+// on c only through c^2, so the mode's dt kappa^2 and dt g H are both set to c.
+double sesm_stability_limit(const double ab[3], const double am[4])
+{
+    auto log_radius = [&](double c) {
+        double A[6][6] = {};
+        const double k = c, w = c;
+        A[0][0] = 1; A[0][3] = k * ab[0]; A[0][4] = k * ab[1]; A[0][5] = k * ab[2];
+        A[1][0] = 1;
+        A[2][1] = 1;
+        A[3][0] = -w * (am[0] + am[1]); A[3][1] = -w * am[2]; A[3][2] = -w * am[3];
+        A[3][3] = 1 - w * am[0] * k * ab[0]; A[3][4] = -w * am[0] * k * ab[1]; A[3][5] = -w * am[0] * k * ab[2];
+        A[4][3] = 1;
+        A[5][4] = 1;
+        double logs = 0.0;
+        for (int it = 0; it < 12; it++) {
+            double B[6][6] = {};
+            for (int i = 0; i < 6; i++)
+                for (int j = 0; j < 6; j++)
+                    for (int l = 0; l < 6; l++) B[i][j] += A[i][l] * A[l][j];
+            double mx = 0.0;
+            for (int i = 0; i < 6; i++)
+                for (int j = 0; j < 6; j++) mx = std::max(mx, fabs(B[i][j]));
+            if (!(mx > 0.0) || !std::isfinite(mx)) return 1e9;
+            logs = 2.0 * logs + log(mx);
+            for (int i = 0; i < 6; i++)
+                for (int j = 0; j < 6; j++) A[i][j] = B[i][j] / mx;
+        }
+        return logs / 4096.0;
+    };
+    double lo = 0.0, hi = 4.0;
+    if (log_radius(hi) <= 1e-5) return hi;
+    for (int it = 0; it < 50; it++) {
+        const double mid = 0.5 * (lo + hi);
+        if (log_radius(mid) <= 1e-5) lo = mid; else hi = mid;
+    }
+    return lo;
 }
 
 }  // namespace
@@ -457,6 +533,11 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
         CK(c, sesw::persistent_prepare(plan));
     } else {
+        TRY(zalloc(c, &s.eta_x[0], hm.nv, "eta_x"));
+        TRY(zalloc(c, &s.eta_x[1], hm.nv, "eta_x"));
+        TRY(zalloc(c, &s.eta_x[2], hm.nv, "eta_x"));
+        TRY(zalloc(c, &s.U_x[0], hm.nslot, "U_x"));
+        TRY(zalloc(c, &s.U_x[1], hm.nslot, "U_x"));
         CK(c, sesw::substep_smem_attr(d));
     }
     CK(c, cudaStreamSynchronize(c->stream));
@@ -516,6 +597,18 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
     DeviceGuard dg(c->device);
     const sesw_params *p = &ps[0];
     double cmax_all = 0.0, limit = 0.0;
+    // SESM coefficients (Eq. 4.7); all zero: beta of Sect. 3.2 and Eq. dp_6 at chi = theta / 2
+    double beta = p->sesm_beta, delta = p->sesm_delta, gam = p->sesm_gamma, zeta = p->sesm_zeta;
+    if (beta == 0.0 && delta == 0.0 && gam == 0.0 && zeta == 0.0) {
+        const double chi = 0.5 * p->theta;
+        beta = 0.281105;
+        gam = 0.083 - 0.514 * chi;
+        zeta = 0.010 - 0.135 * chi;
+        delta = 2.0 * chi + gam + 2.0 * zeta + 0.5;
+    }
+    const double ab[3] = {1.5 + beta, -(0.5 + 2.0 * beta), beta};
+    const double am[4] = {delta, 1.0 - delta - gam - zeta, gam, zeta};
+    const double sesm_limit = p->scheme == 1 ? sesm_stability_limit(ab, am) : 0.0;
     for (int b = 0; b < n; b++) {
         const sesw_params &q = ps[b];
         if (!(q.g > 0.0) || !isfinite(q.g)) return fail(c, SESW_EINVAL, "g must be positive and finite");
@@ -523,18 +616,22 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
         if (!(q.tau > 0.0) || !isfinite(q.tau)) return fail(c, SESW_EINVAL, "tau must be positive and finite");
         if (q.M < 1 || q.M > 65536) return fail(c, SESW_EINVAL, "M must be in [1, 65536]");
         if (q.nonlinear_h != 0 && q.nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
-        if (q.scheme != 0) return fail(c, SESW_EINVAL, "scheme must be 0 (dissipative forward-backward)");
+        if (q.scheme != 0 && q.scheme != 1) return fail(c, SESW_EINVAL, "scheme must be 0 (SE) or 1 (SESM)");
+        if (q.scheme == 1 && c->mode == SESW_MODE_PERSISTENT)
+            return fail(c, SESW_EINVAL, "the SESM scheme runs in SESW_MODE_GRAPH; set the mode before the upload");
         if (q.g != p->g || q.theta != p->theta || q.M != p->M || q.nonlinear_h != p->nonlinear_h ||
-            q.flags != p->flags || q.eta_bound != p->eta_bound)
+            q.flags != p->flags || q.eta_bound != p->eta_bound || q.scheme != p->scheme ||
+            q.sesm_beta != p->sesm_beta || q.sesm_delta != p->sesm_delta || q.sesm_gamma != p->sesm_gamma ||
+            q.sesm_zeta != p->sesm_zeta)
             return fail(c, SESW_EINVAL, "meshes of one batch may differ only in tau");
         const double dt = q.tau / q.M;
         // upper bound of dt sqrt(lambda_max(-div g H0 grad)), see prepare_mesh
         const double cmax = sqrt(q.g * c->basin_stiffness[b]) * dt;
-        limit = 2.0 / sqrt(1.0 + 2.0 * q.theta);
+        limit = q.scheme == 1 ? sesm_limit : 2.0 / sqrt(1.0 + 2.0 * q.theta);
         if (cmax > limit && !(q.flags & SESW_FLAG_NO_STABILITY_CHECK)) {
             char buf[320];
             snprintf(buf, sizeof buf,
-                     "%s%ssubstep Courant number bound %.4f exceeds the stability limit 2/sqrt(1+2 theta) = %.4f; "
+                     "%s%ssubstep Courant number bound %.4f exceeds the stability limit %.4f of the scheme; "
                      "increase M",
                      n > 1 ? "basin " : "", n > 1 ? (std::to_string(b) + ": ").c_str() : "", cmax, limit);
             return fail(c, SESW_EINVAL, buf);
@@ -551,6 +648,13 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
     a.inv_M = (float)(1.0 / p->M);
     a.eta_bound = (float)c->params.eta_bound;
     a.nonlinear_h = p->nonlinear_h;
+    a.ab0 = (float)ab[0];
+    a.ab1 = (float)ab[1];
+    a.ab2 = (float)ab[2];
+    a.am0 = (float)am[0];
+    a.am1 = (float)am[1];
+    a.am2 = (float)am[2];
+    a.am3 = (float)am[3];
     // a bounded wait gives up after about one second (2e9 cycles at ~2 GHz); the test
     // hook silences patch 0 and shortens the budget to about 10 ms
     const bool test_timeout = (p->flags & SESW_FLAG_TEST_FORCE_TIMEOUT) != 0;

@@ -134,11 +134,26 @@ struct DevState {
     unsigned *flags = nullptr;            // substeps completed by each patch in the running step, one
                                           // 128-byte line per patch, then the abort word
     unsigned *abort_flag = nullptr;       // set by a block whose bounded wait gave up
+    // SESM (graph mode): five elevation levels (eta[0], eta[1] and three more) and two
+    // extra transport levels per slot (U is the third)
+    float *eta_x[3] = {nullptr, nullptr, nullptr};
+    float2 *U_x[2] = {nullptr, nullptr};
+};
+
+// Level pointers of one SESM launch (see k_sesm).
+struct SesmPtrs {
+    const float2 *u1, *u2, *u3;
+    float2 *u0;
+    const float *e0, *e1, *e2, *e3;
+    float *enew;
+    int update, vertex;
 };
 
 // Scheme constants shared by all patches (the substep dt is per patch, DevMesh::patch_dt).
 struct StepArgs {
     float g, theta, inv_M, eta_bound;
+    float ab0, ab1, ab2;            // SESM: AB3 weights (Eq. 4.7)
+    float am0, am1, am2, am3;       // SESM: AM4 weights (Eq. 4.7)
     int nonlinear_h;
     int silent_patch;          // persistent kernel: this patch never publishes progress (-1: none; test hook)
     long long wait_cycles;     // persistent kernel: budget of one bounded wait, in SM clock cycles
@@ -152,6 +167,8 @@ cudaError_t launch_substep(const DevMesh &m, const DevState &s, const StepArgs &
 cudaError_t substep_smem_attr(const DevMesh &m);
 cudaError_t launch_step_epilogue(const DevMesh &m, const DevState &s, const StepArgs &a,
                                  cudaStream_t stream);
+cudaError_t launch_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, const SesmPtrs &q, int block,
+                        cudaStream_t stream);
 cudaError_t launch_scatter_state(const DevMesh &m, const DevState &s, const double *eta,
                                  const double *U, int parity, cudaStream_t stream);
 cudaError_t launch_scatter_forcing(const DevMesh &m, const DevState &s, const double *R,

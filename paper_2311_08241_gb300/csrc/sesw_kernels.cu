@@ -121,6 +121,102 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
     if (bad) atomicOr(status, 1u);
 }
 
+// ---------------------------------------------------------------------------------
+// SESM substep (AB3-AM4 with dissipative coefficients, Eqs. 4.7-4.8), one launch per
+// substep in graph mode. Launch m first completes the momentum update of substep m-1,
+//     U^m = U^{m-1} + dt ( -f e_z x U_AB^{m-1} - g H_AM grad(eta_AM) + R ),
+//     eta_AM = am0 eta^m + am1 eta^{m-1} + am2 eta^{m-2} + am3 eta^{m-3},
+//     U_AB^{m-1} = ab0 U^{m-1} + ab1 U^{m-2} + ab2 U^{m-3}
+// (skipped for m = 0), then forms U_AB^m = ab0 U^m + ab1 U^{m-1} + ab2 U^{m-2}, adds it
+// to the compensated sum S and updates eta^{m+1} = eta^m - dt div(U_AB^m). Levels before
+// the start of the subcycle are passed as aliases of level 0.
+struct SesmLevels {
+    const float2 *u1, *u2, *u3;      // U^{m-1}, U^{m-2}, U^{m-3}
+    float2 *u0;                      // U^m (written when update != 0, else read)
+    const float *e0, *e1, *e2, *e3;  // eta^m, eta^{m-1}, eta^{m-2}, eta^{m-3}
+    float *enew;                     // eta^{m+1}
+    int update;                      // 1: compute U^m first
+    int vertex;                      // 1: continuity update (0 only in the closing launch)
+};
+
+template <int NONLIN>
+__global__ void __launch_bounds__(kSubstepMaxThreads)
+k_sesm(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 *__restrict__ sc,
+       const float2 *__restrict__ R, float2 *__restrict__ Shi, float2 *__restrict__ Slo,
+       const int *__restrict__ patch_slot, const int *__restrict__ patch_own, const int *__restrict__ patch_v,
+       const int *__restrict__ vcsr_off, const uint32_t *__restrict__ vcsr, const float *__restrict__ inv_av,
+       const float *__restrict__ patch_dt, SesmLevels L, StepArgs a, unsigned *__restrict__ status)
+{
+    extern __shared__ float sflux[];
+    const int p = blockIdx.x;
+    const float dt = patch_dt[p];
+    const int s0 = patch_slot[p];
+    const int n = patch_slot[p + 1] - s0;
+    const int nown = patch_own[p];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = s0 + i;
+        const int4 v = sv[s];
+        const float4 g = sg[s];
+        const float2 u1 = L.u1[s], u2 = L.u2[s];
+        float2 u0;
+        if (L.update) {
+            const float4 c = sc[s];
+            const float2 u3 = L.u3[s], r = R[s];
+            const float abx = a.ab0 * u1.x + a.ab1 * u2.x + a.ab2 * u3.x;
+            const float aby = a.ab0 * u1.y + a.ab1 * u2.y + a.ab2 * u3.y;
+            float em[3];
+            const int vv[3] = {v.x, v.y, v.z};
+#pragma unroll
+            for (int k = 0; k < 3; k++)
+                em[k] = a.am0 * L.e0[vv[k]] + a.am1 * L.e1[vv[k]] + a.am2 * L.e2[vv[k]] + a.am3 * L.e3[vv[k]];
+            const float d0 = em[0] - em[2], d1 = em[1] - em[2];
+            const float gx = d0 * g.x + d1 * g.z;
+            const float gy = d0 * g.y + d1 * g.w;
+            float H = c.y;
+            if (NONLIN) H += (em[0] + em[1] + em[2]) * (1.0f / 3.0f);
+            const float gH = a.g * H;
+            // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
+            u0.x = u1.x + dt * (c.z * aby - gH * gx + r.x);
+            u0.y = u1.y + dt * (-c.z * abx - gH * gy + r.y);
+            L.u0[s] = u0;
+        } else {
+            u0 = L.u0[s];
+        }
+        if (!L.vertex) continue;
+        const float fx = a.ab0 * u0.x + a.ab1 * u1.x + a.ab2 * u2.x;
+        const float fy = a.ab0 * u0.y + a.ab1 * u1.y + a.ab2 * u2.y;
+        if (i < nown) {
+            float2 hi = Shi[s], lo = Slo[s];
+            two_sum_acc(hi.x, lo.x, fx);
+            two_sum_acc(hi.y, lo.y, fy);
+            Shi[s] = hi;
+            Slo[s] = lo;
+        }
+        const float w = dt * sc[s].x;
+        const float c0 = w * (fx * g.x + fy * g.y);
+        const float c1 = w * (fx * g.z + fy * g.w);
+        sflux[3 * i + 0] = c0;
+        sflux[3 * i + 1] = c1;
+        sflux[3 * i + 2] = -(c0 + c1);
+    }
+    if (!L.vertex) return;
+    __syncthreads();
+    const int v1 = patch_v[p + 1];
+    bool bad = false;
+    for (int v = patch_v[p] + threadIdx.x; v < v1; v += blockDim.x) {
+        const int k1 = vcsr_off[v + 1];
+        float sum = 0.0f;
+        for (int k = vcsr_off[v]; k < k1; k++) {
+            const uint32_t q = vcsr[k];
+            sum += sflux[3 * (q >> 2) + (q & 3u)];
+        }
+        const float e = L.e0[v] + sum * inv_av[v];
+        L.enew[v] = e;
+        bad |= !(fabsf(e) <= a.eta_bound);
+    }
+    if (bad) atomicOr(status, 1u);
+}
+
 // End of a baroclinic step: <<U>> = S / M for owned slots, then S is cleared.
 __global__ void k_epilogue(const int4 *__restrict__ sv, float2 *__restrict__ Shi, float2 *__restrict__ Slo,
                            float2 *__restrict__ Umean, int nslot, float inv_M)
@@ -690,10 +786,41 @@ int raise_smem_limit(const void *fn)
 cudaError_t substep_smem_attr(const DevMesh &m)
 {
     const size_t need = sizeof(float) * 3 * (size_t)m.max_patch_slots;
-    const int l0 = raise_smem_limit((const void *)k_substep<0>);
-    const int l1 = raise_smem_limit((const void *)k_substep<1>);
-    if (l0 < 0 || l1 < 0 || (size_t)l0 < need || (size_t)l1 < need) return cudaErrorInvalidValue;
+    const void *fns[4] = {(const void *)k_substep<0>, (const void *)k_substep<1>, (const void *)k_sesm<0>,
+                          (const void *)k_sesm<1>};
+    for (const void *fn : fns) {
+        const int l = raise_smem_limit(fn);
+        if (l < 0 || (size_t)l < need) return cudaErrorInvalidValue;
+    }
     return cudaSuccess;
+}
+
+cudaError_t launch_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, const SesmPtrs &q, int block,
+                        cudaStream_t stream)
+{
+    const int threads = block > 0 ? block : 256;
+    const size_t smem = sizeof(float) * 3 * (size_t)m.max_patch_slots;
+    SesmLevels L;
+    L.u1 = q.u1;
+    L.u2 = q.u2;
+    L.u3 = q.u3;
+    L.u0 = q.u0;
+    L.e0 = q.e0;
+    L.e1 = q.e1;
+    L.e2 = q.e2;
+    L.e3 = q.e3;
+    L.enew = q.enew;
+    L.update = q.update;
+    L.vertex = q.vertex;
+    if (a.nonlinear_h)
+        k_sesm<1><<<m.npatch, threads, smem, stream>>>(m.slot_v, m.slot_g, m.slot_c, s.R, s.S_hi, s.S_lo,
+                                                       m.patch_slot, m.patch_own, m.patch_v, m.vcsr_off, m.vcsr,
+                                                       m.inv_av, m.patch_dt, L, a, s.status);
+    else
+        k_sesm<0><<<m.npatch, threads, smem, stream>>>(m.slot_v, m.slot_g, m.slot_c, s.R, s.S_hi, s.S_lo,
+                                                       m.patch_slot, m.patch_own, m.patch_v, m.vcsr_off, m.vcsr,
+                                                       m.inv_av, m.patch_dt, L, a, s.status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_step_epilogue(const DevMesh &m, const DevState &s, const StepArgs &a, cudaStream_t stream)

@@ -69,7 +69,8 @@ class Params:
     tau: float = 600.0
     M: int = 30
     nonlinear_h: int = 1
-    scheme: int = 0            # 0: dissipative forward-backward (Eq. 4.10)
+    scheme: int = 0            # 0: dissipative forward-backward (Eq. 4.10); 1: AB3-AM4 (Eqs. 4.7-4.8)
+    sesm: tuple = None         # (beta, delta, gamma, zeta) for scheme 1; None: the library's default
 
 
 @dataclasses.dataclass

@@ -60,7 +60,8 @@ class sesw_mesh(ctypes.Structure):
 class sesw_params(ctypes.Structure):
     _fields_ = [("g", ctypes.c_double), ("theta", ctypes.c_double), ("tau", ctypes.c_double),
                 ("M", ctypes.c_int32), ("nonlinear_h", ctypes.c_int32), ("scheme", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("eta_bound", ctypes.c_double)]
+                ("flags", ctypes.c_int32), ("eta_bound", ctypes.c_double), ("sesm_beta", ctypes.c_double),
+                ("sesm_delta", ctypes.c_double), ("sesm_gamma", ctypes.c_double), ("sesm_zeta", ctypes.c_double)]
 
 
 class sesw_info(ctypes.Structure):
@@ -297,8 +298,9 @@ class Subcycle:
 
 
 def _params_struct(p, flags=0, eta_bound=0.0):
+    coef = getattr(p, "sesm", None) or (0.0, 0.0, 0.0, 0.0)
     return sesw_params(float(p.g), float(p.theta), float(p.tau), int(p.M), int(p.nonlinear_h),
-                       int(getattr(p, "scheme", 0)), int(flags), float(eta_bound))
+                       int(getattr(p, "scheme", 0)), int(flags), float(eta_bound), *(float(x) for x in coef))
 
 
 def _mesh_struct(mesh):

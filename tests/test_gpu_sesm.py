@@ -1,0 +1,127 @@
+"""SESM substep (AB3-AM4, Eqs. 4.7-4.8) on the GPU against the FP64 oracle, same tolerance rule
+as the SE path: within twice the drift of the FP32 build of the oracle, plus a floor of 8 ulp."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import closed
+from oracle import runner as orc
+from paper_2311_08241_gb300 import inputs as I
+from parity_util import ENVELOPE_FACTOR, GRAPH, PERSISTENT, ULP_FLOOR, _maxabs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_2311_08241_gb300 import sesw
+
+    sesw.load()
+    return sesw
+
+
+def _sesm(case, theta=0.14):
+    p = case.params
+    case.params = I.Params(g=p.g, theta=theta, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h, scheme=1)
+    return closed.sesm_params(theta / 2.0)
+
+
+def _run(S, case, nsteps):
+    with S.Subcycle() as s:
+        s.sesw_set_mode(GRAPH)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_set_forcing(case.R)
+        s.sesw_set_state(case.eta0, case.U0)
+        s.sesw_advance(nsteps)
+        info = s.sesw_get_info()
+        return s.sesw_get_state(), info
+
+
+def _check(case, coef, got, nsteps, what):
+    ref = orc.OracleMesh(case.mesh).advance_sesm(case.R, case.params, coef, nsteps, case.eta0, case.U0)
+    r32 = orc.OracleMesh(case.mesh, orc.lib_fp32()).advance_sesm(case.R, case.params, coef, nsteps, case.eta0,
+                                                                   case.U0)
+    for k, name in enumerate(("eta", "U", "<<U>>")):
+        scale = max(_maxabs(ref[k]), 1e-30)
+        err = _maxabs(got[k] - ref[k])
+        env = _maxabs(r32[k] - ref[k])
+        tol = ENVELOPE_FACTOR * env + ULP_FLOOR * scale
+        print(f"{what} {name}: err {err:.3e} env32 {env:.3e} tol {tol:.3e}")
+        assert err <= tol, f"{what} {name}: err {err:.3e} > tol {tol:.3e}"
+    return ref
+
+
+@pytest.mark.parametrize("name", ["basin", "tiny", "channel", "sphere6"])
+def test_sesm_matches_oracle(S, name):
+    case = {"basin": lambda: I.basin_case(nsteps=5),
+            "tiny": lambda: I.tiny_jittered_case(nx=21, ny=15, seed=5, M=7, tau=70.0),
+            "channel": lambda: I.channel_case(nsteps=10),
+            "sphere6": lambda: I.sphere_case(level=6, nsteps=5)}[name]()
+    coef = _sesm(case)
+    (got, info) = _run(S, case, case.nsteps)
+    assert info["mode"] == GRAPH
+    _check(case, coef, got, case.nsteps, name)
+
+
+def test_sesm_periodic_wave_closed_form(S):
+    case = I.periodic_wave_case(n=32, kx=3, ky=1, nsteps=4, M=30, tau=450.0)
+    coef = _sesm(case)
+    (eta, U, Um), _ = _run(S, case, case.nsteps)
+    p = case.params
+    u, e = closed.sesm_mode_amplitude(closed.kappa2_square(32, 10e3, 3, 1), p.g * 4000.0, p.tau / p.M, coef, p.M,
+                                      case.nsteps)
+    assert np.max(np.abs(eta - e * case.eta0)) < 1e-5
+
+
+def test_sesm_summation_identity_and_volume(S):
+    case = I.basin_case(nsteps=1)
+    _sesm(case)
+    om = orc.OracleMesh(case.mesh)
+    av, _ = om.areas()
+    with S.Subcycle() as s:
+        s.sesw_set_mode(GRAPH)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_set_state(case.eta0, case.U0)
+        prev = s.sesw_get_state()[0]
+        for _ in range(6):
+            s.sesw_advance(1)
+            eta, U, Um = s.sesw_get_state()
+            assert np.max(np.abs((eta - prev) + case.params.tau * om.divergence(Um))) < 2e-5
+            prev = eta
+        vol, _ = s.sesw_diagnostics()
+    v0 = float(np.sum(av * case.eta0))
+    bound = 4 * 2.0 ** -24 * math.sqrt(6 * case.params.M) * math.sqrt(float(np.sum((av * case.eta0) ** 2)))
+    assert abs(vol - v0) <= bound
+
+
+def test_sesm_rules(S):
+    case = I.tiny_jittered_case()
+    _sesm(case)
+    with S.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload(case.mesh)
+        with pytest.raises(S.SeswError, match="SESW_MODE_GRAPH"):
+            s.sesw_set_params(case.params)
+    with S.Subcycle() as s:
+        s.sesw_set_mode(GRAPH)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        lim = s.sesw_get_info()["courant_limit"]
+    # the library's limit equals the spectral-radius limit of the per-mode matrix (numpy eigenvalues)
+    coef = closed.sesm_params(0.07)
+    lo, hi = 0.0, 4.0
+    for _ in range(50):
+        mid = 0.5 * (lo + hi)
+        A = closed.sesm_lattice_matrix(mid * mid, 1.0, 1.0, *coef)
+        if np.max(np.abs(np.linalg.eigvals(A))) <= 1 + 1e-9:
+            lo = mid
+        else:
+            hi = mid
+    assert abs(lim - lo) < 2e-3, (lim, lo)
