@@ -242,6 +242,17 @@ int sesw_advance(sesw_ctx *ctx, int32_t nsteps);
  * copies are only enqueued. */
 int sesw_get_state(sesw_ctx *ctx, double *eta, double *U, double *Umean, int where);
 
+/* Keep (enable = 1) or stop keeping (0) the step-mean elevation
+ * eta_bar = (1/M) sum_{m=0..M-1} eta^m of every baroclinic step (SE scheme): the time
+ * mean that enters the exactly summed momentum equation of a step,
+ * U^M - U^0 + tau [ f e_z x S' + g H grad(eta_bar) - R ] = 0 (linear H), with
+ * S' = <<U>> - (theta/M)(U^M - U^0) + (U^0 - U^M)/(2M). Costs one read-modify-write per
+ * vertex and substep while enabled. */
+int sesw_set_eta_mean(sesw_ctx *ctx, int32_t enable);
+
+/* Copy out eta_bar of the last step [nv] in caller order (host: synchronises). */
+int sesw_get_eta_mean(sesw_ctx *ctx, double *eta_mean, int where);
+
 /* FP64 diagnostics of the current state: volume sum_v A_v eta_v (m^3) and energy
  * sum_v A_v g eta_v^2/2 + sum_e A_e |U_e|^2 / (2 H_e) (m^5/s^2). Synchronises. */
 int sesw_diagnostics(sesw_ctx *ctx, double *volume, double *energy);
@@ -278,6 +289,62 @@ int sesw_diagnostics_batch(sesw_ctx *ctx, double *volume, double *energy);
 int sesw_diagnostics_noalloc(int64_t nv, int64_t ne, const double *area_v, const double *eta,
                              const double *area_e, const double *h_e, const double *U, double g,
                              double *out, void *cuda_stream);
+
+/* ---- Learned surrogate of one baroclinic step (SE scheme, single mesh).
+ * The paper has no surrogate. A message-passing network (3 layers, width 64, bfloat16
+ * weights, float accumulation; vertex inputs eta/s_eta and H0/s_H; element inputs U/s_U,
+ * R/s_R, f/s_f and H0_e/s_H; each layer updates elements from the P1 gradients of the
+ * vertex features and vertices from the area-weighted mean of the element features)
+ * predicts the increments of <<U>> (Eq. 4.12), of U^M and of the step-mean elevation
+ * eta_bar over one step. Its kernels (forward, backward, Adam) run on the context's
+ * stream. Scales s = (eta, H, U, R, f, L, out_U, out_eta): L multiplies the P1 gradients;
+ * out_U and out_eta scale the two output groups. Samples live on the device in the
+ * library's order; inputs in caller order are converted on the way in. */
+
+/* Create the surrogate for the uploaded mesh with room for `capacity` samples;
+ * weights Glorot-uniform from `seed`, scales 1. Replaces an existing surrogate. */
+int sesw_surrogate_init(sesw_ctx *ctx, int32_t capacity, int32_t seed);
+/* Number of parameters (floats). */
+int sesw_surrogate_nparam(sesw_ctx *ctx, int64_t *nparam);
+/* Read (get != NULL) and/or replace (set != NULL) the float master weights [nparam], host. */
+int sesw_surrogate_weights(sesw_ctx *ctx, float *get, const float *set);
+/* Read (get) and/or replace (set) the 8 scales, host doubles; scales must be > 0. */
+int sesw_surrogate_scales(sesw_ctx *ctx, double *get, const double *set);
+/* Store sample `index`: inputs eta [nv], U [ne][2], R [ne][2] and targets
+ * <<U>> - U [ne][2], U^M - U [ne][2], eta_bar - eta [nv], caller order, doubles at `where`. */
+int sesw_surrogate_set_sample(sesw_ctx *ctx, int64_t index, const double *eta, const double *U,
+                              const double *R, const double *d_umean, const double *d_um,
+                              const double *d_etabar, int where);
+/* Store the context's current state and forcing as the inputs of sample `index`
+ * (call before sesw_advance(ctx, 1)) ... */
+int sesw_surrogate_record_input(sesw_ctx *ctx, int64_t index);
+/* ... and the result of that step as its targets (needs sesw_set_eta_mean(ctx, 1)). */
+int sesw_surrogate_record_target(sesw_ctx *ctx, int64_t index);
+/* Set the scales from the RMS of samples [0, nsamples) (eta, U, R, both output groups),
+ * the largest |H0_e| and |f|, and length_scale for L. */
+int sesw_surrogate_fit_scales(sesw_ctx *ctx, int64_t nsamples, double length_scale);
+/* One Adam step (learning_rate, betas 0.9/0.999, eps 1e-8) per listed sample, in order;
+ * mean_loss (may be NULL) receives the mean of the losses before each step. The loss
+ * is the mean squared error of the normalised outputs over elements and channels plus
+ * that over vertices. */
+int sesw_surrogate_train(sesw_ctx *ctx, const int64_t *indices, int32_t n, double learning_rate,
+                         double *mean_loss);
+/* Mean loss of the listed samples without training. */
+int sesw_surrogate_loss(sesw_ctx *ctx, const int64_t *indices, int32_t n, double *mean_loss);
+/* Loss of sample `index` and its gradient with respect to the weights [nparam] (host). */
+int sesw_surrogate_gradient(sesw_ctx *ctx, int64_t index, float *grad, double *loss);
+/* Normalised outputs for sample `index`, caller order: out_e [ne][4], out_v [nv] (host). */
+int sesw_surrogate_predict(sesw_ctx *ctx, int64_t index, double *out_e, double *out_v);
+/* Advance nsteps steps with the surrogate. Each step applies the predicted <<U>> and U^M,
+ * sets eta^{n+1} = eta^n - tau div <<U>> (exact volume, Eq. 4.11 holds), and measures the
+ * residual of the step's exactly summed momentum equation,
+ *   r = U^M - U^0 + tau [ f e_z x S' + g H grad(eta_bar) - R ],
+ *   S' = <<U>> - (theta/M)(U^M - U^0) + (U^0 - U^M)/(2M),
+ * as sqrt(sum A |r|^2 / sum A |U^M - U^0|^2). A step whose residual exceeds resid_tol is
+ * undone and taken by the plain subcycle; *n_fallback counts those steps and
+ * *last_resid receives the last residual (either may be NULL). Synchronises per step. */
+int sesw_surrogate_advance(sesw_ctx *ctx, int32_t nsteps, double resid_tol, int32_t *n_fallback,
+                           double *last_resid);
 
 /* Synchronise and return SESW_OK, SESW_EUNSTABLE or SESW_ETIMEOUT from the device
  * status word; clears the word. */

@@ -361,10 +361,12 @@ int oracle_diagnostics(void *hm, const double *eta, const double *U, double g, i
  *   U      ne*2, in: U^0 of the first step (the carried <U>^n), out: U^M of the last
  *   Umean  ne*2, out: <<U>> of the last step (Eq. 4.12)
  *   diag   NULL or nsteps*2: (volume, energy) after each step
+ *   eta_mean_out  NULL or nv: (1/M) sum_{m=0..M-1} eta^m of the last step
  * Returns 0, or -4 on allocation failure, -5 if M < 1.
  */
 int oracle_advance(void *hm, const double *R_in, double g_in, double theta_in, double tau, int M,
-                   int nonlinear_h, int nsteps, double *eta_io, double *U_io, double *Umean_out, double *diag)
+                   int nonlinear_h, int nsteps, double *eta_io, double *U_io, double *Umean_out, double *diag,
+                   double *eta_mean_out)
 {
     omesh *m = (omesh *)hm;
     if (M < 1) return -5;
@@ -389,7 +391,11 @@ int oracle_advance(void *hm, const double *R_in, double g_in, double theta_in, d
     for (int n = 0; n < nsteps; n++) {
         memcpy(U0, U, sizeof(real) * 2 * (size_t)ne);
         memset(sumU, 0, sizeof(real) * 2 * (size_t)ne);
+        if (eta_mean_out)
+            for (int v = 0; v < nv; v++) eta_mean_out[v] = 0.0;
         for (int s = 0; s < M; s++) {
+            if (eta_mean_out)
+                for (int v = 0; v < nv; v++) eta_mean_out[v] += (double)eta[v] / (double)M;
             /* momentum: Crank-Nicolson Coriolis, pressure at eta^m with H^m, frozen R */
             #pragma omp parallel for schedule(static)
             for (int e = 0; e < ne; e++) {

@@ -49,7 +49,7 @@ def _bind(path):
     L.oracle_gradient.argtypes = [P, P, P]
     L.oracle_divergence.argtypes = [P, P, P]
     L.oracle_diagnostics.argtypes = [P, P, P, D, I, ctypes.POINTER(D), ctypes.POINTER(D)]
-    L.oracle_advance.argtypes = [P, P, D, D, D, I, I, I, P, P, P, P]
+    L.oracle_advance.argtypes = [P, P, D, D, D, I, I, I, P, P, P, P, P]
     L.oracle_set_threads.argtypes = [I]
     L.oracle_advance_sesm.argtypes = [P, P, D, D, D, D, D, D, I, I, I, P, P, P]
     L.oracle_advance_sesm.restype = I
@@ -185,19 +185,24 @@ class OracleMesh:
                                  ctypes.byref(v), ctypes.byref(e))
         return v.value, e.value
 
-    def advance(self, R, params, nsteps, eta, U, want_diag=False):
-        """Advance nsteps baroclinic steps. Returns (eta, U, Umean, diag or None); inputs untouched."""
+    def advance(self, R, params, nsteps, eta, U, want_diag=False, want_eta_mean=False):
+        """Advance nsteps baroclinic steps. Returns (eta, U, Umean, diag or None) and, with
+        want_eta_mean, the step-mean elevation of the last step as a fifth item; inputs untouched."""
         R = np.ascontiguousarray(R, dtype=np.float64)
         eta = np.array(eta, dtype=np.float64, copy=True)
         U = np.array(U, dtype=np.float64, copy=True)
         Umean = np.zeros((self.ne, 2))
         diag = np.zeros((max(nsteps, 1), 2)) if want_diag else None
+        emean = np.zeros(self.nv) if want_eta_mean else None
         rc = self._L.oracle_advance(self._h, _p(R), float(params.g), float(params.theta),
                                   float(params.tau), int(params.M), int(params.nonlinear_h),
                                   int(nsteps), _p(eta), _p(U), _p(Umean),
-                                  _p(diag) if diag is not None else None)
+                                  _p(diag) if diag is not None else None,
+                                  _p(emean) if emean is not None else None)
         if rc:
             raise RuntimeError(f"oracle_advance failed ({rc})")
+        if want_eta_mean:
+            return eta, U, Umean, diag, emean
         return eta, U, Umean, diag
 
 

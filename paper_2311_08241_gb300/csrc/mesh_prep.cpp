@@ -332,9 +332,11 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
 
     out.inv_av.resize(nv);
     out.area_v.resize(nv);
+    out.h0_v.resize(nv);
     for (int i = 0; i < nv; i++) {
         out.area_v[i] = Av[vperm[i]];
         out.inv_av[i] = (float)(1.0 / Av[vperm[i]]);
+        out.h0_v[i] = (float)m.depth[vperm[i]];
     }
     out.area_e.resize(ne);
     out.h0_e.resize(ne);
@@ -419,6 +421,7 @@ void concat_meshes(std::vector<HostMesh> &parts, HostMesh &out)
         for (int v = 1; v <= h.nv; v++) out.vcsr_off.push_back(h.vcsr_off[v] + co);
         out.vcsr.insert(out.vcsr.end(), h.vcsr.begin(), h.vcsr.end());
         out.inv_av.insert(out.inv_av.end(), h.inv_av.begin(), h.inv_av.end());
+        out.h0_v.insert(out.h0_v.end(), h.h0_v.begin(), h.h0_v.end());
         out.area_v.insert(out.area_v.end(), h.area_v.begin(), h.area_v.end());
         out.area_e.insert(out.area_e.end(), h.area_e.begin(), h.area_e.end());
         out.h0_e.insert(out.h0_e.end(), h.h0_e.begin(), h.h0_e.end());

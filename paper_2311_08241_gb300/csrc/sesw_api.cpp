@@ -13,39 +13,6 @@
 
 #include "sesw_internal.h"
 
-struct sesw_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    cudaStream_t cap_stream = nullptr;
-    sesw_alloc_fn alloc = nullptr;
-    sesw_free_fn free_fn = nullptr;
-    void *user = nullptr;
-    std::string err;
-    int patch_vertices = 256;
-    int block_threads = 256;
-    int mode_req = SESW_MODE_AUTO, mode = SESW_MODE_GRAPH;
-    int blocks_per_sm = 0;         // persistent mode; 0 = try 2, then 1
-    sesw::PersistentPlan plan;
-    bool persist_graph_ok = true;
-    bool have_mesh = false, have_params = false;
-    sesw::DevMesh dm;
-    sesw::DevState ds;
-    std::vector<std::pair<void *, size_t>> allocs;
-    int64_t device_bytes = 0;
-    sesw_params params{};
-    sesw::StepArgs args{};
-    int parity = 0;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int diag_blocks = 1;
-    double grad_gram_max_h = 0.0;
-    double courant_max = 0.0, courant_limit = 0.0;
-    int npatch = 0, nslot = 0, max_patch_slots = 0, patch_vertices_used = 0;
-    int nbasin = 1;
-    std::vector<int> patch_basin;
-    std::vector<double> basin_stiffness;
-    std::vector<float> patch_dt_host;
-};
-
 namespace {
 
 struct DeviceGuard {
@@ -148,7 +115,9 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     cudaGraph_t g = nullptr;
     CK(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
-    if (c->mode == SESW_MODE_PERSISTENT) {
+    if (c->ds.eta_sum) e = cudaMemsetAsync(c->ds.eta_sum, 0, sizeof(float) * (size_t)c->dm.nv, c->cap_stream);
+    if (e != cudaSuccess) {
+    } else if (c->mode == SESW_MODE_PERSISTENT) {
         e = sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->plan, c->cap_stream);
     } else if (c->params.scheme == 1) {
         // SESM: level rings, U^m in B[m % 3] (B[0] holds U^0 and, at the end, U^M) and
@@ -278,6 +247,13 @@ double sesm_stability_limit(const double ab[3], const double am[4])
 }
 
 }  // namespace
+
+namespace sesw {
+int ctx_fail(sesw_ctx *c, int code, const std::string &msg) { return fail(c, code, msg); }
+int ctx_fail_cuda(sesw_ctx *c, const char *what, cudaError_t e) { return fail_cuda(c, what, e); }
+void *ctx_alloc(sesw_ctx *c, size_t bytes) { return dalloc(c, bytes); }
+int ctx_enqueue_step(sesw_ctx *c) { return enqueue_step(c); }
+}  // namespace sesw
 
 extern "C" {
 
@@ -438,6 +414,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
 
     CK(c, cudaStreamSynchronize(c->stream));
     drop_graphs(c);
+    sesw::surrogate_release(c);
     free_all(c);
     c->have_mesh = c->have_params = false;
 
@@ -457,6 +434,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     TRY(upload(c, &d.vcsr_off, hm.vcsr_off, "vcsr_off"));
     TRY(upload(c, &d.vcsr, hm.vcsr, "vcsr"));
     TRY(upload(c, &d.inv_av, hm.inv_av, "inv_av"));
+    TRY(upload(c, &d.h0_v, hm.h0_v, "h0_v"));
     TRY(upload(c, &d.area_v, hm.area_v, "area_v"));
     TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
@@ -778,6 +756,35 @@ int sesw_diagnostics_batch(sesw_ctx *c, double *volume, double *energy)
     return SESW_OK;
 }
 
+int sesw_set_eta_mean(sesw_ctx *c, int32_t enable)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh first");
+    if (c->params.scheme == 1 && enable) return fail(c, SESW_EINVAL, "the step-mean elevation is kept for the SE scheme");
+    DeviceGuard dg(c->device);
+    if (enable && !c->ds.eta_sum) TRY(zalloc(c, &c->ds.eta_sum, c->dm.nv, "eta_sum"));
+    if (!enable) c->ds.eta_sum = nullptr;      // the buffer stays with the context until the next upload
+    drop_graphs(c);
+    if (c->mode == SESW_MODE_PERSISTENT) c->persist_graph_ok = true;
+    return SESW_OK;
+}
+
+int sesw_get_eta_mean(sesw_ctx *c, double *eta_mean, int where)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->ds.eta_sum) return fail(c, SESW_ESTATE, "enable the step-mean elevation before advancing");
+    if (!eta_mean) return fail(c, SESW_EINVAL, "eta_mean is NULL");
+    if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    DeviceGuard dg(c->device);
+    double *dst = where == SESW_HOST ? c->ds.stage : eta_mean;
+    CK(c, sesw::launch_gather_scaled(c->dm, c->ds.eta_sum, (double)c->args.inv_M, dst, c->stream));
+    if (where == SESW_HOST) {
+        CK(c, cudaMemcpyAsync(eta_mean, dst, sizeof(double) * (size_t)c->dm.nv, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    return SESW_OK;
+}
+
 int sesw_status(sesw_ctx *c)
 {
     if (!c) return SESW_EINVAL;
@@ -864,6 +871,7 @@ void sesw_destroy(sesw_ctx *c)
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
         drop_graphs(c);
+        sesw::surrogate_release(c);
         free_all(c);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
         cudaGetLastError();

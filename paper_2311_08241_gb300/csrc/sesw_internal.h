@@ -40,6 +40,7 @@ struct HostMesh {
     std::vector<int> vcsr_off;     // [nv+1] incidence list of each vertex
     std::vector<uint32_t> vcsr;    // (local slot << 2) | corner, local to the vertex's patch
     std::vector<float> inv_av;     // 1 / median-dual area
+    std::vector<float> h0_v;       // rest depth at vertices (new order)
     std::vector<double> area_v;    // median-dual area (FP64, for diagnostics)
     std::vector<double> area_e;    // element area (FP64), new element order
     std::vector<double> h0_e;      // element rest depth (FP64), new element order
@@ -96,6 +97,7 @@ struct DevMesh {
     int *vcsr_off = nullptr;
     uint32_t *vcsr = nullptr;
     float *inv_av = nullptr;
+    float *h0_v = nullptr;
     double *area_v = nullptr;
     int *vperm = nullptr;
     int *eperm = nullptr;
@@ -138,6 +140,8 @@ struct DevState {
     // extra transport levels per slot (U is the third)
     float *eta_x[3] = {nullptr, nullptr, nullptr};
     float2 *U_x[2] = {nullptr, nullptr};
+    // optional sum of eta^0 .. eta^{M-1} over the last step (SE; cleared at each step start)
+    float *eta_sum = nullptr;
 };
 
 // Level pointers of one SESM launch (see k_sesm).
@@ -173,6 +177,7 @@ cudaError_t launch_scatter_state(const DevMesh &m, const DevState &s, const doub
                                  const double *U, int parity, cudaStream_t stream);
 cudaError_t launch_scatter_forcing(const DevMesh &m, const DevState &s, const double *R,
                                    cudaStream_t stream);
+cudaError_t launch_gather_scaled(const DevMesh &m, const float *x, double scale, double *out, cudaStream_t stream);
 cudaError_t launch_gather_state(const DevMesh &m, const DevState &s, int parity, double *eta,
                                 double *U, double *Umean, cudaStream_t stream);
 cudaError_t launch_diagnostics(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
@@ -196,4 +201,50 @@ size_t persistent_flag_bytes(int npatch);
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                               const PersistentPlan &plan, cudaStream_t stream);
 
+struct Surrogate;
+void surrogate_release(sesw_ctx *c);
+
+}  // namespace sesw
+
+// The context behind the C-ABI handle.
+struct sesw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    sesw_alloc_fn alloc = nullptr;
+    sesw_free_fn free_fn = nullptr;
+    void *user = nullptr;
+    std::string err;
+    int patch_vertices = 256;
+    int block_threads = 256;
+    int mode_req = SESW_MODE_AUTO, mode = SESW_MODE_GRAPH;
+    int blocks_per_sm = 0;         // persistent mode; 0 = try 2, then 1
+    sesw::PersistentPlan plan;
+    bool persist_graph_ok = true;
+    bool have_mesh = false, have_params = false;
+    sesw::DevMesh dm;
+    sesw::DevState ds;
+    std::vector<std::pair<void *, size_t>> allocs;
+    int64_t device_bytes = 0;
+    sesw_params params{};
+    sesw::StepArgs args{};
+    int parity = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int diag_blocks = 1;
+    double grad_gram_max_h = 0.0;
+    double courant_max = 0.0, courant_limit = 0.0;
+    int npatch = 0, nslot = 0, max_patch_slots = 0, patch_vertices_used = 0;
+    int nbasin = 1;
+    std::vector<int> patch_basin;
+    std::vector<double> basin_stiffness;
+    std::vector<float> patch_dt_host;
+    sesw::Surrogate *sur = nullptr;
+};
+
+namespace sesw {
+// Helpers of sesw_api.cpp for other translation units.
+int ctx_fail(sesw_ctx *c, int code, const std::string &msg);
+int ctx_fail_cuda(sesw_ctx *c, const char *what, cudaError_t e);
+void *ctx_alloc(sesw_ctx *c, size_t bytes);
+int ctx_enqueue_step(sesw_ctx *c);
 }  // namespace sesw

@@ -56,7 +56,7 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
           const int *__restrict__ patch_v, const int *__restrict__ vcsr_off,
           const uint32_t *__restrict__ vcsr, const float *__restrict__ inv_av,
           const float *__restrict__ eta_in, float *__restrict__ eta_out, const float *__restrict__ patch_dt,
-          StepArgs a, unsigned *__restrict__ status)
+          float *__restrict__ eta_sum, StepArgs a, unsigned *__restrict__ status)
 {
     extern __shared__ float sflux[];
     const int p = blockIdx.x;
@@ -115,6 +115,7 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
             sum += sflux[3 * (q >> 2) + (q & 3u)];
         }
         const float e = eta_in[v] + sum * inv_av[v];
+        if (eta_sum) eta_sum[v] += eta_in[v];     // sum of eta^0 .. eta^{M-1} (time mean of the step)
         eta_out[v] = e;
         bad |= !(fabsf(e) <= a.eta_bound);
     }
@@ -247,6 +248,13 @@ __global__ void k_scatter_slots(const int4 *__restrict__ sv, const int *__restri
         const int e = eperm[w >= 0 ? w : -1 - w];
         out[s] = make_float2((float)in[2 * (size_t)e], (float)in[2 * (size_t)e + 1]);
     }
+}
+
+__global__ void k_gather_scaled(const int *__restrict__ vperm, const float *__restrict__ x, double scale,
+                                double *__restrict__ out, int nv)
+{
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+        out[vperm[v]] = (double)x[v] * scale;
 }
 
 __global__ void k_gather(const int4 *__restrict__ sv, const int *__restrict__ vperm, const int *__restrict__ eperm,
@@ -403,6 +411,7 @@ struct PArgs {
     const float *patch_dt;
     const float *eta_in;
     float *eta_out;
+    float *eta_sum;         // null, or sum over the substeps of eta^0 .. eta^{M-1} (own vertices)
     float *xb[2];
     unsigned *flags;        // [npatch], then the abort word
     unsigned *status;
@@ -631,6 +640,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                 inv = P.inv_av[v0 + i];
             }
             const float e = seta[i] + sum * inv;
+            if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
             seta[i] = e;
             if (more) __stcg(xout + v0 + i, e);
             bad |= !(fabsf(e) <= a.eta_bound);
@@ -743,11 +753,11 @@ cudaError_t launch_substep(const DevMesh &m, const DevState &s, const StepArgs &
     if (a.nonlinear_h)
         k_substep<1><<<m.npatch, threads, smem, stream>>>(
             m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
-            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, a, s.status);
+            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, s.eta_sum, a, s.status);
     else
         k_substep<0><<<m.npatch, threads, smem, stream>>>(
             m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
-            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, a, s.status);
+            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, s.eta_sum, a, s.status);
     return cudaGetLastError();
 }
 
@@ -848,6 +858,12 @@ cudaError_t launch_scatter_forcing(const DevMesh &m, const DevState &s, const do
     return cudaGetLastError();
 }
 
+cudaError_t launch_gather_scaled(const DevMesh &m, const float *x, double scale, double *out, cudaStream_t stream)
+{
+    k_gather_scaled<<<grid_for(m.nv, kAuxThreads), kAuxThreads, 0, stream>>>(m.vperm, x, scale, out, m.nv);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather_state(const DevMesh &m, const DevState &s, int parity, double *eta, double *U,
                                 double *Umean, cudaStream_t stream)
 {
@@ -944,6 +960,7 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     P.patch_dt = m.patch_dt;
     P.eta_in = s.eta[parity];
     P.eta_out = s.eta[parity ^ 1];
+    P.eta_sum = s.eta_sum;
     P.xb[0] = s.xbuf[0];
     P.xb[1] = s.xbuf[1];
     P.flags = s.flags;

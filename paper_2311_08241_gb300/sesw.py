@@ -39,8 +39,12 @@ EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_blocks_p
            "sesw_set_block_threads",
            "sesw_mesh_upload", "sesw_mesh_upload_batch", "sesw_set_params_batch", "sesw_diagnostics_batch",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
-           "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_status", "sesw_mesh_check",
-           "sesw_get_info", "sesw_last_error", "sesw_destroy")
+           "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_set_eta_mean", "sesw_get_eta_mean", "sesw_status", "sesw_mesh_check",
+           "sesw_get_info", "sesw_last_error", "sesw_destroy",
+           "sesw_surrogate_init", "sesw_surrogate_nparam", "sesw_surrogate_weights", "sesw_surrogate_scales",
+           "sesw_surrogate_set_sample", "sesw_surrogate_record_input", "sesw_surrogate_record_target",
+           "sesw_surrogate_fit_scales", "sesw_surrogate_train", "sesw_surrogate_loss", "sesw_surrogate_gradient",
+           "sesw_surrogate_predict", "sesw_surrogate_advance")
 SESW_NOALLOC_MAX_CHUNKS = 8192
 SESW_NOALLOC_MAX_ITEMS = SESW_NOALLOC_MAX_CHUNKS * 4096
 
@@ -113,10 +117,27 @@ def load(build_if_missing: bool = True):
         L.sesw_get_state.argtypes = [P, P, P, P, I]
         L.sesw_diagnostics.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.sesw_status.argtypes = [P]
+        L.sesw_set_eta_mean.argtypes = [P, ctypes.c_int32]
+        L.sesw_get_eta_mean.argtypes = [P, P, I]
         L.sesw_diagnostics_noalloc.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, P, D, P, P]
         L.sesw_get_info.argtypes = [P, ctypes.POINTER(sesw_info)]
         L.sesw_mesh_check.argtypes = [ctypes.POINTER(sesw_mesh), ctypes.c_int32, ctypes.POINTER(sesw_info),
                                       ctypes.c_char_p, ctypes.c_size_t]
+        I64 = ctypes.c_int64
+        L.sesw_surrogate_init.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
+        L.sesw_surrogate_nparam.argtypes = [P, ctypes.POINTER(I64)]
+        L.sesw_surrogate_weights.argtypes = [P, P, P]
+        L.sesw_surrogate_scales.argtypes = [P, P, P]
+        L.sesw_surrogate_set_sample.argtypes = [P, I64, P, P, P, P, P, P, I]
+        L.sesw_surrogate_record_input.argtypes = [P, I64]
+        L.sesw_surrogate_record_target.argtypes = [P, I64]
+        L.sesw_surrogate_fit_scales.argtypes = [P, I64, D]
+        L.sesw_surrogate_train.argtypes = [P, P, ctypes.c_int32, D, ctypes.POINTER(D)]
+        L.sesw_surrogate_loss.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(D)]
+        L.sesw_surrogate_gradient.argtypes = [P, I64, P, ctypes.POINTER(D)]
+        L.sesw_surrogate_predict.argtypes = [P, I64, P, P]
+        L.sesw_surrogate_advance.argtypes = [P, ctypes.c_int32, D, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(D)]
         L.sesw_last_error.argtypes = [P]
         L.sesw_last_error.restype = ctypes.c_char_p
         L.sesw_destroy.argtypes = [P]
@@ -282,6 +303,82 @@ class Subcycle:
         where = _where(next(x for x in (eta, U, Umean) if x is not None))
         self._check(self._L.sesw_get_state(self._h, _ptr(eta), _ptr(U), _ptr(Umean), where))
         return eta, U, Umean
+
+    def sesw_set_eta_mean(self, enable: bool = True):
+        return self._check(self._L.sesw_set_eta_mean(self._h, int(bool(enable))))
+
+    def sesw_get_eta_mean(self, out=None):
+        if out is None:
+            out = np.empty(self.nv)
+        self._check(self._L.sesw_get_eta_mean(self._h, _ptr(out), _where(out)))
+        return out
+
+    # -- surrogate
+    def sesw_surrogate_init(self, capacity: int, seed: int = 0):
+        return self._check(self._L.sesw_surrogate_init(self._h, int(capacity), int(seed)))
+
+    def sesw_surrogate_nparam(self):
+        n = ctypes.c_int64()
+        self._check(self._L.sesw_surrogate_nparam(self._h, ctypes.byref(n)))
+        return n.value
+
+    def sesw_surrogate_weights(self, set=None):
+        w = np.empty(self.sesw_surrogate_nparam(), dtype=np.float32)
+        s = None if set is None else np.ascontiguousarray(set, dtype=np.float32)
+        self._check(self._L.sesw_surrogate_weights(self._h, _ptr(w), _ptr(s)))
+        return w
+
+    def sesw_surrogate_scales(self, set=None):
+        g = np.empty(8)
+        s = None if set is None else np.ascontiguousarray(set, dtype=np.float64)
+        self._check(self._L.sesw_surrogate_scales(self._h, _ptr(g), _ptr(s)))
+        return g
+
+    def sesw_surrogate_set_sample(self, index, eta, U, R, d_umean, d_um, d_etabar):
+        arrs = [_as_f64(x) for x in (eta, U, R, d_umean, d_um, d_etabar)]
+        return self._check(self._L.sesw_surrogate_set_sample(self._h, int(index), *[_ptr(a) for a in arrs],
+                                                             _where(arrs[0])))
+
+    def sesw_surrogate_record_input(self, index):
+        return self._check(self._L.sesw_surrogate_record_input(self._h, int(index)))
+
+    def sesw_surrogate_record_target(self, index):
+        return self._check(self._L.sesw_surrogate_record_target(self._h, int(index)))
+
+    def sesw_surrogate_fit_scales(self, nsamples, length_scale):
+        return self._check(self._L.sesw_surrogate_fit_scales(self._h, int(nsamples), float(length_scale)))
+
+    def sesw_surrogate_train(self, indices, learning_rate):
+        idx = np.ascontiguousarray(indices, dtype=np.int64)
+        loss = ctypes.c_double()
+        self._check(self._L.sesw_surrogate_train(self._h, _ptr(idx), len(idx), float(learning_rate),
+                                                 ctypes.byref(loss)))
+        return loss.value
+
+    def sesw_surrogate_loss(self, indices):
+        idx = np.ascontiguousarray(indices, dtype=np.int64)
+        loss = ctypes.c_double()
+        self._check(self._L.sesw_surrogate_loss(self._h, _ptr(idx), len(idx), ctypes.byref(loss)))
+        return loss.value
+
+    def sesw_surrogate_gradient(self, index):
+        g = np.empty(self.sesw_surrogate_nparam(), dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._L.sesw_surrogate_gradient(self._h, int(index), _ptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def sesw_surrogate_predict(self, index):
+        oe = np.empty((self.ne, 4))
+        ov = np.empty(self.nv)
+        self._check(self._L.sesw_surrogate_predict(self._h, int(index), _ptr(oe), _ptr(ov)))
+        return oe, ov
+
+    def sesw_surrogate_advance(self, nsteps, resid_tol):
+        nf = ctypes.c_int32()
+        r = ctypes.c_double()
+        self._check(self._L.sesw_surrogate_advance(self._h, int(nsteps), float(resid_tol), ctypes.byref(nf),
+                                                   ctypes.byref(r)))
+        return nf.value, r.value
 
     def sesw_diagnostics(self):
         v, e = ctypes.c_double(), ctypes.c_double()

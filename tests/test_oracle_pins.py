@@ -414,3 +414,55 @@ def test_sesm_pins_catch_planted_mistake(golden_se, plant):
     e2, U2, M2 = brute.advance_sesm(case.mesh, case.R, case.params, coef, case.nsteps, case.eta0, case.U0)
     err = max(np.max(np.abs(e1 - e2)), np.max(np.abs(U1 - U2)) / max(1.0, np.max(np.abs(U2))))
     assert err > 1e-6, f"planted mistake {plant} went unnoticed"
+
+
+def test_oracle_summed_momentum_identity():
+    """Summing Eq. 4.10 over a step (linear H): U^M - U^0 + tau [f e_z x S' + g H0 grad(eta_bar) - R] = 0,
+    S' = <<U>> - (theta/M)(U^M - U^0) + (U^0 - U^M)/(2M), eta_bar = (1/M) sum_{m<M} eta^m."""
+    case = I.tiny_jittered_case(nx=9, ny=7, seed=8, nonlinear_h=0, M=9, tau=90.0)
+    om = orc.OracleMesh(case.mesh)
+    p = case.params
+    eta1, U1, Um, _, eb = om.advance(case.R, p, 1, case.eta0, case.U0, want_eta_mean=True)
+    M, th, tau = p.M, p.theta, p.tau
+    Sp = Um - th / M * (U1 - case.U0) + (case.U0 - U1) / (2 * M)
+    f = case.mesh.coriolis[:, None]
+    cor = np.stack([-Sp[:, 1], Sp[:, 0]], axis=1) * f
+    H0e = case.mesh.depth[case.mesh.tri].mean(axis=1)[:, None]
+    resid = U1 - case.U0 + tau * (cor + p.g * H0e * om.gradient(eb) - case.R)
+    assert np.max(np.abs(resid)) < 1e-10 * np.max(np.abs(U1 - case.U0))
+    assert np.max(np.abs(U1 - case.U0)) > 1.0
+
+
+# ---------------------------------------------------------------- surrogate reference network
+
+def test_mpnn_reference_gradient_matches_finite_differences():
+    """The numpy FP64 backward of the surrogate equals central differences of its forward."""
+    from oracle import mpnn
+
+    case = I.tiny_jittered_case(nx=6, ny=5, seed=2)
+    G = mpnn.Graph(case.mesh)
+    rng = np.random.default_rng(0)
+    s = dict(eta=0.3, H=3000.0, U=5.0, R=1e-3, f=1e-4, L=1e4, out_U=1.0, out_eta=0.1)
+    xv, xe = mpnn.features(G, case.eta0, case.U0, case.R, s)
+    te = rng.standard_normal((G.ne, 4))
+    tv = rng.standard_normal((G.nv, 1))
+    w = 0.3 * rng.standard_normal(mpnn.nparams())
+    L0, g = mpnn.loss_and_grad(G, w, xv, xe, te, tv, s)
+    idx = rng.choice(len(w), 40, replace=False)
+    for i in idx:
+        h = 1e-6
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (mpnn.loss(*mpnn.forward(G, wp, xv, xe, s), te, tv) - mpnn.loss(*mpnn.forward(G, wm, xv, xe, s), te, tv)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mpnn_bf16_rounding():
+    from oracle import mpnn
+
+    x = np.array([1.0, 1.00390625, 1.005859375, -3.14159, 1e-3], dtype=np.float32)
+    r = mpnn.bf16_round(x)
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0078125      # ties to even, then round up
+    assert abs(r[3] - (-3.140625)) < 1e-12
+    assert abs(r[4] - 1e-3) < 4e-6
