@@ -54,8 +54,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-substeps", type=int, default=4,
                     help="substeps of the channel per reference-arm step (a bounded sample)")
-    ap.add_argument("--workload", choices=["channel", "ensemble"], default="channel",
-                    help="channel: the headline workload; ensemble: 64 basins of uneven size, batched")
+    ap.add_argument("--workload", choices=["channel", "ensemble", "surrogate"], default="channel",
+                    help="channel: the headline workload; ensemble: 64 basins of uneven size, batched; "
+                         "surrogate: train and evaluate the learned surrogate on the sphere")
+    ap.add_argument("--surrogate-level", type=int, default=8)
+    ap.add_argument("--surrogate-traj", type=int, default=40)
+    ap.add_argument("--surrogate-steps", type=int, default=50)
+    ap.add_argument("--surrogate-epochs", type=int, default=3)
+    ap.add_argument("--resid-tol", type=float, default=0.1)
     ap.add_argument("--ensemble-basins", type=int, default=64)
     ap.add_argument("--ensemble-scale", type=float, default=1.0)
     ap.add_argument("--sequential-steps", type=int, default=10)
@@ -344,6 +350,64 @@ def run_ensemble(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_surrogate(args, world, rank, local):
+    """Learned surrogate on the global-like sphere: data from the plain subcycle, training on the GPU,
+    held-out loss against persistence, rollouts against the plain subcycle (and fewer substeps)."""
+    import torch
+
+    from paper_2311_08241_gb300 import inputs as I
+    from paper_2311_08241_gb300 import sesw as S
+    from paper_2311_08241_gb300 import surrogate as SG
+
+    torch.cuda.set_device(local)
+    case = I.sphere_case(level=args.surrogate_level, nsteps=args.surrogate_steps)
+    V, E, M = case.mesh.nv, case.mesh.ne, case.params.M
+    ntraj, nst = args.surrogate_traj, args.surrogate_steps
+    base_seed = 20231119 + 1000 * rank
+    forcing = lambda k: SG.sphere_forcing(case, base_seed + k)
+    sim = S.Subcycle(local)
+    sim.sesw_mesh_upload(case.mesh)
+    sim.sesw_set_params(case.params)
+    sim.sesw_surrogate_init(ntraj * nst, seed=1)
+    t0 = time.perf_counter()
+    SG.generate(sim, case.mesh, forcing, ntraj, nst)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    sp = SG.split(ntraj, nst)
+    xy = case.mesh.xy
+    edge = float(np.sqrt(np.mean((xy[:, 1] - xy[:, 0]) ** 2 * 2)))
+    sim.sesw_surrogate_fit_scales(ntraj * nst, edge)
+    baseline = SG.persistence_loss(sim, sp.test)
+    untrained = sim.sesw_surrogate_loss(sp.test)
+    t0 = time.perf_counter()
+    hist = SG.train(sim, sp.train, args.surrogate_epochs, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    test_loss = sim.sesw_surrogate_loss(sp.test)
+    weights = sim.sesw_surrogate_weights()
+    scales = sim.sesw_surrogate_scales()
+    sim.close()
+    k_test = ntraj - 1
+    roll = SG.rollout_error(case, forcing(k_test), case.params, weights, scales, nst, args.resid_tol,
+                            coarse_M=(M // 2,), device=local)
+    plain_ms = roll["plain"]["ms_per_step"]
+    sur_ms = roll["surrogate"]["ms_per_step"]
+    line = {"metric": METRIC, "value": V * M / (sur_ms * 1e-3), "unit": METRIC, "n_gpus": 1,
+            "steps": nst, "warmup": 1, "ms_per_step": sur_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 weights, f32 accumulate", "data": "synthetic",
+            "config": {"workload": f"learned surrogate on the icosahedral sphere level {args.surrogate_level} "
+                                   f"(V={V}, E={E}, M={M}, tau={case.params.tau:g} s)",
+                       "samples": ntraj * nst, "trajectories": ntraj, "held_out_trajectories": int(sp.ntraj - len(sp.train) // nst),
+                       "epochs": args.surrogate_epochs, "resid_tol": args.resid_tol},
+            "surrogate": {"held_out_loss": test_loss, "persistence_loss": baseline, "untrained_loss": untrained,
+                          "loss_ratio_vs_persistence": test_loss / baseline, "train_loss_per_epoch": hist,
+                          "generate_s": t_gen, "train_s": t_train,
+                          "speedup_vs_plain": plain_ms / sur_ms, "rollout": roll},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     """The oracle on the host cores, on bounded samples of the same workload."""
     if rank != 0:
@@ -497,6 +561,8 @@ def main():
             run_reference(args, world, rank)
         elif args.workload == "ensemble":
             run_ensemble(args, world, rank, local)
+        elif args.workload == "surrogate":
+            run_surrogate(args, world, rank, local)
         else:
             run_ours(args, world, rank, local)
     finally:

@@ -149,3 +149,25 @@ def test_step_mean_elevation_matches_oracle_and_summed_momentum(S):
     H0e = case.mesh.depth[case.mesh.tri].mean(axis=1)[:, None]
     r = U1 - case.U0 + p.tau * (cor + p.g * H0e * om.gradient(eb) - case.R)
     assert np.max(np.abs(r)) < 1e-4 * np.max(np.abs(U1 - case.U0))
+
+
+def test_trained_surrogate_gains_over_persistence_on_held_out_data(S):
+    """What training buys: on held-out trajectories of a small sphere, the trained network's loss is
+    well below that of persistence (zero increments, the prediction without the network)."""
+    from paper_2311_08241_gb300 import surrogate as SG
+
+    case = I.sphere_case(level=4, nsteps=10)
+    forcing = lambda k: SG.sphere_forcing(case, 500 + k)
+    ntraj, nst = 10, 10
+    with S.Subcycle() as s:
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_surrogate_init(ntraj * nst, seed=1)
+        SG.generate(s, case.mesh, forcing, ntraj, nst)
+        sp = SG.split(ntraj, nst, test_fraction=0.2)
+        s.sesw_surrogate_fit_scales(ntraj * nst, 2e5)
+        base = SG.persistence_loss(s, sp.test)
+        SG.train(s, sp.train, 12, lr=3e-3)
+        test = s.sesw_surrogate_loss(sp.test)
+    print("held-out loss", test, "persistence", base)
+    assert test < 0.5 * base
