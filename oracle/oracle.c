@@ -12,7 +12,9 @@
  * -ffp-contract=off):
  *
  *   Barotropic system, Eq. (4.5):  dU/dt + f e_z x U + g H grad(eta) = R,
- *                                  deta/dt + div(U) = 0,   H = H0 + eta   (W = 0).
+ *                                  deta/dt + div(U) + W = 0,   H = H0 + eta
+ *   (W = 0 except in oracle_advance_ext, which also adds the viscous regularisation
+ *   of Eq. (viscosity_BT); its discretisation is described there).
  *   Substep of the dissipative forward-backward scheme, Eq. (4.10), dt = tau/M:
  *       U^{m+1} = U^m - dt [ (f/2) e_z x (U^{m+1} + U^m) + g H^m grad(eta^m) - R ]
  *       eta^{m+1} = eta^m - dt div[ (1+theta) U^{m+1} - theta U^m ]
@@ -528,6 +530,157 @@ int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_i
     for (int k = 0; k < 3; k++) free(U[k]);
     for (int k = 0; k < 4; k++) free(E[k]);
     free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef);
+    return 0;
+}
+
+/*
+ * Barotropic viscous regularisation R_hV = div( H A grad(U/H) ) (Eq. viscosity_BT), edge by
+ * edge: for an interior edge of length L between triangles e1 and e2 with centroid
+ * distance d (measured in the plane unfolded across the edge; L is the mean of the edge's
+ * length in the two element frames), velocities u = U/H on
+ * the triangles, and u2' = u2 rotated into e1's frame (the rotation that maps the
+ * edge direction of e2's frame onto that of e1's frame),
+ *     flux into e1 = H_edge A_edge (u2' - u1) L / d,   H_edge = (H1 + H2)/2,
+ *     A_edge = A_bg + C_v |u2' - u1| L,
+ * added to e1 divided by A_e1, and the opposite flux (rotated back) to e2. Coast edges
+ * carry no flux (free slip). H is H0 (+ corner-mean eta when nonlinear).
+ */
+static void viscosity(const omesh *m, const real *U, const real *eta, int nonlinear_h, real Abg, real Cv,
+                      const double *xy, real *out)
+{
+    memset(out, 0, sizeof(real) * 2 * (size_t)m->ne);
+    for (int q = 0; q < m->ned; q++) {
+        const int e1 = m->edge_e[2 * q], e2 = m->edge_e[2 * q + 1];
+        if (e1 < 0 || e2 < 0) continue;
+        const int a = m->edge_v[2 * q], b = m->edge_v[2 * q + 1];
+        double geo[2][4];       /* per side: edge angle, along-edge centroid coordinate, height, edge length */
+        const int es[2] = {e1, e2};
+        for (int side = 0; side < 2; side++) {
+            const int e = es[side];
+            const double *p = xy + 6 * (size_t)e;
+            int ka = 0, kb = 0;
+            for (int c = 0; c < 3; c++) {
+                if (m->tri[3 * e + c] == a) ka = c;
+                if (m->tri[3 * e + c] == b) kb = c;
+            }
+            const double ax = p[2 * ka], ay = p[2 * ka + 1], bx = p[2 * kb], by = p[2 * kb + 1];
+            const double cx = (p[0] + p[2] + p[4]) / 3.0, cy = (p[1] + p[3] + p[5]) / 3.0;
+            const double ex = bx - ax, ey = by - ay, len = sqrt(ex * ex + ey * ey);
+            geo[side][0] = atan2(ey, ex);
+            geo[side][1] = ((cx - ax) * ex + (cy - ay) * ey) / len;
+            geo[side][2] = fabs((cx - ax) * ey - (cy - ay) * ex) / len;
+            geo[side][3] = len;
+        }
+        const double L = 0.5 * (geo[0][3] + geo[1][3]);   /* the two frames may differ slightly (sphere) */
+        const double d = sqrt((geo[0][1] - geo[1][1]) * (geo[0][1] - geo[1][1]) +
+                              (geo[0][2] + geo[1][2]) * (geo[0][2] + geo[1][2]));
+        const double rot = geo[0][0] - geo[1][0];     /* from e2's frame to e1's frame */
+        const real cr = (real)cos(rot), sr = (real)sin(rot);
+        const real H1 = element_depth(m, e1, eta, nonlinear_h), H2 = element_depth(m, e2, eta, nonlinear_h);
+        const real u1x = U[2 * e1] / H1, u1y = U[2 * e1 + 1] / H1;
+        const real v2x = U[2 * e2] / H2, v2y = U[2 * e2 + 1] / H2;
+        const real u2x = cr * v2x - sr * v2y, u2y = sr * v2x + cr * v2y;
+        const real dx = u2x - u1x, dy = u2y - u1y;
+        const real A = Abg + Cv * (real)sqrt((double)(dx * dx + dy * dy)) * (real)L;
+        const real k = (H1 + H2) / 2 * A * (real)(L / d);
+        const real fx = k * dx, fy = k * dy;                   /* into e1, e1's frame */
+        out[2 * e1] += fx / m->area_e[e1];
+        out[2 * e1 + 1] += fy / m->area_e[e1];
+        /* into e2: the opposite flux rotated back into e2's frame */
+        out[2 * e2] += (-(cr * fx + sr * fy)) / m->area_e[e2];
+        out[2 * e2 + 1] += (-(-sr * fx + cr * fy)) / m->area_e[e2];
+    }
+}
+
+int oracle_viscosity(void *hm, const double *xy, const double *U_in, const double *eta_in, int nonlinear_h,
+                     double Abg, double Cv, double *out)
+{
+    omesh *m = (omesh *)hm;
+    real *U = (real *)calloc(2 * (size_t)m->ne, sizeof(real));
+    real *eta = (real *)calloc((size_t)m->nv, sizeof(real));
+    real *o = (real *)calloc(2 * (size_t)m->ne, sizeof(real));
+    if (!U || !eta || !o) { free(U); free(eta); free(o); return -4; }
+    for (size_t i = 0; i < 2 * (size_t)m->ne; i++) U[i] = (real)U_in[i];
+    for (int v = 0; v < m->nv; v++) eta[v] = (real)eta_in[v];
+    viscosity(m, U, eta, nonlinear_h, (real)Abg, (real)Cv, xy, o);
+    for (size_t i = 0; i < 2 * (size_t)m->ne; i++) out[i] = (double)o[i];
+    free(U); free(eta); free(o);
+    return 0;
+}
+
+/*
+ * SE steps (as oracle_advance) with the two optional terms of Eq. (4.5) and
+ * Eq. (viscosity_BT): the freshwater flux W (m/s per vertex, positive out of the ocean),
+ *     eta^{m+1} = eta^m - dt ( div[(1+theta) U^{m+1} - theta U^m] + W ),
+ * and the viscous regularisation added to the forcing as R + R_hV(U^m) - R_hV(U^0)
+ * (its value at the start of the step subtracted, Sect. 2.2), H of R_hV at eta^m.
+ * W or xy may be NULL to leave the term out.
+ */
+int oracle_advance_ext(void *hm, const double *xy, const double *R_in, const double *W_in, double g_in,
+                       double theta_in, double tau, int M, int nonlinear_h, double Abg, double Cv, int nsteps,
+                       double *eta_io, double *U_io, double *Umean_out)
+{
+    omesh *m = (omesh *)hm;
+    if (M < 1) return -5;
+    const int ne = m->ne, nv = m->nv;
+    const real dt = (real)(tau / (double)M);
+    const real g = (real)g_in, theta = (real)theta_in;
+    real *F = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *U = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *U0 = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *sumU = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *R = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *V0 = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *Vm = (real *)malloc(sizeof(real) * 2 * (size_t)ne);
+    real *W = (real *)calloc((size_t)nv, sizeof(real));
+    real *eta = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *div = (real *)malloc(sizeof(real) * (size_t)nv);
+    real *ef = (real *)malloc(sizeof(real) * (size_t)m->ned);
+    if (!F || !U || !U0 || !sumU || !R || !V0 || !Vm || !W || !eta || !div || !ef) {
+        free(F); free(U); free(U0); free(sumU); free(R); free(V0); free(Vm); free(W); free(eta); free(div); free(ef);
+        return -4;
+    }
+    for (size_t i = 0; i < 2 * (size_t)ne; i++) { U[i] = (real)U_io[i]; R[i] = (real)R_in[i]; }
+    for (int v = 0; v < nv; v++) { eta[v] = (real)eta_io[v]; if (W_in) W[v] = (real)W_in[v]; }
+    for (int n = 0; n < nsteps; n++) {
+        memcpy(U0, U, sizeof(real) * 2 * (size_t)ne);
+        memset(sumU, 0, sizeof(real) * 2 * (size_t)ne);
+        if (xy) viscosity(m, U, eta, nonlinear_h, (real)Abg, (real)Cv, xy, V0);
+        for (int s = 0; s < M; s++) {
+            if (xy) viscosity(m, U, eta, nonlinear_h, (real)Abg, (real)Cv, xy, Vm);
+            #pragma omp parallel for schedule(static)
+            for (int e = 0; e < ne; e++) {
+                real gx, gy;
+                gradient_e(m, e, eta, &gx, &gy);
+                real H = element_depth(m, e, eta, nonlinear_h);
+                real a = dt * m->f_e[e] / 2;
+                real ux = U[2 * e], uy = U[2 * e + 1];
+                real rx = R[2 * e], ry = R[2 * e + 1];
+                if (xy) { rx += Vm[2 * e] - V0[2 * e]; ry += Vm[2 * e + 1] - V0[2 * e + 1]; }
+                real A11 = 1, A12 = -a, A21 = a, A22 = 1;
+                real bx = ux + a * uy + dt * (-g * H * gx + rx);
+                real by = -a * ux + uy + dt * (-g * H * gy + ry);
+                real det = A11 * A22 - A12 * A21;
+                real nx = (bx * A22 - A12 * by) / det;
+                real ny = (A11 * by - A21 * bx) / det;
+                F[2 * e] = (1 + theta) * nx - theta * ux;
+                F[2 * e + 1] = (1 + theta) * ny - theta * uy;
+                U[2 * e] = nx;
+                U[2 * e + 1] = ny;
+                sumU[2 * e] += nx;
+                sumU[2 * e + 1] += ny;
+            }
+            divergence(m, F, ef, div);
+            #pragma omp parallel for schedule(static)
+            for (int v = 0; v < nv; v++) eta[v] -= dt * (div[v] + W[v]);
+        }
+        for (int e = 0; e < ne; e++)
+            for (int c = 0; c < 2; c++)
+                Umean_out[2 * e + c] = (double)(sumU[2 * e + c] / (real)M + theta / (real)M * (U[2 * e + c] - U0[2 * e + c]));
+    }
+    for (size_t i = 0; i < 2 * (size_t)ne; i++) U_io[i] = (double)U[i];
+    for (int v = 0; v < nv; v++) eta_io[v] = (double)eta[v];
+    free(F); free(U); free(U0); free(sumU); free(R); free(V0); free(Vm); free(W); free(eta); free(div); free(ef);
     return 0;
 }
 

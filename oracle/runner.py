@@ -53,6 +53,10 @@ def _bind(path):
     L.oracle_set_threads.argtypes = [I]
     L.oracle_advance_sesm.argtypes = [P, P, D, D, D, D, D, D, I, I, I, P, P, P]
     L.oracle_advance_sesm.restype = I
+    L.oracle_viscosity.argtypes = [P, P, P, P, I, D, D, P]
+    L.oracle_viscosity.restype = I
+    L.oracle_advance_ext.argtypes = [P, P, P, P, D, D, D, I, I, D, D, I, P, P, P]
+    L.oracle_advance_ext.restype = I
     for f in ("oracle_mesh_info", "oracle_areas", "oracle_edges", "oracle_gradient",
               "oracle_divergence", "oracle_diagnostics", "oracle_advance",
               "oracle_set_threads"):
@@ -205,6 +209,34 @@ class OracleMesh:
             return eta, U, Umean, diag, emean
         return eta, U, Umean, diag
 
+
+    def viscosity(self, U, eta, nonlinear_h, Abg, Cv):
+        """R_hV of Eq. (viscosity_BT) per element (element frames), at transport U and elevation eta."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        out = np.zeros((self.ne, 2))
+        rc = self._L.oracle_viscosity(self._h, _p(self._xy), _p(U), _p(eta), int(nonlinear_h), float(Abg),
+                                      float(Cv), _p(out))
+        if rc:
+            raise RuntimeError(f"oracle_viscosity failed ({rc})")
+        return out
+
+    def advance_ext(self, R, params, nsteps, eta, U, W=None, visc=None):
+        """SE steps with the freshwater flux W ([V] m/s, positive out of the ocean) and/or the
+        viscous regularisation visc = (A_bg, C_v); either may be None."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        Wc = None if W is None else np.ascontiguousarray(W, dtype=np.float64)
+        Abg, Cv = (0.0, 0.0) if visc is None else (float(visc[0]), float(visc[1]))
+        eta = np.array(eta, dtype=np.float64, copy=True)
+        U = np.array(U, dtype=np.float64, copy=True)
+        Umean = np.zeros((self.ne, 2))
+        rc = self._L.oracle_advance_ext(self._h, _p(self._xy) if visc is not None else None, _p(R),
+                                        _p(Wc) if Wc is not None else None, float(params.g), float(params.theta),
+                                        float(params.tau), int(params.M), int(params.nonlinear_h), Abg, Cv,
+                                        int(nsteps), _p(eta), _p(U), _p(Umean))
+        if rc:
+            raise RuntimeError(f"oracle_advance_ext failed ({rc})")
+        return eta, U, Umean
 
     def advance_sesm(self, R, params, coef, nsteps, eta, U):
         """SESM steps (Eqs. 4.7-4.8); coef = (beta, delta, gamma, zeta). Returns (eta, U, Umean)."""
