@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto")
     ap.add_argument("--scheme", choices=["se", "sesm"], default="se",
                     help="se: dissipative forward-backward (Eq. 4.10); sesm: AB3-AM4 (Eqs. 4.7-4.8, graph mode)")
+    ap.add_argument("--visc", type=str, default=None, metavar="A_BG,C_V",
+                    help="barotropic viscosity of Eq. (viscosity_BT): background (m^2/s) and flow coefficient; "
+                         "'auto' picks a background at viscous number 0.2 and C_v = 1")
+    ap.add_argument("--freshwater", type=float, default=0.0, metavar="AMP",
+                    help="freshwater flux W of Eq. (4.5): seeded random field of this amplitude (m/s)")
     ap.add_argument("--patch-vertices", type=int, default=256)
     ap.add_argument("--block-threads", type=int, default=256)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
@@ -87,6 +92,19 @@ def algorithmic_bytes_per_substep(V, E):
     per element U r/w 16, mean pair r/w 32, corners 12, gradients 16, H0 and f 8, R 8 (92 B);
     per vertex eta r/w 8, 1/A_v 4 (12 B)."""
     return 12 * V + 92 * E
+
+
+def sesm_bytes_per_substep(V, E):
+    """SESM substep (k_sesm): per element three transport levels read and one written 32, mean
+    pair r/w 32, corners 12, gradients 16, H0 and f 8, R 8 (108 B); per vertex four elevation
+    levels read and one written 20, 1/A_v 4 (24 B)."""
+    return 24 * V + 108 * E
+
+
+def viscosity_bytes_per_substep(V, E):
+    """k_viscosity: per element corners and coefficients 32, U 8, R 8, V0 8, Reff 8, neighbour
+    table 16, edge geometry 48 (128 B); per vertex eta 4. The substep then reads Reff in place of R."""
+    return 4 * V + 128 * E
 
 
 def measured_hbm_peak():
@@ -179,7 +197,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_baseline(case, seconds, rank):
+def cpu_baseline(case, seconds, rank, W=None):
     """The FP64 oracle, as it stands, on the host cores: whole baroclinic steps until `seconds` elapse."""
     from oracle import runner as orc
 
@@ -187,9 +205,13 @@ def cpu_baseline(case, seconds, rank):
     cores = orc.set_threads(0)
     eta, U = case.eta0.copy(), case.U0.copy()
     steps = 0
+    visc = getattr(case.params, "visc", None)
     t0 = time.perf_counter()
     while True:
-        eta, U, _, _ = om.advance(case.R, case.params, 1, eta, U)
+        if visc is None and W is None:
+            eta, U, _, _ = om.advance(case.R, case.params, 1, eta, U)
+        else:
+            eta, U, _ = om.advance_ext(case.R, case.params, 1, eta, U, W=W, visc=visc)
         steps += 1
         if time.perf_counter() - t0 >= seconds:
             break
@@ -403,7 +425,7 @@ def run_surrogate(args, world, rank, local):
                           "loss_ratio_vs_persistence": test_loss / baseline, "train_loss_per_epoch": hist,
                           "generate_s": t_gen, "train_s": t_train,
                           "speedup_vs_plain": plain_ms / sur_ms, "rollout": roll},
-            "gpu_launches": None}
+            "gpu_launches": roll["surrogate"]["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -456,6 +478,23 @@ def run_ours(args, world, rank, local):
         case.params = I.Params(g=p.g, theta=p.theta, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h, scheme=1)
         args.mode = "graph"
         desc = dict(desc, scheme="SESM (AB3-AM4, Eqs. 4.7-4.8)")
+    W = None
+    if args.freshwater:
+        W = args.freshwater * (0.3 + np.random.default_rng(20231119).standard_normal(case.mesh.nv))
+        desc = dict(desc, freshwater=f"W = {args.freshwater:g} m/s x (0.3 + N(0,1)), seeded (Eq. 4.5)")
+    if args.visc:
+        from paper_2311_08241_gb300 import inputs as I
+
+        p = case.params
+        if args.visc == "auto":
+            stiff = S.sesw_mesh_check(case.mesh)["visc_stiffness"]
+            visc = (0.2 / (p.tau / p.M * stiff), 1.0)
+        else:
+            visc = tuple(float(x) for x in args.visc.split(","))
+        case.params = I.Params(g=p.g, theta=p.theta, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h,
+                               scheme=p.scheme, visc=visc)
+        args.mode = "graph"
+        desc = dict(desc, viscosity=f"A = {visc[0]:.4g} m^2/s + {visc[1]:g} |du| L (Eq. viscosity_BT)")
     V, E, M = case.mesh.nv, case.mesh.ne, case.params.M
     stream = torch.cuda.current_stream(dev)
     sim = S.Subcycle(local, stream=stream)
@@ -467,6 +506,8 @@ def run_ours(args, world, rank, local):
     sim.sesw_mesh_upload(case.mesh)
     sim.sesw_set_params(case.params)
     sim.sesw_set_forcing(case.R)
+    if W is not None:
+        sim.sesw_set_freshwater(W)
     sim.sesw_set_state(case.eta0, case.U0)
     info = sim.sesw_get_info()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -503,14 +544,24 @@ def run_ours(args, world, rank, local):
     # does all M substeps, so a launch moves M * B_alg algorithmic bytes. Graph mode: M
     # k_substep launches per step, each B_alg (the step's short epilogue launch is
     # included in the event time, which understates the kernel's rate).
+    # SESM (graph): M + 1 k_sesm launches per step, rated per substep with its own byte
+    # count. Viscosity (graph): each substep is a k_viscosity and a k_substep launch, rated
+    # together per substep.
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
-    b_alg = algorithmic_bytes_per_substep(V, E)
+    if args.scheme == "sesm":
+        b_alg = sesm_bytes_per_substep(V, E)
+    else:
+        b_alg = algorithmic_bytes_per_substep(V, E)
+    if args.visc:
+        b_alg += viscosity_bytes_per_substep(V, E)
     mean_step_s = statistics.mean(step_ms) * 1e-3
     per_launch = b_alg * M if persistent else b_alg
     launch_s = mean_step_s if persistent else mean_step_s / M
     achieved = per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
     kname = "k_persistent" if persistent else ("k_sesm" if args.scheme == "sesm" else "k_substep")
+    if args.visc:
+        kname = "k_viscosity+k_substep"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(kname), "peak_source": peak_src, "kernel": kname,
                 "bytes_per_launch": per_launch}
@@ -542,10 +593,12 @@ def run_ours(args, world, rank, local):
                            npatch=info["npatch"],
                            nslot=info["nslot"], l2="flushed between timed steps (256 MiB write)",
                            parallelism=f"replicas{world}"),
-            "roofline": roofline, "e2e": e2e, "gpu_launches": args.steps * (1 if persistent else M + 1),
+            "roofline": roofline, "e2e": e2e,
+            "gpu_launches": args.steps * (1 if persistent else
+                                          (2 * M if args.visc else (M + 1 if args.scheme == "sesm" else M)) + 1),
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds, rank)
+        line["cpu_baseline"] = cpu_baseline(case, args.cpu_seconds, rank, W=W)
     sim.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

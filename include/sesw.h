@@ -108,7 +108,22 @@ typedef struct sesw_mesh {
  *   sesm_beta, sesm_delta, sesm_gamma, sesm_zeta
  *                SESM coefficients of Eq. (4.7); all zero selects beta = 0.281105 and, with
  *                chi = theta/2, gamma = 0.083 - 0.514 chi, zeta = 0.010 - 0.135 chi,
- *                delta = 2 chi + gamma + 2 zeta + 1/2 (Eqs. dp_4, dp_6) */
+ *                delta = 2 chi + gamma + 2 zeta + 1/2 (Eqs. dp_4, dp_6)
+ *   visc_background, visc_flow
+ *                barotropic viscous regularisation R_hV = div(H A grad(U/H)) of Eq.
+ *                (viscosity_BT), added to the momentum forcing with its start-of-step value
+ *                subtracted (Sect. 2.2): each substep uses R + R_hV(U^m, eta^m) - R_hV(U^0, eta^0).
+ *                The paper fixes neither the discretisation nor A beyond "background plus a
+ *                part proportional to the velocity differences across edges"; the library
+ *                takes a two-point flux between neighbouring triangles across each edge of
+ *                length L, H_edge (u_nb - u) A L/d with u = U/H, H_edge the mean of the two
+ *                triangles' H, d the distance of their centroids in the plane unfolded across
+ *                the edge, u_nb turned into the triangle's frame, and
+ *                A = visc_background (m^2/s) + visc_flow (dimensionless) |u_nb - u| L.
+ *                Coast edges carry no flux. Both 0 (the default) leaves the term out; it needs
+ *                scheme 0 and SESW_MODE_GRAPH. The check of the stability test also bounds the
+ *                viscous number dt visc_background max_e 2 sum_edges (H0_edge/H0_e)(L/d)/A_e
+ *                by 1 (reported in sesw_info.visc_number). */
 #define SESW_FLAG_NO_STABILITY_CHECK 1
 #define SESW_FLAG_TEST_FORCE_TIMEOUT 2
 typedef struct sesw_params {
@@ -124,6 +139,8 @@ typedef struct sesw_params {
     double sesm_delta;
     double sesm_gamma;
     double sesm_zeta;
+    double visc_background;
+    double visc_flow;
 } sesw_params;
 
 /* Read-only facts about the uploaded mesh and its device layout. */
@@ -148,6 +165,10 @@ typedef struct sesw_info {
     int32_t npack;           /* persistent mode: cooperative launches per step (packs of meshes
                                 that together fit the resident grid) */
     int32_t reserved2;
+    double visc_number;      /* viscous number of the barotropic viscosity (see sesw_params;
+                                0 until parameters are set) */
+    double visc_stiffness;   /* max_e 2 sum_edges (H0_edge/H0_e)(L/d)/A_e (1/m^2): visc_number =
+                                (tau/M) visc_background visc_stiffness */
 } sesw_info;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a
@@ -160,7 +181,8 @@ int sesw_create(sesw_ctx **out, int device, void *cuda_stream,
 int sesw_set_stream(sesw_ctx *ctx, void *cuda_stream);
 
 /* Set the target number of vertices per patch (>= 32) of SESW_MODE_GRAPH for the
- * next mesh upload; default 256. (The persistent mode uses one patch per SM.) */
+ * next mesh upload; default 256. (SESW_MODE_PERSISTENT sizes its patches itself so that
+ * the largest mesh fills the grid of resident blocks.) */
 int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
 
 /* Execution modes of a baroclinic step.
@@ -208,7 +230,8 @@ int sesw_mesh_upload(sesw_ctx *ctx, const sesw_mesh *mesh);
 int sesw_mesh_upload_batch(sesw_ctx *ctx, int32_t nmesh, const sesw_mesh *meshes);
 
 /* Parameters of a batch, one set per mesh (n = number of uploaded meshes). All sets
- * must agree in g, theta, M, nonlinear_h, scheme, flags and eta_bound; tau (hence the
+ * must agree in g, theta, M, nonlinear_h, scheme, flags, eta_bound, the SESM and the
+ * viscosity coefficients; tau (hence the
  * substep dt = tau/M) may differ per mesh. Each mesh gets its own stability check. */
 int sesw_set_params_batch(sesw_ctx *ctx, int32_t n, const sesw_params *params);
 
@@ -229,6 +252,19 @@ int sesw_set_state(sesw_ctx *ctx, const double *eta, const double *U, int where)
 
 /* Set the frozen forcing R [ne][2] (m^2/s^2) of Eq. (4.4), caller order. */
 int sesw_set_forcing(sesw_ctx *ctx, const double *R, int where);
+
+/* Set the freshwater flux W [nv] (m/s, positive out of the ocean) of Eq. (4.5), caller
+ * order, frozen like R: every substep then updates eta^{m+1} = eta^m - dt (div F + W),
+ * so a step changes the volume by -tau sum_v A_v W_v and Eq. (4.11) reads
+ * eta^{n+1} = eta^n - tau (div <<U>> + W). W = NULL removes the term (the default). All
+ * schemes and modes. */
+int sesw_set_freshwater(sesw_ctx *ctx, const double *W, int where);
+
+/* Evaluate the barotropic viscous regularisation R_hV (see sesw_params) at the current
+ * state with the current parameters into out [ne][2] (m^2/s^2, element frames, caller
+ * order); zero when both coefficients are 0. SESW_MODE_GRAPH only. With SESW_HOST the
+ * call synchronises. */
+int sesw_viscosity(sesw_ctx *ctx, double *out, int where);
 
 /* Advance nsteps >= 0 baroclinic steps (nsteps*M substeps). Asynchronous on the
  * context's stream; device-side instability is reported by sesw_status or
@@ -342,7 +378,9 @@ int sesw_surrogate_predict(sesw_ctx *ctx, int64_t index, double *out_e, double *
  *   S' = <<U>> - (theta/M)(U^M - U^0) + (U^0 - U^M)/(2M),
  * as sqrt(sum A |r|^2 / sum A |U^M - U^0|^2). A step whose residual exceeds resid_tol is
  * undone and taken by the plain subcycle; *n_fallback counts those steps and
- * *last_resid receives the last residual (either may be NULL). Synchronises per step. */
+ * *last_resid receives the last residual (either may be NULL). Synchronises per step.
+ * Refused (SESW_EINVAL) while the barotropic viscosity or a freshwater flux is set: the
+ * network and the residual check know neither term. */
 int sesw_surrogate_advance(sesw_ctx *ctx, int32_t nsteps, double resid_tol, int32_t *n_fallback,
                            double *last_resid);
 

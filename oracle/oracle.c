@@ -446,20 +446,20 @@ int oracle_advance(void *hm, const double *R_in, double g_in, double theta_in, d
 
 /*
  * Advance nsteps baroclinic steps of the AB3-AM4 substep with dissipative coefficients
- * (SESM), Eqs. (4.7)-(4.8), W = 0:
+ * (SESM), Eqs. (4.7)-(4.8), with the freshwater flux W (NULL: W = 0):
  *     U_AB   = (3/2 + beta) U^m - (1/2 + 2 beta) U^{m-1} + beta U^{m-2}
- *     eta^{m+1} = eta^m - dt div(U_AB)
+ *     eta^{m+1} = eta^m - dt (div(U_AB) + W)
  *     eta_AM = delta eta^{m+1} + (1 - delta - gamma - zeta) eta^m + gamma eta^{m-1} + zeta eta^{m-2}
  *     U^{m+1} = U^m + dt ( -f e_z x U_AB - g H_AM grad(eta_AM) + R ),  H_AM = H0 + eta_AM
  *                                                    (H0 alone when nonlinear_h = 0)
  * Levels before the start of the subcycle (m - k < 0) are taken equal to level 0.
  * The time-mean transport is the mean of the transports the continuity equation used,
  *     <<U>> = (1/M) sum_{m=0..M-1} U_AB^m,
- * which makes eta^M - eta^0 = -tau div <<U>> exact (Eq. 4.11).
+ * which makes eta^M - eta^0 = -tau (div <<U>> + W) exact (Eq. 4.11).
  */
-int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_in, double delta_in,
-                        double gamma_in, double zeta_in, double tau, int M, int nonlinear_h, int nsteps,
-                        double *eta_io, double *U_io, double *Umean_out)
+static int advance_sesm(void *hm, const double *R_in, const double *W_in, double g_in, double beta_in,
+                        double delta_in, double gamma_in, double zeta_in, double tau, int M, int nonlinear_h,
+                        int nsteps, double *eta_io, double *U_io, double *Umean_out)
 {
     omesh *m = (omesh *)hm;
     if (M < 1) return -5;
@@ -478,17 +478,18 @@ int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_i
     real *eAM = (real *)malloc(sizeof(real) * (size_t)nv);
     real *div = (real *)malloc(sizeof(real) * (size_t)nv);
     real *ef = (real *)malloc(sizeof(real) * (size_t)m->ned);
-    int ok = UAB && sumF && R && eAM && div && ef;
+    real *W = (real *)calloc((size_t)nv, sizeof(real));
+    int ok = UAB && sumF && R && eAM && div && ef && W;
     for (int k = 0; k < 3; k++) ok = ok && U[k];
     for (int k = 0; k < 4; k++) ok = ok && E[k];
     if (!ok) {
         for (int k = 0; k < 3; k++) free(U[k]);
         for (int k = 0; k < 4; k++) free(E[k]);
-        free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef);
+        free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef); free(W);
         return -4;
     }
     for (size_t i = 0; i < 2 * (size_t)ne; i++) { U[0][i] = (real)U_io[i]; R[i] = (real)R_in[i]; }
-    for (int v = 0; v < nv; v++) E[0][v] = (real)eta_io[v];
+    for (int v = 0; v < nv; v++) { E[0][v] = (real)eta_io[v]; if (W_in) W[v] = (real)W_in[v]; }
     for (int n = 0; n < nsteps; n++) {
         /* U[0] = U^m, U[1] = U^{m-1}, U[2] = U^{m-2}; E[0] = eta^m, E[1..3] older levels */
         memcpy(U[1], U[0], sizeof(real) * 2 * (size_t)ne);
@@ -503,7 +504,7 @@ int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_i
             /* continuity with the AB3 transport: eta^{m+1} into the oldest level's array */
             divergence(m, UAB, ef, div);
             real *enew = E[3];
-            for (int v = 0; v < nv; v++) enew[v] = E[0][v] - dt * div[v];
+            for (int v = 0; v < nv; v++) enew[v] = E[0][v] - dt * (div[v] + W[v]);
             /* AM4 elevation: eta^{m+1}, eta^m, eta^{m-1}, eta^{m-2} */
             for (int v = 0; v < nv; v++) eAM[v] = am0 * enew[v] + am1 * E[0][v] + am2 * E[1][v] + am3 * E[2][v];
             /* momentum with explicit Coriolis on U_AB and the AM4 pressure gradient; U^{m+1}
@@ -529,8 +530,24 @@ int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_i
     for (int v = 0; v < nv; v++) eta_io[v] = (double)E[0][v];
     for (int k = 0; k < 3; k++) free(U[k]);
     for (int k = 0; k < 4; k++) free(E[k]);
-    free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef);
+    free(UAB); free(sumF); free(R); free(eAM); free(div); free(ef); free(W);
     return 0;
+}
+
+int oracle_advance_sesm(void *hm, const double *R_in, double g_in, double beta_in, double delta_in,
+                        double gamma_in, double zeta_in, double tau, int M, int nonlinear_h, int nsteps,
+                        double *eta_io, double *U_io, double *Umean_out)
+{
+    return advance_sesm(hm, R_in, NULL, g_in, beta_in, delta_in, gamma_in, zeta_in, tau, M, nonlinear_h, nsteps,
+                        eta_io, U_io, Umean_out);
+}
+
+int oracle_advance_sesm_w(void *hm, const double *R_in, const double *W_in, double g_in, double beta_in,
+                          double delta_in, double gamma_in, double zeta_in, double tau, int M, int nonlinear_h,
+                          int nsteps, double *eta_io, double *U_io, double *Umean_out)
+{
+    return advance_sesm(hm, R_in, W_in, g_in, beta_in, delta_in, gamma_in, zeta_in, tau, M, nonlinear_h, nsteps,
+                        eta_io, U_io, Umean_out);
 }
 
 /*

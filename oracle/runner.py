@@ -53,6 +53,8 @@ def _bind(path):
     L.oracle_set_threads.argtypes = [I]
     L.oracle_advance_sesm.argtypes = [P, P, D, D, D, D, D, D, I, I, I, P, P, P]
     L.oracle_advance_sesm.restype = I
+    L.oracle_advance_sesm_w.argtypes = [P, P, P, D, D, D, D, D, D, I, I, I, P, P, P]
+    L.oracle_advance_sesm_w.restype = I
     L.oracle_viscosity.argtypes = [P, P, P, P, I, D, D, P]
     L.oracle_viscosity.restype = I
     L.oracle_advance_ext.argtypes = [P, P, P, P, D, D, D, I, I, D, D, I, P, P, P]
@@ -238,16 +240,23 @@ class OracleMesh:
             raise RuntimeError(f"oracle_advance_ext failed ({rc})")
         return eta, U, Umean
 
-    def advance_sesm(self, R, params, coef, nsteps, eta, U):
-        """SESM steps (Eqs. 4.7-4.8); coef = (beta, delta, gamma, zeta). Returns (eta, U, Umean)."""
+    def advance_sesm(self, R, params, coef, nsteps, eta, U, W=None):
+        """SESM steps (Eqs. 4.7-4.8); coef = (beta, delta, gamma, zeta); W: optional freshwater
+        flux [V]. Returns (eta, U, Umean)."""
         R = np.ascontiguousarray(R, dtype=np.float64)
         eta = np.array(eta, dtype=np.float64, copy=True)
         U = np.array(U, dtype=np.float64, copy=True)
         Umean = np.zeros((self.ne, 2))
         b, d, g, z = (float(x) for x in coef)
-        rc = self._L.oracle_advance_sesm(self._h, _p(R), float(params.g), b, d, g, z, float(params.tau),
-                                         int(params.M), int(params.nonlinear_h), int(nsteps), _p(eta), _p(U),
-                                         _p(Umean))
+        if W is None:
+            rc = self._L.oracle_advance_sesm(self._h, _p(R), float(params.g), b, d, g, z, float(params.tau),
+                                             int(params.M), int(params.nonlinear_h), int(nsteps), _p(eta), _p(U),
+                                             _p(Umean))
+        else:
+            Wc = np.ascontiguousarray(W, dtype=np.float64)
+            rc = self._L.oracle_advance_sesm_w(self._h, _p(R), _p(Wc), float(params.g), b, d, g, z,
+                                               float(params.tau), int(params.M), int(params.nonlinear_h),
+                                               int(nsteps), _p(eta), _p(U), _p(Umean))
         if rc:
             raise RuntimeError(f"oracle_advance_sesm failed ({rc})")
         return eta, U, Umean

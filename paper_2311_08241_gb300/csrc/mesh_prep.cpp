@@ -122,8 +122,9 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     // off-diagonal stiffness of each edge, K_ab = sum_e A_e H0_e dphi_a . dphi_b, is
     // summed on the way for the Gershgorin bound below.
     std::vector<double> kdiag(nv, 0.0), koff(nv, 0.0);
+    std::vector<int> nb_c(3 * (size_t)ne, -1);    // neighbour across edge (corner k, corner k+1), caller ids
     {
-        struct HE { uint64_t key; double k; };
+        struct HE { uint64_t key; double k; int ek; };
         std::vector<HE> he(3 * (size_t)ne);
         for (int e = 0; e < ne; e++) {
             const int32_t *t = m.tri + 3 * (size_t)e;
@@ -136,6 +137,7 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
                 // low bit: direction (1 when traversed from the higher to the lower index)
                 he[3 * (size_t)e + k].key = (((uint64_t)lo * (uint64_t)nv + hi) << 1) | (a > b ? 1u : 0u);
                 he[3 * (size_t)e + k].k = A[e] * h0 * (g[2 * k] * g[2 * kn] + g[2 * k + 1] * g[2 * kn + 1]);
+                he[3 * (size_t)e + k].ek = 3 * e + k;
                 kdiag[t[k]] += A[e] * h0 * (g[2 * k] * g[2 * k] + g[2 * k + 1] * g[2 * k + 1]);
             }
         }
@@ -147,6 +149,10 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
             if (j - i == 2 && (he[i].key & 1u) == (he[i + 1].key & 1u)) {
                 err = "two triangles traverse a shared edge in the same direction (inconsistent orientation)";
                 return SESW_EINVAL;
+            }
+            if (j - i == 2) {
+                nb_c[he[i].ek] = he[i + 1].ek / 3;
+                nb_c[he[i + 1].ek] = he[i].ek / 3;
             }
             double kab = 0.0;
             for (size_t q = i; q < j; q++) kab += he[q].k;
@@ -365,12 +371,64 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
     double gersh = 0.0;
     for (int v = 0; v < nv; v++) gersh = std::max(gersh, (kdiag[v] + koff[v]) / Av[v]);
     out.grad_gram_max_h = std::min(3.0 * gmax, gersh);
+
+    // ---- neighbours across edges and the two-point flux geometry of the barotropic
+    // viscosity (Eq. viscosity_BT): for edge k of an element (corner k to corner k+1)
+    // with a neighbour, the rotation from the neighbour's frame into this one, L/d and L
+    // (L: edge length, the mean of its lengths in the two frames; d: centroid distance
+    // in the plane unfolded across the edge).
+    out.visc_nb.resize(ne);
+    out.visc_geo.resize(3 * (size_t)ne);
+    double vstiff = 0.0;
+    for (int i = 0; i < ne; i++) {
+        const int e = eperm[i];
+        const int32_t *t = m.tri + 3 * (size_t)e;
+        int nbn[3];
+        double srow = 0.0;
+        for (int k = 0; k < 3; k++) {
+            const int o = nb_c[3 * (size_t)e + k];
+            nbn[k] = o < 0 ? -1 : einv[o];
+            out.visc_geo[3 * (size_t)i + k] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+            if (o < 0) continue;
+            const int va = t[k], vb = t[(k + 1) % 3];
+            const int32_t *to = m.tri + 3 * (size_t)o;
+            int oa = 0, ob = 0;
+            for (int c = 0; c < 3; c++) {
+                if (to[c] == va) oa = c;
+                if (to[c] == vb) ob = c;
+            }
+            double ang[2], along[2], perp[2], len[2];
+            const int el[2] = {e, o}, ca[2] = {k, oa}, cb[2] = {(k + 1) % 3, ob};
+            for (int side = 0; side < 2; side++) {
+                const double *p = m.xy + 6 * (size_t)el[side];
+                const double ax = p[2 * ca[side]], ay = p[2 * ca[side] + 1];
+                const double ex = p[2 * cb[side]] - ax, ey = p[2 * cb[side] + 1] - ay;
+                const double cx = (p[0] + p[2] + p[4]) / 3.0 - ax, cy = (p[1] + p[3] + p[5]) / 3.0 - ay;
+                len[side] = std::sqrt(ex * ex + ey * ey);
+                ang[side] = std::atan2(ey, ex);
+                along[side] = (cx * ex + cy * ey) / len[side];
+                perp[side] = std::fabs(cx * ey - cy * ex) / len[side];
+            }
+            const double L = 0.5 * (len[0] + len[1]);
+            const double da = along[0] - along[1], dp = perp[0] + perp[1];
+            const double d = std::sqrt(da * da + dp * dp);
+            const double rot = ang[0] - ang[1];
+            out.visc_geo[3 * (size_t)i + k] =
+                make_float4((float)std::cos(rot), (float)std::sin(rot), (float)(L / d), (float)L);
+            const double ho = (m.depth[to[0]] + m.depth[to[1]] + m.depth[to[2]]) / 3.0;
+            srow += 0.5 * (out.h0_e[i] + ho) / out.h0_e[i] * (L / d);
+        }
+        out.visc_nb[i] = make_int4(nbn[0], nbn[1], nbn[2], 0);
+        vstiff = std::max(vstiff, 2.0 * srow / out.area_e[i]);
+    }
+    out.visc_stiffness = vstiff;
     out.nbasin = 1;
     out.patch_basin.assign(npatch, 0);
     out.basin_v = {0, nv};
     out.basin_e = {0, ne};
     out.basin_patch = {0, npatch};
     out.basin_stiffness = {out.grad_gram_max_h};
+    out.basin_visc_stiffness = {out.visc_stiffness};
     return SESW_OK;
 }
 
@@ -425,6 +483,12 @@ void concat_meshes(std::vector<HostMesh> &parts, HostMesh &out)
         out.area_v.insert(out.area_v.end(), h.area_v.begin(), h.area_v.end());
         out.area_e.insert(out.area_e.end(), h.area_e.begin(), h.area_e.end());
         out.h0_e.insert(out.h0_e.end(), h.h0_e.begin(), h.h0_e.end());
+        for (const int4 &q : h.visc_nb)
+            out.visc_nb.push_back(make_int4(q.x < 0 ? -1 : q.x + eo, q.y < 0 ? -1 : q.y + eo,
+                                            q.z < 0 ? -1 : q.z + eo, 0));
+        out.visc_geo.insert(out.visc_geo.end(), h.visc_geo.begin(), h.visc_geo.end());
+        out.visc_stiffness = std::max(out.visc_stiffness, h.visc_stiffness);
+        out.basin_visc_stiffness.push_back(h.visc_stiffness);
         out.max_patch_slots = std::max(out.max_patch_slots, h.max_patch_slots);
         out.max_patch_vertices = std::max(out.max_patch_vertices, h.max_patch_vertices);
         out.patch_vertices = std::max(out.patch_vertices, h.patch_vertices);

@@ -152,11 +152,22 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
             e = cudaMemcpyAsync(Er[0], Er[M % 5], sizeof(float) * (size_t)c->dm.nv, cudaMemcpyDeviceToDevice,
                                 c->cap_stream);
     } else {
+        // with the barotropic viscosity each substep reads U^m from one buffer (its
+        // neighbours' too) and writes U^{m+1} to the other; U^M goes back to ds.U
         int p = parity;
+        float2 *B[2] = {c->ds.U, c->ds.U_x[0]};
         for (int m = 0; m < c->params.M && e == cudaSuccess; m++) {
-            e = sesw::launch_substep(c->dm, c->ds, c->args, p, c->block_threads, c->cap_stream);
+            if (c->visc_on) {
+                sesw::SubstepViscArgs v{c->vargs, m == 0, B[m & 1], B[(m + 1) & 1]};
+                e = sesw::launch_substep(c->dm, c->ds, c->args, p, c->block_threads, c->cap_stream, &v);
+            } else {
+                e = sesw::launch_substep(c->dm, c->ds, c->args, p, c->block_threads, c->cap_stream);
+            }
             p ^= 1;
         }
+        if (e == cudaSuccess && c->visc_on && (c->params.M & 1))
+            e = cudaMemcpyAsync(B[0], B[1], sizeof(float2) * (size_t)c->dm.nslot, cudaMemcpyDeviceToDevice,
+                                c->cap_stream);
         if (e == cudaSuccess) e = sesw::launch_step_epilogue(c->dm, c->ds, c->args, c->cap_stream);
     }
     cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
@@ -417,6 +428,10 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     sesw::surrogate_release(c);
     free_all(c);
     c->have_mesh = c->have_params = false;
+    c->visc_on = c->have_W = false;
+    c->visc_out = nullptr;
+    c->W_buf = nullptr;
+    c->visc_number = 0.0;
 
     sesw::DevMesh &d = c->dm;
     d.nv = hm.nv;
@@ -516,6 +531,17 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.eta_x[2], hm.nv, "eta_x"));
         TRY(zalloc(c, &s.U_x[0], hm.nslot, "U_x"));
         TRY(zalloc(c, &s.U_x[1], hm.nslot, "U_x"));
+        // viscosity neighbours as owner slots
+        std::vector<int> eslot(hm.ne, -1);
+        for (int q = 0; q < hm.nslot; q++)
+            if (hm.slot_v[q].w >= 0) eslot[hm.slot_v[q].w] = q;
+        std::vector<int4> nbs(hm.ne);
+        for (int i = 0; i < hm.ne; i++) {
+            const int4 o = hm.visc_nb[i];
+            nbs[i] = make_int4(o.x < 0 ? -1 : eslot[o.x], o.y < 0 ? -1 : eslot[o.y], o.z < 0 ? -1 : eslot[o.z], 0);
+        }
+        TRY(upload(c, &d.visc_nb, nbs, "visc_nb"));
+        TRY(upload(c, &d.visc_geo, hm.visc_geo, "visc_geo"));
         CK(c, sesw::substep_smem_attr(d));
     }
     CK(c, cudaStreamSynchronize(c->stream));
@@ -528,6 +554,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     c->nbasin = hm.nbasin;
     c->patch_basin = hm.patch_basin;
     c->basin_stiffness = hm.basin_stiffness;
+    c->basin_visc_stiffness = hm.basin_visc_stiffness;
     c->npatch = hm.npatch;
     c->nslot = hm.nslot;
     c->max_patch_slots = hm.max_patch_slots;
@@ -574,7 +601,7 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
 {
     DeviceGuard dg(c->device);
     const sesw_params *p = &ps[0];
-    double cmax_all = 0.0, limit = 0.0;
+    double cmax_all = 0.0, limit = 0.0, vnum_all = 0.0;
     // SESM coefficients (Eq. 4.7); all zero: beta of Sect. 3.2 and Eq. dp_6 at chi = theta / 2
     double beta = p->sesm_beta, delta = p->sesm_delta, gam = p->sesm_gamma, zeta = p->sesm_zeta;
     if (beta == 0.0 && delta == 0.0 && gam == 0.0 && zeta == 0.0) {
@@ -597,10 +624,18 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
         if (q.scheme != 0 && q.scheme != 1) return fail(c, SESW_EINVAL, "scheme must be 0 (SE) or 1 (SESM)");
         if (q.scheme == 1 && c->mode == SESW_MODE_PERSISTENT)
             return fail(c, SESW_EINVAL, "the SESM scheme runs in SESW_MODE_GRAPH; set the mode before the upload");
+        if (!(q.visc_background >= 0.0) || !isfinite(q.visc_background) || !(q.visc_flow >= 0.0) ||
+            !isfinite(q.visc_flow))
+            return fail(c, SESW_EINVAL, "visc_background and visc_flow must be >= 0 and finite");
+        const bool visc = q.visc_background > 0.0 || q.visc_flow > 0.0;
+        if (visc && q.scheme != 0)
+            return fail(c, SESW_EINVAL, "the barotropic viscosity is available with the SE scheme (scheme 0)");
+        if (visc && c->mode == SESW_MODE_PERSISTENT)
+            return fail(c, SESW_EINVAL, "the barotropic viscosity runs in SESW_MODE_GRAPH; set the mode before the upload");
         if (q.g != p->g || q.theta != p->theta || q.M != p->M || q.nonlinear_h != p->nonlinear_h ||
             q.flags != p->flags || q.eta_bound != p->eta_bound || q.scheme != p->scheme ||
             q.sesm_beta != p->sesm_beta || q.sesm_delta != p->sesm_delta || q.sesm_gamma != p->sesm_gamma ||
-            q.sesm_zeta != p->sesm_zeta)
+            q.sesm_zeta != p->sesm_zeta || q.visc_background != p->visc_background || q.visc_flow != p->visc_flow)
             return fail(c, SESW_EINVAL, "meshes of one batch may differ only in tau");
         const double dt = q.tau / q.M;
         // upper bound of dt sqrt(lambda_max(-div g H0 grad)), see prepare_mesh
@@ -615,7 +650,21 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
             return fail(c, SESW_EINVAL, buf);
         }
         cmax_all = std::max(cmax_all, cmax);
+        // explicit viscous step: dt times a Gershgorin bound of the background part's
+        // eigenvalues (at rest depth) must stay below 1, half the forward-Euler limit
+        const double vnum = dt * q.visc_background * c->basin_visc_stiffness[b];
+        if (vnum > 1.0 && !(q.flags & SESW_FLAG_NO_STABILITY_CHECK)) {
+            char buf[320];
+            snprintf(buf, sizeof buf,
+                     "%s%sviscous number %.4f of the barotropic viscosity exceeds 1; lower visc_background or "
+                     "increase M",
+                     n > 1 ? "basin " : "", n > 1 ? (std::to_string(b) + ": ").c_str() : "", vnum);
+            return fail(c, SESW_EINVAL, buf);
+        }
+        vnum_all = std::max(vnum_all, vnum);
     }
+    const bool visc_on = p->visc_background > 0.0 || p->visc_flow > 0.0;
+    if (visc_on && !c->ds.V0) TRY(zalloc(c, &c->ds.V0, (size_t)c->dm.nslot, "V0"));
     drop_graphs(c);
     c->params = *p;
     if (!(c->params.eta_bound > 0.0)) c->params.eta_bound = 1e4;
@@ -646,6 +695,11 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
     CK(c, cudaStreamSynchronize(c->stream));
     c->courant_max = cmax_all;
     c->courant_limit = limit;
+    c->visc_on = visc_on;
+    c->vargs.background = (float)p->visc_background;
+    c->vargs.flow = (float)p->visc_flow;
+    c->vargs.nonlinear_h = p->nonlinear_h;
+    c->visc_number = vnum_all;
     c->have_params = true;
     return SESW_OK;
 }
@@ -687,6 +741,61 @@ int sesw_set_forcing(sesw_ctx *c, const double *R, int where)
         dr = st;
     }
     CK(c, sesw::launch_scatter_forcing(c->dm, c->ds, dr, c->stream));
+    return SESW_OK;
+}
+
+int sesw_set_freshwater(sesw_ctx *c, const double *W, int where)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting the freshwater flux");
+    if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    DeviceGuard dg(c->device);
+    if (!W) {
+        if (c->have_W) {
+            // the step graphs hold the pointer: capture again without it
+            drop_graphs(c);
+            c->ds.W = nullptr;
+            c->have_W = false;
+        }
+        return SESW_OK;
+    }
+    if (!c->W_buf) TRY(zalloc(c, &c->W_buf, (size_t)c->dm.nv, "W"));
+    const double *dw = W;
+    if (where == SESW_HOST) {
+        double *st = c->ds.stage;
+        CK(c, cudaMemcpyAsync(st, W, sizeof(double) * c->dm.nv, cudaMemcpyHostToDevice, c->stream));
+        dw = st;
+    }
+    sesw::DevState tmp = c->ds;
+    tmp.eta[0] = c->W_buf;
+    CK(c, sesw::launch_scatter_state(c->dm, tmp, dw, nullptr, 0, c->stream));
+    if (!c->have_W) {
+        drop_graphs(c);
+        c->ds.W = c->W_buf;
+        c->have_W = true;
+    }
+    return SESW_OK;
+}
+
+int sesw_viscosity(sesw_ctx *c, double *out, int where)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh || !c->have_params) return fail(c, SESW_ESTATE, "mesh and parameters must be set first");
+    if (!out) return fail(c, SESW_EINVAL, "out is NULL");
+    if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    if (c->mode != SESW_MODE_GRAPH)
+        return fail(c, SESW_EINVAL, "the barotropic viscosity runs in SESW_MODE_GRAPH; set the mode before the upload");
+    DeviceGuard dg(c->device);
+    if (!c->visc_out) TRY(zalloc(c, &c->visc_out, (size_t)c->dm.ne, "visc_out"));
+    CK(c, sesw::launch_viscosity(c->dm, c->ds, c->vargs, c->parity, c->visc_out, c->stream));
+    sesw::DevState tmp = c->ds;
+    tmp.Umean = c->visc_out;
+    double *dst = where == SESW_DEVICE ? out : c->ds.stage;
+    CK(c, sesw::launch_gather_state(c->dm, tmp, c->parity, nullptr, nullptr, dst, c->stream));
+    if (where == SESW_HOST) {
+        CK(c, cudaMemcpyAsync(out, dst, sizeof(double) * 2 * c->dm.ne, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
     return SESW_OK;
 }
 
@@ -829,6 +938,7 @@ int sesw_mesh_check(const sesw_mesh *mesh, int32_t patch_vertices, sesw_info *in
         info->max_patch_slots = hm.max_patch_slots;
         info->patch_vertices = hm.patch_vertices;
         info->stiffness_bound = hm.grad_gram_max_h;
+        info->visc_stiffness = hm.visc_stiffness;
     }
     return rc;
 }
@@ -855,6 +965,8 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->device_bytes = c->device_bytes;
     info->nbasin = c->nbasin;
     info->npack = c->mode == SESW_MODE_PERSISTENT ? (int32_t)c->dm.pack_off.size() - 1 : 0;
+    info->visc_number = c->have_params ? c->visc_number : 0.0;
+    for (double v : c->basin_visc_stiffness) info->visc_stiffness = std::max(info->visc_stiffness, v);
     return SESW_OK;
 }
 

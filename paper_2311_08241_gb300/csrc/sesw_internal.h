@@ -45,6 +45,12 @@ struct HostMesh {
     std::vector<double> area_e;    // element area (FP64), new element order
     std::vector<double> h0_e;      // element rest depth (FP64), new element order
     double grad_gram_max_h = 0.0;  // upper bound of lambda_max(-div H0 grad) (m/s^2 units without g)
+    // Barotropic viscosity (Eq. viscosity_BT), new element order: neighbours across the
+    // edges (corner k, corner k+1) as element ids (-1: coast), and per edge the rotation
+    // from the neighbour's frame (cos, sin), L/d and L of the two-point flux.
+    std::vector<int4> visc_nb;
+    std::vector<float4> visc_geo;  // [ne][3]
+    double visc_stiffness = 0.0;   // max_e 2 sum_k (H0_edge / H0_e)(L/d) / A_e (1/m^2)
 
     // Batches: a layout may hold several independent meshes ("basins"), each prepared
     // on its own and concatenated; patches never straddle basins.
@@ -54,6 +60,7 @@ struct HostMesh {
     std::vector<int> basin_e;          // [nbasin+1] caller element ranges
     std::vector<int> basin_patch;      // [nbasin+1] patch ranges
     std::vector<double> basin_stiffness;   // per basin, as grad_gram_max_h
+    std::vector<double> basin_visc_stiffness;   // per basin, as visc_stiffness
 
     // Halo structure for the persistent kernel (filled by build_halos). A patch keeps
     // its own vertices at local indices [0, n_own) and its halo vertices (corners of
@@ -103,6 +110,8 @@ struct DevMesh {
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
     float *patch_dt = nullptr;     // [npatch] substep length tau/M of the patch's basin
+    int4 *visc_nb = nullptr;       // [ne] owner slots of the neighbours across the edges (-1: coast)
+    float4 *visc_geo = nullptr;    // [ne][3] (cos, sin, L/d, L), see HostMesh
     int nbasin = 1;
     int *basin_v = nullptr;        // [nbasin+1] vertex ranges (new order = caller order per basin)
     int *basin_slot = nullptr;     // [nbasin+1] slot ranges
@@ -142,6 +151,26 @@ struct DevState {
     float2 *U_x[2] = {nullptr, nullptr};
     // optional sum of eta^0 .. eta^{M-1} over the last step (SE; cleared at each step start)
     float *eta_sum = nullptr;
+    // freshwater flux W (m/s, positive out of the ocean), new vertex order; NULL when unset
+    float *W = nullptr;
+    // barotropic viscosity (SE, graph mode): its start-of-step value per slot
+    float2 *V0 = nullptr;
+};
+
+// Viscosity coefficients of one launch (Eq. viscosity_BT): A = background + flow |du| L.
+struct ViscArgs {
+    float background, flow;
+    int nonlinear_h;
+};
+
+// A substep with the barotropic viscosity (graph mode): transports are read from U_in
+// (U^m) and written to U_out (U^{m+1}); start = 1 on substep 0 of a step, which stores
+// the term's start-of-step value in DevState::V0.
+struct SubstepViscArgs {
+    ViscArgs va;
+    int start;
+    const float2 *U_in;
+    float2 *U_out;
 };
 
 // Level pointers of one SESM launch (see k_sesm).
@@ -167,12 +196,16 @@ struct StepArgs {
 // Kernel launchers (sesw_kernels.cu). All enqueue on `stream` and return the
 // launch error.
 cudaError_t launch_substep(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
-                           int block, cudaStream_t stream);
+                           int block, cudaStream_t stream, const SubstepViscArgs *visc = nullptr);
 cudaError_t substep_smem_attr(const DevMesh &m);
 cudaError_t launch_step_epilogue(const DevMesh &m, const DevState &s, const StepArgs &a,
                                  cudaStream_t stream);
 cudaError_t launch_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, const SesmPtrs &q, int block,
                         cudaStream_t stream);
+// The barotropic viscosity alone at the state (s.U, s.eta[parity]): R_hV of every
+// element into out[new element].
+cudaError_t launch_viscosity(const DevMesh &m, const DevState &s, const ViscArgs &v, int parity, float2 *out,
+                             cudaStream_t stream);
 cudaError_t launch_scatter_state(const DevMesh &m, const DevState &s, const double *eta,
                                  const double *U, int parity, cudaStream_t stream);
 cudaError_t launch_scatter_forcing(const DevMesh &m, const DevState &s, const double *R,
@@ -237,7 +270,14 @@ struct sesw_ctx {
     int nbasin = 1;
     std::vector<int> patch_basin;
     std::vector<double> basin_stiffness;
+    std::vector<double> basin_visc_stiffness;
     std::vector<float> patch_dt_host;
+    double visc_number = 0.0;      // largest dt A_bg visc_stiffness over the basins
+    bool visc_on = false;          // barotropic viscosity in the step (graph mode, SE)
+    sesw::ViscArgs vargs{};
+    float2 *visc_out = nullptr;    // [ne] scratch of sesw_viscosity (allocated on first use)
+    float *W_buf = nullptr;        // [nv] freshwater flux (allocated on first use)
+    bool have_W = false;
     sesw::Surrogate *sur = nullptr;
 };
 

@@ -1,6 +1,7 @@
 // CUDA kernels of libsesw (sm_103a): the split-explicit barotropic substep of
-// Eq. (4.10), the time-mean transport of Eq. (4.12), state transfer and FP64
-// diagnostics.
+// Eq. (4.10) (with the freshwater flux W of Eq. 4.5), the SESM substep of Eqs.
+// (4.7)-(4.8), the barotropic viscous regularisation of Eq. (viscosity_BT), the
+// time-mean transport of Eq. (4.12), state transfer and FP64 diagnostics.
 //
 // Substep kernel layout. One thread block per vertex patch (a contiguous range of
 // Hilbert-ordered vertices). The block first updates every element slot of the
@@ -37,26 +38,81 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
     lo = __fadd_rn(lo, err);
 }
 
+// Barotropic viscous regularisation, Eq. (viscosity_BT), of the element w held by a
+// slot with depth H and transport Us: a two-point flux across each edge with a
+// neighbour (owner slot nb.k, or -1 at a coast),
+//   u = U / H here and on the neighbour, du = rot(u_nb) - u with rot the turn from the
+//   neighbour's frame into this one, A = background + flow |du| L,
+//   R_hV = (1/A_e) sum_edges (H + H_nb)/2 A (L/d) du,
+// H_nb = H0 (+ corner mean of eta when nonlinear) of the neighbour. Every copy of an
+// element evaluates this from the same owner-slot inputs, so guests stay equal to owners.
+__device__ __forceinline__ float2 visc_of(int w, float H, float2 Us, float area, const int4 *__restrict__ sv,
+                                          const float4 *__restrict__ sc, const float2 *U,
+                                          const int4 *__restrict__ vnb, const float4 *__restrict__ vgeo,
+                                          const float *__restrict__ eta, const ViscArgs va)
+{
+    const float ux = Us.x / H, uy = Us.y / H;
+    const int4 nb = vnb[w];
+    const int nbs[3] = {nb.x, nb.y, nb.z};
+    float fx = 0.0f, fy = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int q = nbs[k];
+        if (q < 0) continue;
+        const float4 gq = vgeo[3 * (size_t)w + k];
+        float Hn = sc[q].y;
+        if (va.nonlinear_h) {
+            const int4 vq = sv[q];
+            Hn += (eta[vq.x] + eta[vq.y] + eta[vq.z]) * (1.0f / 3.0f);
+        }
+        const float2 Uq = U[q];
+        const float nx = Uq.x / Hn, ny = Uq.y / Hn;
+        const float dx = (gq.x * nx - gq.y * ny) - ux;
+        const float dy = (gq.y * nx + gq.x * ny) - uy;
+        const float A = va.background + va.flow * sqrtf(dx * dx + dy * dy) * gq.w;
+        const float kq = 0.5f * (H + Hn) * A * gq.z;
+        fx += kq * dx;
+        fy += kq * dy;
+    }
+    return make_float2(fx / area, fy / area);
+}
+
+// Viscosity inputs of the substep kernel (VISC = 1): transports are read from U_in (level
+// m, also the neighbours') and written to U_out (level m + 1), and the forcing of the
+// substep is R + (R_hV - V0) with V0 the value at substep 0 of the step (start = 1
+// stores it; Sect. 2.2 subtracts the term's start value).
+struct SubstepVisc {
+    const int4 *vnb;
+    const float4 *vgeo;
+    float2 *V0;
+    ViscArgs va;
+    int start;
+};
+
 // One substep of Eq. (4.10) for all slots and vertices of the patch blockIdx.x.
 //
 // Element part (per slot, corners v0, v1, v2, gradients g0, g1, g2 = -g0 - g1):
 //   grad eta = (eta0 - eta2) g0 + (eta1 - eta2) g1
 //   H        = H0_e (+ (eta0 + eta1 + eta2)/3 when nonlinear)
 //   a        = f dt / 2
-//   r        = (Ux + a Uy, Uy - a Ux) + dt (R - g H grad eta)
+//   r        = (Ux + a Uy, Uy - a Ux) + dt (R' - g H grad eta),  R' = R (+ R_hV - V0 with VISC)
 //   U'       = (rx + a ry, ry - a rx) / (1 + a^2)           Crank-Nicolson Coriolis
 //   F        = (1 + theta) U' - theta U
 //   c_k      = dt A_e F . g_k, k = 0, 1;  c_2 = -(c_0 + c_1)  flux into corner k's cell
-// Vertex part: eta' = eta + (sum of c over the vertex's incidences) / A_v.
-template <int NONLIN>
+// Vertex part: eta' = eta + (sum of c over the vertex's incidences) / A_v - dt W
+// (W: freshwater flux of Eq. 4.5, positive out of the ocean; W == NULL means 0).
+// Without VISC, U_in and U_out are the same array (each slot is read, then written, by
+// one thread).
+template <int NONLIN, int VISC>
 __global__ void __launch_bounds__(kSubstepMaxThreads)
 k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 *__restrict__ sc,
-          const float2 *__restrict__ R, float2 *__restrict__ U, float2 *__restrict__ Shi,
+          const float2 *__restrict__ R, const float2 *U_in, float2 *U_out, float2 *__restrict__ Shi,
           float2 *__restrict__ Slo, const int *__restrict__ patch_slot, const int *__restrict__ patch_own,
           const int *__restrict__ patch_v, const int *__restrict__ vcsr_off,
           const uint32_t *__restrict__ vcsr, const float *__restrict__ inv_av,
           const float *__restrict__ eta_in, float *__restrict__ eta_out, const float *__restrict__ patch_dt,
-          float *__restrict__ eta_sum, StepArgs a, unsigned *__restrict__ status)
+          float *__restrict__ eta_sum, const float *__restrict__ W, SubstepVisc vis, StepArgs a,
+          unsigned *__restrict__ status)
 {
     extern __shared__ float sflux[];
     const int p = blockIdx.x;
@@ -71,14 +127,24 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
         const int4 v = sv[s];
         const float4 g = sg[s];
         const float4 c = sc[s];
-        const float2 r = R[s];
-        const float2 u = U[s];
+        float2 r = R[s];
+        const float2 u = U_in[s];
         const float e0 = eta_in[v.x], e1 = eta_in[v.y], e2 = eta_in[v.z];
         const float d0 = e0 - e2, d1 = e1 - e2;
         const float gx = d0 * g.x + d1 * g.z;
         const float gy = d0 * g.y + d1 * g.w;
         float H = c.y;
         if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
+        if (VISC) {
+            const float2 V = visc_of(v.w >= 0 ? v.w : -1 - v.w, H, u, c.x, sv, sc, U_in, vis.vnb, vis.vgeo, eta_in,
+                                     vis.va);
+            if (vis.start) {
+                vis.V0[s] = V;      // R' = R + (V - V) = R
+            } else {
+                const float2 z = vis.V0[s];
+                r = make_float2(r.x + (V.x - z.x), r.y + (V.y - z.y));
+            }
+        }
         const float gH = a.g * H;
         const float aa = c.z * half_dt;
         const float rx = u.x + aa * u.y + dt * (r.x - gH * gx);
@@ -86,7 +152,7 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
         const float inv = 1.0f / (1.0f + aa * aa);
         const float nx = (rx + aa * ry) * inv;
         const float ny = (ry - aa * rx) * inv;
-        U[s] = make_float2(nx, ny);
+        U_out[s] = make_float2(nx, ny);
         const float fx = one_p_theta * nx - a.theta * u.x;
         const float fy = one_p_theta * ny - a.theta * u.y;
         if (i < nown) {
@@ -114,7 +180,8 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
             const uint32_t q = vcsr[k];
             sum += sflux[3 * (q >> 2) + (q & 3u)];
         }
-        const float e = eta_in[v] + sum * inv_av[v];
+        float e = eta_in[v] + sum * inv_av[v];
+        if (W) e -= dt * W[v];
         if (eta_sum) eta_sum[v] += eta_in[v];     // sum of eta^0 .. eta^{M-1} (time mean of the step)
         eta_out[v] = e;
         bad |= !(fabsf(e) <= a.eta_bound);
@@ -129,7 +196,7 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
 //     eta_AM = am0 eta^m + am1 eta^{m-1} + am2 eta^{m-2} + am3 eta^{m-3},
 //     U_AB^{m-1} = ab0 U^{m-1} + ab1 U^{m-2} + ab2 U^{m-3}
 // (skipped for m = 0), then forms U_AB^m = ab0 U^m + ab1 U^{m-1} + ab2 U^{m-2}, adds it
-// to the compensated sum S and updates eta^{m+1} = eta^m - dt div(U_AB^m). Levels before
+// to the compensated sum S and updates eta^{m+1} = eta^m - dt (div(U_AB^m) + W). Levels before
 // the start of the subcycle are passed as aliases of level 0.
 struct SesmLevels {
     const float2 *u1, *u2, *u3;      // U^{m-1}, U^{m-2}, U^{m-3}
@@ -146,7 +213,8 @@ k_sesm(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 
        const float2 *__restrict__ R, float2 *__restrict__ Shi, float2 *__restrict__ Slo,
        const int *__restrict__ patch_slot, const int *__restrict__ patch_own, const int *__restrict__ patch_v,
        const int *__restrict__ vcsr_off, const uint32_t *__restrict__ vcsr, const float *__restrict__ inv_av,
-       const float *__restrict__ patch_dt, SesmLevels L, StepArgs a, unsigned *__restrict__ status)
+       const float *__restrict__ patch_dt, const float *__restrict__ W, SesmLevels L, StepArgs a,
+       unsigned *__restrict__ status)
 {
     extern __shared__ float sflux[];
     const int p = blockIdx.x;
@@ -211,7 +279,8 @@ k_sesm(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 
             const uint32_t q = vcsr[k];
             sum += sflux[3 * (q >> 2) + (q & 3u)];
         }
-        const float e = L.e0[v] + sum * inv_av[v];
+        float e = L.e0[v] + sum * inv_av[v];
+        if (W) e -= dt * W[v];
         L.enew[v] = e;
         bad |= !(fabsf(e) <= a.eta_bound);
     }
@@ -229,6 +298,23 @@ __global__ void k_epilogue(const int4 *__restrict__ sv, float2 *__restrict__ Shi
         Umean[w] = make_float2((hi.x + lo.x) * inv_M, (hi.y + lo.y) * inv_M);
         Shi[s] = make_float2(0.0f, 0.0f);
         Slo[s] = make_float2(0.0f, 0.0f);
+    }
+}
+
+// R_hV of every element at (U, eta) into out[element] (the operator alone; the step
+// evaluates it inside k_substep). One thread per owned slot.
+__global__ void __launch_bounds__(kAuxThreads)
+k_viscosity(const int4 *__restrict__ sv, const float4 *__restrict__ sc, const float2 *__restrict__ U,
+            const int4 *__restrict__ vnb, const float4 *__restrict__ vgeo, const float *__restrict__ eta,
+            ViscArgs va, float2 *__restrict__ out, int nslot)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslot; s += gridDim.x * blockDim.x) {
+        const int4 v = sv[s];
+        if (v.w < 0) continue;
+        const float4 c = sc[s];
+        float H = c.y;
+        if (va.nonlinear_h) H += (eta[v.x] + eta[v.y] + eta[v.z]) * (1.0f / 3.0f);
+        out[v.w] = visc_of(v.w, H, U[s], c.x, sv, sc, U, vnb, vgeo, eta, va);
     }
 }
 
@@ -412,6 +498,7 @@ struct PArgs {
     const float *eta_in;
     float *eta_out;
     float *eta_sum;         // null, or sum over the substeps of eta^0 .. eta^{M-1} (own vertices)
+    const float *W;         // null, or the freshwater flux of each vertex (Eq. 4.5)
     float *xb[2];
     unsigned *flags;        // [npatch], then the abort word
     unsigned *status;
@@ -512,7 +599,7 @@ __device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a, f
     return make_float4(dt * c.x, a.g * c.y, aa, 1.0f / (1.0f + aa * aa));
 }
 
-template <int SPT, int NONLIN, int CACHED>
+template <int SPT, int NONLIN, int CACHED, int FW>
 __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -639,7 +726,8 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                 }
                 inv = P.inv_av[v0 + i];
             }
-            const float e = seta[i] + sum * inv;
+            float e = seta[i] + sum * inv;
+            if (FW) e -= dt * __ldg(P.W + v0 + i);
             if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
             seta[i] = e;
             if (more) __stcg(xout + v0 + i, e);
@@ -669,30 +757,33 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     }
 }
 
+// fw: the freshwater flux is set (a separate instantiation keeps the path without it
+// free of the extra load and branch)
 template <int SPT, int CACHED>
-void *persistent_fn(int nonlin)
+void *persistent_fn(int nonlin, int fw)
 {
-    return nonlin ? (void *)k_persistent<SPT, 1, CACHED> : (void *)k_persistent<SPT, 0, CACHED>;
+    if (fw) return nonlin ? (void *)k_persistent<SPT, 1, CACHED, 1> : (void *)k_persistent<SPT, 0, CACHED, 1>;
+    return nonlin ? (void *)k_persistent<SPT, 1, CACHED, 0> : (void *)k_persistent<SPT, 0, CACHED, 0>;
 }
 
-void *persistent_kernel(int spt, int nonlin, int cached)
+void *persistent_kernel(int spt, int nonlin, int cached, int fw)
 {
     if (cached) {
         switch (spt) {
-        case 1: return persistent_fn<1, 1>(nonlin);
-        case 2: return persistent_fn<2, 1>(nonlin);
-        case 3: return persistent_fn<3, 1>(nonlin);
-        case 4: return persistent_fn<4, 1>(nonlin);
+        case 1: return persistent_fn<1, 1>(nonlin, fw);
+        case 2: return persistent_fn<2, 1>(nonlin, fw);
+        case 3: return persistent_fn<3, 1>(nonlin, fw);
+        case 4: return persistent_fn<4, 1>(nonlin, fw);
         default: return nullptr;
         }
     }
     switch (spt) {
-    case 1: return persistent_fn<1, 0>(nonlin);
-    case 2: return persistent_fn<2, 0>(nonlin);
-    case 3: return persistent_fn<3, 0>(nonlin);
-    case 4: return persistent_fn<4, 0>(nonlin);
-    case 6: return persistent_fn<6, 0>(nonlin);
-    case 8: return persistent_fn<8, 0>(nonlin);
+    case 1: return persistent_fn<1, 0>(nonlin, fw);
+    case 2: return persistent_fn<2, 0>(nonlin, fw);
+    case 3: return persistent_fn<3, 0>(nonlin, fw);
+    case 4: return persistent_fn<4, 0>(nonlin, fw);
+    case 6: return persistent_fn<6, 0>(nonlin, fw);
+    case 8: return persistent_fn<8, 0>(nonlin, fw);
     default: return nullptr;
     }
 }
@@ -744,20 +835,34 @@ int grid_for(int n, int threads)
 }  // namespace
 
 cudaError_t launch_substep(const DevMesh &m, const DevState &s, const StepArgs &a, int parity, int block,
-                           cudaStream_t stream)
+                           cudaStream_t stream, const SubstepViscArgs *visc)
 {
     const int threads = block > 0 ? block : 256;
     const size_t smem = sizeof(float) * 3 * (size_t)m.max_patch_slots;
     const float *ein = s.eta[parity];
     float *eout = s.eta[parity ^ 1];
-    if (a.nonlinear_h)
-        k_substep<1><<<m.npatch, threads, smem, stream>>>(
-            m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
-            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, s.eta_sum, a, s.status);
-    else
-        k_substep<0><<<m.npatch, threads, smem, stream>>>(
-            m.slot_v, m.slot_g, m.slot_c, s.R, s.U, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,
-            m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, s.eta_sum, a, s.status);
+    SubstepVisc vis{};
+    const float2 *uin = s.U;
+    float2 *uout = s.U;
+    if (visc) {
+        vis.vnb = m.visc_nb;
+        vis.vgeo = m.visc_geo;
+        vis.V0 = s.V0;
+        vis.va = visc->va;
+        vis.start = visc->start;
+        uin = visc->U_in;
+        uout = visc->U_out;
+    }
+#define SESW_SUBSTEP(NL, VI)                                                                                      \
+    k_substep<NL, VI><<<m.npatch, threads, smem, stream>>>(                                                      \
+        m.slot_v, m.slot_g, m.slot_c, s.R, uin, uout, s.S_hi, s.S_lo, m.patch_slot, m.patch_own, m.patch_v,      \
+        m.vcsr_off, m.vcsr, m.inv_av, ein, eout, m.patch_dt, s.eta_sum, s.W, vis, a, s.status)
+    if (a.nonlinear_h) {
+        if (visc) SESW_SUBSTEP(1, 1); else SESW_SUBSTEP(1, 0);
+    } else {
+        if (visc) SESW_SUBSTEP(0, 1); else SESW_SUBSTEP(0, 0);
+    }
+#undef SESW_SUBSTEP
     return cudaGetLastError();
 }
 
@@ -796,8 +901,9 @@ int raise_smem_limit(const void *fn)
 cudaError_t substep_smem_attr(const DevMesh &m)
 {
     const size_t need = sizeof(float) * 3 * (size_t)m.max_patch_slots;
-    const void *fns[4] = {(const void *)k_substep<0>, (const void *)k_substep<1>, (const void *)k_sesm<0>,
-                          (const void *)k_sesm<1>};
+    const void *fns[6] = {(const void *)k_substep<0, 0>, (const void *)k_substep<1, 0>,
+                          (const void *)k_substep<0, 1>, (const void *)k_substep<1, 1>,
+                          (const void *)k_sesm<0>, (const void *)k_sesm<1>};
     for (const void *fn : fns) {
         const int l = raise_smem_limit(fn);
         if (l < 0 || (size_t)l < need) return cudaErrorInvalidValue;
@@ -825,11 +931,19 @@ cudaError_t launch_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, 
     if (a.nonlinear_h)
         k_sesm<1><<<m.npatch, threads, smem, stream>>>(m.slot_v, m.slot_g, m.slot_c, s.R, s.S_hi, s.S_lo,
                                                        m.patch_slot, m.patch_own, m.patch_v, m.vcsr_off, m.vcsr,
-                                                       m.inv_av, m.patch_dt, L, a, s.status);
+                                                       m.inv_av, m.patch_dt, s.W, L, a, s.status);
     else
         k_sesm<0><<<m.npatch, threads, smem, stream>>>(m.slot_v, m.slot_g, m.slot_c, s.R, s.S_hi, s.S_lo,
                                                        m.patch_slot, m.patch_own, m.patch_v, m.vcsr_off, m.vcsr,
-                                                       m.inv_av, m.patch_dt, L, a, s.status);
+                                                       m.inv_av, m.patch_dt, s.W, L, a, s.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_viscosity(const DevMesh &m, const DevState &s, const ViscArgs &v, int parity, float2 *out,
+                             cudaStream_t stream)
+{
+    k_viscosity<<<grid_for(m.nslot, kAuxThreads), kAuxThreads, 0, stream>>>(
+        m.slot_v, m.slot_c, s.U, m.visc_nb, m.visc_geo, s.eta[parity], v, out, m.nslot);
     return cudaGetLastError();
 }
 
@@ -911,13 +1025,18 @@ PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm)
     int cached = (spt <= 4 && L.total_cached <= budget && m.max_patch_csr < 65536 && m.max_patch_slots < 16384) ? 1 : 0;
     const size_t smem = cached ? L.total_cached : L.total_plain;
     if (smem > budget) return plan;
-    void *fn = persistent_kernel(spt, 1, cached);
-    int occ = 0;
-    if (!fn || raise_smem_limit(fn) < (int)smem ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, smem) != cudaSuccess || occ < blocks_per_sm) {
-        cudaGetLastError();
-        return plan;
-    }
+    // every variant the plan may launch must reach blocks_per_sm resident blocks
+    for (int nonlin = 0; nonlin < 2; nonlin++)
+        for (int fw = 0; fw < 2; fw++) {
+            void *fn = persistent_kernel(spt, nonlin, cached, fw);
+            int occ = 0;
+            if (!fn || raise_smem_limit(fn) < (int)smem ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, smem) != cudaSuccess ||
+                occ < blocks_per_sm) {
+                cudaGetLastError();
+                return plan;
+            }
+        }
     plan.slots_per_thread = spt;
     plan.threads = t;
     plan.cached = cached;
@@ -927,11 +1046,11 @@ PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm)
 
 cudaError_t persistent_prepare(const PersistentPlan &plan)
 {
-    void *fn0 = persistent_kernel(plan.slots_per_thread, 0, plan.cached);
-    void *fn1 = persistent_kernel(plan.slots_per_thread, 1, plan.cached);
-    if (!fn0 || !fn1) return cudaErrorInvalidValue;
-    const int l0 = raise_smem_limit(fn0), l1 = raise_smem_limit(fn1);
-    if (l0 < (int)plan.smem || l1 < (int)plan.smem) return cudaErrorInvalidValue;
+    for (int nonlin = 0; nonlin < 2; nonlin++)
+        for (int fw = 0; fw < 2; fw++) {
+            void *fn = persistent_kernel(plan.slots_per_thread, nonlin, plan.cached, fw);
+            if (!fn || raise_smem_limit(fn) < (int)plan.smem) return cudaErrorInvalidValue;
+        }
     return cudaSuccess;
 }
 
@@ -961,6 +1080,7 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     P.eta_in = s.eta[parity];
     P.eta_out = s.eta[parity ^ 1];
     P.eta_sum = s.eta_sum;
+    P.W = s.W;
     P.xb[0] = s.xbuf[0];
     P.xb[1] = s.xbuf[1];
     P.flags = s.flags;
@@ -979,7 +1099,7 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     P.off_inv = L.off_inv;
     P.off_halo = L.off_halo;
     P.pack_patch = m.pack_patch;
-    void *fn = persistent_kernel(plan.slots_per_thread, a.nonlinear_h, plan.cached);
+    void *fn = persistent_kernel(plan.slots_per_thread, a.nonlinear_h, plan.cached, s.W != nullptr);
     if (!fn) return cudaErrorInvalidValue;
     // one cooperative launch per pack; all packs of a step use the same elevation parity
     for (size_t k = 0; k + 1 < m.pack_off.size(); k++) {

@@ -1181,6 +1181,9 @@ int sesw_surrogate_advance(sesw_ctx *c, int32_t nsteps, double resid_tol, int32_
     Surrogate &S = *c->sur;
     if (!c->have_params) return sesw::ctx_fail(c, SESW_ESTATE, "set parameters first");
     if (c->params.scheme != 0) return sesw::ctx_fail(c, SESW_EINVAL, "the surrogate replaces the SE subcycle");
+    if (c->visc_on || c->have_W)
+        return sesw::ctx_fail(c, SESW_EINVAL,
+                              "the surrogate is trained without the barotropic viscosity and the freshwater flux");
     int fb = 0;
     double resid = 0.0;
     const float tau = (float)c->params.tau;

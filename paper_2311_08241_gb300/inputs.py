@@ -71,6 +71,7 @@ class Params:
     nonlinear_h: int = 1
     scheme: int = 0            # 0: dissipative forward-backward (Eq. 4.10); 1: AB3-AM4 (Eqs. 4.7-4.8)
     sesm: tuple = None         # (beta, delta, gamma, zeta) for scheme 1; None: the library's default
+    visc: tuple = None         # (A_bg m^2/s, C_v) of the barotropic viscosity, Eq. (viscosity_BT); None: off
 
 
 @dataclasses.dataclass

@@ -38,7 +38,8 @@ _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", 
 EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_blocks_per_sm", "sesw_set_patch_vertices",
            "sesw_set_block_threads",
            "sesw_mesh_upload", "sesw_mesh_upload_batch", "sesw_set_params_batch", "sesw_diagnostics_batch",
-           "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_advance", "sesw_get_state",
+           "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_set_freshwater", "sesw_viscosity",
+           "sesw_advance", "sesw_get_state",
            "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_set_eta_mean", "sesw_get_eta_mean", "sesw_status", "sesw_mesh_check",
            "sesw_get_info", "sesw_last_error", "sesw_destroy",
            "sesw_surrogate_init", "sesw_surrogate_nparam", "sesw_surrogate_weights", "sesw_surrogate_scales",
@@ -65,7 +66,8 @@ class sesw_params(ctypes.Structure):
     _fields_ = [("g", ctypes.c_double), ("theta", ctypes.c_double), ("tau", ctypes.c_double),
                 ("M", ctypes.c_int32), ("nonlinear_h", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("eta_bound", ctypes.c_double), ("sesm_beta", ctypes.c_double),
-                ("sesm_delta", ctypes.c_double), ("sesm_gamma", ctypes.c_double), ("sesm_zeta", ctypes.c_double)]
+                ("sesm_delta", ctypes.c_double), ("sesm_gamma", ctypes.c_double), ("sesm_zeta", ctypes.c_double),
+                ("visc_background", ctypes.c_double), ("visc_flow", ctypes.c_double)]
 
 
 class sesw_info(ctypes.Structure):
@@ -75,7 +77,8 @@ class sesw_info(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("slots_per_thread", ctypes.c_int32),
                 ("cached", ctypes.c_int32), ("nbasin", ctypes.c_int32), ("courant_max", ctypes.c_double),
                 ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64), ("npack", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_int64), ("npack", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("visc_number", ctypes.c_double), ("visc_stiffness", ctypes.c_double)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -113,6 +116,8 @@ def load(build_if_missing: bool = True):
         L.sesw_diagnostics_batch.argtypes = [P, P, P]
         L.sesw_set_state.argtypes = [P, P, P, I]
         L.sesw_set_forcing.argtypes = [P, P, I]
+        L.sesw_set_freshwater.argtypes = [P, P, I]
+        L.sesw_viscosity.argtypes = [P, P, I]
         L.sesw_advance.argtypes = [P, ctypes.c_int32]
         L.sesw_get_state.argtypes = [P, P, P, P, I]
         L.sesw_diagnostics.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(D)]
@@ -291,6 +296,19 @@ class Subcycle:
         R = _as_f64(R)
         return self._check(self._L.sesw_set_forcing(self._h, _ptr(R), _where(R)))
 
+    def sesw_set_freshwater(self, W):
+        """Freshwater flux [nv] (m/s, positive out of the ocean); None removes it."""
+        W = _as_f64(W)
+        where = SESW_HOST if W is None else _where(W)
+        return self._check(self._L.sesw_set_freshwater(self._h, _ptr(W), where))
+
+    def sesw_viscosity(self, out=None):
+        """The barotropic viscous regularisation at the current state, [ne][2] in caller order."""
+        if out is None:
+            out = np.empty((self.ne, 2))
+        self._check(self._L.sesw_viscosity(self._h, _ptr(out), _where(out)))
+        return out
+
     def sesw_advance(self, nsteps: int):
         return self._check(self._L.sesw_advance(self._h, int(nsteps)))
 
@@ -396,8 +414,10 @@ class Subcycle:
 
 def _params_struct(p, flags=0, eta_bound=0.0):
     coef = getattr(p, "sesm", None) or (0.0, 0.0, 0.0, 0.0)
+    visc = getattr(p, "visc", None) or (0.0, 0.0)
     return sesw_params(float(p.g), float(p.theta), float(p.tau), int(p.M), int(p.nonlinear_h),
-                       int(getattr(p, "scheme", 0)), int(flags), float(eta_bound), *(float(x) for x in coef))
+                       int(getattr(p, "scheme", 0)), int(flags), float(eta_bound), *(float(x) for x in coef),
+                       *(float(x) for x in visc))
 
 
 def _mesh_struct(mesh):

@@ -85,6 +85,9 @@ def persistence_loss(sim, idx):
         sim.sesw_surrogate_weights(set=w)
 
 
+SURROGATE_STEP_KERNELS = 27
+
+
 def rollout_error(case, R, params_ref, weights, scales, nsteps, resid_tol, coarse_M=(), device=0,
                   surrogate_capacity=1):
     """From rest under forcing R: max |eta| difference to the plain subcycle after nsteps for the
@@ -125,6 +128,7 @@ def rollout_error(case, R, params_ref, weights, scales, nsteps, resid_tol, coars
         s.sesw_surrogate_scales(set=scales)
         s.sesw_set_forcing(R)
         s.sesw_set_state(np.zeros(case.mesh.nv), np.zeros((case.mesh.ne, 2)))
+        info = s.sesw_get_info()
         s.sesw_surrogate_advance(1, resid_tol)
         s.sesw_set_state(np.zeros(case.mesh.nv), np.zeros((case.mesh.ne, 2)))
         torch.cuda.synchronize()
@@ -138,9 +142,13 @@ def rollout_error(case, R, params_ref, weights, scales, nsteps, resid_tol, coars
         _, resid_nofb = s.sesw_surrogate_advance(nsteps, 1e30)
         eta_nofb = s.sesw_get_state()[0]
         t_nofb = (time.perf_counter() - t1) / nsteps
+    # kernels per surrogate step: state copy-in, features, 22 of the forward pass, apply to
+    # elements and vertices, residual; a fallback adds one plain step (one cooperative launch
+    # per pack, or M substeps and the epilogue in graph mode)
+    plain_launches = max(1, info["npack"]) if info["mode"] == S.SESW_MODE_PERSISTENT else params_ref.M + 1
     out["surrogate"] = {"resid_tol": resid_tol, "fallback_steps": nfb, "steps": nsteps,
                         "ms_per_step": 1e3 * t, "max_ssh_error_m": float(np.max(np.abs(eta - ref))),
-                        "last_residual": resid}
+                        "last_residual": resid, "gpu_launches": nsteps * SURROGATE_STEP_KERNELS + nfb * plain_launches}
     out["surrogate_no_fallback"] = {"ms_per_step": 1e3 * t_nofb,
                                     "max_ssh_error_m": float(np.max(np.abs(eta_nofb - ref))),
                                     "last_residual": resid_nofb}

@@ -267,10 +267,36 @@ def pin_freshwater_volume_and_eq_4_11(L=None):
         eta, U = e1, U1
 
 
+def pin_sesm_freshwater(L=None):
+    """The SESM continuity update carries W as Eq. (4.8) prints it: a uniform W from rest lowers a
+    flat surface by exactly tau W per step, and with a random state and W the volume falls by
+    tau sum A_v W per step while eta^{n+1} - eta^n = -tau (div <<U>> + W)."""
+    from oracle import closed
+    coef = closed.sesm_params(0.07)
+    case = I.tiny_jittered_case(nx=8, ny=6, seed=29, M=7, tau=70.0)
+    m = case.mesh
+    om = orc.OracleMesh(m, L)
+    eta, U, Um = om.advance_sesm(np.zeros((m.ne, 2)), case.params, coef, 3, np.zeros(m.nv), np.zeros((m.ne, 2)),
+                                 W=np.full(m.nv, 4e-5))
+    assert np.max(np.abs(eta + 3 * 70.0 * 4e-5)) <= 1e-15
+    assert np.max(np.abs(U)) <= 1e-12
+    av, _ = om.areas()
+    W = 1e-5 * np.random.default_rng(9).standard_normal(m.nv)
+    e0 = case.eta0
+    e1, U1, Um = om.advance_sesm(case.R, case.params, coef, 1, e0, case.U0, W=W)
+    assert abs(float(np.sum(av * (e1 - e0))) + 70.0 * float(np.sum(av * W))) <= 1e-12 * float(np.sum(av * np.abs(e0)))
+    r = (e1 - e0) + 70.0 * (om.divergence(Um) + W)
+    assert np.max(np.abs(r)) <= 1e-12 * max(1.0, np.max(np.abs(e0)))
+    ref = om.advance_sesm(case.R, case.params, coef, 2, e0, case.U0)
+    got = om.advance_sesm(case.R, case.params, coef, 2, e0, case.U0, W=np.zeros(m.nv))
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
 PINS = [pin_right_lattice_bloch, pin_equilateral_convergence, pin_uniform_velocity_is_free,
         pin_conserves_momentum_on_the_plane, pin_dissipates, pin_flow_dependent_part, pin_frame_covariance,
         pin_zero_coefficients_and_M1_are_the_plain_step, pin_start_value_is_subtracted,
-        pin_uniform_freshwater_closed_form, pin_freshwater_volume_and_eq_4_11]
+        pin_uniform_freshwater_closed_form, pin_freshwater_volume_and_eq_4_11, pin_sesm_freshwater]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -297,6 +323,8 @@ PLANTS = {
                                    "rx += Vm[2 * e]; ry += Vm[2 * e + 1];"),
     "freshwater_sign": ("for (int v = 0; v < nv; v++) eta[v] -= dt * (div[v] + W[v]);",
                         "for (int v = 0; v < nv; v++) eta[v] -= dt * (div[v] - W[v]);"),
+    "sesm_freshwater_sign": ("for (int v = 0; v < nv; v++) enew[v] = E[0][v] - dt * (div[v] + W[v]);",
+                             "for (int v = 0; v < nv; v++) enew[v] = E[0][v] - dt * (div[v] - W[v]);"),
     "viscosity_at_start_depth": ("if (xy) viscosity(m, U, eta, nonlinear_h, (real)Abg, (real)Cv, xy, Vm);",
                                  "if (xy) viscosity(m, U, eta, 0, (real)Abg, (real)Cv, xy, Vm);"),
 }
