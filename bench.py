@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -102,9 +103,11 @@ def sesm_bytes_per_substep(V, E):
 
 
 def viscosity_bytes_per_substep(V, E):
-    """k_viscosity: per element corners and coefficients 32, U 8, R 8, V0 8, Reff 8, neighbour
-    table 16, edge geometry 48 (128 B); per vertex eta 4. The substep then reads Reff in place of R."""
-    return 4 * V + 128 * E
+    """What the viscosity adds to a substep (fused into k_substep, planar frames): per element the
+    edge table (neighbour slots, opposite corners, rest depths, L/d, L^2/d: 64 B) and the
+    start-of-step value V0 (8 B). The neighbours' U and eta are re-reads of arrays the substep
+    already streams."""
+    return 72 * E
 
 
 def measured_hbm_peak():
@@ -117,9 +120,14 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+KERNEL_SOURCE = {"k_persistent": "sesw_persistent.cu"}
+
+
+def kernel_source_hash(kernel="k_persistent"):
+    """Hash of the source file that holds `kernel` (its profile is stale once this changes)."""
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", "sesw_kernels.cu"), "rb") as fh:
+    name = KERNEL_SOURCE.get(kernel, "sesw_kernels.cu")
+    with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", name), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -137,7 +145,7 @@ def profiled_traffic_for(kernel, workload):
         return None
     m1 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m1 or not m2 or m1.group(1) != kernel_source_hash():
+    if not m1 or not m2 or m1.group(1) != kernel_source_hash(kernel):
         return None
     return float(m2.group(1))
 
@@ -197,29 +205,59 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "CPU part") and v.strip():
+                    return v.strip()
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(case, seconds, rank, W=None):
-    """The FP64 oracle, as it stands, on the host cores: whole baroclinic steps until `seconds` elapse."""
+    """The FP64 oracle, as it stands, on the host cores: whole baroclinic steps until `seconds` elapse,
+    all cores (the reported value), then a shorter single-thread sample for context."""
     from oracle import runner as orc
 
     om = orc.OracleMesh(case.mesh)
-    cores = orc.set_threads(0)
-    eta, U = case.eta0.copy(), case.U0.copy()
-    steps = 0
     visc = getattr(case.params, "visc", None)
-    t0 = time.perf_counter()
-    while True:
-        if visc is None and W is None:
-            eta, U, _, _ = om.advance(case.R, case.params, 1, eta, U)
-        else:
-            eta, U, _ = om.advance_ext(case.R, case.params, 1, eta, U, W=W, visc=visc)
-        steps += 1
-        if time.perf_counter() - t0 >= seconds:
-            break
-    dt = time.perf_counter() - t0
+    sesm = getattr(case.params, "scheme", 0) == 1
+    if sesm:
+        from oracle import closed
+
+        coef = closed.sesm_params(case.params.theta / 2.0)
+
+    def sample(budget):
+        eta, U = case.eta0.copy(), case.U0.copy()
+        steps = 0
+        t0 = time.perf_counter()
+        while True:
+            if sesm:
+                eta, U, _ = om.advance_sesm(case.R, case.params, coef, 1, eta, U, W=W)
+            elif visc is None and W is None:
+                eta, U, _, _ = om.advance(case.R, case.params, 1, eta, U)
+            else:
+                eta, U, _ = om.advance_ext(case.R, case.params, 1, eta, U, W=W, visc=visc)
+            steps += 1
+            if time.perf_counter() - t0 >= budget:
+                break
+        return steps, time.perf_counter() - t0
+
+    cores = orc.set_threads(0)
+    steps, dt = sample(seconds)
+    orc.set_threads(1)
+    steps1, dt1 = sample(max(1.0, seconds / 4))
+    orc.set_threads(cores)
     om.close()
-    return {"value": case.mesh.nv * case.params.M * steps / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+    rate = lambda n, t: case.mesh.nv * case.params.M * n / t
+    return {"value": rate(steps, dt), "unit": METRIC, "cores": cores, "kind": "oracle",
+            "single_thread_value": rate(steps1, dt1), "cpu_model": cpu_model(),
             "sample": f"{steps} baroclinic steps ({steps * case.params.M} substeps) of the benchmark workload "
-                      f"from rest, FP64, OpenMP over {cores} threads, {dt:.1f} s wall"}
+                      f"from rest, FP64, OpenMP over {cores} threads, {dt:.1f} s wall; single thread: "
+                      f"{steps1} steps in {dt1:.1f} s"}
 
 
 def dist_setup(args):

@@ -1,6 +1,6 @@
 """Build libsesw.so in-tree with nvcc for sm_103a (GB300).
 
-The three translation units compile in parallel; the shared library links the CUDA
+The translation units compile in parallel; the shared library links the CUDA
 runtime statically so it does not depend on a runtime library path.
 """
 from __future__ import annotations
@@ -15,8 +15,10 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsesw.so")
-SOURCES = ["sesw_kernels.cu", "sesw_noalloc.cu", "sesw_surrogate.cu", "sesw_api.cpp", "mesh_prep.cpp"]
-HEADERS = [os.path.join(CSRC, "sesw_internal.h"), os.path.join(ROOT, "include", "sesw.h")]
+SOURCES = ["sesw_kernels.cu", "sesw_persistent.cu", "sesw_noalloc.cu", "sesw_surrogate.cu", "sesw_api.cpp",
+           "mesh_prep.cpp"]
+HEADERS = [os.path.join(CSRC, "sesw_internal.h"), os.path.join(CSRC, "sesw_device.cuh"),
+           os.path.join(ROOT, "include", "sesw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -374,20 +374,24 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
 
     // ---- neighbours across edges and the two-point flux geometry of the barotropic
     // viscosity (Eq. viscosity_BT): for edge k of an element (corner k to corner k+1)
-    // with a neighbour, the rotation from the neighbour's frame into this one, L/d and L
-    // (L: edge length, the mean of its lengths in the two frames; d: centroid distance
-    // in the plane unfolded across the edge).
+    // with a neighbour, the neighbour, its corner opposite the edge, the rotation from
+    // the neighbour's frame into this one, L/d and L^2/d (L: edge length, the mean of its
+    // lengths in the two frames; d: centroid distance in the plane unfolded across the
+    // edge).
     out.visc_nb.resize(ne);
+    out.visc_opp.resize(ne);
     out.visc_geo.resize(3 * (size_t)ne);
+    out.visc_rot = false;
     double vstiff = 0.0;
     for (int i = 0; i < ne; i++) {
         const int e = eperm[i];
         const int32_t *t = m.tri + 3 * (size_t)e;
-        int nbn[3];
+        int nbn[3], opp[3];
         double srow = 0.0;
         for (int k = 0; k < 3; k++) {
             const int o = nb_c[3 * (size_t)e + k];
             nbn[k] = o < 0 ? -1 : einv[o];
+            opp[k] = -1;
             out.visc_geo[3 * (size_t)i + k] = make_float4(1.0f, 0.0f, 0.0f, 0.0f);
             if (o < 0) continue;
             const int va = t[k], vb = t[(k + 1) % 3];
@@ -397,6 +401,7 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
                 if (to[c] == va) oa = c;
                 if (to[c] == vb) ob = c;
             }
+            opp[k] = vinv[to[3 - oa - ob]];
             double ang[2], along[2], perp[2], len[2];
             const int el[2] = {e, o}, ca[2] = {k, oa}, cb[2] = {(k + 1) % 3, ob};
             for (int side = 0; side < 2; side++) {
@@ -413,12 +418,16 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
             const double da = along[0] - along[1], dp = perp[0] + perp[1];
             const double d = std::sqrt(da * da + dp * dp);
             const double rot = ang[0] - ang[1];
-            out.visc_geo[3 * (size_t)i + k] =
-                make_float4((float)std::cos(rot), (float)std::sin(rot), (float)(L / d), (float)L);
+            const float cr = (float)std::cos(rot), sr = (float)std::sin(rot);
+            // frames that agree up to rounding (planar meshes, periodic unwrapping) count as
+            // the identity: a turn below 1e-7 rad is below the FP32 rounding of the velocities
+            if (!(cr == 1.0f && std::fabs(sr) < 1e-7f)) out.visc_rot = true;
+            out.visc_geo[3 * (size_t)i + k] = make_float4(cr, sr, (float)(L / d), (float)(L * L / d));
             const double ho = (m.depth[to[0]] + m.depth[to[1]] + m.depth[to[2]]) / 3.0;
             srow += 0.5 * (out.h0_e[i] + ho) / out.h0_e[i] * (L / d);
         }
         out.visc_nb[i] = make_int4(nbn[0], nbn[1], nbn[2], 0);
+        out.visc_opp[i] = make_int4(opp[0], opp[1], opp[2], 0);
         vstiff = std::max(vstiff, 2.0 * srow / out.area_e[i]);
     }
     out.visc_stiffness = vstiff;
@@ -486,7 +495,11 @@ void concat_meshes(std::vector<HostMesh> &parts, HostMesh &out)
         for (const int4 &q : h.visc_nb)
             out.visc_nb.push_back(make_int4(q.x < 0 ? -1 : q.x + eo, q.y < 0 ? -1 : q.y + eo,
                                             q.z < 0 ? -1 : q.z + eo, 0));
+        for (const int4 &q : h.visc_opp)
+            out.visc_opp.push_back(make_int4(q.x < 0 ? -1 : q.x + vo, q.y < 0 ? -1 : q.y + vo,
+                                             q.z < 0 ? -1 : q.z + vo, 0));
         out.visc_geo.insert(out.visc_geo.end(), h.visc_geo.begin(), h.visc_geo.end());
+        out.visc_rot = out.visc_rot || h.visc_rot;
         out.visc_stiffness = std::max(out.visc_stiffness, h.visc_stiffness);
         out.basin_visc_stiffness.push_back(h.visc_stiffness);
         out.max_patch_slots = std::max(out.max_patch_slots, h.max_patch_slots);

@@ -431,6 +431,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     c->visc_on = c->have_W = false;
     c->visc_out = nullptr;
     c->W_buf = nullptr;
+    c->eta_sum_buf = nullptr;
     c->visc_number = 0.0;
 
     sesw::DevMesh &d = c->dm;
@@ -531,17 +532,49 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.eta_x[2], hm.nv, "eta_x"));
         TRY(zalloc(c, &s.U_x[0], hm.nslot, "U_x"));
         TRY(zalloc(c, &s.U_x[1], hm.nslot, "U_x"));
-        // viscosity neighbours as owner slots
+        // viscosity tables per slot: neighbours as owner slots, their corners opposite
+        // the shared edges and rest depths, and the edge geometry
         std::vector<int> eslot(hm.ne, -1);
         for (int q = 0; q < hm.nslot; q++)
             if (hm.slot_v[q].w >= 0) eslot[hm.slot_v[q].w] = q;
-        std::vector<int4> nbs(hm.ne);
-        for (int i = 0; i < hm.ne; i++) {
-            const int4 o = hm.visc_nb[i];
-            nbs[i] = make_int4(o.x < 0 ? -1 : eslot[o.x], o.y < 0 ? -1 : eslot[o.y], o.z < 0 ? -1 : eslot[o.z], 0);
+        std::vector<int4> tq(hm.nslot), tc(hm.nslot);
+        std::vector<float4> ta(hm.nslot), tb(hm.nslot), tr(hm.visc_rot ? hm.nslot : 0);
+        std::vector<float2> tr2(hm.visc_rot ? hm.nslot : 0);
+        auto fbits = [](float f) {
+            int i;
+            memcpy(&i, &f, sizeof i);
+            return i;
+        };
+        for (int q = 0; q < hm.nslot; q++) {
+            const int w = hm.slot_v[q].w >= 0 ? hm.slot_v[q].w : -1 - hm.slot_v[q].w;
+            const int nb[3] = {hm.visc_nb[w].x, hm.visc_nb[w].y, hm.visc_nb[w].z};
+            const int op[3] = {hm.visc_opp[w].x, hm.visc_opp[w].y, hm.visc_opp[w].z};
+            int qs[3];
+            float h[3];
+            float4 g[3];
+            for (int k = 0; k < 3; k++) {
+                qs[k] = nb[k] < 0 ? -1 : eslot[nb[k]];
+                h[k] = nb[k] < 0 ? 0.0f : (float)hm.h0_e[nb[k]];
+                g[k] = hm.visc_geo[3 * (size_t)w + k];
+            }
+            tq[q] = make_int4(qs[0], qs[1], qs[2], fbits(h[0]));
+            tc[q] = make_int4(op[0], op[1], op[2], fbits(h[1]));
+            ta[q] = make_float4(g[0].z, g[1].z, g[2].z, h[2]);
+            tb[q] = make_float4(g[0].w, g[1].w, g[2].w, 0.0f);
+            if (hm.visc_rot) {
+                tr[q] = make_float4(g[0].x, g[0].y, g[1].x, g[1].y);
+                tr2[q] = make_float2(g[2].x, g[2].y);
+            }
         }
-        TRY(upload(c, &d.visc_nb, nbs, "visc_nb"));
-        TRY(upload(c, &d.visc_geo, hm.visc_geo, "visc_geo"));
+        TRY(upload(c, &d.visc_q, tq, "visc_q"));
+        TRY(upload(c, &d.visc_c, tc, "visc_c"));
+        TRY(upload(c, &d.visc_a, ta, "visc_a"));
+        TRY(upload(c, &d.visc_b, tb, "visc_b"));
+        if (hm.visc_rot) {
+            TRY(upload(c, &d.visc_r, tr, "visc_r"));
+            TRY(upload(c, &d.visc_r2, tr2, "visc_r2"));
+        }
+        d.visc_rot = hm.visc_rot ? 1 : 0;
         CK(c, sesw::substep_smem_attr(d));
     }
     CK(c, cudaStreamSynchronize(c->stream));
@@ -871,8 +904,8 @@ int sesw_set_eta_mean(sesw_ctx *c, int32_t enable)
     if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh first");
     if (c->params.scheme == 1 && enable) return fail(c, SESW_EINVAL, "the step-mean elevation is kept for the SE scheme");
     DeviceGuard dg(c->device);
-    if (enable && !c->ds.eta_sum) TRY(zalloc(c, &c->ds.eta_sum, c->dm.nv, "eta_sum"));
-    if (!enable) c->ds.eta_sum = nullptr;      // the buffer stays with the context until the next upload
+    if (enable && !c->eta_sum_buf) TRY(zalloc(c, &c->eta_sum_buf, c->dm.nv, "eta_sum"));
+    c->ds.eta_sum = enable ? c->eta_sum_buf : nullptr;   // the buffer stays until the next upload
     drop_graphs(c);
     if (c->mode == SESW_MODE_PERSISTENT) c->persist_graph_ok = true;
     return SESW_OK;

@@ -46,10 +46,13 @@ struct HostMesh {
     std::vector<double> h0_e;      // element rest depth (FP64), new element order
     double grad_gram_max_h = 0.0;  // upper bound of lambda_max(-div H0 grad) (m/s^2 units without g)
     // Barotropic viscosity (Eq. viscosity_BT), new element order: neighbours across the
-    // edges (corner k, corner k+1) as element ids (-1: coast), and per edge the rotation
-    // from the neighbour's frame (cos, sin), L/d and L of the two-point flux.
+    // edges (corner k, corner k+1) as element ids (-1: coast), the neighbour's corner
+    // opposite the edge (new vertex id), and per edge the rotation from the neighbour's
+    // frame (cos, sin), L/d and L^2/d of the two-point flux.
     std::vector<int4> visc_nb;
+    std::vector<int4> visc_opp;
     std::vector<float4> visc_geo;  // [ne][3]
+    bool visc_rot = false;         // some neighbour frame is turned (sphere)
     double visc_stiffness = 0.0;   // max_e 2 sum_k (H0_edge / H0_e)(L/d) / A_e (1/m^2)
 
     // Batches: a layout may hold several independent meshes ("basins"), each prepared
@@ -110,8 +113,16 @@ struct DevMesh {
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
     float *patch_dt = nullptr;     // [npatch] substep length tau/M of the patch's basin
-    int4 *visc_nb = nullptr;       // [ne] owner slots of the neighbours across the edges (-1: coast)
-    float4 *visc_geo = nullptr;    // [ne][3] (cos, sin, L/d, L), see HostMesh
+    // barotropic viscosity, per slot (graph mode): edge k joins corners k and k+1; q_k is
+    // the neighbour's owner slot (-1: coast), c_k its corner opposite the edge, h_k its
+    // H0, a_k = L/d, b_k = L^2/d, (cos, sin)_k the turn from its frame into this one
+    int4 *visc_q = nullptr;        // (q0, q1, q2, bits of h0)
+    int4 *visc_c = nullptr;        // (c0, c1, c2, bits of h1)
+    float4 *visc_a = nullptr;      // (a0, a1, a2, h2)
+    float4 *visc_b = nullptr;      // (b0, b1, b2, 0)
+    float4 *visc_r = nullptr;      // (cos0, sin0, cos1, sin1), only when visc_rot
+    float2 *visc_r2 = nullptr;     // (cos2, sin2), only when visc_rot
+    int visc_rot = 0;
     int nbasin = 1;
     int *basin_v = nullptr;        // [nbasin+1] vertex ranges (new order = caller order per basin)
     int *basin_slot = nullptr;     // [nbasin+1] slot ranges
@@ -277,6 +288,7 @@ struct sesw_ctx {
     sesw::ViscArgs vargs{};
     float2 *visc_out = nullptr;    // [ne] scratch of sesw_viscosity (allocated on first use)
     float *W_buf = nullptr;        // [nv] freshwater flux (allocated on first use)
+    float *eta_sum_buf = nullptr;  // [nv] sum of the substep elevations (allocated on first use)
     bool have_W = false;
     sesw::Surrogate *sur = nullptr;
 };
