@@ -238,18 +238,22 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
         }
     };
 
+    // Slots updated before the wait: whole rounds of interior slots (one per thread
+    // each), so that no thread does more rounds in total than ceil(ns / T); the interior
+    // slots left over go after the wait with the boundary slots.
+    const int npre = nint >= T ? (nint / T) * T : nint;
     for (int m = 0; m < P.M; m++) {
         if (m == 0) {
             elements(0, ns, nullptr);
         } else {
-            elements(0, nint, nullptr);
+            elements(0, npre, nullptr);
             if (threadIdx.x < 32) {
                 const bool ok = warp0_wait_neighbours(P, p, (unsigned)m);
                 if (threadIdx.x == 0) s_ok = ok;
             }
             __syncthreads();
             if (!s_ok) break;
-            elements(nint, ns, P.xb[m & 1]);
+            elements(npre, ns, P.xb[m & 1]);
         }
         __syncthreads();
 
