@@ -15,6 +15,11 @@ f/s_f, H0_e/s_H], with H0_e the corner mean of H0.
         h_v = h_v + tanh(z_v Wv_l + bv_l)
     o_e = h_e Weo + beo (4),  o_v = h_v Wvo + bvo (1)
 
+With bf16_msgs (the GPU's form) the concatenated inputs z_e and z_v of the message layers are
+rounded to bfloat16 values when they are formed: the layers run on BF16 tensor-core operands.
+The backward then passes gradients through the rounding unchanged, and the weight gradients
+use the rounded inputs.
+
 Predicted one-step increments: <<U>> - U = s_out_U o_e[0:2], U^M - U = s_out_U o_e[2:4],
 eta_bar - eta = s_out_eta o_v. Loss: mean over elements and channels of (o_e - t_e)^2
 plus mean over vertices of (o_v - t_v)^2 (t: targets divided by their scales).
@@ -122,17 +127,18 @@ def features(G, eta, U, R, s):
     return xv, xe
 
 
-def forward(G, w, xv, xe, s, keep=False):
+def forward(G, w, xv, xe, s, keep=False, bf16_msgs=False):
     p = unflatten(w)
+    q = bf16_round if bf16_msgs else (lambda x: x)
     hv = np.tanh(xv @ p["Wv0"] + p["bv0"])
     he = np.tanh(xe @ p["We0"] + p["be0"])
     cache = {"hv": [hv], "he": [he], "ye": [], "yv": [], "ze": [], "zv": []}
     for l in range(1, LAYERS + 1):
         gx, gy = G.grad_msg(hv, s["L"])
-        ze = np.concatenate([he, gx, gy], axis=1)
+        ze = q(np.concatenate([he, gx, gy], axis=1))
         ye = np.tanh(ze @ p[f"We{l}"] + p[f"be{l}"])
         he = he + ye
-        zv = np.concatenate([hv, G.mean_msg(he)], axis=1)
+        zv = q(np.concatenate([hv, G.mean_msg(he)], axis=1))
         yv = np.tanh(zv @ p[f"Wv{l}"] + p[f"bv{l}"])
         hv = hv + yv
         if keep:
@@ -151,10 +157,10 @@ def loss(oe, ov, te, tv):
     return float(np.mean((oe - te) ** 2) + np.mean((ov - tv) ** 2))
 
 
-def loss_and_grad(G, w, xv, xe, te, tv, s):
+def loss_and_grad(G, w, xv, xe, te, tv, s, bf16_msgs=False):
     """Loss and its gradient with respect to the flat parameter vector (analytic backward)."""
     p = unflatten(w)
-    oe, ov, c = forward(G, w, xv, xe, s, keep=True)
+    oe, ov, c = forward(G, w, xv, xe, s, keep=True, bf16_msgs=bf16_msgs)
     L = loss(oe, ov, te, tv)
     g = {k: np.zeros_like(v) for k, v in p.items()}
     doe = 2.0 * (oe - te) / oe.size

@@ -2,6 +2,7 @@
 // kernels of libsesw. Not part of the public interface (include/sesw.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -247,6 +248,12 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
 
 struct Surrogate;
 void surrogate_release(sesw_ctx *c);
+
+// Dense layer on the tensor cores (sesw_tc.cu): Y[n][j] = act(sum_k X[n][k] W[k][j] + b[j])
+// for N rows, K inputs holding bfloat16 values, 64 outputs; W is K x 64 row-major bf16.
+bool linear_tc_supported(int K, int P);
+cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *W, const float *bias, int act,
+                             float *Y, unsigned *status, cudaStream_t st);
 
 }  // namespace sesw
 

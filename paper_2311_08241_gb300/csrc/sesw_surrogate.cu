@@ -1,7 +1,8 @@
 // Learned surrogate of one baroclinic step: a message-passing network on the
 // vertex-element graph of the uploaded mesh, trained and run with the kernels below.
 //
-// Network (hidden width 64, 3 layers; weights bfloat16, accumulation float):
+// Network (hidden width 64, 3 layers; weights bfloat16, accumulation float; the six
+// message layers take bfloat16 inputs and run on the tensor cores, sesw_tc.cu):
 //   vertex inputs  x_v = [eta/s_eta, H0/s_H]
 //   element inputs x_e = [U/s_U, R/s_R, f/s_f, H0_e/s_H]
 //   h_v = tanh(x_v Wv0 + bv0),  h_e = tanh(x_e We0 + be0)
@@ -191,6 +192,10 @@ __global__ void k_axpy(size_t n, const float *__restrict__ x, float *__restrict_
 // thread per (node, channel), 64 channels per node
 
 // Z_e = [h_e, L sum_k gx_k h_vk, L sum_k gy_k h_vk]
+// The message-layer inputs are rounded to bfloat16 values when they are formed: the
+// tensor-core layers read them as BF16 operands, and the weight gradients see the same values.
+__device__ __forceinline__ float bf16_value(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
 __global__ void k_msg_elem(int E, const int4 *__restrict__ etri, const float4 *__restrict__ egrad, float L,
                            const float *__restrict__ he, const float *__restrict__ hv, float *__restrict__ Z)
 {
@@ -204,9 +209,9 @@ __global__ void k_msg_elem(int E, const int4 *__restrict__ etri, const float4 *_
         const float gx = g.x * h0 + g.z * h1 - (g.x + g.z) * h2;
         const float gy = g.y * h0 + g.w * h1 - (g.y + g.w) * h2;
         float *z = Z + (size_t)e * 3 * HC;
-        z[c] = he[t];
-        z[HC + c] = L * gx;
-        z[2 * HC + c] = L * gy;
+        z[c] = bf16_value(he[t]);
+        z[HC + c] = bf16_value(L * gx);
+        z[2 * HC + c] = bf16_value(L * gy);
     }
 }
 
@@ -255,8 +260,8 @@ __global__ void k_msg_vert(int V, const int *__restrict__ voff, const int *__res
             s += earea[e] * he[(size_t)e * HC + c];
         }
         float *z = Z + (size_t)v * 2 * HC;
-        z[c] = hv[t];
-        z[HC + c] = s * vinvA[v];
+        z[c] = bf16_value(hv[t]);
+        z[HC + c] = bf16_value(s * vinvA[v]);
     }
 }
 
@@ -632,6 +637,7 @@ struct Surrogate {
     float2 *save_U = nullptr;
     double *stage = nullptr;    // host samples in transit: 2 V + 8 E doubles
     size_t smem_mm = 0;
+    unsigned *status = nullptr; // the context's device status word (timeout bit of the tensor-core waits)
 };
 
 void surrogate_release(sesw_ctx *c)
@@ -666,6 +672,8 @@ int salloc(sesw_ctx *c, T **p, size_t n)
 cudaError_t mm(Surrogate &S, cudaStream_t st, int N, int Kin, int P, const float *X, const __nv_bfloat16 *W,
                int trans, const float *bias, int act, const float *res, float *Y)
 {
+    // the message layers (K = 192 or 128 inputs, 64 outputs) run on the tensor cores
+    if (!trans && !res && linear_tc_supported(Kin, P)) return launch_linear_tc(N, Kin, X, W, bias, act, Y, S.status, st);
     const size_t smem = sizeof(float) * ((size_t)TILE_ROWS * (Kin + 1) + (size_t)Kin * P);
     const int grid = (N + TILE_ROWS - 1) / TILE_ROWS;
     if (grid == 0) return cudaSuccess;
@@ -802,6 +810,7 @@ int sesw_surrogate_init(sesw_ctx *c, int32_t capacity, int32_t seed)
     Surrogate &S = *Sp;
     const int V = c->dm.nv, E = c->dm.ne;
     S.V = V;
+    S.status = c->ds.status;
     S.E = E;
     S.cap = capacity;
     // graph

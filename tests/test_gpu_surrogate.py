@@ -52,13 +52,21 @@ def test_forward_and_gradient_match_fp64_reference(S):
     wq = mpnn.quantise(w.astype(np.float64))
     te = np.concatenate([dum, duM], axis=1) / sc["out_U"]
     tv = (deb / sc["out_eta"])[:, None]
-    L_ref, g_ref = mpnn.loss_and_grad(G, wq, xv, xe, te, tv, sc)
-    oe_ref, ov_ref = mpnn.forward(G, wq, xv, xe, sc)
-    print("loss", loss, L_ref, "max|g|", np.abs(g_ref).max(), "max|dg|", np.abs(g - g_ref).max())
-    assert abs(loss - L_ref) <= 1e-4 * abs(L_ref)
-    assert np.max(np.abs(oe - oe_ref)) <= 1e-4 * np.max(np.abs(oe_ref)) + 1e-6
-    assert np.max(np.abs(ov - ov_ref[:, 0])) <= 1e-4 * np.max(np.abs(ov_ref)) + 1e-6
+    # the message layers take BF16 inputs on the tensor cores; the reference rounds the same values
+    L_ref, g_ref = mpnn.loss_and_grad(G, wq, xv, xe, te, tv, sc, bf16_msgs=True)
+    oe_ref, ov_ref = mpnn.forward(G, wq, xv, xe, sc, bf16_msgs=True)
+    print("loss", loss, L_ref, "max|g|", np.abs(g_ref).max(), "max|dg|", np.abs(g - g_ref).max(),
+          "max|doe|", np.abs(oe - oe_ref).max(), "max|oe|", np.abs(oe_ref).max())
+    # The GPU forms the message inputs in FP32 and the reference in FP64; where a value sits on
+    # a bfloat16 rounding boundary the two round it to neighbouring values (2^-8 apart in
+    # relative terms), which moves outputs by about 1e-4 of their scale. The bound below is
+    # ten times that; a wrong operand layout or accumulation gives errors of order one.
+    assert abs(loss - L_ref) <= 1e-3 * abs(L_ref)
+    assert np.max(np.abs(oe - oe_ref)) <= 1e-3 * np.max(np.abs(oe_ref)) + 1e-6
+    assert np.max(np.abs(ov - ov_ref[:, 0])) <= 1e-3 * np.max(np.abs(ov_ref)) + 1e-6
     assert np.max(np.abs(g - g_ref)) <= 1e-3 * np.max(np.abs(g_ref))
+    # most outputs agree to FP32 accumulation order
+    assert np.median(np.abs(oe - oe_ref)) <= 1e-5 * np.max(np.abs(oe_ref))
 
 
 def _record(s, case, nsamples, nsteps_between=1):
