@@ -250,9 +250,13 @@ struct Surrogate;
 void surrogate_release(sesw_ctx *c);
 
 // Dense layer on the tensor cores (sesw_tc.cu): Y[n][j] = act(sum_k X[n][k] W[k][j] + b[j])
-// for N rows, K inputs holding bfloat16 values, 64 outputs; W is K x 64 row-major bf16.
+// for N rows, K inputs holding bfloat16 values, 64 outputs. W (K x 64 row-major bf16) is
+// first packed by pack_linear_tc into linear_tc_packed_elems(K) elements (the shared-memory
+// image of W^T), which launch_linear_tc then reads.
 bool linear_tc_supported(int K, int P);
-cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *W, const float *bias, int act,
+size_t linear_tc_packed_elems(int K);
+cudaError_t pack_linear_tc(int K, const __nv_bfloat16 *W, __nv_bfloat16 *packed, cudaStream_t st);
+cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *packed, const float *bias, int act,
                              float *Y, unsigned *status, cudaStream_t st);
 
 }  // namespace sesw

@@ -601,6 +601,7 @@ int grid1(size_t n, int threads = 256)
 struct Layer {
     int K, C;        // matrix is K x C
     size_t w, b;     // offsets in the parameter vector
+    long tc = -1;    // offset of the tensor-core copy of W (packed W^T) in Surrogate::wtc, or -1
 };
 
 struct Surrogate {
@@ -615,6 +616,8 @@ struct Surrogate {
     int nparam = 0;
     float *w32 = nullptr, *grad = nullptr, *am = nullptr, *av = nullptr;
     __nv_bfloat16 *w16 = nullptr;
+    __nv_bfloat16 *wtc = nullptr;   // packed copies of the tensor-core layers' weights
+    size_t ntc = 0;
     long adam_t = 0;
     double lr = 1e-3, b1 = 0.9, b2 = 0.999, eps = 1e-8;
     float *scales = nullptr;   // device [8]
@@ -672,8 +675,7 @@ int salloc(sesw_ctx *c, T **p, size_t n)
 cudaError_t mm(Surrogate &S, cudaStream_t st, int N, int Kin, int P, const float *X, const __nv_bfloat16 *W,
                int trans, const float *bias, int act, const float *res, float *Y)
 {
-    // the message layers (K = 192 or 128 inputs, 64 outputs) run on the tensor cores
-    if (!trans && !res && linear_tc_supported(Kin, P)) return launch_linear_tc(N, Kin, X, W, bias, act, Y, S.status, st);
+
     const size_t smem = sizeof(float) * ((size_t)TILE_ROWS * (Kin + 1) + (size_t)Kin * P);
     const int grid = (N + TILE_ROWS - 1) / TILE_ROWS;
     if (grid == 0) return cudaSuccess;
@@ -682,6 +684,26 @@ cudaError_t mm(Surrogate &S, cudaStream_t st, int N, int Kin, int P, const float
     else
         k_mm<12><<<grid, 256, smem, st>>>(N, Kin, P, X, W, trans, bias, act, res, Y);
     return cudaGetLastError();
+}
+
+// Forward of one layer, Y = act(X W + b): the message layers on the tensor cores (their
+// inputs hold bfloat16 values and their weights a packed copy), the others on k_mm.
+cudaError_t linear(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const float *X, int act, float *Y)
+{
+    if (ly.tc >= 0)
+        return launch_linear_tc(N, ly.K, X, S.wtc + ly.tc, S.w32 + ly.b, act, Y, S.status, st);
+    return mm(S, st, N, ly.K, ly.C, X, S.w16 + ly.w, 0, S.w32 + ly.b, act, nullptr, Y);
+}
+
+// Refresh the packed tensor-core copies after the bfloat16 weights changed.
+cudaError_t pack_tc(Surrogate &S, cudaStream_t st)
+{
+    for (const Layer &ly : S.L)
+        if (ly.tc >= 0) {
+            const cudaError_t e = pack_linear_tc(ly.K, S.w16 + ly.w, S.wtc + ly.tc, st);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
 }
 
 // gradient of layer l's matrix and bias from its input Z [N][K] and dA [N][C]
@@ -713,8 +735,7 @@ cudaError_t forward(Surrogate &S, cudaStream_t st)
     for (int l = 0; l < NL; l++) {
         const Layer &le = S.L[2 + 2 * l], &lv = S.L[3 + 2 * l];
         k_msg_elem<<<grid1((size_t)S.E * HC), 256, 0, st>>>(S.E, S.etri, S.egrad, Ls, S.he[l], S.hv[l], S.ze);
-        if ((e = mm(S, st, S.E, 3 * HC, HC, S.ze, S.w16 + le.w, 0, S.w32 + le.b, 1, nullptr, S.ye[l])) != cudaSuccess)
-            return e;
+        if ((e = linear(S, st, le, S.E, S.ze, 1, S.ye[l])) != cudaSuccess) return e;
         // h_e(l+1) = h_e(l) + y_e(l)
         if ((e = cudaMemcpyAsync(S.he[l + 1], S.he[l], sizeof(float) * (size_t)S.E * HC, cudaMemcpyDeviceToDevice, st)) !=
             cudaSuccess)
@@ -722,8 +743,7 @@ cudaError_t forward(Surrogate &S, cudaStream_t st)
         k_axpy<<<grid1((size_t)S.E * HC), 256, 0, st>>>((size_t)S.E * HC, S.ye[l], S.he[l + 1]);
         k_msg_vert<<<grid1((size_t)S.V * HC), 256, 0, st>>>(S.V, S.voff, S.vinc, S.earea, S.vinvA, S.hv[l], S.he[l + 1],
                                                             S.zv);
-        if ((e = mm(S, st, S.V, 2 * HC, HC, S.zv, S.w16 + lv.w, 0, S.w32 + lv.b, 1, nullptr, S.yv[l])) != cudaSuccess)
-            return e;
+        if ((e = linear(S, st, lv, S.V, S.zv, 1, S.yv[l])) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(S.hv[l + 1], S.hv[l], sizeof(float) * (size_t)S.V * HC, cudaMemcpyDeviceToDevice, st)) !=
             cudaSuccess)
             return e;
@@ -863,6 +883,10 @@ int sesw_surrogate_init(sesw_ctx *c, int32_t capacity, int32_t seed)
         S.nparam += K * C;
         ly.b = S.nparam;
         S.nparam += C;
+        if (sesw::linear_tc_supported(K, C)) {
+            ly.tc = (long)S.ntc;
+            S.ntc += sesw::linear_tc_packed_elems(K);
+        }
         S.L.push_back(ly);
     };
     add(2, sesw::HC);
@@ -878,6 +902,7 @@ int sesw_surrogate_init(sesw_ctx *c, int32_t capacity, int32_t seed)
     STRY(sesw::salloc(c, &S.am, S.nparam));
     STRY(sesw::salloc(c, &S.av, S.nparam));
     STRY(sesw::salloc(c, &S.w16, S.nparam));
+    STRY(sesw::salloc(c, &S.wtc, S.ntc));
     {
         // Glorot-uniform matrices, zero biases, from a seeded generator
         std::vector<float> w(S.nparam, 0.0f);
@@ -891,6 +916,7 @@ int sesw_surrogate_init(sesw_ctx *c, int32_t capacity, int32_t seed)
         SCK(cudaMemsetAsync(S.am, 0, sizeof(float) * S.nparam, c->stream));
         SCK(cudaMemsetAsync(S.av, 0, sizeof(float) * S.nparam, c->stream));
         sesw::k_to_bf16<<<sesw::grid1(S.nparam), 256, 0, c->stream>>>(S.nparam, S.w32, S.w16);
+        SCK(sesw::pack_tc(S, c->stream));
         SCK(cudaStreamSynchronize(c->stream));
     }
     STRY(sesw::salloc(c, &S.scales, sesw::NSCALE));
@@ -971,6 +997,7 @@ int sesw_surrogate_weights(sesw_ctx *c, float *get, const float *set)
         SCK(cudaMemcpyAsync(S.w32, set, sizeof(float) * S.nparam, cudaMemcpyHostToDevice, c->stream));
         sesw::k_to_bf16<<<sesw::grid1(S.nparam), 256, 0, c->stream>>>(S.nparam, S.w32, S.w16);
         SCK(cudaGetLastError());
+        SCK(sesw::pack_tc(S, c->stream));
     }
     if (get) SCK(cudaMemcpyAsync(get, S.w32, sizeof(float) * S.nparam, cudaMemcpyDeviceToHost, c->stream));
     SCK(cudaStreamSynchronize(c->stream));
@@ -1107,6 +1134,7 @@ static int run_sample(sesw_ctx *c, long i, bool grad, bool adam, double *loss)
                                                                        (float)S.lr, (float)S.b1, (float)S.b2,
                                                                        (float)S.eps, c1, c2);
             SCK(cudaGetLastError());
+            SCK(sesw::pack_tc(S, c->stream));
         }
     }
     if (loss) {

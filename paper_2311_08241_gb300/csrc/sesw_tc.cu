@@ -3,13 +3,14 @@
 // with X already rounded to bfloat16 values (stored as float) and W in bfloat16; the
 // products accumulate in FP32 in tensor memory.
 //
-// One CTA of 128 threads computes 128 rows. It stages its X tile and the whole W (as
-// W^T) in shared memory in the K-major layout without swizzle that tcgen05.mma reads:
+// One CTA of 256 threads computes 128 rows. It stages its X tile and the whole W (as
+// W^T, from a copy packed once per weight update by k_pack_wt) in shared memory in the
+// K-major layout without swizzle that tcgen05.mma reads:
 // core matrices of 8 rows x 8 bf16 (16 bytes per row, 128 bytes each), core matrices
 // adjacent along K 128 bytes apart, along M (or N) K * 16 bytes apart. One thread
 // issues K/16 MMAs of shape 128 x 64 x 16 into a 64-column TMEM accumulator and commits
-// them to an mbarrier; after a bounded wait every warp reads its 32 rows back with
-// tcgen05.ld, applies bias and activation, and stores.
+// them to an mbarrier; after a bounded wait every warp reads 32 rows x 32 columns back
+// with tcgen05.ld, applies bias and activation, and stores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,7 +24,7 @@ namespace {
 
 constexpr int TC_M = 128;        // rows per CTA: one MMA with M = 128
 constexpr int TC_N = 64;         // output columns: the hidden width
-constexpr int TC_THREADS = 128;  // four warps, one per 32 TMEM lanes
+constexpr int TC_THREADS = 256;  // eight warps: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns 32 (w / 4) .. + 31
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -65,9 +66,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, long long budget)
     }
 }
 
+// W (K x 64, row-major bf16) as the shared-memory image of W^T that k_linear_tc copies:
+// 16-byte chunk c = (jg * K/8 + kc) * 8 + jl holds W[8 kc .. 8 kc + 7][8 jg + jl].
+__global__ void k_pack_wt(int K, const __nv_bfloat16 *__restrict__ W, uint4 *__restrict__ out)
+{
+    const int KC = K / 8;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < TC_N * KC; c += gridDim.x * blockDim.x) {
+        const int jl = c & 7, kc = (c >> 3) % KC, jg = (c >> 3) / KC;
+        const int j = jg * 8 + jl;
+        unsigned short h[8];
+#pragma unroll
+        for (int t = 0; t < 8; t++) h[t] = __bfloat16_as_ushort(W[(size_t)(kc * 8 + t) * TC_N + j]);
+        out[c] = make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16),
+                            (uint32_t)h[4] | ((uint32_t)h[5] << 16), (uint32_t)h[6] | ((uint32_t)h[7] << 16));
+    }
+}
+
 template <int K>
 __global__ void __launch_bounds__(TC_THREADS)
-k_linear_tc(int N, const float *__restrict__ X, const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
+k_linear_tc(int N, const float *__restrict__ X, const uint4 *__restrict__ Wp, const float *__restrict__ bias,
             int act, float *__restrict__ Y, unsigned *__restrict__ status, long long wait_cycles)
 {
     static_assert(K % 16 == 0 && K <= 256, "K must be a multiple of 16");
@@ -92,28 +109,37 @@ k_linear_tc(int N, const float *__restrict__ X, const __nv_bfloat16 *__restrict_
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // A tile: chunk c is row r = 8 rg + rl, columns 8 kc .. 8 kc + 7; consecutive threads
-    // fill consecutive 16-byte rows of one core matrix
-    for (int c = tid; c < TC_M * KC; c += TC_THREADS) {
-        const int rl = c & 7, kc = (c >> 3) % KC, rg = (c >> 3) / KC;
-        const int n = n0 + rg * 8 + rl;
-        uint4 q = make_uint4(0u, 0u, 0u, 0u);
-        if (n < N) {
-            const float4 a = *reinterpret_cast<const float4 *>(X + (size_t)n * K + kc * 8);
-            const float4 b = *reinterpret_cast<const float4 *>(X + (size_t)n * K + kc * 8 + 4);
-            q = make_uint4(pack_bf16x2(a.x, a.y), pack_bf16x2(a.z, a.w), pack_bf16x2(b.x, b.y), pack_bf16x2(b.z, b.w));
-        }
-        As[(rg * KC + kc) * 8 + rl] = q;
-    }
-    // B tile: row j of W^T (output column j), columns 8 kc .. 8 kc + 7
-    for (int c = tid; c < TC_N * KC; c += TC_THREADS) {
-        const int jl = c & 7, kc = (c >> 3) % KC, jg = (c >> 3) / KC;
-        const int j = jg * 8 + jl;
-        unsigned short h[8];
+    // fill consecutive 16-byte rows of one core matrix. Four chunks' loads are issued
+    // before any is converted, so that their latencies overlap.
+    constexpr int PER = TC_M * KC / TC_THREADS;
+    static_assert(PER % 4 == 0, "chunks per thread must be a multiple of 4");
 #pragma unroll
-        for (int t = 0; t < 8; t++) h[t] = __bfloat16_as_ushort(W[(size_t)(kc * 8 + t) * TC_N + j]);
-        Bs[(jg * KC + kc) * 8 + jl] = make_uint4((uint32_t)h[0] | ((uint32_t)h[1] << 16), (uint32_t)h[2] | ((uint32_t)h[3] << 16),
-                                                 (uint32_t)h[4] | ((uint32_t)h[5] << 16), (uint32_t)h[6] | ((uint32_t)h[7] << 16));
+    for (int b = 0; b < PER; b += 4) {
+        float4 va[4], vb[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int c = tid + (b + u) * TC_THREADS;
+            const int rl = c & 7, kc = (c >> 3) % KC, rg = (c >> 3) / KC;
+            const int n = n0 + rg * 8 + rl;
+            va[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            vb[u] = va[u];
+            if (n < N) {
+                va[u] = *reinterpret_cast<const float4 *>(X + (size_t)n * K + kc * 8);
+                vb[u] = *reinterpret_cast<const float4 *>(X + (size_t)n * K + kc * 8 + 4);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const int c = tid + (b + u) * TC_THREADS;
+            const int rl = c & 7, kc = (c >> 3) % KC, rg = (c >> 3) / KC;
+            As[(rg * KC + kc) * 8 + rl] =
+                make_uint4(pack_bf16x2(va[u].x, va[u].y), pack_bf16x2(va[u].z, va[u].w),
+                           pack_bf16x2(vb[u].x, vb[u].y), pack_bf16x2(vb[u].z, vb[u].w));
+        }
     }
+    // B tile: the packed image of W^T, copied as is
+#pragma unroll 4
+    for (int c = tid; c < TC_N * KC; c += TC_THREADS) Bs[c] = Wp[c];
     // make the generic-proxy writes of the tiles visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -147,11 +173,12 @@ k_linear_tc(int N, const float *__restrict__ X, const __nv_bfloat16 *__restrict_
 
     if (s_ok) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int row = warp * 32 + lane;
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
         const int n = n0 + row;
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
-        for (int q = 0; q < TC_N / 16; q++) {
+        for (int q = 2 * half; q < 2 * half + 2; q++) {
             uint32_t r[16];
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
@@ -186,7 +213,7 @@ k_linear_tc(int N, const float *__restrict__ X, const __nv_bfloat16 *__restrict_
 }
 
 template <int K>
-cudaError_t launch_k(int N, const float *X, const __nv_bfloat16 *W, const float *bias, int act, float *Y,
+cudaError_t launch_k(int N, const float *X, const uint4 *Wp, const float *bias, int act, float *Y,
                      unsigned *status, cudaStream_t st)
 {
     const size_t smem = (size_t)(TC_M + TC_N) * K * 2;
@@ -196,7 +223,7 @@ cudaError_t launch_k(int N, const float *X, const __nv_bfloat16 *W, const float 
     const int grid = (N + TC_M - 1) / TC_M;
     if (grid == 0) return cudaSuccess;
     // about one second of SM clock for the MMA completion wait
-    k_linear_tc<K><<<grid, TC_THREADS, smem, st>>>(N, X, W, bias, act, Y, status, 2000000000ll);
+    k_linear_tc<K><<<grid, TC_THREADS, smem, st>>>(N, X, Wp, bias, act, Y, status, 2000000000ll);
     return cudaGetLastError();
 }
 
@@ -204,11 +231,21 @@ cudaError_t launch_k(int N, const float *X, const __nv_bfloat16 *W, const float 
 
 bool linear_tc_supported(int K, int P) { return P == TC_N && (K == 128 || K == 192); }
 
-cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *W, const float *bias, int act,
+size_t linear_tc_packed_elems(int K) { return (size_t)TC_N * K; }
+
+cudaError_t pack_linear_tc(int K, const __nv_bfloat16 *W, __nv_bfloat16 *packed, cudaStream_t st)
+{
+    const int n = TC_N * K / 8;
+    k_pack_wt<<<(n + 255) / 256, 256, 0, st>>>(K, W, reinterpret_cast<uint4 *>(packed));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *packed, const float *bias, int act,
                              float *Y, unsigned *status, cudaStream_t st)
 {
-    if (K == 128) return launch_k<128>(N, X, W, bias, act, Y, status, st);
-    if (K == 192) return launch_k<192>(N, X, W, bias, act, Y, status, st);
+    const uint4 *Wp = reinterpret_cast<const uint4 *>(packed);
+    if (K == 128) return launch_k<128>(N, X, Wp, bias, act, Y, status, st);
+    if (K == 192) return launch_k<192>(N, X, Wp, bias, act, Y, status, st);
     return cudaErrorInvalidValue;
 }
 
