@@ -52,7 +52,8 @@ def parse():
                          "'auto' picks a background at viscous number 0.2 and C_v = 1")
     ap.add_argument("--freshwater", type=float, default=0.0, metavar="AMP",
                     help="freshwater flux W of Eq. (4.5): seeded random field of this amplitude (m/s)")
-    ap.add_argument("--patch-vertices", type=int, default=256)
+    ap.add_argument("--patch-vertices", type=int, default=None,
+                    help="graph-mode patch size (default 256; with --visc, one wave of the fused kernel)")
     ap.add_argument("--block-threads", type=int, default=256)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=400)
@@ -546,7 +547,18 @@ def run_ours(args, world, rank, local):
     sim = S.Subcycle(local, stream=stream)
     sim.sesw_set_mode({"auto": S.SESW_MODE_AUTO, "graph": S.SESW_MODE_GRAPH,
                        "persistent": S.SESW_MODE_PERSISTENT}[args.mode])
-    sim.sesw_set_patch_vertices(args.patch_vertices)
+    pv = args.patch_vertices
+    if pv is None:
+        if args.visc:
+            # the fused viscosity substep (56 registers x 256 threads) keeps 4 blocks per SM:
+            # patches sized so that the channel is exactly one wave of them
+            from paper_2311_08241_gb300.autotune import wave_patch_sizes
+
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            pv = wave_patch_sizes(V, nsm, (4,))[0]
+        else:
+            pv = 256
+    sim.sesw_set_patch_vertices(pv)
     sim.sesw_set_block_threads(args.block_threads)
     sim.sesw_set_blocks_per_sm(args.blocks_per_sm)
     sim.sesw_mesh_upload(case.mesh)

@@ -18,6 +18,14 @@ from . import sesw as S
 PERSISTENT_BLOCKS = (1, 2, 4)
 GRAPH_PATCHES = (128, 256, 512, 1024)
 GRAPH_THREADS = (128, 256, 512)
+WAVE_BLOCKS_PER_SM = (2, 4, 8)
+
+
+def wave_patch_sizes(nv_max, nsm, blocks_per_sm=WAVE_BLOCKS_PER_SM):
+    """Graph-mode patch sizes that make the largest mesh exactly one wave of blocks when
+    `k` blocks of the substep kernel are resident per SM (a partial second wave of a
+    latency-bound kernel costs nearly a full one)."""
+    return tuple(sorted({max(32, -(-int(nv_max) // (nsm * k))) for k in blocks_per_sm}))
 
 
 @dataclasses.dataclass
@@ -107,7 +115,9 @@ def autotune(meshes, params, forcing=None, steps=5, warmup=2, device=0, include_
             if verbose:
                 print(c.label(), t)
     if include_graph:
-        for pv in graph_patches:
+        nsm = torch.cuda.get_device_properties(device).multi_processor_count
+        patches = tuple(sorted(set(graph_patches) | set(wave_patch_sizes(max(m.nv for m in meshes), nsm))))
+        for pv in patches:
             try:
                 res = run(Choice(S.SESW_MODE_GRAPH, patch_vertices=pv))
             except S.SeswError:
