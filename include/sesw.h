@@ -278,6 +278,23 @@ int sesw_advance(sesw_ctx *ctx, int32_t nsteps);
  * copies are only enqueued. */
 int sesw_get_state(sesw_ctx *ctx, double *eta, double *U, double *Umean, int where);
 
+/* Asynchronous host transfers, for callers that pipeline steps: the copies run on the
+ * library's own copy streams and overlap the steps before and after them; a ticket names
+ * each state read-back. Host buffers should be pinned (page-locked) for the copies to be
+ * asynchronous.
+ *   sesw_set_forcing_async  as sesw_set_forcing with a host R; R may be changed again once
+ *                           sesw_wait has returned for a ticket issued after this call
+ *   sesw_get_state_async    as sesw_get_state into host buffers (any may be NULL); returns
+ *                           at once with *ticket > 0; the buffers hold the state once
+ *                           sesw_wait(ctx, ticket) returns
+ *   sesw_wait               waits until the read-back `ticket` has landed (0: until every
+ *                           transfer and step issued so far has finished); returns
+ *                           SESW_EUNSTABLE if the device had flagged instability by then,
+ *                           SESW_EINVAL for a ticket not issued yet. */
+int sesw_set_forcing_async(sesw_ctx *ctx, const double *R);
+int sesw_get_state_async(sesw_ctx *ctx, double *eta, double *U, double *Umean, uint64_t *ticket);
+int sesw_wait(sesw_ctx *ctx, uint64_t ticket);
+
 /* Keep (enable = 1) or stop keeping (0) the step-mean elevation
  * eta_bar = (1/M) sum_{m=0..M-1} eta^m of every baroclinic step (SE scheme): the time
  * mean that enters the exactly summed momentum equation of a step,

@@ -432,6 +432,8 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     c->visc_out = nullptr;
     c->W_buf = nullptr;
     c->eta_sum_buf = nullptr;
+    c->stage_in[0] = c->stage_in[1] = nullptr;
+    c->stage_out[0] = c->stage_out[1] = nullptr;
     c->visc_number = 0.0;
 
     sesw::DevMesh &d = c->dm;
@@ -832,6 +834,96 @@ int sesw_viscosity(sesw_ctx *c, double *out, int where)
     return SESW_OK;
 }
 
+// Copy streams, events and staging of the asynchronous host transfers (first use).
+static int async_setup(sesw_ctx *c)
+{
+    if (!c->h2d_stream) {
+        CK(c, cudaStreamCreateWithFlags(&c->h2d_stream, cudaStreamNonBlocking));
+        CK(c, cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; b++)
+            for (cudaEvent_t *ev : {&c->in_done[b], &c->in_free[b], &c->out_ready[b], &c->out_done[b]})
+                CK(c, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+        CK(c, cudaMallocHost(&c->status_h, 2 * sizeof(unsigned)));
+        c->status_h[0] = c->status_h[1] = 0u;
+    }
+    for (int b = 0; b < 2; b++) {
+        if (!c->stage_in[b]) TRY(zalloc(c, &c->stage_in[b], 2 * (size_t)c->dm.ne, "async staging"));
+        if (!c->stage_out[b]) TRY(zalloc(c, &c->stage_out[b], (size_t)c->dm.nv + 4 * (size_t)c->dm.ne, "async staging"));
+    }
+    return SESW_OK;
+}
+
+int sesw_set_forcing_async(sesw_ctx *c, const double *R)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before setting the forcing");
+    if (!R) return fail(c, SESW_EINVAL, "R is NULL");
+    DeviceGuard dg(c->device);
+    TRY(async_setup(c));
+    const int b = c->in_idx;
+    c->in_idx ^= 1;
+    // the upload waits until the scatter that last read this staging buffer has run, and
+    // the scatter on the context's stream waits for the upload
+    CK(c, cudaStreamWaitEvent(c->h2d_stream, c->in_free[b], 0));
+    CK(c, cudaMemcpyAsync(c->stage_in[b], R, sizeof(double) * 2 * c->dm.ne, cudaMemcpyHostToDevice, c->h2d_stream));
+    CK(c, cudaEventRecord(c->in_done[b], c->h2d_stream));
+    CK(c, cudaStreamWaitEvent(c->stream, c->in_done[b], 0));
+    CK(c, sesw::launch_scatter_forcing(c->dm, c->ds, c->stage_in[b], c->stream));
+    CK(c, cudaEventRecord(c->in_free[b], c->stream));
+    return SESW_OK;
+}
+
+int sesw_get_state_async(sesw_ctx *c, double *eta, double *U, double *Umean, uint64_t *ticket)
+{
+    if (!c) return SESW_EINVAL;
+    if (!c->have_mesh) return fail(c, SESW_ESTATE, "upload a mesh before reading the state");
+    DeviceGuard dg(c->device);
+    TRY(async_setup(c));
+    const int b = c->out_idx;
+    c->out_idx ^= 1;
+    const size_t nv = c->dm.nv, ne = c->dm.ne;
+    double *st = c->stage_out[b];
+    double *se = eta ? st : nullptr, *su = U ? st + nv : nullptr, *sm = Umean ? st + nv + 2 * ne : nullptr;
+    // the gather waits until the download that last read this staging buffer has finished
+    CK(c, cudaStreamWaitEvent(c->stream, c->out_done[b], 0));
+    CK(c, sesw::launch_gather_state(c->dm, c->ds, c->parity, se, su, sm, c->stream));
+    CK(c, cudaEventRecord(c->out_ready[b], c->stream));
+    CK(c, cudaStreamWaitEvent(c->d2h_stream, c->out_ready[b], 0));
+    if (eta) CK(c, cudaMemcpyAsync(eta, se, sizeof(double) * nv, cudaMemcpyDeviceToHost, c->d2h_stream));
+    if (U) CK(c, cudaMemcpyAsync(U, su, sizeof(double) * 2 * ne, cudaMemcpyDeviceToHost, c->d2h_stream));
+    if (Umean) CK(c, cudaMemcpyAsync(Umean, sm, sizeof(double) * 2 * ne, cudaMemcpyDeviceToHost, c->d2h_stream));
+    // the status bits only ever get set, so a copy that also sees a later step's bits
+    // reports a flag early, never late
+    CK(c, cudaMemcpyAsync(c->status_h + b, c->ds.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->d2h_stream));
+    CK(c, cudaEventRecord(c->out_done[b], c->d2h_stream));
+    c->out_seq++;
+    if (ticket) *ticket = c->out_seq;
+    return SESW_OK;
+}
+
+int sesw_wait(sesw_ctx *c, uint64_t ticket)
+{
+    if (!c) return SESW_EINVAL;
+    if (ticket > c->out_seq) return fail(c, SESW_EINVAL, "unknown ticket");
+    DeviceGuard dg(c->device);
+    unsigned status = 0;
+    if (ticket == 0) {
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (c->h2d_stream) CK(c, cudaStreamSynchronize(c->h2d_stream));
+        if (c->d2h_stream) CK(c, cudaStreamSynchronize(c->d2h_stream));
+        CK(c, cudaMemcpyAsync(&status, c->ds.status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    } else {
+        // the buffer's event was recorded by this ticket or a later one on the same copy
+        // stream, so its completion implies this ticket's
+        const int b = (int)((ticket - 1) & 1);
+        CK(c, cudaEventSynchronize(c->out_done[b]));
+        status = c->status_h[b];
+    }
+    if (status & 1u) return fail(c, SESW_EUNSTABLE, "non-finite or out-of-bound elevation detected");
+    return SESW_OK;
+}
+
 int sesw_advance(sesw_ctx *c, int32_t nsteps)
 {
     if (!c) return SESW_EINVAL;
@@ -1019,6 +1111,18 @@ void sesw_destroy(sesw_ctx *c)
         sesw::surrogate_release(c);
         free_all(c);
         if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+        if (c->h2d_stream) {
+            cudaStreamSynchronize(c->h2d_stream);
+            cudaStreamDestroy(c->h2d_stream);
+        }
+        if (c->d2h_stream) {
+            cudaStreamSynchronize(c->d2h_stream);
+            cudaStreamDestroy(c->d2h_stream);
+        }
+        for (int b = 0; b < 2; b++)
+            for (cudaEvent_t ev : {c->in_done[b], c->in_free[b], c->out_ready[b], c->out_done[b]})
+                if (ev) cudaEventDestroy(ev);
+        if (c->status_h) cudaFreeHost(c->status_h);
         cudaGetLastError();
     }
     delete c;

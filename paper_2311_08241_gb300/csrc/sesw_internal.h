@@ -300,6 +300,14 @@ struct sesw_ctx {
     float2 *visc_out = nullptr;    // [ne] scratch of sesw_viscosity (allocated on first use)
     float *W_buf = nullptr;        // [nv] freshwater flux (allocated on first use)
     float *eta_sum_buf = nullptr;  // [nv] sum of the substep elevations (allocated on first use)
+    // asynchronous host transfers: copy streams and double-buffered device staging
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+    cudaEvent_t in_done[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_done[2] = {};
+    double *stage_in[2] = {nullptr, nullptr};    // [2 ne] forcing in transit
+    double *stage_out[2] = {nullptr, nullptr};   // [nv + 4 ne] state in transit
+    unsigned *status_h = nullptr;                // [2] pinned: the status word as of each buffer's last download
+    int in_idx = 0, out_idx = 0;
+    uint64_t out_seq = 0;
     bool have_W = false;
     sesw::Surrogate *sur = nullptr;
 };

@@ -39,6 +39,7 @@ EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_blocks_p
            "sesw_set_block_threads",
            "sesw_mesh_upload", "sesw_mesh_upload_batch", "sesw_set_params_batch", "sesw_diagnostics_batch",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_set_freshwater", "sesw_viscosity",
+           "sesw_set_forcing_async", "sesw_get_state_async", "sesw_wait",
            "sesw_advance", "sesw_get_state",
            "sesw_diagnostics", "sesw_diagnostics_noalloc", "sesw_set_eta_mean", "sesw_get_eta_mean", "sesw_status", "sesw_mesh_check",
            "sesw_get_info", "sesw_last_error", "sesw_destroy",
@@ -117,6 +118,9 @@ def load(build_if_missing: bool = True):
         L.sesw_set_state.argtypes = [P, P, P, I]
         L.sesw_set_forcing.argtypes = [P, P, I]
         L.sesw_set_freshwater.argtypes = [P, P, I]
+        L.sesw_set_forcing_async.argtypes = [P, P]
+        L.sesw_get_state_async.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.sesw_wait.argtypes = [P, ctypes.c_uint64]
         L.sesw_viscosity.argtypes = [P, P, I]
         L.sesw_advance.argtypes = [P, ctypes.c_int32]
         L.sesw_get_state.argtypes = [P, P, P, P, I]
@@ -295,6 +299,25 @@ class Subcycle:
     def sesw_set_forcing(self, R):
         R = _as_f64(R)
         return self._check(self._L.sesw_set_forcing(self._h, _ptr(R), _where(R)))
+
+    def sesw_set_forcing_async(self, R):
+        """Forcing from a host buffer (pinned for overlap); keep R unchanged until a later ticket's wait."""
+        R = _as_f64(R)
+        if _where(R) != SESW_HOST:
+            raise ValueError("sesw_set_forcing_async takes a host buffer")
+        return self._check(self._L.sesw_set_forcing_async(self._h, _ptr(R)))
+
+    def sesw_get_state_async(self, eta=None, U=None, Umean=None):
+        """Start reading the state into host buffers; returns the ticket for sesw_wait."""
+        for x in (eta, U, Umean):
+            if x is not None and _where(x) != SESW_HOST:
+                raise ValueError("sesw_get_state_async fills host buffers")
+        t = ctypes.c_uint64()
+        self._check(self._L.sesw_get_state_async(self._h, _ptr(eta), _ptr(U), _ptr(Umean), ctypes.byref(t)))
+        return t.value
+
+    def sesw_wait(self, ticket: int = 0):
+        return self._check(self._L.sesw_wait(self._h, int(ticket)))
 
     def sesw_set_freshwater(self, W):
         """Freshwater flux [nv] (m/s, positive out of the ocean); None removes it."""

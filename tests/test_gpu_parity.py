@@ -293,3 +293,53 @@ def test_contexts_with_different_layouts_coexist(sesw):
         ra, rb = a.sesw_get_state(), b.sesw_get_state()
     assert np.array_equal(ra[0], sesw.run_case(big, nsteps=2, mode=PERSISTENT)[0])
     assert np.array_equal(rb[0], sesw.run_case(small, nsteps=2, mode=PERSISTENT)[0])
+
+
+@MODES
+def test_async_host_transfers_match_the_synchronous_path(sesw, mode):
+    """Pipelined steps through sesw_set_forcing_async / sesw_get_state_async (double-buffered,
+    waited on two steps later) give bitwise the results of the synchronous calls."""
+    import torch
+
+    case = I.tiny_jittered_case(nx=12, ny=9, seed=41, M=6, tau=60.0)
+    rng = np.random.default_rng(3)
+    forcings = [case.R * (1.0 + 0.5 * rng.standard_normal()) for _ in range(6)]
+    ref = []
+    with sesw.Subcycle() as s:
+        s.sesw_set_mode(mode)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_set_state(case.eta0, case.U0)
+        for R in forcings:
+            s.sesw_set_forcing(R)
+            s.sesw_advance(1)
+            ref.append(s.sesw_get_state())
+    pin = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory()
+    Rh = [pin((case.mesh.ne, 2)) for _ in range(2)]
+    outs = [(pin(case.mesh.nv), pin((case.mesh.ne, 2)), pin((case.mesh.ne, 2))) for _ in range(2)]
+    tickets = [0, 0]
+    got = []
+    with sesw.Subcycle() as s:
+        s.sesw_set_mode(mode)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_set_state(case.eta0, case.U0)
+        for n, R in enumerate(forcings):
+            k = n & 1
+            if n >= 2:
+                s.sesw_wait(tickets[k])
+                got.append(tuple(x.numpy().copy() for x in outs[k]))
+            Rh[k].copy_(torch.from_numpy(R))
+            s.sesw_set_forcing_async(Rh[k])
+            s.sesw_advance(1)
+            tickets[k] = s.sesw_get_state_async(*outs[k])
+        for n in (len(forcings) - 2, len(forcings) - 1):
+            s.sesw_wait(tickets[n & 1])
+            got.append(tuple(x.numpy().copy() for x in outs[n & 1]))
+        s.sesw_wait(0)
+        with pytest.raises(sesw.SeswError, match="ticket"):
+            s.sesw_wait(tickets[1] + 5)
+    assert len(got) == len(ref)
+    for a, b in zip(ref, got):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
