@@ -291,8 +291,9 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
         // store, and a release is cumulative over what precedes it in causality order,
         // so no separate fence is needed: a neighbour whose acquire load sees m + 1 also
         // sees the stores (and the barrier after its own acquire passes them on to its
-        // other threads).
-        if (threadIdx.x == 0 && p != a.silent_patch)
+        // other threads). The last warp publishes, so that the release's latency does not
+        // delay warp 0, which polls the neighbours next.
+        if (threadIdx.x == ((T - 1) & ~31) && p != a.silent_patch)
             st_release_gpu(P.flags + (size_t)p * kFlagStride, (unsigned)(m + 1));
     }
     __syncthreads();
