@@ -524,8 +524,9 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     s.stage_elems = (size_t)hm.nv + 4 * (size_t)hm.ne;
     TRY(zalloc(c, &s.stage, s.stage_elems, "stage"));
     if (mode == SESW_MODE_PERSISTENT) {
-        TRY(zalloc(c, &s.xbuf[0], hm.nv, "xbuf"));
-        TRY(zalloc(c, &s.xbuf[1], hm.nv, "xbuf"));
+        // tagged 64-bit exchange words: two floats per vertex
+        TRY(zalloc(c, &s.xbuf[0], 2 * (size_t)hm.nv, "xbuf"));
+        TRY(zalloc(c, &s.xbuf[1], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
         CK(c, sesw::persistent_prepare(plan));
     } else {

@@ -154,6 +154,7 @@ struct DevState {
     size_t stage_elems = 0;
     // persistent kernel
     float *xbuf[2] = {nullptr, nullptr};  // boundary elevation exchanged between patches, per substep parity
+                                          // (persistent kernel: 64-bit tagged words, 2 floats per vertex)
     unsigned *flags = nullptr;            // substeps completed by each patch in the running step, one
                                           // 128-byte line per patch, then the abort word
     unsigned *abort_flag = nullptr;       // set by a block whose bounded wait gave up

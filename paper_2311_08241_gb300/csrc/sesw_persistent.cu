@@ -21,12 +21,20 @@ namespace {
 // (CACHED), the patch's static slot data, incidence lists, 1/A_v and halo index list
 // are also copied to shared memory once per step.
 //
-// Substep m: update the interior slots (corners all own vertices); wait until the
-// patches owning the halo vertices have published elevation m; read it from the
-// exchange buffer of parity m; update the other slots; vertex pass; write the own
-// vertices' new elevation to the exchange buffer of parity m+1 and publish m+1.
-// A block overwrites an exchange buffer two substeps later, after its neighbours
-// have published a count that shows they finished reading it.
+// Substep m: update the interior slots (corners all own vertices); update the other
+// slots, reading the halo elevation from the exchange buffer of parity m; vertex pass;
+// write the own vertices' new elevation to the exchange buffer of parity m+1.
+//
+// Exchange protocol. Every exchanged elevation is one 64-bit word holding the substep
+// it belongs to (high half) and its value (low half), written and read as a single
+// relaxed access at GPU scope. A reader uses a word only when its tag is the substep
+// it needs, re-reading it (bounded) otherwise, so it can never take a stale or a torn
+// value, and no flag, fence or block-wide barrier is needed for the exchange. A block
+// overwrites a parity buffer (tag m with m + 2) only after its substep m + 1, which
+// needed every neighbour's tag-(m + 1) values; a neighbour writes those only after its
+// own substep m, in which it read the tag-m values (the neighbour relation is
+// symmetric: each patch reads halo values from every patch that reads from it). The
+// buffers are cleared after every step, so tags never carry over between launches.
 struct PArgs {
     const int *patch_slot, *patch_own, *patch_int, *patch_v, *patch_halo, *halo_v, *patch_nbr, *nbr;
     const int *vcsr_off;
@@ -42,8 +50,8 @@ struct PArgs {
     float *eta_out;
     float *eta_sum;         // null, or sum over the substeps of eta^0 .. eta^{M-1} (own vertices)
     const float *W;         // null, or the freshwater flux of each vertex (Eq. 4.5)
-    float *xb[2];
-    unsigned *flags;        // [npatch], then the abort word
+    unsigned long long *xb[2];  // tagged elevation words (tag << 32 | float bits), per substep parity
+    unsigned *flags;        // the abort word at [npatch * kFlagStride]
     unsigned *status;
     const int *pack_patch;  // patch of each block: pack_patch[pack_base + blockIdx.x]
     int pack_base;
@@ -53,11 +61,16 @@ struct PArgs {
     int off_flux, off_g, off_c, off_r, off_l, off_off, off_csr, off_inv, off_halo;
 };
 
-__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p)
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p));
     return v;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
@@ -67,41 +80,33 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Flags are padded to one 128-byte line each so that publishing and polling
-// patches do not contend for the same L2 line.
+// The flag buffer holds npatch + 1 lines of 128 bytes; the abort word is the first word
+// of the last line.
 constexpr int kFlagStride = 32;
 
-// Warp 0 waits until every neighbour of patch p has published `target` substeps
-// (lanes poll one neighbour each). Returns false when the wait gave up; it then sets
-// the timeout bit and the abort word, which makes every other wait give up too.
-__device__ bool warp0_wait_neighbours(const PArgs &P, int p, unsigned target)
+// The halo elevation of vertex v for substep `tag`, given the exchange word `w` already
+// read from xs[v]: re-read until the word carries that tag. A wait that exceeds the
+// budget (or sees the abort word) gives up: it sets the timeout bit and the abort word,
+// which makes every other wait give up too, and clears `ok`; the value returned then is
+// meaningless. (The first reads of a slot's corners are issued together by the caller,
+// so that their latencies overlap.)
+__device__ __forceinline__ float halo_eta(const PArgs &P, const unsigned long long *xs, int v,
+                                          unsigned long long w, unsigned tag, bool &ok)
 {
-    const int lane = threadIdx.x & 31;
-    const int b = P.patch_nbr[p], e = P.patch_nbr[p + 1];
+    if ((unsigned)(w >> 32) == tag) return __uint_as_float((unsigned)w);
     const unsigned *abort_word = P.flags + (size_t)P.npatch * kFlagStride;
-    bool ok = true;
-    for (int k = b + lane; k < e && ok; k += 32) {
-        const unsigned *f = P.flags + (size_t)P.nbr[k] * kFlagStride;
-        const long long t0 = clock64();
-        while (ld_acquire_gpu(f) < target) {
-            if (ld_relaxed_gpu(abort_word) != 0u || clock64() - t0 > P.a.wait_cycles) {
-                ok = false;
-                break;
-            }
-            __nanosleep(20);
+    const long long t0 = clock64();
+    while (ok) {
+        __nanosleep(20);
+        w = ld_relaxed_gpu_u64(xs + v);
+        if ((unsigned)(w >> 32) == tag) return __uint_as_float((unsigned)w);
+        if (ld_relaxed_gpu(abort_word) != 0u || clock64() - t0 > P.a.wait_cycles) {
+            ok = false;
+            atomicOr(P.status, 2u);
+            atomicExch(const_cast<unsigned *>(abort_word), 1u);
         }
     }
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok && lane == 0) {
-        atomicOr(P.status, 2u);
-        atomicExch(P.flags + (size_t)P.npatch * kFlagStride, 1u);
-    }
-    return ok;
+    return 0.0f;
 }
 
 // Element update of one slot (Eq. 4.10, first row, and the theta-weighted flux);
@@ -148,7 +153,7 @@ template <int SPT, int NONLIN, int CACHED, int EXTRA>
 __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_ok;
+    __shared__ int s_abort;
     const int p = P.pack_patch[P.pack_base + blockIdx.x];
     const int T = blockDim.x;
     const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
@@ -188,6 +193,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
         for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
         for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
     }
+    if (threadIdx.x == 0) s_abort = 0;
     float2 u[SPT], shi[SPT], slo[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; j++) {
@@ -201,8 +207,9 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     const float one_p_theta = 1.0f + a.theta;
     // Element update of the slots with local index in [lo, hi). Corner elevations of
     // own vertices come from shared memory; with `halo_src` set, those of halo vertices
-    // are read from that exchange buffer (boundary slots, substeps m >= 1).
-    auto elements = [&](int lo, int hi, const float *halo_src) {
+    // are read from that exchange buffer with tag `tag` (boundary slots, substeps m >= 1).
+    bool ok = true;
+    auto elements = [&](int lo, int hi, const unsigned long long *halo_src, unsigned tag) {
 #pragma unroll
         for (int j = 0; j < SPT; j++) {
             const int i = threadIdx.x + j * T;
@@ -224,9 +231,14 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                 float e0, e1, e2;
                 if (halo_src) {
                     const int *hid = CACHED ? s_halo : P.halo_v + hb;
-                    e0 = l.x < nown ? seta[l.x] : __ldcg(halo_src + hid[l.x - nown]);
-                    e1 = l.y < nown ? seta[l.y] : __ldcg(halo_src + hid[l.y - nown]);
-                    e2 = l.z < nown ? seta[l.z] : __ldcg(halo_src + hid[l.z - nown]);
+                    const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
+                              h2 = l.z < nown ? -1 : hid[l.z - nown];
+                    const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h0);
+                    const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h1);
+                    const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h2);
+                    e0 = h0 < 0 ? seta[l.x] : halo_eta(P, halo_src, h0, w0, tag, ok);
+                    e1 = h1 < 0 ? seta[l.y] : halo_eta(P, halo_src, h1, w1, tag, ok);
+                    e2 = h2 < 0 ? seta[l.z] : halo_eta(P, halo_src, h2, w2, tag, ok);
                 } else {
                     e0 = seta[l.x];
                     e1 = seta[l.y];
@@ -238,28 +250,26 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
         }
     };
 
-    // Slots updated before the wait: whole rounds of interior slots (one per thread
-    // each), so that no thread does more rounds in total than ceil(ns / T); the interior
-    // slots left over go after the wait with the boundary slots.
+    // Slots updated first: whole rounds of interior slots (one per thread each), so that
+    // no thread does more rounds in total than ceil(ns / T); the interior slots left over
+    // go with the boundary slots, whose halo reads may have to wait for a neighbour.
     const int npre = nint >= T ? (nint / T) * T : nint;
     for (int m = 0; m < P.M; m++) {
         if (m == 0) {
-            elements(0, ns, nullptr);
+            elements(0, ns, nullptr, 0u);
         } else {
-            elements(0, npre, nullptr);
-            if (threadIdx.x < 32) {
-                const bool ok = warp0_wait_neighbours(P, p, (unsigned)m);
-                if (threadIdx.x == 0) s_ok = ok;
-            }
-            __syncthreads();
-            if (!s_ok) break;
-            elements(npre, ns, P.xb[m & 1]);
+            elements(0, npre, nullptr, 0u);
+            elements(npre, ns, P.xb[m & 1], (unsigned)m);
+            if (!ok) s_abort = 1;
         }
         __syncthreads();
+        if (s_abort) break;
 
         // vertex pass; the new elevation of own vertices also goes to the exchange buffer
         const bool more = m + 1 < P.M;
-        float *xout = P.xb[(m + 1) & 1];
+        unsigned long long *xout = P.xb[(m + 1) & 1];
+        const unsigned long long tag_out = (unsigned long long)(m + 1) << 32;
+        const bool publish = more && p != a.silent_patch;
         bool bad = false;
         for (int i = threadIdx.x; i < nown; i += T) {
             float sum = 0.0f, inv;
@@ -281,20 +291,12 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                 if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
             }
             seta[i] = e;
-            if (more) __stcg(xout + v0 + i, e);
+            if (publish) st_relaxed_gpu_u64(xout + v0 + i, tag_out | __float_as_uint(e));
             bad |= !(fabsf(e) <= a.eta_bound);
         }
         if (bad) atomicOr(P.status, 1u);
         __syncthreads();
         if (!more) break;
-        // The barrier orders every thread's exchange-buffer stores before this release
-        // store, and a release is cumulative over what precedes it in causality order,
-        // so no separate fence is needed: a neighbour whose acquire load sees m + 1 also
-        // sees the stores (and the barrier after its own acquire passes them on to its
-        // other threads). The last warp publishes, so that the release's latency does not
-        // delay warp 0, which polls the neighbours next.
-        if (threadIdx.x == ((T - 1) & ~31) && p != a.silent_patch)
-            st_release_gpu(P.flags + (size_t)p * kFlagStride, (unsigned)(m + 1));
     }
     __syncthreads();
 
@@ -475,8 +477,8 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     P.eta_out = s.eta[parity ^ 1];
     P.eta_sum = s.eta_sum;
     P.W = s.W;
-    P.xb[0] = s.xbuf[0];
-    P.xb[1] = s.xbuf[1];
+    P.xb[0] = reinterpret_cast<unsigned long long *>(s.xbuf[0]);
+    P.xb[1] = reinterpret_cast<unsigned long long *>(s.xbuf[1]);
     P.flags = s.flags;
     P.status = s.status;
     P.a = a;
@@ -504,8 +506,11 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(plan.threads), args, plan.smem, stream);
         if (e != cudaSuccess) return e;
     }
-    // flags and the abort word start from zero in the next step
-    return cudaMemsetAsync(s.flags, 0, flag_bytes(m.npatch), stream);
+    // the abort word and the exchange tags start from zero in the next step
+    cudaError_t e = cudaMemsetAsync(s.flags, 0, flag_bytes(m.npatch), stream);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++)
+        e = cudaMemsetAsync(s.xbuf[k], 0, sizeof(unsigned long long) * (size_t)m.nv, stream);
+    return e;
 }
 
 }  // namespace sesw
