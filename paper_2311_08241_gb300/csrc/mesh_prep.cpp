@@ -209,6 +209,28 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
         for (int v = patch_v[p]; v < patch_v[p + 1]; v++) vpatch[v] = p;
         maxpv = std::max(maxpv, patch_v[p + 1] - patch_v[p]);
     }
+    // Inside each patch, the vertices that another patch reads (corners of elements that
+    // also touch another patch) come first, keeping the curve order otherwise: the
+    // persistent kernel's vertex pass then publishes all of them in its first round.
+    {
+        std::vector<char> exported(nv, 0);
+        for (int e = 0; e < ne; e++) {
+            const int c[3] = {vinv[m.tri[3 * (size_t)e]], vinv[m.tri[3 * (size_t)e + 1]],
+                              vinv[m.tri[3 * (size_t)e + 2]]};
+            for (int k = 0; k < 3; k++)
+                for (int j = 0; j < 3; j++)
+                    if (vpatch[c[k]] != vpatch[c[j]]) exported[c[k]] = 1;
+        }
+        std::vector<int> order(nv);
+        for (int p = 0; p < npatch; p++) {
+            int w = patch_v[p];
+            for (int pass = 0; pass < 2; pass++)
+                for (int v = patch_v[p]; v < patch_v[p + 1]; v++)
+                    if ((exported[v] != 0) == (pass == 0)) order[w++] = vperm[v];
+        }
+        vperm.swap(order);
+        for (int i = 0; i < nv; i++) vinv[vperm[i]] = i;
+    }
 
     // ---- element order: by owner patch (patch of the lowest new corner), then corners
     struct EK { int lo, mid, hi, e; };

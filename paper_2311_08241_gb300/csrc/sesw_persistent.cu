@@ -25,16 +25,26 @@ namespace {
 // slots, reading the halo elevation from the exchange buffer of parity m; vertex pass;
 // write the own vertices' new elevation to the exchange buffer of parity m+1.
 //
-// Exchange protocol. Every exchanged elevation is one 64-bit word holding the substep
-// it belongs to (high half) and its value (low half), written and read as a single
-// relaxed access at GPU scope. A reader uses a word only when its tag is the substep
-// it needs, re-reading it (bounded) otherwise, so it can never take a stale or a torn
-// value, and no flag, fence or block-wide barrier is needed for the exchange. A block
-// overwrites a parity buffer (tag m with m + 2) only after its substep m + 1, which
-// needed every neighbour's tag-(m + 1) values; a neighbour writes those only after its
-// own substep m, in which it read the tag-m values (the neighbour relation is
-// symmetric: each patch reads halo values from every patch that reads from it). The
-// buffers are cleared after every step, so tags never carry over between launches.
+// Exchange protocol. Every exchanged elevation is one 64-bit word holding a tag (high
+// half) and its value (low half), written and read as a single relaxed access at GPU
+// scope. The tag of substep m is base + m, where base is this launch's tag base. A
+// reader uses a word only when its tag is the one it needs, re-reading it (bounded)
+// otherwise, so it can never take a stale or a torn value, and no flag, fence or
+// block-wide barrier is needed for the exchange. Within a launch, a block overwrites a
+// parity buffer (tag m with m + 2) only after its substep m + 1, which needed every
+// neighbour's tag-(m + 1) values; a neighbour writes those only after its own substep
+// m, in which it read the tag-m values (the neighbour relation is symmetric: each patch
+// reads halo values from every patch that reads from it). Between launches, the last
+// block to leave advances the base by M + 1 (one word per pack in the flag buffer), so
+// every word left by an earlier launch carries a tag that this launch never waits for
+// and the buffers need no clearing. Tags wrap modulo 2^32; a wrapped tag could only
+// match a word that no launch has rewritten since, and every launch rewrites every word
+// that is read.
+//
+// Vertex order. Mesh preparation puts the vertices that other patches read first in
+// each patch, so the vertex pass publishes them in its first round; the halo words of a
+// thread's last-round slot are then requested right after its first element round and
+// have usually arrived by the time the slot is updated.
 struct PArgs {
     const int *patch_slot, *patch_own, *patch_int, *patch_v, *patch_halo, *halo_v, *patch_nbr, *nbr;
     const int *vcsr_off;
@@ -51,10 +61,10 @@ struct PArgs {
     float *eta_sum;         // null, or sum over the substeps of eta^0 .. eta^{M-1} (own vertices)
     const float *W;         // null, or the freshwater flux of each vertex (Eq. 4.5)
     unsigned long long *xb[2];  // tagged elevation words (tag << 32 | float bits), per substep parity
-    unsigned *flags;        // the abort word at [npatch * kFlagStride]
+    unsigned *flags;        // line 0: abort word; line 1 + 2k: tag base of pack k; line 2 + 2k: its exit count
     unsigned *status;
     const int *pack_patch;  // patch of each block: pack_patch[pack_base + blockIdx.x]
-    int pack_base;
+    int pack_base, pack_index;
     StepArgs a;
     int M, npatch;
     // shared-memory carve-up (CACHED), in bytes from the dynamic shared base
@@ -80,30 +90,29 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
     return v;
 }
 
-// The flag buffer holds npatch + 1 lines of 128 bytes; the abort word is the first word
-// of the last line.
+// The flag buffer holds 2 npatch + 1 lines of 128 bytes (at most one pack per patch).
 constexpr int kFlagStride = 32;
 
-// The halo elevation of vertex v for substep `tag`, given the exchange word `w` already
+// The halo elevation of vertex v with tag `tag`, given the exchange word `w` already
 // read from xs[v]: re-read until the word carries that tag. A wait that exceeds the
-// budget (or sees the abort word) gives up: it sets the timeout bit and the abort word,
-// which makes every other wait give up too, and clears `ok`; the value returned then is
-// meaningless. (The first reads of a slot's corners are issued together by the caller,
-// so that their latencies overlap.)
+// budget (or finds the abort word set to this launch's `abort_val`) gives up: it sets
+// the timeout bit and the abort word, which makes every other wait of the launch give
+// up too, and clears `ok`; the value returned then is meaningless. (The first reads of
+// a slot's corners are issued together by the caller, so that their latencies overlap.)
 __device__ __forceinline__ float halo_eta(const PArgs &P, const unsigned long long *xs, int v,
-                                          unsigned long long w, unsigned tag, bool &ok)
+                                          unsigned long long w, unsigned tag, unsigned abort_val, bool &ok)
 {
     if ((unsigned)(w >> 32) == tag) return __uint_as_float((unsigned)w);
-    const unsigned *abort_word = P.flags + (size_t)P.npatch * kFlagStride;
+    const unsigned *abort_word = P.flags;
     const long long t0 = clock64();
     while (ok) {
         __nanosleep(20);
         w = ld_relaxed_gpu_u64(xs + v);
         if ((unsigned)(w >> 32) == tag) return __uint_as_float((unsigned)w);
-        if (ld_relaxed_gpu(abort_word) != 0u || clock64() - t0 > P.a.wait_cycles) {
+        if (ld_relaxed_gpu(abort_word) == abort_val || clock64() - t0 > P.a.wait_cycles) {
             ok = false;
             atomicOr(P.status, 2u);
-            atomicExch(const_cast<unsigned *>(abort_word), 1u);
+            atomicExch(const_cast<unsigned *>(abort_word), abort_val);
         }
     }
     return 0.0f;
@@ -163,6 +172,10 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
     const StepArgs a = P.a;
     const float dt = P.patch_dt[p];
+    unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
+    unsigned *exit_count = base_word + kFlagStride;
+    const unsigned base = ld_relaxed_gpu(base_word);
+    const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
 
     float *seta = reinterpret_cast<float *>(smem_raw);
     float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
@@ -205,70 +218,76 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     __syncthreads();
 
     const float one_p_theta = 1.0f + a.theta;
-    // Element update of the slots with local index in [lo, hi). Corner elevations of
-    // own vertices come from shared memory; with `halo_src` set, those of halo vertices
-    // are read from that exchange buffer with tag `tag` (boundary slots, substeps m >= 1).
-    bool ok = true;
-    auto elements = [&](int lo, int hi, const unsigned long long *halo_src, unsigned tag) {
-#pragma unroll
-        for (int j = 0; j < SPT; j++) {
-            const int i = threadIdx.x + j * T;
-            if (i >= lo && i < hi) {
-                float4 g, coef;
-                float2 r;
-                ushort4 l;
-                if (CACHED) {
-                    g = s_g[i];
-                    coef = s_c[i];
-                    r = s_r[i];
-                    l = s_l[i];
-                } else {
-                    g = P.sg[s0 + i];
-                    coef = slot_coef(P.sc[s0 + i], a, dt);
-                    r = P.R[s0 + i];
-                    l = P.sl[s0 + i];
-                }
-                float e0, e1, e2;
-                if (halo_src) {
-                    const int *hid = CACHED ? s_halo : P.halo_v + hb;
-                    const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
-                              h2 = l.z < nown ? -1 : hid[l.z - nown];
-                    const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h0);
-                    const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h1);
-                    const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h2);
-                    e0 = h0 < 0 ? seta[l.x] : halo_eta(P, halo_src, h0, w0, tag, ok);
-                    e1 = h1 < 0 ? seta[l.y] : halo_eta(P, halo_src, h1, w1, tag, ok);
-                    e2 = h2 < 0 ? seta[l.z] : halo_eta(P, halo_src, h2, w2, tag, ok);
-                } else {
-                    e0 = seta[l.x];
-                    e1 = seta[l.y];
-                    e2 = seta[l.z];
-                }
-                element_update<NONLIN>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
-                                       a.theta, one_p_theta, dt, a.g);
-            }
+    const int *hid = CACHED ? s_halo : P.halo_v + hb;
+    // the exchange-buffer index of a corner's vertex, -1 for an own vertex
+    auto halo_of = [&](unsigned l) { return (int)l < nown ? -1 : hid[l - nown]; };
+    // element update of slot i (round j of this thread) from its corner elevations
+    auto slot_update = [&](int j, int i, float e0, float e1, float e2) {
+        float4 g, coef;
+        float2 r;
+        if (CACHED) {
+            g = s_g[i];
+            coef = s_c[i];
+            r = s_r[i];
+        } else {
+            g = P.sg[s0 + i];
+            coef = slot_coef(P.sc[s0 + i], a, dt);
+            r = P.R[s0 + i];
         }
+        element_update<NONLIN>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i, a.theta,
+                               one_p_theta, dt, a.g);
     };
 
     // Slots updated first: whole rounds of interior slots (one per thread each), so that
     // no thread does more rounds in total than ceil(ns / T); the interior slots left over
     // go with the boundary slots, whose halo reads may have to wait for a neighbour.
     const int npre = nint >= T ? (nint / T) * T : nint;
+    // the last round's slot, when it is one of the latter: its halo words are requested
+    // right after the first round
+    const int ilast = threadIdx.x + (SPT - 1) * T;
+    const bool early = SPT > 1 && ilast >= npre && ilast < ns;
+    bool ok = true;
     for (int m = 0; m < P.M; m++) {
-        if (m == 0) {
-            elements(0, ns, nullptr, 0u);
-        } else {
-            elements(0, npre, nullptr, 0u);
-            elements(npre, ns, P.xb[m & 1], (unsigned)m);
-            if (!ok) s_abort = 1;
+        const unsigned tag = base + (unsigned)m;
+        const unsigned long long *xs = P.xb[m & 1];
+        unsigned long long q0 = 0ull, q1 = 0ull, q2 = 0ull;   // the last round's early words
+#pragma unroll
+        for (int j = 0; j < SPT; j++) {
+            const int i = threadIdx.x + j * T;
+            if (i < ns) {
+                const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                if (m == 0 || i < npre) {
+                    slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
+                } else {
+                    const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
+                    unsigned long long w0 = q0, w1 = q1, w2 = q2;
+                    if (!(early && j == SPT - 1)) {
+                        w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
+                        w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
+                        w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
+                    }
+                    const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, w0, tag, abort_val, ok);
+                    const float e1 = h1 < 0 ? seta[l.y] : halo_eta(P, xs, h1, w1, tag, abort_val, ok);
+                    const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, w2, tag, abort_val, ok);
+                    slot_update(j, i, e0, e1, e2);
+                }
+            }
+            if (j == 0 && early && m > 0) {
+                const ushort4 l = CACHED ? s_l[ilast] : P.sl[s0 + ilast];
+                const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
+                if (h0 >= 0) q0 = ld_relaxed_gpu_u64(xs + h0);
+                if (h1 >= 0) q1 = ld_relaxed_gpu_u64(xs + h1);
+                if (h2 >= 0) q2 = ld_relaxed_gpu_u64(xs + h2);
+            }
         }
+        if (!ok) s_abort = 1;
         __syncthreads();
         if (s_abort) break;
 
         // vertex pass; the new elevation of own vertices also goes to the exchange buffer
         const bool more = m + 1 < P.M;
         unsigned long long *xout = P.xb[(m + 1) & 1];
-        const unsigned long long tag_out = (unsigned long long)(m + 1) << 32;
+        const unsigned long long tag_out = (unsigned long long)(tag + 1u) << 32;
         const bool publish = more && p != a.silent_patch;
         bool bad = false;
         for (int i = threadIdx.x; i < nown; i += T) {
@@ -312,6 +331,12 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
             }
         }
     }
+    // the last block of the pack to leave (every block has read the base by then) sets
+    // the next launch's base
+    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == gridDim.x - 1) {
+        *exit_count = 0u;
+        *base_word = base + (unsigned)P.M + 1u;
+    }
 }
 
 // extra: the freshwater flux or the step-mean elevation is set
@@ -344,7 +369,7 @@ void *persistent_kernel(int spt, int nonlin, int cached, int extra)
     }
 }
 
-size_t flag_bytes(int npatch) { return sizeof(unsigned) * ((size_t)npatch + 1) * kFlagStride; }
+size_t flag_bytes(int npatch) { return sizeof(unsigned) * (2 * (size_t)npatch + 1) * kFlagStride; }
 
 struct SmemLayout {
     int off_flux, off_g, off_c, off_r, off_l, off_off, off_csr, off_inv, off_halo;
@@ -498,19 +523,17 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
     void *fn = persistent_kernel(plan.slots_per_thread, a.nonlinear_h, plan.cached,
                                   s.W != nullptr || s.eta_sum != nullptr);
     if (!fn) return cudaErrorInvalidValue;
-    // one cooperative launch per pack; all packs of a step use the same elevation parity
+    // one cooperative launch per pack; all packs of a step use the same elevation parity,
+    // and each pack has its own tag base (the exchange buffers need no clearing)
     for (size_t k = 0; k + 1 < m.pack_off.size(); k++) {
         P.pack_base = m.pack_off[k];
+        P.pack_index = (int)k;
         const int nblocks = m.pack_off[k + 1] - m.pack_off[k];
         void *args[] = {&P};
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(plan.threads), args, plan.smem, stream);
         if (e != cudaSuccess) return e;
     }
-    // the abort word and the exchange tags start from zero in the next step
-    cudaError_t e = cudaMemsetAsync(s.flags, 0, flag_bytes(m.npatch), stream);
-    for (int k = 0; k < 2 && e == cudaSuccess; k++)
-        e = cudaMemsetAsync(s.xbuf[k], 0, sizeof(unsigned long long) * (size_t)m.nv, stream);
-    return e;
+    return cudaSuccess;
 }
 
 }  // namespace sesw

@@ -276,6 +276,37 @@ def test_persistent_wait_gives_up_and_context_stays_usable(sesw):
     assert _maxabs(got[0] - ref[0]) < 1e-5
 
 
+def test_persistent_tags_continue_across_launches_with_changing_substep_counts(sesw):
+    """The persistent kernel's exchange buffers are never cleared: each launch's tags continue
+    from where the previous launch left them, advancing by M + 1. Steps with different M in a
+    row, in one context, match the oracle run through the same sequence."""
+    case = I.channel_case(nsteps=1)
+    p0 = case.params
+    dt = p0.tau / p0.M
+    seq = [(40, 2), (7, 1), (13, 2), (40, 1)]
+    om, om32 = orc.OracleMesh(case.mesh), orc.OracleMesh(case.mesh, orc.lib_fp32())
+    ref = (case.eta0, case.U0)
+    r32 = (case.eta0, case.U0)
+    with sesw.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload(case.mesh)
+        assert s.sesw_get_info()["mode"] == PERSISTENT and s.sesw_get_info()["npatch"] > 1
+        s.sesw_set_forcing(case.R)
+        s.sesw_set_state(case.eta0, case.U0)
+        for M, n in seq:
+            p = I.Params(g=p0.g, theta=p0.theta, tau=dt * M, M=M, nonlinear_h=p0.nonlinear_h)
+            s.sesw_set_params(p)
+            s.sesw_advance(n)
+            assert s.sesw_status() == sesw.SESW_OK
+            ref = om.advance(case.R, p, n, ref[0], ref[1])[:3]
+            r32 = om32.advance(case.R, p, n, r32[0], r32[1])[:3]
+        got = s.sesw_get_state()
+    for k, name in enumerate(("eta", "U", "<<U>>")):
+        tol = ENVELOPE_FACTOR * _maxabs(r32[k] - ref[k]) + ULP_FLOOR * _maxabs(ref[k])
+        assert _maxabs(got[k] - ref[k]) <= tol, name
+    assert _maxabs(got[0] - ref[0]) <= ETA_ABS_TOL
+
+
 def test_contexts_with_different_layouts_coexist(sesw):
     """Kernel attributes are process-wide: a context with large patches keeps working after a
     context with small patches has been set up (and the other way round)."""
