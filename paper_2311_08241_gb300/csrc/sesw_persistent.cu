@@ -218,10 +218,54 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     __syncthreads();
 
     const float one_p_theta = 1.0f + a.theta;
-    const int *hid = CACHED ? s_halo : P.halo_v + hb;
-    // the exchange-buffer index of a corner's vertex, -1 for an own vertex
-    auto halo_of = [&](unsigned l) { return (int)l < nown ? -1 : hid[l - nown]; };
-    // element update of slot i (round j of this thread) from its corner elevations
+    // Element update of the slots with local index in [lo, hi). Corner elevations of
+    // own vertices come from shared memory; with `halo_src` set, those of halo vertices
+    // are read from that exchange buffer with tag `tag`. Used for the first substep (all
+    // halo values are in shared memory then) and, with one slot per thread, for all.
+    bool ok = true;
+    auto elements = [&](int lo, int hi, const unsigned long long *halo_src, unsigned tag) {
+#pragma unroll
+        for (int j = 0; j < SPT; j++) {
+            const int i = threadIdx.x + j * T;
+            if (i >= lo && i < hi) {
+                float4 g, coef;
+                float2 r;
+                ushort4 l;
+                if (CACHED) {
+                    g = s_g[i];
+                    coef = s_c[i];
+                    r = s_r[i];
+                    l = s_l[i];
+                } else {
+                    g = P.sg[s0 + i];
+                    coef = slot_coef(P.sc[s0 + i], a, dt);
+                    r = P.R[s0 + i];
+                    l = P.sl[s0 + i];
+                }
+                float e0, e1, e2;
+                if (halo_src) {
+                    const int *hid = CACHED ? s_halo : P.halo_v + hb;
+                    const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
+                              h2 = l.z < nown ? -1 : hid[l.z - nown];
+                    const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h0);
+                    const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h1);
+                    const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(halo_src + h2);
+                    e0 = h0 < 0 ? seta[l.x] : halo_eta(P, halo_src, h0, w0, tag, abort_val, ok);
+                    e1 = h1 < 0 ? seta[l.y] : halo_eta(P, halo_src, h1, w1, tag, abort_val, ok);
+                    e2 = h2 < 0 ? seta[l.z] : halo_eta(P, halo_src, h2, w2, tag, abort_val, ok);
+                } else {
+                    e0 = seta[l.x];
+                    e1 = seta[l.y];
+                    e2 = seta[l.z];
+                }
+                element_update<NONLIN>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
+                                       a.theta, one_p_theta, dt, a.g);
+            }
+        }
+    };
+
+    // element update of slot i (round j of this thread) from its corner elevations; the
+    // round's registers are selected by comparison (j is a constant once unrolled)
     auto slot_update = [&](int j, int i, float e0, float e1, float e2) {
         float4 g, coef;
         float2 r;
@@ -234,60 +278,89 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
             coef = slot_coef(P.sc[s0 + i], a, dt);
             r = P.R[s0 + i];
         }
-        element_update<NONLIN>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i, a.theta,
+        float2 uu = u[0], sh = shi[0], sl = slo[0];
+#pragma unroll
+        for (int q = 1; q < SPT; q++)
+            if (q == j) { uu = u[q]; sh = shi[q]; sl = slo[q]; }
+        element_update<NONLIN>(e0, e1, e2, g, coef, r, uu, sh, sl, i < nown_s, sflux + 3 * i, a.theta,
                                one_p_theta, dt, a.g);
+#pragma unroll
+        for (int q = 0; q < SPT; q++)
+            if (q == j) { u[q] = uu; shi[q] = sh; slo[q] = sl; }
     };
 
     // Slots updated first: whole rounds of interior slots (one per thread each), so that
     // no thread does more rounds in total than ceil(ns / T); the interior slots left over
     // go with the boundary slots, whose halo reads may have to wait for a neighbour.
     const int npre = nint >= T ? (nint / T) * T : nint;
-    // the last round's slot, when it is one of the latter: its halo words are requested
-    // right after the first round
-    const int ilast = threadIdx.x + (SPT - 1) * T;
-    const bool early = SPT > 1 && ilast >= npre && ilast < ns;
-    bool ok = true;
     for (int m = 0; m < P.M; m++) {
-        const unsigned tag = base + (unsigned)m;
-        const unsigned long long *xs = P.xb[m & 1];
-        unsigned long long q0 = 0ull, q1 = 0ull, q2 = 0ull;   // the last round's early words
+        if (m == 0 || SPT == 1) {
+            if (m == 0) {
+                elements(0, ns, nullptr, 0u);
+            } else {
+                elements(0, npre, nullptr, 0u);
+                elements(npre, ns, P.xb[m & 1], base + (unsigned)m);
+            }
+        } else {
+            // The last round's slot, when it is not a whole-round interior one, has its
+            // halo words requested right after the first round, so that their L2 round
+            // trip overlaps the rounds in between; the other boundary slots issue their
+            // three reads together when they come.
+            const unsigned long long *xs = P.xb[m & 1];
+            const int *hid = CACHED ? s_halo : P.halo_v + hb;
+            unsigned long long q0 = 0ull, q1 = 0ull, q2 = 0ull;
+            const int ilast = threadIdx.x + (SPT - 1) * T;
+            const bool early = ilast >= npre && ilast < ns;
 #pragma unroll
-        for (int j = 0; j < SPT; j++) {
-            const int i = threadIdx.x + j * T;
-            if (i < ns) {
-                const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
-                if (m == 0 || i < npre) {
-                    slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
-                } else {
-                    const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
-                    unsigned long long w0 = q0, w1 = q1, w2 = q2;
-                    if (!(early && j == SPT - 1)) {
-                        w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
-                        w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
-                        w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (j == SPT - 1) {
+                    if (early) {
+                        const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                        const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
+                                  h2 = l.z < nown ? -1 : hid[l.z - nown];
+                        const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, q0, base + (unsigned)m, abort_val, ok);
+                        const float e1 = h1 < 0 ? seta[l.y] : halo_eta(P, xs, h1, q1, base + (unsigned)m, abort_val, ok);
+                        const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, q2, base + (unsigned)m, abort_val, ok);
+                        slot_update(j, i, e0, e1, e2);
+                    } else if (i < npre) {
+                        const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                        slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                     }
-                    const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, w0, tag, abort_val, ok);
-                    const float e1 = h1 < 0 ? seta[l.y] : halo_eta(P, xs, h1, w1, tag, abort_val, ok);
-                    const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, w2, tag, abort_val, ok);
-                    slot_update(j, i, e0, e1, e2);
+                } else if (i < ns) {
+                    const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                    if (i < npre) {
+                        slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
+                    } else {
+                        const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
+                                  h2 = l.z < nown ? -1 : hid[l.z - nown];
+                        const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
+                        const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
+                        const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
+                        const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, w0, base + (unsigned)m, abort_val, ok);
+                        const float e1 = h1 < 0 ? seta[l.y] : halo_eta(P, xs, h1, w1, base + (unsigned)m, abort_val, ok);
+                        const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, w2, base + (unsigned)m, abort_val, ok);
+                        slot_update(j, i, e0, e1, e2);
+                    }
+                }
+                if (j == 0 && early) {
+                    const ushort4 l = CACHED ? s_l[ilast] : P.sl[s0 + ilast];
+                    const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
+                              h2 = l.z < nown ? -1 : hid[l.z - nown];
+                    if (h0 >= 0) q0 = ld_relaxed_gpu_u64(xs + h0);
+                    if (h1 >= 0) q1 = ld_relaxed_gpu_u64(xs + h1);
+                    if (h2 >= 0) q2 = ld_relaxed_gpu_u64(xs + h2);
                 }
             }
-            if (j == 0 && early && m > 0) {
-                const ushort4 l = CACHED ? s_l[ilast] : P.sl[s0 + ilast];
-                const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
-                if (h0 >= 0) q0 = ld_relaxed_gpu_u64(xs + h0);
-                if (h1 >= 0) q1 = ld_relaxed_gpu_u64(xs + h1);
-                if (h2 >= 0) q2 = ld_relaxed_gpu_u64(xs + h2);
-            }
         }
-        if (!ok) s_abort = 1;
+        if (m > 0 && !ok) s_abort = 1;
         __syncthreads();
         if (s_abort) break;
 
         // vertex pass; the new elevation of own vertices also goes to the exchange buffer
         const bool more = m + 1 < P.M;
         unsigned long long *xout = P.xb[(m + 1) & 1];
-        const unsigned long long tag_out = (unsigned long long)(tag + 1u) << 32;
+        const unsigned long long tag_out = (unsigned long long)(base + (unsigned)(m + 1)) << 32;
         const bool publish = more && p != a.silent_patch;
         bool bad = false;
         for (int i = threadIdx.x; i < nown; i += T) {
