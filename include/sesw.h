@@ -101,7 +101,7 @@ typedef struct sesw_mesh {
  *   flags        bit 0 (SESW_FLAG_NO_STABILITY_CHECK): accept parameters whose Courant
  *                bound exceeds the stability limit (the bound is conservative);
  *                bit 1 (SESW_FLAG_TEST_FORCE_TIMEOUT, for testing failure detection):
- *                in SESW_MODE_PERSISTENT patch 0 never publishes its progress and each
+ *                in SESW_MODE_PERSISTENT patch 0 never publishes its halo values and each
  *                bounded wait gives up after ~1e7 cycles instead of ~1 s, so the step
  *                ends early and sesw_status reports SESW_ETIMEOUT
  *   eta_bound    |eta| above this (m) or a non-finite value sets SESW_EUNSTABLE; <= 0 means 1e4

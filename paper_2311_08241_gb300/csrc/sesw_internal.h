@@ -201,7 +201,7 @@ struct StepArgs {
     float ab0, ab1, ab2;            // SESM: AB3 weights (Eq. 4.7)
     float am0, am1, am2, am3;       // SESM: AM4 weights (Eq. 4.7)
     int nonlinear_h;
-    int silent_patch;          // persistent kernel: this patch never publishes progress (-1: none; test hook)
+    int silent_patch;          // persistent kernel: this patch never publishes its halo values (-1: none; test hook)
     long long wait_cycles;     // persistent kernel: budget of one bounded wait, in SM clock cycles
     double g64;
 };
