@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto")
     ap.add_argument("--scheme", choices=["se", "sesm"], default="se",
-                    help="se: dissipative forward-backward (Eq. 4.10); sesm: AB3-AM4 (Eqs. 4.7-4.8, graph mode)")
+                    help="se: dissipative forward-backward (Eq. 4.10); sesm: AB3-AM4 (Eqs. 4.7-4.8)")
     ap.add_argument("--visc", type=str, default=None, metavar="A_BG,C_V",
                     help="barotropic viscosity of Eq. (viscosity_BT): background (m^2/s) and flow coefficient; "
                          "'auto' picks a background at viscous number 0.2 and C_v = 1")
@@ -121,7 +121,7 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCE = {"k_persistent": "sesw_persistent.cu"}
+KERNEL_SOURCE = {"k_persistent": "sesw_persistent.cu", "k_persistent_sesm": "sesw_persistent.cu"}
 
 
 def kernel_source_hash(kernel="k_persistent"):
@@ -523,7 +523,6 @@ def run_ours(args, world, rank, local):
 
         p = case.params
         case.params = I.Params(g=p.g, theta=p.theta, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h, scheme=1)
-        args.mode = "graph"
         desc = dict(desc, scheme="SESM (AB3-AM4, Eqs. 4.7-4.8)")
     W = None
     if args.freshwater:
@@ -602,9 +601,9 @@ def run_ours(args, world, rank, local):
     # does all M substeps, so a launch moves M * B_alg algorithmic bytes. Graph mode: M
     # k_substep launches per step, each B_alg (the step's short epilogue launch is
     # included in the event time, which understates the kernel's rate).
-    # SESM (graph): M + 1 k_sesm launches per step, rated per substep with its own byte
-    # count. Viscosity (graph): fused into the substep kernel, rated per substep with the
-    # bytes it adds.
+    # SESM: the same with its own byte count per substep (persistent: one k_persistent_sesm
+    # launch per step; graph: M + 1 k_sesm launches). Viscosity (graph): fused into the
+    # substep kernel, rated per substep with the bytes it adds.
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
     if args.scheme == "sesm":
         b_alg = sesm_bytes_per_substep(V, E)
@@ -617,7 +616,10 @@ def run_ours(args, world, rank, local):
     launch_s = mean_step_s if persistent else mean_step_s / M
     achieved = per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
-    kname = "k_persistent" if persistent else ("k_sesm" if args.scheme == "sesm" else "k_substep")
+    if args.scheme == "sesm":
+        kname = "k_persistent_sesm" if persistent else "k_sesm"
+    else:
+        kname = "k_persistent" if persistent else "k_substep"
     if args.visc:
         kname = "k_substep (viscosity fused)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -95,9 +95,11 @@ typedef struct sesw_mesh {
  *   M            substeps per baroclinic step, 1..65536
  *   nonlinear_h  1: H = H0 + eta on each triangle (corner mean); 0: H = H0
  *   scheme       0: dissipative forward-backward (Eq. 4.10, "SE");
- *                1: AB3-AM4 with dissipative coefficients (Eqs. 4.7-4.8, "SESM"), SESW_MODE_GRAPH
- *                   only; levels before the start of a subcycle are taken equal to level 0 and
- *                   <<U>> is the mean of the AB3 transports, which keeps Eq. 4.11 exact
+ *                1: AB3-AM4 with dissipative coefficients (Eqs. 4.7-4.8, "SESM"); levels
+ *                   before the start of a subcycle are taken equal to level 0 and <<U>> is the
+ *                   mean of the AB3 transports, which keeps Eq. 4.11 exact. In
+ *                   SESW_MODE_PERSISTENT it needs patches of at most 1536 slots and 768 own
+ *                   vertices (SESW_EINVAL otherwise: upload in SESW_MODE_GRAPH instead)
  *   flags        bit 0 (SESW_FLAG_NO_STABILITY_CHECK): accept parameters whose Courant
  *                bound exceeds the stability limit (the bound is conservative);
  *                bit 1 (SESW_FLAG_TEST_FORCE_TIMEOUT, for testing failure detection):

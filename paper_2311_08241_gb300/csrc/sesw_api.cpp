@@ -118,7 +118,9 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     if (c->ds.eta_sum) e = cudaMemsetAsync(c->ds.eta_sum, 0, sizeof(float) * (size_t)c->dm.nv, c->cap_stream);
     if (e != cudaSuccess) {
     } else if (c->mode == SESW_MODE_PERSISTENT) {
-        e = sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->plan, c->cap_stream);
+        e = c->params.scheme == 1
+                ? sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, parity, c->plan_sesm, c->cap_stream)
+                : sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->plan, c->cap_stream);
     } else if (c->params.scheme == 1) {
         // SESM: level rings, U^m in B[m % 3] (B[0] holds U^0 and, at the end, U^M) and
         // eta^m in Er[m % 5] (Er[0] holds eta^0 and, at the end, eta^M); levels before
@@ -193,7 +195,11 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
 int enqueue_step(sesw_ctx *c)
 {
     if (c->mode == SESW_MODE_PERSISTENT && !c->persist_graph_ok) {
-        CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->plan, c->stream));
+        if (c->params.scheme == 1)
+            CK(c, sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, c->parity, c->plan_sesm,
+                                               c->stream));
+        else
+            CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->plan, c->stream));
         c->parity ^= 1;
         return SESW_OK;
     }
@@ -372,7 +378,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     std::string err;
     int rc;
     int mode = SESW_MODE_GRAPH;
-    sesw::PersistentPlan plan;
+    sesw::PersistentPlan plan, plan_sesm;
     try {
         if (c->mode_req != SESW_MODE_GRAPH) {
             // persistent: blocks_per_sm patches per SM, all resident
@@ -529,6 +535,8 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.xbuf[1], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
         CK(c, sesw::persistent_prepare(plan));
+        plan_sesm = sesw::persistent_plan_sesm(d, plan.blocks_per_sm);
+        if (plan_sesm.slots_per_thread > 0) CK(c, sesw::persistent_prepare_sesm(plan_sesm));
     } else {
         TRY(zalloc(c, &s.eta_x[0], hm.nv, "eta_x"));
         TRY(zalloc(c, &s.eta_x[1], hm.nv, "eta_x"));
@@ -585,6 +593,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     c->parity = 0;
     c->mode = mode;
     c->plan = plan;
+    c->plan_sesm = plan_sesm;
     c->persist_graph_ok = true;
     c->grad_gram_max_h = hm.grad_gram_max_h;
     c->nbasin = hm.nbasin;
@@ -658,8 +667,9 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
         if (q.M < 1 || q.M > 65536) return fail(c, SESW_EINVAL, "M must be in [1, 65536]");
         if (q.nonlinear_h != 0 && q.nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
         if (q.scheme != 0 && q.scheme != 1) return fail(c, SESW_EINVAL, "scheme must be 0 (SE) or 1 (SESM)");
-        if (q.scheme == 1 && c->mode == SESW_MODE_PERSISTENT)
-            return fail(c, SESW_EINVAL, "the SESM scheme runs in SESW_MODE_GRAPH; set the mode before the upload");
+        if (q.scheme == 1 && c->mode == SESW_MODE_PERSISTENT && c->plan_sesm.slots_per_thread == 0)
+            return fail(c, SESW_EINVAL, "the patches of this mesh do not fit the persistent SESM kernel; set "
+                                        "SESW_MODE_GRAPH before the upload");
         if (!(q.visc_background >= 0.0) || !isfinite(q.visc_background) || !(q.visc_flow >= 0.0) ||
             !isfinite(q.visc_flow))
             return fail(c, SESW_EINVAL, "visc_background and visc_flow must be >= 0 and finite");
@@ -1080,11 +1090,13 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->nslot = c->nslot;
     info->max_patch_slots = c->max_patch_slots;
     info->patch_vertices = c->patch_vertices_used;
-    info->block_threads = c->mode == SESW_MODE_PERSISTENT ? c->plan.threads : c->block_threads;
+    // the persistent plan of the scheme in use (SE until SESM parameters are set)
+    const sesw::PersistentPlan &pl = c->have_params && c->params.scheme == 1 ? c->plan_sesm : c->plan;
+    info->block_threads = c->mode == SESW_MODE_PERSISTENT ? pl.threads : c->block_threads;
     info->mode = c->mode;
-    info->blocks_per_sm = c->mode == SESW_MODE_PERSISTENT ? c->plan.blocks_per_sm : 0;
-    info->slots_per_thread = c->mode == SESW_MODE_PERSISTENT ? c->plan.slots_per_thread : 0;
-    info->cached = c->mode == SESW_MODE_PERSISTENT ? c->plan.cached : 0;
+    info->blocks_per_sm = c->mode == SESW_MODE_PERSISTENT ? pl.blocks_per_sm : 0;
+    info->slots_per_thread = c->mode == SESW_MODE_PERSISTENT ? pl.slots_per_thread : 0;
+    info->cached = c->mode == SESW_MODE_PERSISTENT ? pl.cached : 0;
     info->courant_max = c->courant_max;
     info->courant_limit = c->have_params ? c->courant_limit : 0.0;
     info->stiffness_bound = c->grad_gram_max_h;

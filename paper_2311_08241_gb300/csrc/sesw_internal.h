@@ -246,6 +246,12 @@ cudaError_t persistent_prepare(const PersistentPlan &plan);
 size_t persistent_flag_bytes(int npatch);
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                               const PersistentPlan &plan, cudaStream_t stream);
+// The SESM scheme in the persistent form (k_persistent_sesm): cached patches of at most
+// 4 x 384 slots and 2 x 384 own vertices; an empty plan when the mesh does not fit.
+PersistentPlan persistent_plan_sesm(const DevMesh &m, int blocks_per_sm);
+cudaError_t persistent_prepare_sesm(const PersistentPlan &plan);
+cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                                   const PersistentPlan &plan, cudaStream_t stream);
 
 struct Surrogate;
 void surrogate_release(sesw_ctx *c);
@@ -276,6 +282,7 @@ struct sesw_ctx {
     int mode_req = SESW_MODE_AUTO, mode = SESW_MODE_GRAPH;
     int blocks_per_sm = 0;         // persistent mode; 0 = try 2, then 1
     sesw::PersistentPlan plan;
+    sesw::PersistentPlan plan_sesm;   // the SESM scheme's plan (empty: graph mode only)
     bool persist_graph_ok = true;
     bool have_mesh = false, have_params = false;
     sesw::DevMesh dm;

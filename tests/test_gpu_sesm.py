@@ -1,5 +1,7 @@
-"""SESM substep (AB3-AM4, Eqs. 4.7-4.8) on the GPU against the FP64 oracle, same tolerance rule
-as the SE path: within twice the drift of the FP32 build of the oracle, plus a floor of 8 ulp."""
+"""SESM substep (AB3-AM4, Eqs. 4.7-4.8) on the GPU against the FP64 oracle, in both execution modes
+(graph: one launch per substep; persistent: one launch per step, exchanging the AM4 elevation
+between patches), same tolerance rule as the SE path: within twice the drift of the FP32 build of
+the oracle, plus a floor of 8 ulp."""
 import math
 
 import numpy as np
@@ -8,7 +10,7 @@ import pytest
 from oracle import closed
 from oracle import runner as orc
 from paper_2311_08241_gb300 import inputs as I
-from parity_util import ENVELOPE_FACTOR, GRAPH, PERSISTENT, ULP_FLOOR, _maxabs
+from parity_util import ENVELOPE_FACTOR, GRAPH, MODES, PERSISTENT, ULP_FLOOR, _maxabs
 
 pytestmark = pytest.mark.gpu
 
@@ -31,9 +33,9 @@ def _sesm(case, theta=0.14):
     return closed.sesm_params(theta / 2.0)
 
 
-def _run(S, case, nsteps):
+def _run(S, case, nsteps, mode=GRAPH):
     with S.Subcycle() as s:
-        s.sesw_set_mode(GRAPH)
+        s.sesw_set_mode(mode)
         s.sesw_mesh_upload(case.mesh)
         s.sesw_set_params(case.params)
         s.sesw_set_forcing(case.R)
@@ -57,35 +59,39 @@ def _check(case, coef, got, nsteps, what):
     return ref
 
 
+@MODES
 @pytest.mark.parametrize("name", ["basin", "tiny", "channel", "sphere6"])
-def test_sesm_matches_oracle(S, name):
+def test_sesm_matches_oracle(S, name, mode):
     case = {"basin": lambda: I.basin_case(nsteps=5),
             "tiny": lambda: I.tiny_jittered_case(nx=21, ny=15, seed=5, M=7, tau=70.0),
             "channel": lambda: I.channel_case(nsteps=10),
             "sphere6": lambda: I.sphere_case(level=6, nsteps=5)}[name]()
     coef = _sesm(case)
-    (got, info) = _run(S, case, case.nsteps)
-    assert info["mode"] == GRAPH
-    _check(case, coef, got, case.nsteps, name)
+    (got, info) = _run(S, case, case.nsteps, mode)
+    assert info["mode"] == mode
+    _check(case, coef, got, case.nsteps, f"{name} mode={mode}")
 
 
-def test_sesm_periodic_wave_closed_form(S):
+@MODES
+def test_sesm_periodic_wave_closed_form(S, mode):
     case = I.periodic_wave_case(n=32, kx=3, ky=1, nsteps=4, M=30, tau=450.0)
     coef = _sesm(case)
-    (eta, U, Um), _ = _run(S, case, case.nsteps)
+    (eta, U, Um), info = _run(S, case, case.nsteps, mode)
+    assert info["mode"] == mode
     p = case.params
     u, e = closed.sesm_mode_amplitude(closed.kappa2_square(32, 10e3, 3, 1), p.g * 4000.0, p.tau / p.M, coef, p.M,
                                       case.nsteps)
     assert np.max(np.abs(eta - e * case.eta0)) < 1e-5
 
 
-def test_sesm_summation_identity_and_volume(S):
+@MODES
+def test_sesm_summation_identity_and_volume(S, mode):
     case = I.basin_case(nsteps=1)
     _sesm(case)
     om = orc.OracleMesh(case.mesh)
     av, _ = om.areas()
     with S.Subcycle() as s:
-        s.sesw_set_mode(GRAPH)
+        s.sesw_set_mode(mode)
         s.sesw_mesh_upload(case.mesh)
         s.sesw_set_params(case.params)
         s.sesw_set_state(case.eta0, case.U0)
@@ -104,11 +110,23 @@ def test_sesm_summation_identity_and_volume(S):
 def test_sesm_rules(S):
     case = I.tiny_jittered_case()
     _sesm(case)
+    # persistent SESM needs patches of at most 4 x 384 slots: one block per SM on the
+    # channel gives patches of ~1300 vertices, which it refuses (the SE kernel takes them)
+    big = I.channel_case(nsteps=1)
+    _sesm(big)
     with S.Subcycle() as s:
         s.sesw_set_mode(PERSISTENT)
-        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_blocks_per_sm(1)
+        s.sesw_mesh_upload(big.mesh)
+        assert s.sesw_get_info()["mode"] == PERSISTENT
         with pytest.raises(S.SeswError, match="SESW_MODE_GRAPH"):
-            s.sesw_set_params(case.params)
+            s.sesw_set_params(big.params)
+    with S.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload(big.mesh)
+        s.sesw_set_params(big.params)
+        info = s.sesw_get_info()
+        assert info["mode"] == PERSISTENT and info["slots_per_thread"] >= 1 and info["block_threads"] <= 384
     with S.Subcycle() as s:
         s.sesw_set_mode(GRAPH)
         s.sesw_mesh_upload(case.mesh)
@@ -125,3 +143,24 @@ def test_sesm_rules(S):
         else:
             hi = mid
     assert abs(lim - lo) < 2e-3, (lim, lo)
+
+
+def test_sesm_persistent_batch_in_packs(S):
+    """A batch of basins with the SESM scheme in persistent mode, more patches than resident blocks
+    (several cooperative launches per step, each with its own tag base), matches the oracle per basin."""
+    cases = I.ensemble_cases(nbasins=14, scale=0.04, seed=11, nsteps=2)
+    coefs = [_sesm(c) for c in cases]
+    with S.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload_batch([c.mesh for c in cases])
+        s.sesw_set_params_batch([c.params for c in cases])
+        s.sesw_set_forcing(np.concatenate([c.R for c in cases]))
+        s.sesw_set_state(np.concatenate([c.eta0 for c in cases]), np.concatenate([c.U0 for c in cases]))
+        s.sesw_advance(2)
+        info = s.sesw_get_info()
+        eta, U, Um = s.sesw_get_state()
+    assert info["mode"] == PERSISTENT and info["npack"] > 1, info
+    iv = np.cumsum([c.mesh.nv for c in cases])[:-1]
+    ie = np.cumsum([c.mesh.ne for c in cases])[:-1]
+    for c, coef, e, u, um in zip(cases, coefs, np.split(eta, iv), np.split(U, ie), np.split(Um, ie)):
+        _check(c, coef, (e, u, um), 2, f"{c.name} packs={info['npack']}")

@@ -145,14 +145,16 @@ def test_freshwater_matches_oracle_in_both_modes(S, name, mode):
     _envelope_check(ref, r32, got, f"SE+W {name} mode {mode}")
 
 
+@MODES
 @pytest.mark.parametrize("name", ["tiny", "basin"])
-def test_sesm_freshwater_matches_oracle(S, name):
+def test_sesm_freshwater_matches_oracle(S, name, mode):
     case = CASES[name]()
     p = case.params
     case.params = I.Params(g=p.g, theta=0.14, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h, scheme=1)
     coef = closed.sesm_params(0.07)
     W = _freshwater(case, seed=5)
-    got, _ = _run(S, case, case.nsteps, W=W)
+    got, info = _run(S, case, case.nsteps, mode=mode, W=W)
+    assert info["mode"] == mode
     ref = orc.OracleMesh(case.mesh).advance_sesm(case.R, case.params, coef, case.nsteps, case.eta0, case.U0, W=W)
     r32 = orc.OracleMesh(case.mesh, orc.lib_fp32()).advance_sesm(case.R, case.params, coef, case.nsteps,
                                                                    case.eta0, case.U0, W=W)
