@@ -119,8 +119,8 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     if (e != cudaSuccess) {
     } else if (c->mode == SESW_MODE_PERSISTENT) {
         e = c->params.scheme == 1
-                ? sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, parity, c->plan_sesm, c->cap_stream)
-                : sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->plan, c->cap_stream);
+                ? sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, parity, c->packs, c->cap_stream)
+                : sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->packs, c->cap_stream);
     } else if (c->params.scheme == 1) {
         // SESM: level rings, U^m in B[m % 3] (B[0] holds U^0 and, at the end, U^M) and
         // eta^m in Er[m % 5] (Er[0] holds eta^0 and, at the end, eta^M); levels before
@@ -196,10 +196,9 @@ int enqueue_step(sesw_ctx *c)
 {
     if (c->mode == SESW_MODE_PERSISTENT && !c->persist_graph_ok) {
         if (c->params.scheme == 1)
-            CK(c, sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, c->parity, c->plan_sesm,
-                                               c->stream));
+            CK(c, sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, c->parity, c->packs, c->stream));
         else
-            CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->plan, c->stream));
+            CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->packs, c->stream));
         c->parity ^= 1;
         return SESW_OK;
     }
@@ -344,11 +343,12 @@ int sesw_set_mode(sesw_ctx *c, int32_t mode)
     return SESW_OK;
 }
 
-static int prepare_parts(sesw_ctx *c, const sesw_mesh *meshes, int n, int pv, sesw::HostMesh &hm, std::string &err)
+static int prepare_parts(sesw_ctx *c, const sesw_mesh *meshes, int n, const std::vector<int> &pv, sesw::HostMesh &hm,
+                         std::string &err)
 {
     std::vector<sesw::HostMesh> parts(n);
     for (int b = 0; b < n; b++) {
-        int rc = sesw::prepare_mesh(meshes[b], pv, parts[b], err);
+        int rc = sesw::prepare_mesh(meshes[b], pv[b], parts[b], err);
         if (rc != SESW_OK) {
             if (n > 1) err = "basin " + std::to_string(b) + ": " + err;
             return rc;
@@ -360,6 +360,84 @@ static int prepare_parts(sesw_ctx *c, const sesw_mesh *meshes, int n, int pv, se
         sesw::concat_meshes(parts, hm);
     (void)c;
     return SESW_OK;
+}
+
+// Persistent patch sizes. A single mesh is cut into one grid of resident blocks (nblk
+// patches). In a batch every basin must fit one grid, and basins are packed whole into
+// packs of at most nblk patches, one cooperative launch each: a basin gets the larger of
+// its one-grid size and a common size `base`, the largest patch whose static data fits
+// shared memory (so most basins run the cached kernel), or a smaller one when the whole
+// batch then fits a single pack. Returns base.
+static int persistent_patch_sizes(const sesw_mesh *meshes, int n, int nblk, int bps, std::vector<int> &pv)
+{
+    pv.assign(n, 32);
+    long long total = 0;
+    for (int b = 0; b < n; b++) {
+        total += meshes[b].nv;
+        pv[b] = (int)std::max<long long>(32, (meshes[b].nv + nblk - 1) / nblk);
+    }
+    if (n == 1) return pv[0];
+    const long long cached = bps <= 1 ? 1280 : 1280 / bps;
+    long long base = cached;
+    if (nblk > n) base = std::min<long long>(base, (total + (nblk - n) - 1) / (nblk - n));
+    base = std::max<long long>(32, base);
+    for (int b = 0; b < n; b++) pv[b] = std::max<int>(pv[b], (int)base);
+    return (int)base;
+}
+
+// Packs of a persistent batch: basins of the common patch size and basins of larger
+// patches are packed separately (first fit, largest first), so that a pack's plan is not
+// set by a larger class; each pack gets the plans of its largest patch. Leaves `packs`
+// empty when some pack does not fit the persistent kernel.
+static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int base, int nblk, int bps,
+                       std::vector<sesw::PackPlan> &packs, std::vector<std::vector<int>> &pack_basins)
+{
+    packs.clear();
+    pack_basins.clear();
+    auto np_of = [&](int b) { return hm.basin_patch[b + 1] - hm.basin_patch[b]; };
+    for (int cls = 0; cls < 2; cls++) {
+        std::vector<int> order;
+        for (int b = 0; b < hm.nbasin; b++)
+            if ((pv[b] > base) == (cls == 1)) order.push_back(b);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return np_of(x) > np_of(y); });
+        std::vector<std::vector<int>> bins;
+        std::vector<int> fill;
+        for (int b : order) {
+            if (np_of(b) > nblk) return;
+            size_t k = 0;
+            while (k < bins.size() && fill[k] + np_of(b) > nblk) k++;
+            if (k == bins.size()) {
+                bins.emplace_back();
+                fill.push_back(0);
+            }
+            bins[k].push_back(b);
+            fill[k] += np_of(b);
+        }
+        for (auto &bn : bins) {
+            std::sort(bn.begin(), bn.end());
+            sesw::PackPlan pk;
+            for (int b : bn)
+                for (int q = hm.basin_patch[b]; q < hm.basin_patch[b + 1]; q++) {
+                    const int nvq = hm.patch_v[q + 1] - hm.patch_v[q];
+                    const int nhq = hm.patch_halo[q + 1] - hm.patch_halo[q];
+                    pk.mx.slots = std::max(pk.mx.slots, hm.patch_slot[q + 1] - hm.patch_slot[q]);
+                    pk.mx.vertices = std::max(pk.mx.vertices, nvq);
+                    pk.mx.halo = std::max(pk.mx.halo, nhq);
+                    pk.mx.local = std::max(pk.mx.local, nvq + nhq);
+                    pk.mx.csr = std::max(pk.mx.csr, hm.vcsr_off[hm.patch_v[q + 1]] - hm.vcsr_off[hm.patch_v[q]]);
+                }
+            pk.plan = sesw::persistent_plan(pk.mx, bps);
+            if (pk.plan.slots_per_thread == 0) {
+                packs.clear();
+                pack_basins.clear();
+                return;
+            }
+            pk.plan.blocks_per_sm = bps;
+            pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, bps);
+            packs.push_back(pk);
+            pack_basins.push_back(bn);
+        }
+    }
 }
 
 static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
@@ -379,6 +457,8 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     int rc;
     int mode = SESW_MODE_GRAPH;
     sesw::PersistentPlan plan, plan_sesm;
+    std::vector<sesw::PackPlan> packs;
+    std::vector<std::vector<int>> pack_basins;
     try {
         if (c->mode_req != SESW_MODE_GRAPH) {
             // persistent: blocks_per_sm patches per SM, all resident
@@ -386,29 +466,21 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
             CK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
             const int tries[2] = {c->blocks_per_sm > 0 ? c->blocks_per_sm : 2, c->blocks_per_sm > 0 ? 0 : 1};
             for (int bps : tries) {
-                if (bps <= 0 || plan.slots_per_thread > 0) continue;
-                const long long nblk = (long long)nsm * bps;
-                // Patch size: the smallest (>= 32) that puts the largest mesh into one grid
-                // of resident blocks; meshes are then packed, largest first, into packs of
-                // at most nblk patches, and a step launches the packs one after another.
-                long long vmax = 0;
-                for (int b = 0; b < n; b++) vmax = std::max<long long>(vmax, meshes[b].nv);
-                const long long lo = std::max<long long>(32, (vmax + nblk - 1) / nblk);
-                rc = prepare_parts(c, meshes, n, (int)lo, hm, err);
+                if (bps <= 0 || !packs.empty()) continue;
+                const int nblk = nsm * bps;
+                std::vector<int> pv;
+                const int base = persistent_patch_sizes(meshes, n, nblk, bps, pv);
+                rc = prepare_parts(c, meshes, n, pv, hm, err);
                 if (rc != SESW_OK) return fail(c, rc, err);
-                rc = sesw::build_halos(hm, err);
-                if (rc == SESW_OK) {
-                    sesw::DevMesh probe;
-                    probe.max_patch_slots = hm.max_patch_slots;
-                    probe.max_patch_local = hm.max_patch_local;
-                    probe.max_patch_vertices = hm.max_patch_vertices;
-                    probe.max_patch_halo = hm.max_patch_halo;
-                    probe.max_patch_csr = hm.max_patch_csr;
-                    plan = sesw::persistent_plan(probe, bps);
-                    if (plan.slots_per_thread > 0) plan.blocks_per_sm = bps;
-                }
+                if (sesw::build_halos(hm, err) == SESW_OK) make_packs(hm, pv, base, nblk, bps, packs, pack_basins);
             }
-            if (plan.slots_per_thread > 0) {
+            if (!packs.empty()) {
+                plan = packs[0].plan;
+                plan_sesm = packs[0].plan_sesm;
+                for (const auto &pk : packs)
+                    if (pk.plan_sesm.slots_per_thread == 0) plan_sesm = sesw::PersistentPlan();
+            }
+            if (!packs.empty()) {
                 mode = SESW_MODE_PERSISTENT;
             } else if (c->mode_req == SESW_MODE_PERSISTENT) {
                 return fail(c, SESW_EINVAL, "the mesh does not fit the persistent kernel (patch too large); "
@@ -416,7 +488,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
             }
         }
         if (mode == SESW_MODE_GRAPH) {
-            rc = prepare_parts(c, meshes, n, c->patch_vertices, hm, err);
+            rc = prepare_parts(c, meshes, n, std::vector<int>(n, c->patch_vertices), hm, err);
             if (rc != SESW_OK) return fail(c, rc, err);
         }
     } catch (const std::bad_alloc &) {
@@ -464,33 +536,14 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
     TRY(zalloc(c, &d.patch_dt, hm.npatch, "patch_dt"));
     if (mode == SESW_MODE_PERSISTENT) {
-        // first-fit decreasing packing of whole meshes into packs of at most nblk patches
-        int nsm = 0;
-        CK(c, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-        const int nblk = nsm * plan.blocks_per_sm;
-        std::vector<int> order(hm.nbasin);
-        for (int b = 0; b < hm.nbasin; b++) order[b] = b;
-        auto np_of = [&](int b) { return hm.basin_patch[b + 1] - hm.basin_patch[b]; };
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return np_of(x) > np_of(y); });
-        std::vector<std::vector<int>> packs;
-        std::vector<int> fill;
-        for (int b : order) {
-            if (np_of(b) > nblk) return fail(c, SESW_EINVAL, "a mesh needs more patches than resident blocks");
-            size_t k = 0;
-            while (k < packs.size() && fill[k] + np_of(b) > nblk) k++;
-            if (k == packs.size()) {
-                packs.emplace_back();
-                fill.push_back(0);
-            }
-            packs[k].push_back(b);
-            fill[k] += np_of(b);
-        }
+        // the packs chosen with the layout: their patches, pack by pack
         std::vector<int> pp;
         d.pack_off.assign(1, 0);
-        for (auto &pk : packs) {
-            std::sort(pk.begin(), pk.end());
-            for (int b : pk)
+        for (size_t k = 0; k < packs.size(); k++) {
+            packs[k].base = (int)pp.size();
+            for (int b : pack_basins[k])
                 for (int q = hm.basin_patch[b]; q < hm.basin_patch[b + 1]; q++) pp.push_back(q);
+            packs[k].nblocks = (int)pp.size() - packs[k].base;
             d.pack_off.push_back((int)pp.size());
         }
         TRY(upload(c, &d.pack_patch, pp, "pack_patch"));
@@ -534,9 +587,10 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.xbuf[0], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.xbuf[1], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
-        CK(c, sesw::persistent_prepare(plan));
-        plan_sesm = sesw::persistent_plan_sesm(d, plan.blocks_per_sm);
-        if (plan_sesm.slots_per_thread > 0) CK(c, sesw::persistent_prepare_sesm(plan_sesm));
+        for (const auto &pk : packs) {
+            CK(c, sesw::persistent_prepare(pk.plan));
+            if (plan_sesm.slots_per_thread > 0) CK(c, sesw::persistent_prepare_sesm(pk.plan_sesm));
+        }
     } else {
         TRY(zalloc(c, &s.eta_x[0], hm.nv, "eta_x"));
         TRY(zalloc(c, &s.eta_x[1], hm.nv, "eta_x"));
@@ -594,6 +648,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     c->mode = mode;
     c->plan = plan;
     c->plan_sesm = plan_sesm;
+    c->packs = packs;
     c->persist_graph_ok = true;
     c->grad_gram_max_h = hm.grad_gram_max_h;
     c->nbasin = hm.nbasin;
@@ -1102,7 +1157,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->stiffness_bound = c->grad_gram_max_h;
     info->device_bytes = c->device_bytes;
     info->nbasin = c->nbasin;
-    info->npack = c->mode == SESW_MODE_PERSISTENT ? (int32_t)c->dm.pack_off.size() - 1 : 0;
+    info->npack = c->mode == SESW_MODE_PERSISTENT ? (int32_t)c->packs.size() : 0;
     info->visc_number = c->have_params ? c->visc_number : 0.0;
     for (double v : c->basin_visc_stiffness) info->visc_stiffness = std::max(info->visc_stiffness, v);
     return SESW_OK;

@@ -241,17 +241,28 @@ struct PersistentPlan {
     int blocks_per_sm = 1;
     size_t smem = 0;
 };
-PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm);
+// Largest patch of a pack: what its shared-memory layout and its plan depend on.
+struct PatchMax {
+    int slots = 0, local = 0, vertices = 0, halo = 0, csr = 0;
+};
+// One cooperative launch of a step: blocks [base, base + nblocks) of pack_patch, with the
+// plans of both schemes for its largest patch (the SESM plan may be empty).
+struct PackPlan {
+    int base = 0, nblocks = 0;
+    PatchMax mx;
+    PersistentPlan plan, plan_sesm;
+};
+PersistentPlan persistent_plan(const PatchMax &mx, int blocks_per_sm);
 cudaError_t persistent_prepare(const PersistentPlan &plan);
 size_t persistent_flag_bytes(int npatch);
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                              const PersistentPlan &plan, cudaStream_t stream);
+                              const std::vector<PackPlan> &packs, cudaStream_t stream);
 // The SESM scheme in the persistent form (k_persistent_sesm): cached patches of at most
-// 4 x 384 slots and 2 x 384 own vertices; an empty plan when the mesh does not fit.
-PersistentPlan persistent_plan_sesm(const DevMesh &m, int blocks_per_sm);
+// 4 x 384 slots and 2 x 384 own vertices; an empty plan when the patches do not fit.
+PersistentPlan persistent_plan_sesm(const PatchMax &mx, int blocks_per_sm);
 cudaError_t persistent_prepare_sesm(const PersistentPlan &plan);
 cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                                   const PersistentPlan &plan, cudaStream_t stream);
+                                   const std::vector<PackPlan> &packs, cudaStream_t stream);
 
 struct Surrogate;
 void surrogate_release(sesw_ctx *c);
@@ -283,6 +294,7 @@ struct sesw_ctx {
     int blocks_per_sm = 0;         // persistent mode; 0 = try 2, then 1
     sesw::PersistentPlan plan;
     sesw::PersistentPlan plan_sesm;   // the SESM scheme's plan (empty: graph mode only)
+    std::vector<sesw::PackPlan> packs;   // persistent mode: the launches of a step
     bool persist_graph_ok = true;
     bool have_mesh = false, have_params = false;
     sesw::DevMesh dm;

@@ -673,29 +673,29 @@ struct SmemLayout {
 
 size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-SmemLayout smem_layout(const DevMesh &m)
+SmemLayout smem_layout(const PatchMax &m)
 {
     SmemLayout L;
-    size_t o = align16(sizeof(float) * (size_t)m.max_patch_local);
+    size_t o = align16(sizeof(float) * (size_t)m.local);
     L.off_flux = (int)o;
-    o = align16(o + sizeof(float) * 3 * (size_t)m.max_patch_slots);
+    o = align16(o + sizeof(float) * 3 * (size_t)m.slots);
     L.total_plain = o;
     L.off_g = (int)o;
-    o += sizeof(float4) * (size_t)m.max_patch_slots;
+    o += sizeof(float4) * (size_t)m.slots;
     L.off_c = (int)o;
-    o += sizeof(float4) * (size_t)m.max_patch_slots;
+    o += sizeof(float4) * (size_t)m.slots;
     L.off_r = (int)o;
-    o = align16(o + sizeof(float2) * (size_t)m.max_patch_slots);
+    o = align16(o + sizeof(float2) * (size_t)m.slots);
     L.off_l = (int)o;
-    o = align16(o + sizeof(ushort4) * (size_t)m.max_patch_slots);
+    o = align16(o + sizeof(ushort4) * (size_t)m.slots);
     L.off_inv = (int)o;
-    o = align16(o + sizeof(float) * (size_t)m.max_patch_vertices);
+    o = align16(o + sizeof(float) * (size_t)m.vertices);
     L.off_halo = (int)o;
-    o = align16(o + sizeof(int) * (size_t)m.max_patch_halo);
+    o = align16(o + sizeof(int) * (size_t)m.halo);
     L.off_off = (int)o;
-    o = align16(o + sizeof(unsigned short) * ((size_t)m.max_patch_vertices + 1));
+    o = align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1));
     L.off_csr = (int)o;
-    o = align16(o + sizeof(unsigned short) * (size_t)m.max_patch_csr);
+    o = align16(o + sizeof(unsigned short) * (size_t)m.csr);
     L.total_cached = o;
     return L;
 }
@@ -704,7 +704,7 @@ SmemLayout smem_layout(const DevMesh &m)
 
 size_t persistent_flag_bytes(int npatch) { return flag_bytes(npatch); }
 
-PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm)
+PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
 {
     PersistentPlan plan;
     int dev = 0, smem_optin = 0, smem_sm = 0;
@@ -721,7 +721,7 @@ PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm)
     static const int spts[] = {1, 2, 3, 4, 6, 8};
     int spt = 0, t = 0;
     for (int cand : spts) {
-        const int need = (m.max_patch_slots + cand - 1) / cand;
+        const int need = (m.slots + cand - 1) / cand;
         const int tt = ((need + 31) / 32) * 32;
         if (tt <= max_threads) {
             spt = cand;
@@ -738,7 +738,7 @@ PersistentPlan persistent_plan(const DevMesh &m, int blocks_per_sm)
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
     // the cached variant indexes incidence entries and offsets with 16 bits
-    int cached = (spt <= 4 && L.total_cached <= budget && m.max_patch_csr < 65536 && m.max_patch_slots < 16384) ? 1 : 0;
+    int cached = (spt <= 4 && L.total_cached <= budget && m.csr < 65536 && m.slots < 16384) ? 1 : 0;
     const size_t smem = cached ? L.total_cached : L.total_plain;
     if (smem > budget) return plan;
     // every variant the plan may launch must reach blocks_per_sm resident blocks
@@ -772,7 +772,7 @@ cudaError_t persistent_prepare(const PersistentPlan &plan)
 
 namespace {
 
-PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity)
+PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity, const PatchMax &mx)
 {
     PArgs P;
     P.patch_slot = m.patch_slot;
@@ -805,7 +805,7 @@ PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, 
     P.a = a;
     P.M = M;
     P.npatch = m.npatch;
-    const SmemLayout L = smem_layout(m);
+    const SmemLayout L = smem_layout(mx);
     P.off_flux = L.off_flux;
     P.off_g = L.off_g;
     P.off_c = L.off_c;
@@ -821,16 +821,23 @@ PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, 
     return P;
 }
 
-// One cooperative launch per pack; all packs of a step use the same elevation parity,
-// and each pack has its own tag base (the exchange buffers need no clearing).
-cudaError_t launch_packs(void *fn, PArgs P, const DevMesh &m, const PersistentPlan &plan, cudaStream_t stream)
+// One cooperative launch per pack, with the pack's own plan and shared-memory layout;
+// all packs of a step use the same elevation parity, and each pack has its own tag base
+// (the exchange buffers need no clearing).
+template <class Kernel>
+cudaError_t launch_packs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                         const std::vector<PackPlan> &packs, bool sesm, Kernel kernel, cudaStream_t stream)
 {
-    for (size_t k = 0; k + 1 < m.pack_off.size(); k++) {
-        P.pack_base = m.pack_off[k];
+    for (size_t k = 0; k < packs.size(); k++) {
+        const PackPlan &pk = packs[k];
+        const PersistentPlan &plan = sesm ? pk.plan_sesm : pk.plan;
+        void *fn = kernel(plan);
+        if (!fn) return cudaErrorInvalidValue;
+        PArgs P = make_pargs(m, s, a, M, parity, pk.mx);
+        P.pack_base = pk.base;
         P.pack_index = (int)k;
-        const int nblocks = m.pack_off[k + 1] - m.pack_off[k];
         void *args[] = {&P};
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(nblocks), dim3(plan.threads), args, plan.smem, stream);
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(plan.threads), args, plan.smem, stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -839,15 +846,17 @@ cudaError_t launch_packs(void *fn, PArgs P, const DevMesh &m, const PersistentPl
 }  // namespace
 
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                              const PersistentPlan &plan, cudaStream_t stream)
+                              const std::vector<PackPlan> &packs, cudaStream_t stream)
 {
-    void *fn = persistent_kernel(plan.slots_per_thread, a.nonlinear_h, plan.cached,
-                                  s.W != nullptr || s.eta_sum != nullptr);
-    if (!fn) return cudaErrorInvalidValue;
-    return launch_packs(fn, make_pargs(m, s, a, M, parity), m, plan, stream);
+    const int extra = s.W != nullptr || s.eta_sum != nullptr;
+    return launch_packs(m, s, a, M, parity, packs, false,
+                        [&](const PersistentPlan &p) {
+                            return persistent_kernel(p.slots_per_thread, a.nonlinear_h, p.cached, extra);
+                        },
+                        stream);
 }
 
-PersistentPlan persistent_plan_sesm(const DevMesh &m, int blocks_per_sm)
+PersistentPlan persistent_plan_sesm(const PatchMax &m, int blocks_per_sm)
 {
     PersistentPlan plan;
     int dev = 0, smem_optin = 0, smem_sm = 0;
@@ -862,7 +871,7 @@ PersistentPlan persistent_plan_sesm(const DevMesh &m, int blocks_per_sm)
     // largest patch, whose own vertices must then fit kSesmVpt per thread
     int spt = 0, t = 0;
     for (int cand = 1; cand <= 4; cand++) {
-        const int need = (m.max_patch_slots + cand - 1) / cand;
+        const int need = (m.slots + cand - 1) / cand;
         const int tt = std::max(32, ((need + 31) / 32) * 32);
         if (tt <= kSesmThreads) {
             spt = cand;
@@ -870,13 +879,13 @@ PersistentPlan persistent_plan_sesm(const DevMesh &m, int blocks_per_sm)
             break;
         }
     }
-    if (!spt || m.max_patch_vertices > kSesmVpt * t) return plan;
+    if (!spt || m.vertices > kSesmVpt * t) return plan;
     const SmemLayout L = smem_layout(m);
     size_t budget = (size_t)smem_optin - 1024;
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
-    if (L.total_cached > budget || m.max_patch_csr >= 65536 || m.max_patch_slots >= 16384) return plan;
+    if (L.total_cached > budget || m.csr >= 65536 || m.slots >= 16384) return plan;
     for (int nonlin = 0; nonlin < 2; nonlin++) {
         void *fn = sesm_kernel(spt, nonlin);
         int occ = 0;
@@ -905,11 +914,11 @@ cudaError_t persistent_prepare_sesm(const PersistentPlan &plan)
 }
 
 cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                                   const PersistentPlan &plan, cudaStream_t stream)
+                                   const std::vector<PackPlan> &packs, cudaStream_t stream)
 {
-    void *fn = sesm_kernel(plan.slots_per_thread, a.nonlinear_h);
-    if (!fn) return cudaErrorInvalidValue;
-    return launch_packs(fn, make_pargs(m, s, a, M, parity), m, plan, stream);
+    return launch_packs(m, s, a, M, parity, packs, true,
+                        [&](const PersistentPlan &p) { return sesm_kernel(p.slots_per_thread, a.nonlinear_h); },
+                        stream);
 }
 
 }  // namespace sesw

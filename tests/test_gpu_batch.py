@@ -78,7 +78,7 @@ def test_batch_matches_oracle_per_basin(S, mode):
 
 def test_batch_persistent_packs(S):
     """More patches than resident blocks: the batch runs as several cooperative launches per step."""
-    cases = I.ensemble_cases(nbasins=14, scale=0.04, seed=11, nsteps=2)
+    cases = I.ensemble_cases(nbasins=14, scale=0.2, seed=11, nsteps=2)   # ~276k vertices: two packs
     (eta, U, Um), info, _ = _run_batch(S, cases, PERSISTENT, 2)
     assert info["mode"] == PERSISTENT and info["npack"] > 1, info
     for c, e, u, um in zip(cases, _split(cases, eta, "v"), _split(cases, U, "e"), _split(cases, Um, "e")):
@@ -100,3 +100,43 @@ def test_batch_parameter_rules(S):
         unstable[2] = I.Params(g=p.g, theta=p.theta, tau=p.tau * 8, M=p.M)
         with pytest.raises(S.SeswError, match="basin 2"):
             s.sesw_set_params_batch(unstable)
+
+
+@pytest.fixture(scope="module")
+def full_ensemble():
+    """The batched configuration at full size (64 basins, log-uniform 2e4-4e5 vertices, 8.6 M in
+    total; the benchmark's seed) with its FP64 and FP32 oracle results after 3 steps."""
+    cases = I.ensemble_cases(nbasins=64, scale=1.0, seed=20231118, nsteps=3)
+    ref = [orc.run_case(c, nsteps=3) for c in cases]
+    r32 = [orc.run_case(c, nsteps=3, L=orc.lib_fp32()) for c in cases]
+    return cases, ref, r32
+
+
+@pytest.mark.parametrize("bps", [2, 4])
+def test_full_size_ensemble_matches_oracle(S, full_ensemble, bps):
+    """Every basin of the full-size ensemble, advanced as one batch in persistent packs (the layouts
+    the benchmark's autotuner chooses among), against the oracle: within twice the FP32 oracle's
+    drift plus 8 ulp, and |eta error| <= 1e-5 m."""
+    from parity_util import ENVELOPE_FACTOR, ETA_ABS_TOL, ULP_FLOOR, _maxabs
+
+    cases, ref, r32 = full_ensemble
+    with S.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_set_blocks_per_sm(bps)
+        s.sesw_mesh_upload_batch([c.mesh for c in cases])
+        s.sesw_set_params_batch([c.params for c in cases])
+        s.sesw_set_forcing(np.concatenate([c.R for c in cases]))
+        s.sesw_set_state(np.concatenate([c.eta0 for c in cases]), np.concatenate([c.U0 for c in cases]))
+        s.sesw_advance(3)
+        info = s.sesw_get_info()
+        eta, U, Um = s.sesw_get_state()
+    assert info["mode"] == PERSISTENT and info["nbasin"] == 64 and info["npack"] > 1, info
+    worst = 0.0
+    for b, (c, e, u, um) in enumerate(zip(cases, _split(cases, eta, "v"), _split(cases, U, "e"),
+                                          _split(cases, Um, "e"))):
+        for k, got in enumerate((e, u, um)):
+            err = _maxabs(got - ref[b][k])
+            tol = ENVELOPE_FACTOR * _maxabs(r32[b][k] - ref[b][k]) + ULP_FLOOR * _maxabs(ref[b][k])
+            assert err <= tol, f"basin {b} ({c.mesh.nv} vertices) field {k}: {err:.3e} > {tol:.3e}"
+        worst = max(worst, _maxabs(e - ref[b][0]))
+    assert worst <= ETA_ABS_TOL

@@ -148,7 +148,7 @@ def test_sesm_rules(S):
 def test_sesm_persistent_batch_in_packs(S):
     """A batch of basins with the SESM scheme in persistent mode, more patches than resident blocks
     (several cooperative launches per step, each with its own tag base), matches the oracle per basin."""
-    cases = I.ensemble_cases(nbasins=14, scale=0.04, seed=11, nsteps=2)
+    cases = I.ensemble_cases(nbasins=14, scale=0.2, seed=11, nsteps=2)   # ~276k vertices: two packs
     coefs = [_sesm(c) for c in cases]
     with S.Subcycle() as s:
         s.sesw_set_mode(PERSISTENT)
