@@ -121,15 +121,16 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-KERNEL_SOURCE = {"k_persistent": "sesw_persistent.cu", "k_persistent_sesm": "sesw_persistent.cu"}
+KERNEL_SOURCE = {"k_persistent": ("sesw_persistent.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
+                 "k_persistent_sesm": ("sesw_persistent_sesm.cu", "sesw_persistent.cuh", "sesw_device.cuh")}
 
 
 def kernel_source_hash(kernel="k_persistent"):
-    """Hash of the source file that holds `kernel` (its profile is stale once this changes)."""
+    """Hash of the source files of `kernel` (its profile is stale once one of them changes)."""
     h = hashlib.sha256()
-    name = KERNEL_SOURCE.get(kernel, "sesw_kernels.cu")
-    with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", name), "rb") as fh:
-        h.update(fh.read())
+    for name in KERNEL_SOURCE.get(kernel, ("sesw_kernels.cu",)):
+        with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 

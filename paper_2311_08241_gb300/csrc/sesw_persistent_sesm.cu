@@ -1,0 +1,299 @@
+// The SESM step kernel of libsesw (sm_103a): one cooperative launch runs a baroclinic
+// step of the AB3-AM4 substep of Eqs. (4.7)-(4.8), with the time-mean transport of Eq.
+// (4.12) and the freshwater flux of Eq. (4.5).
+#include "sesw_persistent.cuh"
+
+namespace sesw {
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// The SESM substep (AB3-AM4, Eqs. 4.7-4.8) in the persistent form: one launch runs the
+// M + 1 element passes and M vertex passes of a baroclinic step. Substep m (m >= 1)
+// completes the momentum update
+//     U^m = U^{m-1} + dt ( -f e_z x U_AB^{m-1} - g H_AM grad(eta_AM^m) + R ),
+//     eta_AM^m = am0 eta^m + am1 eta^{m-1} + am2 eta^{m-2} + am3 eta^{m-3},
+// then (m < M) forms U_AB^m = ab0 U^m + ab1 U^{m-1} + ab2 U^{m-2}, adds it to the
+// compensated sum and updates eta^{m+1} = eta^m - dt (div(U_AB^m) + W). Levels before the
+// start of the subcycle are level 0. A slot keeps U^{m-1}, U^{m-2}, U_AB^{m-1} and its sum
+// in registers; a vertex keeps eta^m, eta^{m-1}, eta^{m-2} in the registers of the thread
+// that updates it. The element pass needs only eta_AM at the corners, so the owner of a
+// vertex forms eta_AM^{m+1} right after eta^{m+1} and exchanges that one value, with the
+// same tagged words as the SE kernel (tag base + m for substep m, m = 1 .. M).
+constexpr int kSesmThreads = 384;   // registers: 65536 / (2 x 384) = 85 per thread
+constexpr int kSesmVpt = 2;         // own vertices per thread at most
+
+template <int SPT, int NONLIN>
+__global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    const int p = P.pack_patch[P.pack_base + blockIdx.x];
+    const int T = blockDim.x;
+    const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
+    const int nown_s = P.patch_own[p], nint = P.patch_int[p];
+    const int v0 = P.patch_v[p], nown = P.patch_v[p + 1] - v0;
+    const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
+    const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
+    const StepArgs a = P.a;
+    const float dt = P.patch_dt[p];
+    unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
+    unsigned *exit_count = base_word + kFlagStride;
+    const unsigned base = ld_relaxed_gpu(base_word);
+    const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
+
+    float *sem = reinterpret_cast<float *>(smem_raw);   // eta_AM of the own vertices
+    float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
+    float4 *s_g = reinterpret_cast<float4 *>(smem_raw + P.off_g);
+    float4 *s_c = reinterpret_cast<float4 *>(smem_raw + P.off_c);
+    float2 *s_r = reinterpret_cast<float2 *>(smem_raw + P.off_r);
+    ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + P.off_l);
+    unsigned short *s_off = reinterpret_cast<unsigned short *>(smem_raw + P.off_off);
+    unsigned short *s_csr = reinterpret_cast<unsigned short *>(smem_raw + P.off_csr);
+    float *s_inv = reinterpret_cast<float *>(smem_raw + P.off_inv);
+    int *s_halo = reinterpret_cast<int *>(smem_raw + P.off_halo);
+
+    for (int i = threadIdx.x; i < ns; i += T) {
+        s_g[i] = P.sg[s0 + i];
+        s_c[i] = P.sc[s0 + i];
+        s_r[i] = P.R[s0 + i];
+        s_l[i] = P.sl[s0 + i];
+    }
+    for (int i = threadIdx.x; i <= nown; i += T) s_off[i] = (unsigned short)(P.vcsr_off[v0 + i] - c0);
+    for (int k = threadIdx.x; k < ncsr; k += T) {
+        const uint32_t q = P.vcsr[c0 + k];
+        s_csr[k] = (unsigned short)(3u * (q >> 2) + (q & 3u));
+    }
+    for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
+    for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
+    if (threadIdx.x == 0) s_abort = 0;
+    // slot state: U^{m-1}, U^{m-2}, U_AB^{m-1}, compensated sum; vertex state: eta^m,
+    // eta^{m-1}, eta^{m-2}
+    float2 u1[SPT], u2[SPT], uab[SPT], shi[SPT], slo[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; j++) {
+        const int i = threadIdx.x + j * T;
+        u1[j] = i < ns ? P.U[s0 + i] : make_float2(0.0f, 0.0f);
+        u2[j] = u1[j];
+        uab[j] = make_float2(0.0f, 0.0f);
+        shi[j] = make_float2(0.0f, 0.0f);
+        slo[j] = make_float2(0.0f, 0.0f);
+    }
+    float eh0[kSesmVpt], eh1[kSesmVpt], eh2[kSesmVpt];
+#pragma unroll
+    for (int k = 0; k < kSesmVpt; k++) {
+        const int i = threadIdx.x + k * T;
+        eh0[k] = i < nown ? P.eta_in[v0 + i] : 0.0f;
+        eh1[k] = eh0[k];
+        eh2[k] = eh0[k];
+    }
+    __syncthreads();
+
+    // U_AB of a slot, its flux contributions and (owned slots) the compensated sum
+    auto transport = [&](int j, int i, float2 u0, float2 ua, float2 ub, float4 g, float area) {
+        const float fx = a.ab0 * u0.x + a.ab1 * ua.x + a.ab2 * ub.x;
+        const float fy = a.ab0 * u0.y + a.ab1 * ua.y + a.ab2 * ub.y;
+        if (i < nown_s) {
+            two_sum_acc(shi[j].x, slo[j].x, fx);
+            two_sum_acc(shi[j].y, slo[j].y, fy);
+        }
+        const float w = dt * area;
+        const float q0 = w * (fx * g.x + fy * g.y);
+        const float q1 = w * (fx * g.z + fy * g.w);
+        sflux[3 * i + 0] = q0;
+        sflux[3 * i + 1] = q1;
+        sflux[3 * i + 2] = -(q0 + q1);
+        uab[j] = make_float2(fx, fy);
+    };
+    // element pass of substep m >= 1 over the slots [lo, hi); corner eta_AM of own
+    // vertices from shared memory, of halo vertices (with `xs` set) from the exchange
+    bool ok = true;
+    auto elements = [&](int lo, int hi, const unsigned long long *xs, unsigned tag, bool vertex) {
+#pragma unroll
+        for (int j = 0; j < SPT; j++) {
+            const int i = threadIdx.x + j * T;
+            if (i >= lo && i < hi) {
+                const float4 g = s_g[i], c = s_c[i];
+                const float2 r = s_r[i];
+                const ushort4 l = s_l[i];
+                float e0, e1, e2;
+                if (xs) {
+                    const int h0 = l.x < nown ? -1 : s_halo[l.x - nown], h1 = l.y < nown ? -1 : s_halo[l.y - nown],
+                              h2 = l.z < nown ? -1 : s_halo[l.z - nown];
+                    const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
+                    const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
+                    const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
+                    e0 = h0 < 0 ? sem[l.x] : halo_eta(P, xs, h0, w0, tag, abort_val, ok);
+                    e1 = h1 < 0 ? sem[l.y] : halo_eta(P, xs, h1, w1, tag, abort_val, ok);
+                    e2 = h2 < 0 ? sem[l.z] : halo_eta(P, xs, h2, w2, tag, abort_val, ok);
+                } else {
+                    e0 = sem[l.x];
+                    e1 = sem[l.y];
+                    e2 = sem[l.z];
+                }
+                const float d0 = e0 - e2, d1 = e1 - e2;
+                const float gx = d0 * g.x + d1 * g.z;
+                const float gy = d0 * g.y + d1 * g.w;
+                float H = c.y;
+                if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
+                const float gH = a.g * H;
+                // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
+                float2 u0;
+                u0.x = u1[j].x + dt * (c.z * uab[j].y - gH * gx + r.x);
+                u0.y = u1[j].y + dt * (-c.z * uab[j].x - gH * gy + r.y);
+                if (vertex) transport(j, i, u0, u1[j], u2[j], g, c.x);
+                u2[j] = u1[j];
+                u1[j] = u0;
+            }
+        }
+    };
+
+    const int npre = nint >= T ? (nint / T) * T : nint;
+    for (int m = 0; m <= P.M; m++) {
+        const bool vertex = m < P.M;
+        if (m == 0) {
+            // no momentum update: U_AB^0 from level 0 and its aliases
+#pragma unroll
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (i < ns) transport(j, i, u1[j], u1[j], u1[j], s_g[i], s_c[i].x);
+            }
+        } else {
+            const unsigned tag = base + (unsigned)m;
+            elements(0, npre, nullptr, 0u, vertex);
+            elements(npre, ns, P.xb[m & 1], tag, vertex);
+            if (!ok) s_abort = 1;
+        }
+        if (!vertex) break;
+        __syncthreads();
+        if (s_abort) break;
+
+        // vertex pass: eta^{m+1}, then eta_AM^{m+1} for the own slots and the neighbours
+        unsigned long long *xout = P.xb[(m + 1) & 1];
+        const unsigned long long tag_out = (unsigned long long)(base + (unsigned)(m + 1)) << 32;
+        const bool publish = p != a.silent_patch;
+        bool bad = false;
+#pragma unroll
+        for (int k = 0; k < kSesmVpt; k++) {
+            const int i = threadIdx.x + k * T;
+            if (i < nown) {
+                float sum = 0.0f;
+                const int k1 = s_off[i + 1];
+                for (int q = s_off[i]; q < k1; q++) sum += sflux[s_csr[q]];
+                float e = eh0[k] + sum * s_inv[i];
+                if (P.W) e -= dt * __ldg(P.W + v0 + i);
+                const float em = a.am0 * e + a.am1 * eh0[k] + a.am2 * eh1[k] + a.am3 * eh2[k];
+                eh2[k] = eh1[k];
+                eh1[k] = eh0[k];
+                eh0[k] = e;
+                sem[i] = em;
+                if (publish) st_relaxed_gpu_u64(xout + v0 + i, tag_out | __float_as_uint(em));
+                bad |= !(fabsf(e) <= a.eta_bound);
+            }
+        }
+        if (bad) atomicOr(P.status, 1u);
+        __syncthreads();
+    }
+    __syncthreads();
+
+#pragma unroll
+    for (int k = 0; k < kSesmVpt; k++) {
+        const int i = threadIdx.x + k * T;
+        if (i < nown) P.eta_out[v0 + i] = eh0[k];
+    }
+#pragma unroll
+    for (int j = 0; j < SPT; j++) {
+        const int i = threadIdx.x + j * T;
+        if (i < ns) {
+            P.U[s0 + i] = u1[j];
+            if (i < nown_s) {
+                const int w = P.sv[s0 + i].w;
+                P.Umean[w] = make_float2((shi[j].x + slo[j].x) * a.inv_M, (shi[j].y + slo[j].y) * a.inv_M);
+            }
+        }
+    }
+    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == gridDim.x - 1) {
+        *exit_count = 0u;
+        *base_word = base + (unsigned)P.M + 1u;
+    }
+}
+
+void *sesm_kernel(int spt, int nonlin)
+{
+    switch (spt) {
+    case 1: return nonlin ? (void *)k_persistent_sesm<1, 1> : (void *)k_persistent_sesm<1, 0>;
+    case 2: return nonlin ? (void *)k_persistent_sesm<2, 1> : (void *)k_persistent_sesm<2, 0>;
+    case 3: return nonlin ? (void *)k_persistent_sesm<3, 1> : (void *)k_persistent_sesm<3, 0>;
+    case 4: return nonlin ? (void *)k_persistent_sesm<4, 1> : (void *)k_persistent_sesm<4, 0>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace
+
+PersistentPlan persistent_plan_sesm(const PatchMax &m, int blocks_per_sm)
+{
+    PersistentPlan plan;
+    int dev = 0, smem_optin = 0, smem_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return plan;
+    }
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    // fewest slots per thread such that one block of at most kSesmThreads covers the
+    // largest patch, whose own vertices must then fit kSesmVpt per thread
+    int spt = 0, t = 0;
+    for (int cand = 1; cand <= 4; cand++) {
+        const int need = (m.slots + cand - 1) / cand;
+        const int tt = std::max(32, ((need + 31) / 32) * 32);
+        if (tt <= kSesmThreads) {
+            spt = cand;
+            t = tt;
+            break;
+        }
+    }
+    if (!spt || m.vertices > kSesmVpt * t) return plan;
+    const SmemLayout L = smem_layout(m);
+    size_t budget = (size_t)smem_optin - 1024;
+    const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
+    if (share < 2048) return plan;
+    budget = std::min(budget, share - 2048);
+    if (L.total_cached > budget || m.csr >= 65536 || m.slots >= 16384) return plan;
+    for (int nonlin = 0; nonlin < 2; nonlin++) {
+        void *fn = sesm_kernel(spt, nonlin);
+        int occ = 0;
+        if (!fn || raise_smem_limit(fn) < (int)L.total_cached ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, L.total_cached) != cudaSuccess ||
+            occ < blocks_per_sm) {
+            cudaGetLastError();
+            return plan;
+        }
+    }
+    plan.slots_per_thread = spt;
+    plan.threads = t;
+    plan.cached = 1;
+    plan.blocks_per_sm = blocks_per_sm;
+    plan.smem = L.total_cached;
+    return plan;
+}
+
+cudaError_t persistent_prepare_sesm(const PersistentPlan &plan)
+{
+    for (int nonlin = 0; nonlin < 2; nonlin++) {
+        void *fn = sesm_kernel(plan.slots_per_thread, nonlin);
+        if (!fn || raise_smem_limit(fn) < (int)plan.smem) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                                   const std::vector<PackPlan> &packs, cudaStream_t stream)
+{
+    return launch_packs(m, s, a, M, parity, packs, true,
+                        [&](const PersistentPlan &p) { return sesm_kernel(p.slots_per_thread, a.nonlinear_h); },
+                        stream);
+}
+
+}  // namespace sesw
