@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--freshwater", type=float, default=0.0, metavar="AMP",
                     help="freshwater flux W of Eq. (4.5): seeded random field of this amplitude (m/s)")
     ap.add_argument("--patch-vertices", type=int, default=None,
-                    help="graph-mode patch size (default 256; with --visc, one wave of the fused substep kernel)")
+                    help="graph-mode patch size (default 256; with --visc, one wave of the fused kernel)")
     ap.add_argument("--block-threads", type=int, default=256)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=400)
@@ -122,8 +122,7 @@ def measured_hbm_peak():
 
 
 KERNEL_SOURCE = {"k_persistent": ("sesw_persistent.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
-                 "k_persistent_sesm": ("sesw_persistent_sesm.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
-                 "k_persistent_visc": ("sesw_persistent_visc.cu", "sesw_persistent.cuh", "sesw_device.cuh")}
+                 "k_persistent_sesm": ("sesw_persistent_sesm.cu", "sesw_persistent.cuh", "sesw_device.cuh")}
 
 
 def kernel_source_hash(kernel="k_persistent"):
@@ -541,6 +540,7 @@ def run_ours(args, world, rank, local):
             visc = tuple(float(x) for x in args.visc.split(","))
         case.params = I.Params(g=p.g, theta=p.theta, tau=p.tau, M=p.M, nonlinear_h=p.nonlinear_h,
                                scheme=p.scheme, visc=visc)
+        args.mode = "graph"
         desc = dict(desc, viscosity=f"A = {visc[0]:.4g} m^2/s + {visc[1]:g} |du| L (Eq. viscosity_BT)")
     V, E, M = case.mesh.nv, case.mesh.ne, case.params.M
     stream = torch.cuda.current_stream(dev)
@@ -603,9 +603,8 @@ def run_ours(args, world, rank, local):
     # k_substep launches per step, each B_alg (the step's short epilogue launch is
     # included in the event time, which understates the kernel's rate).
     # SESM: the same with its own byte count per substep (persistent: one k_persistent_sesm
-    # launch per step; graph: M + 1 k_sesm launches). Viscosity: the bytes it adds per
-    # substep (persistent: one k_persistent_visc launch per step; graph: fused into the
-    # substep kernel).
+    # launch per step; graph: M + 1 k_sesm launches). Viscosity (graph): fused into the
+    # substep kernel, rated per substep with the bytes it adds.
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
     if args.scheme == "sesm":
         b_alg = sesm_bytes_per_substep(V, E)
@@ -623,7 +622,7 @@ def run_ours(args, world, rank, local):
     else:
         kname = "k_persistent" if persistent else "k_substep"
     if args.visc:
-        kname = "k_persistent_visc" if persistent else "k_substep (viscosity fused)"
+        kname = "k_substep (viscosity fused)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(kname), "peak_source": peak_src, "kernel": kname,
                 "bytes_per_launch": per_launch}

@@ -110,26 +110,6 @@ int zalloc(sesw_ctx *c, T **dst, size_t n, const char *name)
         if (r_ != SESW_OK) return r_; \
     } while (0)
 
-// The persistent launches of one step: the kernel of the scheme, or of the viscosity.
-static cudaError_t persistent_step(sesw_ctx *c, int parity, cudaStream_t st)
-{
-    if (c->params.scheme == 1)
-        return sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, parity, c->packs, st);
-    if (c->visc_on)
-        return sesw::launch_persistent_visc(c->dm, c->ds, c->args, c->vargs, c->ds.visc_ring, c->params.M, parity,
-                                            c->packs, st);
-    return sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->packs, st);
-}
-
-// Every pack of the layout has a plan for the persistent viscosity kernel.
-static bool visc_persistent_ok(const sesw_ctx *c)
-{
-    if (c->packs.empty()) return false;
-    for (const auto &pk : c->packs)
-        if (pk.plan_visc.slots_per_thread == 0) return false;
-    return true;
-}
-
 int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
 {
     cudaGraph_t g = nullptr;
@@ -138,7 +118,9 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     if (c->ds.eta_sum) e = cudaMemsetAsync(c->ds.eta_sum, 0, sizeof(float) * (size_t)c->dm.nv, c->cap_stream);
     if (e != cudaSuccess) {
     } else if (c->mode == SESW_MODE_PERSISTENT) {
-        e = persistent_step(c, parity, c->cap_stream);
+        e = c->params.scheme == 1
+                ? sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, parity, c->packs, c->cap_stream)
+                : sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->packs, c->cap_stream);
     } else if (c->params.scheme == 1) {
         // SESM: level rings, U^m in B[m % 3] (B[0] holds U^0 and, at the end, U^M) and
         // eta^m in Er[m % 5] (Er[0] holds eta^0 and, at the end, eta^M); levels before
@@ -213,7 +195,10 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
 int enqueue_step(sesw_ctx *c)
 {
     if (c->mode == SESW_MODE_PERSISTENT && !c->persist_graph_ok) {
-        CK(c, persistent_step(c, c->parity, c->stream));
+        if (c->params.scheme == 1)
+            CK(c, sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, c->parity, c->packs, c->stream));
+        else
+            CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->packs, c->stream));
         c->parity ^= 1;
         return SESW_OK;
     }
@@ -449,7 +434,6 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
             }
             pk.plan.blocks_per_sm = bps;
             pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, bps);
-            pk.plan_visc = sesw::persistent_plan_visc(pk.mx, bps);
             packs.push_back(pk);
             pack_basins.push_back(bn);
         }
@@ -606,7 +590,6 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         for (const auto &pk : packs) {
             CK(c, sesw::persistent_prepare(pk.plan));
             if (plan_sesm.slots_per_thread > 0) CK(c, sesw::persistent_prepare_sesm(pk.plan_sesm));
-            if (pk.plan_visc.slots_per_thread > 0) CK(c, sesw::persistent_prepare_visc(pk.plan_visc));
         }
     } else {
         TRY(zalloc(c, &s.eta_x[0], hm.nv, "eta_x"));
@@ -614,9 +597,6 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.eta_x[2], hm.nv, "eta_x"));
         TRY(zalloc(c, &s.U_x[0], hm.nslot, "U_x"));
         TRY(zalloc(c, &s.U_x[1], hm.nslot, "U_x"));
-        CK(c, sesw::substep_smem_attr(d));
-    }
-    {
         // viscosity tables per slot: neighbours as owner slots, their corners opposite
         // the shared edges and rest depths, and the edge geometry
         std::vector<int> eslot(hm.ne, -1);
@@ -660,6 +640,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
             TRY(upload(c, &d.visc_r2, tr2, "visc_r2"));
         }
         d.visc_rot = hm.visc_rot ? 1 : 0;
+        CK(c, sesw::substep_smem_attr(d));
     }
     CK(c, cudaStreamSynchronize(c->stream));
 
@@ -750,9 +731,8 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
         const bool visc = q.visc_background > 0.0 || q.visc_flow > 0.0;
         if (visc && q.scheme != 0)
             return fail(c, SESW_EINVAL, "the barotropic viscosity is available with the SE scheme (scheme 0)");
-        if (visc && c->mode == SESW_MODE_PERSISTENT && !visc_persistent_ok(c))
-            return fail(c, SESW_EINVAL, "the patches of this mesh do not fit the persistent viscosity kernel; set "
-                                        "SESW_MODE_GRAPH before the upload");
+        if (visc && c->mode == SESW_MODE_PERSISTENT)
+            return fail(c, SESW_EINVAL, "the barotropic viscosity runs in SESW_MODE_GRAPH; set the mode before the upload");
         if (q.g != p->g || q.theta != p->theta || q.M != p->M || q.nonlinear_h != p->nonlinear_h ||
             q.flags != p->flags || q.eta_bound != p->eta_bound || q.scheme != p->scheme ||
             q.sesm_beta != p->sesm_beta || q.sesm_delta != p->sesm_delta || q.sesm_gamma != p->sesm_gamma ||
@@ -786,8 +766,6 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
     }
     const bool visc_on = p->visc_background > 0.0 || p->visc_flow > 0.0;
     if (visc_on && !c->ds.V0) TRY(zalloc(c, &c->ds.V0, (size_t)c->dm.nslot, "V0"));
-    if (visc_on && c->mode == SESW_MODE_PERSISTENT && !c->ds.visc_ring)
-        TRY(zalloc(c, &c->ds.visc_ring, sesw::persistent_visc_ring_words(c->dm.nv, c->dm.nslot), "visc_ring"));
     drop_graphs(c);
     c->params = *p;
     if (!(c->params.eta_bound > 0.0)) c->params.eta_bound = 1e4;
@@ -906,6 +884,8 @@ int sesw_viscosity(sesw_ctx *c, double *out, int where)
     if (!c->have_mesh || !c->have_params) return fail(c, SESW_ESTATE, "mesh and parameters must be set first");
     if (!out) return fail(c, SESW_EINVAL, "out is NULL");
     if (where != SESW_HOST && where != SESW_DEVICE) return fail(c, SESW_EINVAL, "where must be SESW_HOST or SESW_DEVICE");
+    if (c->mode != SESW_MODE_GRAPH)
+        return fail(c, SESW_EINVAL, "the barotropic viscosity runs in SESW_MODE_GRAPH; set the mode before the upload");
     DeviceGuard dg(c->device);
     if (!c->visc_out) TRY(zalloc(c, &c->visc_out, (size_t)c->dm.ne, "visc_out"));
     CK(c, sesw::launch_viscosity(c->dm, c->ds, c->vargs, c->parity, c->visc_out, c->stream));

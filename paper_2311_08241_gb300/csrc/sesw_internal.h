@@ -168,7 +168,6 @@ struct DevState {
     float *W = nullptr;
     // barotropic viscosity (SE, graph mode): its start-of-step value per slot
     float2 *V0 = nullptr;
-    unsigned long long *visc_ring = nullptr;   // persistent viscosity: U and eta exchange rings
 };
 
 // Viscosity coefficients of one launch (Eq. viscosity_BT): A = background + flow |du| L.
@@ -251,7 +250,7 @@ struct PatchMax {
 struct PackPlan {
     int base = 0, nblocks = 0;
     PatchMax mx;
-    PersistentPlan plan, plan_sesm, plan_visc;
+    PersistentPlan plan, plan_sesm;
 };
 PersistentPlan persistent_plan(const PatchMax &mx, int blocks_per_sm);
 cudaError_t persistent_prepare(const PersistentPlan &plan);
@@ -264,15 +263,6 @@ PersistentPlan persistent_plan_sesm(const PatchMax &mx, int blocks_per_sm);
 cudaError_t persistent_prepare_sesm(const PersistentPlan &plan);
 cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                                    const std::vector<PackPlan> &packs, cudaStream_t stream);
-// The SE scheme with the barotropic viscosity in the persistent form (k_persistent_visc):
-// cached patches of at most 4 x 384 slots; the exchange rings take
-// persistent_visc_ring_words(nv, nslot) 64-bit words.
-PersistentPlan persistent_plan_visc(const PatchMax &mx, int blocks_per_sm);
-cudaError_t persistent_prepare_visc(const PersistentPlan &plan);
-size_t persistent_visc_ring_words(int nv, int nslot);
-cudaError_t launch_persistent_visc(const DevMesh &m, const DevState &s, const StepArgs &a, const ViscArgs &va,
-                                   unsigned long long *ring, int M, int parity, const std::vector<PackPlan> &packs,
-                                   cudaStream_t stream);
 
 struct Surrogate;
 void surrogate_release(sesw_ctx *c);
