@@ -19,7 +19,8 @@ namespace {
 // in registers; a vertex keeps eta^m, eta^{m-1}, eta^{m-2} in the registers of the thread
 // that updates it. The element pass needs only eta_AM at the corners, so the owner of a
 // vertex forms eta_AM^{m+1} right after eta^{m+1} and exchanges that one value, with the
-// same tagged words as the SE kernel (tag base + m for substep m, m = 1 .. M).
+// same tagged words as the SE kernel (tag base + m for substep m, m = 1 .. M). As in the SE
+// kernel, the halo words of a thread's last-round slot are requested after its first round.
 constexpr int kSesmThreads = 384;   // registers: 65536 / (2 x 384) = 85 per thread
 constexpr int kSesmVpt = 2;         // own vertices per thread at most
 
@@ -105,50 +106,31 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
         sflux[3 * i + 2] = -(q0 + q1);
         uab[j] = make_float2(fx, fy);
     };
-    // element pass of substep m >= 1 over the slots [lo, hi); corner eta_AM of own
-    // vertices from shared memory, of halo vertices (with `xs` set) from the exchange
     bool ok = true;
-    auto elements = [&](int lo, int hi, const unsigned long long *xs, unsigned tag, bool vertex) {
-#pragma unroll
-        for (int j = 0; j < SPT; j++) {
-            const int i = threadIdx.x + j * T;
-            if (i >= lo && i < hi) {
-                const float4 g = s_g[i], c = s_c[i];
-                const float2 r = s_r[i];
-                const ushort4 l = s_l[i];
-                float e0, e1, e2;
-                if (xs) {
-                    const int h0 = l.x < nown ? -1 : s_halo[l.x - nown], h1 = l.y < nown ? -1 : s_halo[l.y - nown],
-                              h2 = l.z < nown ? -1 : s_halo[l.z - nown];
-                    const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
-                    const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
-                    const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
-                    e0 = h0 < 0 ? sem[l.x] : halo_eta(P, xs, h0, w0, tag, abort_val, ok);
-                    e1 = h1 < 0 ? sem[l.y] : halo_eta(P, xs, h1, w1, tag, abort_val, ok);
-                    e2 = h2 < 0 ? sem[l.z] : halo_eta(P, xs, h2, w2, tag, abort_val, ok);
-                } else {
-                    e0 = sem[l.x];
-                    e1 = sem[l.y];
-                    e2 = sem[l.z];
-                }
-                const float d0 = e0 - e2, d1 = e1 - e2;
-                const float gx = d0 * g.x + d1 * g.z;
-                const float gy = d0 * g.y + d1 * g.w;
-                float H = c.y;
-                if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
-                const float gH = a.g * H;
-                // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
-                float2 u0;
-                u0.x = u1[j].x + dt * (c.z * uab[j].y - gH * gx + r.x);
-                u0.y = u1[j].y + dt * (-c.z * uab[j].x - gH * gy + r.y);
-                if (vertex) transport(j, i, u0, u1[j], u2[j], g, c.x);
-                u2[j] = u1[j];
-                u1[j] = u0;
-            }
-        }
+    // momentum update of slot i (round j) from its corner eta_AM
+    auto slot = [&](int j, int i, float e0, float e1, float e2, bool vertex) {
+        const float4 g = s_g[i], c = s_c[i];
+        const float2 r = s_r[i];
+        const float d0 = e0 - e2, d1 = e1 - e2;
+        const float gx = d0 * g.x + d1 * g.z;
+        const float gy = d0 * g.y + d1 * g.w;
+        float H = c.y;
+        if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
+        const float gH = a.g * H;
+        float2 u0;
+        u0.x = u1[j].x + dt * (c.z * uab[j].y - gH * gx + r.x);
+        u0.y = u1[j].y + dt * (-c.z * uab[j].x - gH * gy + r.y);
+        if (vertex) transport(j, i, u0, u1[j], u2[j], g, c.x);
+        u2[j] = u1[j];
+        u1[j] = u0;
     };
+    auto halo_of = [&](unsigned l) { return (int)l < nown ? -1 : s_halo[l - nown]; };
 
     const int npre = nint >= T ? (nint / T) * T : nint;
+    // the last round's slot, when it is not a whole-round interior one: its halo words are
+    // requested right after the first round
+    const int ilast = threadIdx.x + (SPT - 1) * T;
+    const bool early = SPT > 1 && ilast >= npre && ilast < ns;
     for (int m = 0; m <= P.M; m++) {
         const bool vertex = m < P.M;
         if (m == 0) {
@@ -160,8 +142,46 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
             }
         } else {
             const unsigned tag = base + (unsigned)m;
-            elements(0, npre, nullptr, 0u, vertex);
-            elements(npre, ns, P.xb[m & 1], tag, vertex);
+            const unsigned long long *xs = P.xb[m & 1];
+            unsigned long long q0 = 0ull, q1 = 0ull, q2 = 0ull;
+#pragma unroll
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (SPT > 1 && j == SPT - 1) {
+                    if (early) {
+                        const ushort4 l = s_l[i];
+                        const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
+                        const float e0 = h0 < 0 ? sem[l.x] : halo_eta(P, xs, h0, q0, tag, abort_val, ok);
+                        const float e1 = h1 < 0 ? sem[l.y] : halo_eta(P, xs, h1, q1, tag, abort_val, ok);
+                        const float e2 = h2 < 0 ? sem[l.z] : halo_eta(P, xs, h2, q2, tag, abort_val, ok);
+                        slot(j, i, e0, e1, e2, vertex);
+                    } else if (i < npre) {
+                        const ushort4 l = s_l[i];
+                        slot(j, i, sem[l.x], sem[l.y], sem[l.z], vertex);
+                    }
+                } else if (i < ns) {
+                    const ushort4 l = s_l[i];
+                    if (i < npre) {
+                        slot(j, i, sem[l.x], sem[l.y], sem[l.z], vertex);
+                    } else {
+                        const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
+                        const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
+                        const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
+                        const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
+                        const float e0 = h0 < 0 ? sem[l.x] : halo_eta(P, xs, h0, w0, tag, abort_val, ok);
+                        const float e1 = h1 < 0 ? sem[l.y] : halo_eta(P, xs, h1, w1, tag, abort_val, ok);
+                        const float e2 = h2 < 0 ? sem[l.z] : halo_eta(P, xs, h2, w2, tag, abort_val, ok);
+                        slot(j, i, e0, e1, e2, vertex);
+                    }
+                }
+                if (j == 0 && early) {
+                    const ushort4 l = s_l[ilast];
+                    const int h0 = halo_of(l.x), h1 = halo_of(l.y), h2 = halo_of(l.z);
+                    if (h0 >= 0) q0 = ld_relaxed_gpu_u64(xs + h0);
+                    if (h1 >= 0) q1 = ld_relaxed_gpu_u64(xs + h1);
+                    if (h2 >= 0) q2 = ld_relaxed_gpu_u64(xs + h2);
+                }
+            }
             if (!ok) s_abort = 1;
         }
         if (!vertex) break;
