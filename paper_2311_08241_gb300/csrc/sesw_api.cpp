@@ -427,6 +427,11 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                     pk.mx.csr = std::max(pk.mx.csr, hm.vcsr_off[hm.patch_v[q + 1]] - hm.vcsr_off[hm.patch_v[q]]);
                 }
             pk.plan = sesw::persistent_plan(pk.mx, bps);
+            // patches whose state does not fit on chip stream it from global memory
+            if (pk.plan.slots_per_thread == 0 || !pk.plan.cached) {
+                const sesw::PersistentPlan st = sesw::persistent_plan_stream(pk.mx, bps);
+                if (st.slots_per_thread > 0) pk.plan = st;
+            }
             if (pk.plan.slots_per_thread == 0) {
                 packs.clear();
                 pack_basins.clear();
@@ -588,7 +593,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.xbuf[1], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
         for (const auto &pk : packs) {
-            CK(c, sesw::persistent_prepare(pk.plan));
+            CK(c, pk.plan.stream ? sesw::persistent_prepare_stream(pk.plan) : sesw::persistent_prepare(pk.plan));
             if (plan_sesm.slots_per_thread > 0) CK(c, sesw::persistent_prepare_sesm(pk.plan_sesm));
         }
     } else {

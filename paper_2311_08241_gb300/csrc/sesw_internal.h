@@ -238,6 +238,7 @@ struct PersistentPlan {
     int slots_per_thread = 0;   // 0: not possible for this mesh
     int threads = 0;
     int cached = 0;             // 1: the patch's static data lives in shared memory
+    int stream = 0;             // 1: k_persistent_stream (state and static data in global memory)
     int blocks_per_sm = 1;
     size_t smem = 0;
 };
@@ -257,6 +258,12 @@ cudaError_t persistent_prepare(const PersistentPlan &plan);
 size_t persistent_flag_bytes(int npatch);
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                               const std::vector<PackPlan> &packs, cudaStream_t stream);
+// Patches too large for the on-chip state (k_persistent_stream): transport, sums and
+// static data stay in global memory; only the elevation and the fluxes are on chip.
+PersistentPlan persistent_plan_stream(const PatchMax &mx, int blocks_per_sm);
+cudaError_t persistent_prepare_stream(const PersistentPlan &plan);
+cudaError_t launch_persistent_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                                          const PackPlan &pk, int pack_index, cudaStream_t stream);
 // The SESM scheme in the persistent form (k_persistent_sesm): cached patches of at most
 // 4 x 384 slots and 2 x 384 own vertices; an empty plan when the patches do not fit.
 PersistentPlan persistent_plan_sesm(const PatchMax &mx, int blocks_per_sm);

@@ -423,11 +423,23 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
                               const std::vector<PackPlan> &packs, cudaStream_t stream)
 {
     const int extra = s.W != nullptr || s.eta_sum != nullptr;
-    return launch_packs(m, s, a, M, parity, packs, false,
-                        [&](const PersistentPlan &p) {
-                            return persistent_kernel(p.slots_per_thread, a.nonlinear_h, p.cached, extra);
-                        },
-                        stream);
+    for (size_t k = 0; k < packs.size(); k++) {
+        const PackPlan &pk = packs[k];
+        cudaError_t e;
+        if (pk.plan.stream) {
+            e = launch_persistent_stream_pack(m, s, a, M, parity, pk, (int)k, stream);
+        } else {
+            void *fn = persistent_kernel(pk.plan.slots_per_thread, a.nonlinear_h, pk.plan.cached, extra);
+            if (!fn) return cudaErrorInvalidValue;
+            PArgs P = make_pargs(m, s, a, M, parity, pk.mx);
+            P.pack_base = pk.base;
+            P.pack_index = (int)k;
+            void *args[] = {&P};
+            e = cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan.threads), args, pk.plan.smem, stream);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace sesw

@@ -1,0 +1,241 @@
+// The streaming persistent step kernel of libsesw (sm_103a), for patches too large to keep
+// their state on chip: one cooperative launch runs all M substeps of Eq. (4.10) of a
+// baroclinic step, with the time-mean transport of Eq. (4.12) and the freshwater flux of
+// Eq. (4.5), like k_persistent, but the transport, the compensated sum and the static
+// slot data stay in global memory (L2-resident across the substeps) and are read and
+// written slot by slot. Only the elevation of the patch's own and halo vertices and the
+// per-corner fluxes live in shared memory. With no per-slot registers carried between
+// substeps, a block holds any number of slots per thread without spilling, and every
+// load of a slot depends only on the slot's index, so it costs one L2 round trip.
+#include "sesw_persistent.cuh"
+
+namespace sesw {
+
+namespace {
+
+constexpr int kStreamThreads = 512;
+
+struct SArgs {
+    PArgs P;
+    float2 *Shi, *Slo;
+};
+
+// Element update of one slot (Eq. 4.10, first row, and the theta-weighted flux) from its
+// corner elevations, with everything else read from and written back to global memory.
+template <int NONLIN>
+__device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool owned, bool first, float e0, float e1,
+                                            float e2, float dt, float *sflux)
+{
+    const PArgs &P = A.P;
+    const StepArgs &a = P.a;
+    const float4 g = __ldg(P.sg + s), c = __ldg(P.sc + s);
+    const float2 r = __ldg(P.R + s);
+    float2 u = P.U[s];
+    float2 shi = make_float2(0.0f, 0.0f), slo = shi;
+    if (owned && !first) {
+        shi = A.Shi[s];
+        slo = A.Slo[s];
+    }
+    const float d0 = e0 - e2, d1 = e1 - e2;
+    const float gx = d0 * g.x + d1 * g.z;
+    const float gy = d0 * g.y + d1 * g.w;
+    float gH = a.g * c.y;
+    if (NONLIN) gH += a.g * ((e0 + e1 + e2) * (1.0f / 3.0f));
+    const float aa = c.z * (0.5f * dt);
+    const float inv = 1.0f / (1.0f + aa * aa);
+    const float rx = u.x + aa * u.y + dt * (r.x - gH * gx);
+    const float ry = u.y - aa * u.x + dt * (r.y - gH * gy);
+    const float nx = (rx + aa * ry) * inv;
+    const float ny = (ry - aa * rx) * inv;
+    const float fx = (1.0f + a.theta) * nx - a.theta * u.x;
+    const float fy = (1.0f + a.theta) * ny - a.theta * u.y;
+    P.U[s] = make_float2(nx, ny);
+    if (owned) {
+        two_sum_acc(shi.x, slo.x, fx);
+        two_sum_acc(shi.y, slo.y, fy);
+        A.Shi[s] = shi;
+        A.Slo[s] = slo;
+    }
+    const float w = dt * c.x;
+    const float q0 = w * (fx * g.x + fy * g.y);
+    const float q1 = w * (fx * g.z + fy * g.w);
+    sflux[3 * i + 0] = q0;
+    sflux[3 * i + 1] = q1;
+    sflux[3 * i + 2] = -(q0 + q1);
+}
+
+// EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set.
+template <int NONLIN, int EXTRA>
+__global__ void __launch_bounds__(kStreamThreads, 2) k_persistent_stream(SArgs A)
+{
+    const PArgs &P = A.P;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    const int p = P.pack_patch[P.pack_base + blockIdx.x];
+    const int T = blockDim.x;
+    const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
+    const int nown_s = P.patch_own[p], nint = P.patch_int[p];
+    const int v0 = P.patch_v[p], nown = P.patch_v[p + 1] - v0;
+    const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
+    const StepArgs a = P.a;
+    const float dt = P.patch_dt[p];
+    unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
+    unsigned *exit_count = base_word + kFlagStride;
+    const unsigned base = ld_relaxed_gpu(base_word);
+    const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
+
+    float *seta = reinterpret_cast<float *>(smem_raw);
+    float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
+    for (int i = threadIdx.x; i < nown; i += T) seta[i] = P.eta_in[v0 + i];
+    for (int i = threadIdx.x; i < nhalo; i += T) seta[nown + i] = P.eta_in[P.halo_v[hb + i]];
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+
+    const int *hid = P.halo_v + hb;
+    bool ok = true;
+    for (int m = 0; m < P.M; m++) {
+        const unsigned tag = base + (unsigned)m;
+        const unsigned long long *xs = P.xb[m & 1];
+        const bool first = m == 0;
+        // interior slots (all corners own vertices) first, then the others, whose halo
+        // reads may have to wait for a neighbour; every halo value is in shared memory
+        // at m = 0
+        const int nfirst = first ? ns : nint;
+#pragma unroll 2
+        for (int i = threadIdx.x; i < nfirst; i += T) {
+            const ushort4 l = __ldg(P.sl + s0 + i);
+            stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, first, seta[l.x], seta[l.y], seta[l.z], dt, sflux);
+        }
+#pragma unroll 2
+        for (int i = nfirst + threadIdx.x; i < ns; i += T) {
+            const ushort4 l = __ldg(P.sl + s0 + i);
+            const int h0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), h1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
+                      h2 = l.z < nown ? -1 : __ldg(hid + l.z - nown);
+            const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
+            const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
+            const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
+            const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, w0, tag, abort_val, ok);
+            const float e1 = h1 < 0 ? seta[l.y] : halo_eta(P, xs, h1, w1, tag, abort_val, ok);
+            const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, w2, tag, abort_val, ok);
+            stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, first, e0, e1, e2, dt, sflux);
+        }
+        if (!ok) s_abort = 1;
+        __syncthreads();
+        if (s_abort) break;
+
+        // vertex pass; the new elevation of own vertices also goes to the exchange buffer
+        const bool more = m + 1 < P.M;
+        unsigned long long *xout = P.xb[(m + 1) & 1];
+        const unsigned long long tag_out = (unsigned long long)(tag + 1u) << 32;
+        const bool publish = more && p != a.silent_patch;
+        bool bad = false;
+        for (int i = threadIdx.x; i < nown; i += T) {
+            float sum = 0.0f;
+            const int k1 = __ldg(P.vcsr_off + v0 + i + 1);
+            for (int k = __ldg(P.vcsr_off + v0 + i); k < k1; k++) {
+                const uint32_t q = __ldg(P.vcsr + k);
+                sum += sflux[3 * (q >> 2) + (q & 3u)];
+            }
+            float e = seta[i] + sum * __ldg(P.inv_av + v0 + i);
+            if (EXTRA) {
+                if (P.W) e -= dt * __ldg(P.W + v0 + i);
+                if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
+            }
+            seta[i] = e;
+            if (publish) st_relaxed_gpu_u64(xout + v0 + i, tag_out | __float_as_uint(e));
+            bad |= !(fabsf(e) <= a.eta_bound);
+        }
+        if (bad) atomicOr(P.status, 1u);
+        __syncthreads();
+        if (!more) break;
+    }
+    __syncthreads();
+
+    for (int i = threadIdx.x; i < nown; i += T) P.eta_out[v0 + i] = seta[i];
+    for (int i = threadIdx.x; i < nown_s; i += T) {
+        const int s = s0 + i;
+        const int w = P.sv[s].w;
+        const float2 hi = A.Shi[s], lo = A.Slo[s];
+        P.Umean[w] = make_float2((hi.x + lo.x) * a.inv_M, (hi.y + lo.y) * a.inv_M);
+    }
+    // the last block of the pack to leave (every block has read the base by then) sets
+    // the next launch's base
+    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == gridDim.x - 1) {
+        *exit_count = 0u;
+        *base_word = base + (unsigned)P.M + 1u;
+    }
+}
+
+void *stream_kernel(int nonlin, int extra)
+{
+    if (extra) return nonlin ? (void *)k_persistent_stream<1, 1> : (void *)k_persistent_stream<0, 1>;
+    return nonlin ? (void *)k_persistent_stream<1, 0> : (void *)k_persistent_stream<0, 0>;
+}
+
+}  // namespace
+
+PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm)
+{
+    PersistentPlan plan;
+    int dev = 0, smem_optin = 0, smem_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return plan;
+    }
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    // as many threads as the residency allows, but no more than the largest patch has slots
+    const int t = std::min(std::min(kStreamThreads, 1024 / blocks_per_sm), std::max(32, ((m.slots + 31) / 32) * 32));
+    const SmemLayout L = smem_layout(m);
+    size_t budget = (size_t)smem_optin - 1024;
+    const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
+    if (share < 2048) return plan;
+    budget = std::min(budget, share - 2048);
+    if (L.total_plain > budget) return plan;
+    for (int nonlin = 0; nonlin < 2; nonlin++)
+        for (int extra = 0; extra < 2; extra++) {
+            void *fn = stream_kernel(nonlin, extra);
+            int occ = 0;
+            if (!fn || raise_smem_limit(fn) < (int)L.total_plain ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, L.total_plain) != cudaSuccess ||
+                occ < blocks_per_sm) {
+                cudaGetLastError();
+                return plan;
+            }
+        }
+    plan.slots_per_thread = (m.slots + t - 1) / t;   // rounds of the slot loop (not registers)
+    plan.threads = t;
+    plan.cached = 0;
+    plan.stream = 1;
+    plan.blocks_per_sm = blocks_per_sm;
+    plan.smem = L.total_plain;
+    return plan;
+}
+
+cudaError_t persistent_prepare_stream(const PersistentPlan &plan)
+{
+    for (int nonlin = 0; nonlin < 2; nonlin++)
+        for (int extra = 0; extra < 2; extra++) {
+            void *fn = stream_kernel(nonlin, extra);
+            if (!fn || raise_smem_limit(fn) < (int)plan.smem) return cudaErrorInvalidValue;
+        }
+    return cudaSuccess;
+}
+
+cudaError_t launch_persistent_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                                          const PackPlan &pk, int pack_index, cudaStream_t stream)
+{
+    SArgs A;
+    A.P = make_pargs(m, s, a, M, parity, pk.mx);
+    A.P.pack_base = pk.base;
+    A.P.pack_index = pack_index;
+    A.Shi = s.S_hi;
+    A.Slo = s.S_lo;
+    void *fn = stream_kernel(a.nonlinear_h, s.W != nullptr || s.eta_sum != nullptr);
+    if (!fn) return cudaErrorInvalidValue;
+    void *args[] = {&A};
+    return cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan.threads), args, pk.plan.smem, stream);
+}
+
+}  // namespace sesw
