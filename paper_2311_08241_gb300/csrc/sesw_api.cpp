@@ -427,8 +427,10 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                     pk.mx.csr = std::max(pk.mx.csr, hm.vcsr_off[hm.patch_v[q + 1]] - hm.vcsr_off[hm.patch_v[q]]);
                 }
             pk.plan = sesw::persistent_plan(pk.mx, bps);
-            // patches whose state does not fit on chip stream it from global memory
-            if (pk.plan.slots_per_thread == 0 || !pk.plan.cached) {
+            // patches whose state does not fit in registers without heavy spills (8 or more
+            // slots per thread) stream it from global memory; measured on the sphere at
+            // level 8 this is faster, and with 6 slots per thread the register kernel is
+            if (pk.plan.slots_per_thread == 0 || pk.plan.slots_per_thread >= 8) {
                 const sesw::PersistentPlan st = sesw::persistent_plan_stream(pk.mx, bps);
                 if (st.slots_per_thread > 0) pk.plan = st;
             }

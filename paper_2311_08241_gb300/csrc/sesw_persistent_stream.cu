@@ -13,7 +13,7 @@ namespace sesw {
 
 namespace {
 
-constexpr int kStreamThreads = 512;
+constexpr int kStreamThreads = 1024;   // 64 registers per thread at any residency
 
 struct SArgs {
     PArgs P;
@@ -66,7 +66,7 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set.
 template <int NONLIN, int EXTRA>
-__global__ void __launch_bounds__(kStreamThreads, 2) k_persistent_stream(SArgs A)
+__global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A)
 {
     const PArgs &P = A.P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -101,12 +101,12 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_persistent_stream(SArgs A
         // reads may have to wait for a neighbour; every halo value is in shared memory
         // at m = 0
         const int nfirst = first ? ns : nint;
-#pragma unroll 2
+#pragma unroll 4
         for (int i = threadIdx.x; i < nfirst; i += T) {
             const ushort4 l = __ldg(P.sl + s0 + i);
             stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, first, seta[l.x], seta[l.y], seta[l.z], dt, sflux);
         }
-#pragma unroll 2
+#pragma unroll 4
         for (int i = nfirst + threadIdx.x; i < ns; i += T) {
             const ushort4 l = __ldg(P.sl + s0 + i);
             const int h0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), h1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
