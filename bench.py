@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-substeps", type=int, default=4,
                     help="substeps of the channel per reference-arm step (a bounded sample)")
-    ap.add_argument("--workload", choices=["channel", "ensemble", "surrogate"], default="channel",
-                    help="channel: the headline workload; ensemble: 64 basins of uneven size, batched; "
+    ap.add_argument("--workload", choices=["channel", "sphere", "ensemble", "surrogate"], default="channel",
+                    help="channel: the headline workload; sphere: the global-like level-8 sphere "
+                         "(458,683 wet vertices); ensemble: 64 basins of uneven size, batched; "
                          "surrogate: train and evaluate the learned surrogate on the sphere")
     ap.add_argument("--surrogate-level", type=int, default=8)
     ap.add_argument("--surrogate-traj", type=int, default=40)
@@ -75,14 +76,20 @@ def parse():
     return ap.parse_args()
 
 
-def workload():
+def workload(name="channel"):
     from paper_2311_08241_gb300 import inputs as I
 
-    case = I.channel_case()
+    if name == "sphere":
+        case = I.sphere_case(level=8)
+        label = ("global-like sphere: icosahedral level 8, Hilbert order, fractal bathymetry 10-6000 m with "
+                 "30 % land, f = 2 Omega sin(lat), smooth random forcing, tau=1800 s, M=50")
+    else:
+        case = I.channel_case()
+        label = ("wind-driven zonal channel 4000x2000 km, jittered Delaunay lattice, beta plane, "
+                 "Gaussian ridge, tau=480 s, M=40")
     m = case.mesh
     desc = {
-        "workload": "wind-driven zonal channel 4000x2000 km, jittered Delaunay lattice, beta plane, "
-                    "Gaussian ridge, tau=480 s, M=40",
+        "workload": label,
         "V": m.nv, "E": m.ne, "M": case.params.M, "tau_s": case.params.tau, "theta": case.params.theta,
         "nonlinear_h": case.params.nonlinear_h,
     }
@@ -122,7 +129,8 @@ def measured_hbm_peak():
 
 
 KERNEL_SOURCE = {"k_persistent": ("sesw_persistent.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
-                 "k_persistent_sesm": ("sesw_persistent_sesm.cu", "sesw_persistent.cuh", "sesw_device.cuh")}
+                 "k_persistent_sesm": ("sesw_persistent_sesm.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
+                 "k_persistent_stream": ("sesw_persistent_stream.cu", "sesw_persistent.cuh", "sesw_device.cuh")}
 
 
 def kernel_source_hash(kernel="k_persistent"):
@@ -132,10 +140,6 @@ def kernel_source_hash(kernel="k_persistent"):
         with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
-
-
-def profiled_traffic(kernel):
-    return profiled_traffic_for(kernel, "channel")
 
 
 def profiled_traffic_for(kernel, workload):
@@ -485,7 +489,7 @@ def run_reference(args, world, rank):
     from oracle import runner as orc
     from paper_2311_08241_gb300 import inputs as I
 
-    case, desc = workload()
+    case, desc = workload(args.workload)
     S = max(1, args.ref_substeps)
     p = case.params
     sample = I.Params(g=p.g, theta=p.theta, tau=p.tau / p.M * S, M=S, nonlinear_h=p.nonlinear_h)
@@ -518,7 +522,7 @@ def run_ours(args, world, rank, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    case, desc = workload()
+    case, desc = workload(args.workload)
     if args.scheme == "sesm":
         from paper_2311_08241_gb300 import inputs as I
 
@@ -620,11 +624,11 @@ def run_ours(args, world, rank, local):
     if args.scheme == "sesm":
         kname = "k_persistent_sesm" if persistent else "k_sesm"
     else:
-        kname = "k_persistent" if persistent else "k_substep"
+        kname = ("k_persistent_stream" if info["streamed"] else "k_persistent") if persistent else "k_substep"
     if args.visc:
         kname = "k_substep (viscosity fused)"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic(kname), "peak_source": peak_src, "kernel": kname,
+                "traffic": profiled_traffic_for(kname, args.workload), "peak_source": peak_src, "kernel": kname,
                 "bytes_per_launch": per_launch}
 
     # End to end through the public API with pinned host buffers: each step uploads its

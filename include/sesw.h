@@ -155,7 +155,8 @@ typedef struct sesw_info {
     int32_t block_threads;   /* threads per block of the substep (or persistent) kernel */
     int32_t mode;            /* SESW_MODE_GRAPH or SESW_MODE_PERSISTENT (0 from sesw_mesh_check) */
     int32_t blocks_per_sm;   /* persistent mode: resident blocks per SM */
-    int32_t slots_per_thread;/* persistent mode: element slots held in registers per thread */
+    int32_t slots_per_thread;/* persistent mode: element slots per thread (held in registers,
+                                or slot-loop rounds when streamed) */
     int32_t cached;          /* persistent mode: 1 when static slot data lives in shared memory */
     int32_t nbasin;          /* meshes in the uploaded batch (1 for sesw_mesh_upload) */
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
@@ -166,7 +167,8 @@ typedef struct sesw_info {
     int64_t device_bytes;    /* device memory held by the context */
     int32_t npack;           /* persistent mode: cooperative launches per step (packs of meshes
                                 that together fit the resident grid) */
-    int32_t reserved2;
+    int32_t streamed;        /* persistent mode: 1 when the (first) pack streams its transport, sums
+                                and static slot data from L2, for patches too large for registers */
     double visc_number;      /* viscous number of the barotropic viscosity (see sesw_params;
                                 0 until parameters are set) */
     double visc_stiffness;   /* max_e 2 sum_edges (H0_edge/H0_e)(L/d)/A_e (1/m^2): visc_number =

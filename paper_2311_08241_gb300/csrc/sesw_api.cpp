@@ -1159,6 +1159,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->blocks_per_sm = c->mode == SESW_MODE_PERSISTENT ? pl.blocks_per_sm : 0;
     info->slots_per_thread = c->mode == SESW_MODE_PERSISTENT ? pl.slots_per_thread : 0;
     info->cached = c->mode == SESW_MODE_PERSISTENT ? pl.cached : 0;
+    info->streamed = c->mode == SESW_MODE_PERSISTENT ? pl.stream : 0;
     info->courant_max = c->courant_max;
     info->courant_limit = c->have_params ? c->courant_limit : 0.0;
     info->stiffness_bound = c->grad_gram_max_h;

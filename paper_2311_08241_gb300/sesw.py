@@ -78,7 +78,7 @@ class sesw_info(ctypes.Structure):
                 ("mode", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("slots_per_thread", ctypes.c_int32),
                 ("cached", ctypes.c_int32), ("nbasin", ctypes.c_int32), ("courant_max", ctypes.c_double),
                 ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64), ("npack", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("npack", ctypes.c_int32), ("streamed", ctypes.c_int32),
                 ("visc_number", ctypes.c_double), ("visc_stiffness", ctypes.c_double)]
 
 
