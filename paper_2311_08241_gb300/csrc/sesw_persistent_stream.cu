@@ -101,12 +101,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
         // reads may have to wait for a neighbour; every halo value is in shared memory
         // at m = 0
         const int nfirst = first ? ns : nint;
-#pragma unroll 4
+#pragma unroll 8
         for (int i = threadIdx.x; i < nfirst; i += T) {
             const ushort4 l = __ldg(P.sl + s0 + i);
             stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, first, seta[l.x], seta[l.y], seta[l.z], dt, sflux);
         }
-#pragma unroll 4
+#pragma unroll 8
         for (int i = nfirst + threadIdx.x; i < ns; i += T) {
             const ushort4 l = __ldg(P.sl + s0 + i);
             const int h0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), h1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
