@@ -307,6 +307,38 @@ def test_persistent_tags_continue_across_launches_with_changing_substep_counts(s
     assert _maxabs(got[0] - ref[0]) <= ETA_ABS_TOL
 
 
+def test_streaming_layout_with_freshwater_and_step_mean(sesw):
+    """Patches too large for the register kernel (the level-8 sphere in automatic mode) stream their
+    transport, sums and static data from L2. Its variant with the per-vertex terms: the freshwater
+    flux over 2 steps against the oracle, and the step-mean elevation of one step."""
+    case = I.sphere_case(level=8, nsteps=2)
+    W = 2e-6 * (0.3 + np.random.default_rng(31).standard_normal(case.mesh.nv))
+    with sesw.Subcycle() as s:
+        s.sesw_mesh_upload(case.mesh)
+        info = s.sesw_get_info()
+        assert info["mode"] == PERSISTENT and info["streamed"] == 1, info
+        s.sesw_set_params(case.params)
+        s.sesw_set_forcing(case.R)
+        s.sesw_set_freshwater(W)
+        s.sesw_set_state(case.eta0, case.U0)
+        s.sesw_advance(2)
+        got = s.sesw_get_state()
+        s.sesw_set_freshwater(None)
+        s.sesw_set_eta_mean(True)
+        s.sesw_set_state(case.eta0, case.U0)
+        s.sesw_advance(1)
+        eb = s.sesw_get_eta_mean()
+    om = orc.OracleMesh(case.mesh)
+    ref = om.advance_ext(case.R, case.params, 2, case.eta0, case.U0, W=W)
+    r32 = orc.OracleMesh(case.mesh, orc.lib_fp32()).advance_ext(case.R, case.params, 2, case.eta0, case.U0, W=W)
+    for k, name in enumerate(("eta", "U", "<<U>>")):
+        tol = ENVELOPE_FACTOR * _maxabs(r32[k] - ref[k]) + ULP_FLOOR * _maxabs(ref[k])
+        assert _maxabs(got[k] - ref[k]) <= tol, name
+    assert _maxabs(got[0] - ref[0]) <= ETA_ABS_TOL
+    *_, eb_ref = om.advance(case.R, case.params, 1, case.eta0, case.U0, want_eta_mean=True)
+    assert _maxabs(eb - eb_ref) <= ETA_ABS_TOL
+
+
 def test_contexts_with_different_layouts_coexist(sesw):
     """Kernel attributes are process-wide: a context with large patches keeps working after a
     context with small patches has been set up (and the other way round)."""
