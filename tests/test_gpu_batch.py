@@ -140,3 +140,21 @@ def test_full_size_ensemble_matches_oracle(S, full_ensemble, bps):
             assert err <= tol, f"basin {b} ({c.mesh.nv} vertices) field {k}: {err:.3e} > {tol:.3e}"
         worst = max(worst, _maxabs(e - ref[b][0]))
     assert worst <= ETA_ABS_TOL
+
+
+def test_batch_mixes_streamed_and_cached_packs(S):
+    """One step launching different kernels per pack: the level-8 sphere (too large for the register
+    kernel, so its pack streams its state from L2) batched with small basins (cached packs). Every
+    basin against the oracle."""
+    sphere = I.sphere_case(level=8, nsteps=2)
+    small = I.ensemble_cases(nbasins=3, vmin=5000, vmax=20000, M=sphere.params.M, nsteps=2, seed=5)
+    with S.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload(sphere.mesh)
+        assert s.sesw_get_info()["streamed"] == 1
+    cases = small + [sphere]
+    (eta, U, Um), info, _ = _run_batch(S, cases, PERSISTENT, 2)
+    assert info["mode"] == PERSISTENT and info["npack"] >= 2, info
+    assert info["streamed"] == 0 and info["cached"] == 1, info     # the first pack: the small basins
+    for c, e, u, um in zip(cases, _split(cases, eta, "v"), _split(cases, U, "e"), _split(cases, Um, "e")):
+        _assert_close(c, (e, u, um), f"{c.name} in a mixed batch", nsteps=2)
