@@ -544,18 +544,12 @@ int build_halos(HostMesh &hm, std::string &err)
 {
     const int np = hm.npatch;
     hm.patch_halo.assign(np + 1, 0);
-    hm.patch_nbr.assign(np + 1, 0);
     hm.halo_v.clear();
-    hm.nbr.clear();
     hm.slot_l.assign(hm.nslot, make_ushort4(0, 0, 0, 0));
     hm.max_patch_local = 0;
-    hm.max_nbr = 0;
     hm.max_patch_halo = 0;
     hm.max_patch_csr = 0;
-    std::vector<int> vpatch(hm.nv);
-    for (int p = 0; p < np; p++)
-        for (int v = hm.patch_v[p]; v < hm.patch_v[p + 1]; v++) vpatch[v] = p;
-    std::vector<int> halo, nb;
+    std::vector<int> halo;
     for (int p = 0; p < np; p++) {
         const int vlo = hm.patch_v[p], vhi = hm.patch_v[p + 1], nown = vhi - vlo;
         halo.clear();
@@ -584,16 +578,9 @@ int build_halos(HostMesh &hm, std::string &err)
             }
             hm.slot_l[s] = make_ushort4(l[0], l[1], l[2], 0);
         }
-        nb.clear();
-        for (int v : halo) nb.push_back(vpatch[v]);
-        std::sort(nb.begin(), nb.end());
-        nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
         hm.halo_v.insert(hm.halo_v.end(), halo.begin(), halo.end());
-        hm.nbr.insert(hm.nbr.end(), nb.begin(), nb.end());
         hm.patch_halo[p + 1] = (int)hm.halo_v.size();
-        hm.patch_nbr[p + 1] = (int)hm.nbr.size();
         hm.max_patch_local = std::max(hm.max_patch_local, nloc);
-        hm.max_nbr = std::max(hm.max_nbr, (int)nb.size());
         hm.max_patch_halo = std::max(hm.max_patch_halo, (int)halo.size());
         hm.max_patch_csr = std::max(hm.max_patch_csr, hm.vcsr_off[vhi] - hm.vcsr_off[vlo]);
     }

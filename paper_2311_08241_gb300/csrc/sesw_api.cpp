@@ -565,11 +565,8 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     if (mode == SESW_MODE_PERSISTENT) {
         TRY(upload(c, &d.patch_halo, hm.patch_halo, "patch_halo"));
         TRY(upload(c, &d.halo_v, hm.halo_v, "halo_v"));
-        TRY(upload(c, &d.patch_nbr, hm.patch_nbr, "patch_nbr"));
-        TRY(upload(c, &d.nbr, hm.nbr, "nbr"));
         TRY(upload(c, &d.slot_l, hm.slot_l, "slot_l"));
         d.max_patch_local = hm.max_patch_local;
-        d.max_nbr = hm.max_nbr;
         d.max_patch_vertices = hm.max_patch_vertices;
         d.max_patch_halo = hm.max_patch_halo;
         d.max_patch_csr = hm.max_patch_csr;

@@ -71,11 +71,8 @@ struct HostMesh {
     // its slots owned by other patches) at [n_own, n_own + n_halo).
     std::vector<int> patch_halo;   // [npatch+1] ranges into halo_v
     std::vector<int> halo_v;       // halo vertex ids (new order), sorted per patch
-    std::vector<int> patch_nbr;    // [npatch+1] ranges into nbr
-    std::vector<int> nbr;          // neighbour patches (own a halo vertex; the relation is symmetric)
     std::vector<ushort4> slot_l;   // local corner indices of each slot (.w unused)
     int max_patch_local = 0;       // max n_own + n_halo
-    int max_nbr = 0;
     int max_patch_halo = 0;        // max n_halo
     int max_patch_csr = 0;         // max incidence entries of one patch's own vertices
 };
@@ -134,10 +131,8 @@ struct DevMesh {
     // persistent kernel
     int *patch_halo = nullptr;
     int *halo_v = nullptr;
-    int *patch_nbr = nullptr;
-    int *nbr = nullptr;
     ushort4 *slot_l = nullptr;
-    int max_patch_local = 0, max_nbr = 0, max_patch_vertices = 0, max_patch_halo = 0, max_patch_csr = 0;
+    int max_patch_local = 0, max_patch_vertices = 0, max_patch_halo = 0, max_patch_csr = 0;
 };
 
 struct DevState {

@@ -37,7 +37,7 @@ namespace {
 // match a word that no launch has rewritten since, and every launch rewrites every word
 // that is read.
 struct PArgs {
-    const int *patch_slot, *patch_own, *patch_int, *patch_v, *patch_halo, *halo_v, *patch_nbr, *nbr;
+    const int *patch_slot, *patch_own, *patch_int, *patch_v, *patch_halo, *halo_v;
     const int *vcsr_off;
     const uint32_t *vcsr;
     const int4 *sv;
@@ -157,8 +157,6 @@ inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, 
     P.patch_v = m.patch_v;
     P.patch_halo = m.patch_halo;
     P.halo_v = m.halo_v;
-    P.patch_nbr = m.patch_nbr;
-    P.nbr = m.nbr;
     P.vcsr_off = m.vcsr_off;
     P.vcsr = m.vcsr;
     P.sv = m.slot_v;
