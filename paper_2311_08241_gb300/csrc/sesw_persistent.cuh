@@ -195,28 +195,6 @@ inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, 
     return P;
 }
 
-// One cooperative launch per pack, with the pack's own plan and shared-memory layout;
-// all packs of a step use the same elevation parity, and each pack has its own tag base
-// (the exchange buffers need no clearing).
-template <class Kernel>
-cudaError_t launch_packs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                         const std::vector<PackPlan> &packs, bool sesm, Kernel kernel, cudaStream_t stream)
-{
-    for (size_t k = 0; k < packs.size(); k++) {
-        const PackPlan &pk = packs[k];
-        const PersistentPlan &plan = sesm ? pk.plan_sesm : pk.plan;
-        void *fn = kernel(plan);
-        if (!fn) return cudaErrorInvalidValue;
-        PArgs P = make_pargs(m, s, a, M, parity, pk.mx);
-        P.pack_base = pk.base;
-        P.pack_index = (int)k;
-        void *args[] = {&P};
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(plan.threads), args, plan.smem, stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
 }  // namespace
 
 }  // namespace sesw

@@ -311,9 +311,20 @@ cudaError_t persistent_prepare_sesm(const PersistentPlan &plan)
 cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                                    const std::vector<PackPlan> &packs, cudaStream_t stream)
 {
-    return launch_packs(m, s, a, M, parity, packs, true,
-                        [&](const PersistentPlan &p) { return sesm_kernel(p.slots_per_thread, a.nonlinear_h); },
-                        stream);
+    // one cooperative launch per pack, each with its own plan, layout and tag base
+    for (size_t k = 0; k < packs.size(); k++) {
+        const PackPlan &pk = packs[k];
+        void *fn = sesm_kernel(pk.plan_sesm.slots_per_thread, a.nonlinear_h);
+        if (!fn) return cudaErrorInvalidValue;
+        PArgs P = make_pargs(m, s, a, M, parity, pk.mx);
+        P.pack_base = pk.base;
+        P.pack_index = (int)k;
+        void *args[] = {&P};
+        cudaError_t e =
+            cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan_sesm.threads), args, pk.plan_sesm.smem, stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace sesw
