@@ -1,7 +1,8 @@
 // Shared parts of the persistent step kernels of libsesw (sm_103a): kernel arguments,
-// the tagged exchange of halo values through L2, the shared-memory layout of a patch and
-// the launch of a step's packs. Included by sesw_persistent.cu (the SE substep of
-// Eq. 4.10) and sesw_persistent_sesm.cu (the SESM substep of Eqs. 4.7-4.8).
+// the tagged exchange of halo values through L2 and the shared-memory layout of a patch.
+// Included by sesw_persistent.cu (the SE substep of Eq. 4.10), sesw_persistent_stream.cu
+// (the same for patches whose state is streamed from L2) and sesw_persistent_sesm.cu (the
+// SESM substep of Eqs. 4.7-4.8).
 #pragma once
 
 #include <cuda_runtime.h>
