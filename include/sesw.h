@@ -192,10 +192,12 @@ int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
 /* Execution modes of a baroclinic step.
  *   SESW_MODE_GRAPH       M launches of the substep kernel (one block per patch of
  *                         ~patch_vertices vertices) plus an epilogue, as one CUDA graph
- *   SESW_MODE_PERSISTENT  one cooperative launch per step: one block per SM keeps its
- *                         patch's elevation and fluxes in shared memory and its
- *                         transports in registers for all M substeps, exchanging
- *                         boundary elevation with neighbouring blocks through flags
+ *   SESW_MODE_PERSISTENT  one cooperative launch per step (per pack of a batch): each
+ *                         block keeps its patch's elevation and fluxes in shared memory
+ *                         and its transports in registers for all M substeps (patches
+ *                         too large for that stream their transports and static data
+ *                         from L2 instead, see sesw_info.streamed), exchanging boundary
+ *                         elevation with neighbouring blocks as tagged words through L2
  *                         with bounded waits (a wait that gives up sets SESW_ETIMEOUT)
  *   SESW_MODE_AUTO        persistent when the mesh fits it, else graph (default)
  * Results are the same to FP32 rounding; the summation order per vertex depends on
