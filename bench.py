@@ -130,7 +130,9 @@ def measured_hbm_peak():
 
 KERNEL_SOURCE = {"k_persistent": ("sesw_persistent.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
                  "k_persistent_sesm": ("sesw_persistent_sesm.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
-                 "k_persistent_stream": ("sesw_persistent_stream.cu", "sesw_persistent.cuh", "sesw_device.cuh")}
+                 "k_persistent_stream": ("sesw_persistent_stream.cu", "sesw_persistent.cuh", "sesw_device.cuh"),
+                 "k_persistent_sesm_stream": ("sesw_persistent_sesm_stream.cu", "sesw_persistent.cuh",
+                                              "sesw_device.cuh")}
 
 
 def kernel_source_hash(kernel="k_persistent"):
@@ -622,7 +624,7 @@ def run_ours(args, world, rank, local):
     achieved = per_launch / launch_s / 1e9
     peak, peak_src = measured_hbm_peak()
     if args.scheme == "sesm":
-        kname = "k_persistent_sesm" if persistent else "k_sesm"
+        kname = ("k_persistent_sesm_stream" if info["streamed"] else "k_persistent_sesm") if persistent else "k_sesm"
     else:
         kname = ("k_persistent_stream" if info["streamed"] else "k_persistent") if persistent else "k_substep"
     if args.visc:

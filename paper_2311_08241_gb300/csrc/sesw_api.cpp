@@ -441,6 +441,7 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
             }
             pk.plan.blocks_per_sm = bps;
             pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, bps);
+            if (pk.plan_sesm.slots_per_thread == 0) pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, bps);
             packs.push_back(pk);
             pack_basins.push_back(bn);
         }
@@ -593,7 +594,9 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
         for (const auto &pk : packs) {
             CK(c, pk.plan.stream ? sesw::persistent_prepare_stream(pk.plan) : sesw::persistent_prepare(pk.plan));
-            if (plan_sesm.slots_per_thread > 0) CK(c, sesw::persistent_prepare_sesm(pk.plan_sesm));
+            if (plan_sesm.slots_per_thread > 0)
+                CK(c, pk.plan_sesm.stream ? sesw::persistent_prepare_sesm_stream(pk.plan_sesm)
+                                          : sesw::persistent_prepare_sesm(pk.plan_sesm));
         }
     } else {
         TRY(zalloc(c, &s.eta_x[0], hm.nv, "eta_x"));
@@ -770,6 +773,15 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
     }
     const bool visc_on = p->visc_background > 0.0 || p->visc_flow > 0.0;
     if (visc_on && !c->ds.V0) TRY(zalloc(c, &c->ds.V0, (size_t)c->dm.nslot, "V0"));
+    // the streaming SESM kernel keeps U^{m-2} and U_AB^{m-1} in two more slot arrays
+    if (p->scheme == 1 && c->mode == SESW_MODE_PERSISTENT && !c->ds.U_x[0]) {
+        bool streamed = false;
+        for (const auto &pk : c->packs) streamed = streamed || pk.plan_sesm.stream;
+        if (streamed) {
+            TRY(zalloc(c, &c->ds.U_x[0], (size_t)c->dm.nslot, "U_x"));
+            TRY(zalloc(c, &c->ds.U_x[1], (size_t)c->dm.nslot, "U_x"));
+        }
+    }
     drop_graphs(c);
     c->params = *p;
     if (!(c->params.eta_bound > 0.0)) c->params.eta_bound = 1e4;

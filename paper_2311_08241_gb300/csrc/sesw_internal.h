@@ -253,6 +253,12 @@ cudaError_t persistent_prepare(const PersistentPlan &plan);
 size_t persistent_flag_bytes(int npatch);
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                               const std::vector<PackPlan> &packs, cudaStream_t stream);
+// The SESM scheme for patches too large for its on-chip state (k_persistent_sesm_stream):
+// two more slot arrays (DevState::U_x) hold U^{m-2} and U_AB^{m-1}.
+PersistentPlan persistent_plan_sesm_stream(const PatchMax &mx, int blocks_per_sm);
+cudaError_t persistent_prepare_sesm_stream(const PersistentPlan &plan);
+cudaError_t launch_persistent_sesm_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M,
+                                               int parity, const PackPlan &pk, int pack_index, cudaStream_t stream);
 // Patches too large for the on-chip state (k_persistent_stream): transport, sums and
 // static data stay in global memory; only the elevation and the fluxes are on chip.
 PersistentPlan persistent_plan_stream(const PatchMax &mx, int blocks_per_sm);

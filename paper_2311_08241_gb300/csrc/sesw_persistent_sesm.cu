@@ -314,6 +314,11 @@ cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const St
     // one cooperative launch per pack, each with its own plan, layout and tag base
     for (size_t k = 0; k < packs.size(); k++) {
         const PackPlan &pk = packs[k];
+        if (pk.plan_sesm.stream) {
+            const cudaError_t e = launch_persistent_sesm_stream_pack(m, s, a, M, parity, pk, (int)k, stream);
+            if (e != cudaSuccess) return e;
+            continue;
+        }
         void *fn = sesm_kernel(pk.plan_sesm.slots_per_thread, a.nonlinear_h);
         if (!fn) return cudaErrorInvalidValue;
         PArgs P = make_pargs(m, s, a, M, parity, pk.mx);

@@ -1,0 +1,277 @@
+// The streaming SESM step kernel of libsesw (sm_103a), for patches too large to keep the
+// scheme's state on chip: one cooperative launch runs a baroclinic step of the AB3-AM4
+// substep of Eqs. (4.7)-(4.8), like k_persistent_sesm, with the time-mean transport of
+// Eq. (4.12) and the freshwater flux of Eq. (4.5). The transport levels U^{m-1} and
+// U^{m-2}, the AB3 transport U_AB^{m-1}, the compensated sum and the static slot data
+// stay in global memory (L2-resident across the substeps) and are read and written slot
+// by slot; the AM4 elevation of the own and halo vertices, the corner fluxes and the
+// three-level elevation history of the own vertices live in shared memory. The owner of
+// a vertex exchanges its AM4 elevation as in k_persistent_sesm.
+#include "sesw_persistent.cuh"
+
+namespace sesw {
+
+namespace {
+
+constexpr int kSesmStreamThreads = 1024;   // 64 registers per thread at any residency
+
+struct QArgs {
+    PArgs P;
+    float2 *U2, *UAB;     // per slot: U^{m-2} and U_AB^{m-1}
+    float2 *Shi, *Slo;    // per slot: the compensated sum of the AB3 transports
+    int off_hist;         // shared-memory offset of the elevation history (bytes)
+    int vmax;             // own vertices of the largest patch (stride of the history)
+};
+
+// U_AB of slot s from its levels, its flux contributions and (owned) the compensated sum;
+// `first` starts the sum.
+__device__ __forceinline__ float2 sesm_transport(const QArgs &A, int s, int i, bool owned, bool first, float2 u0,
+                                                 float2 ua, float2 ub, float4 g, float area, float dt, float *sflux)
+{
+    const StepArgs &a = A.P.a;
+    const float fx = a.ab0 * u0.x + a.ab1 * ua.x + a.ab2 * ub.x;
+    const float fy = a.ab0 * u0.y + a.ab1 * ua.y + a.ab2 * ub.y;
+    if (owned) {
+        float2 hi = make_float2(0.0f, 0.0f), lo = hi;
+        if (!first) {
+            hi = A.Shi[s];
+            lo = A.Slo[s];
+        }
+        two_sum_acc(hi.x, lo.x, fx);
+        two_sum_acc(hi.y, lo.y, fy);
+        A.Shi[s] = hi;
+        A.Slo[s] = lo;
+    }
+    const float w = dt * area;
+    const float q0 = w * (fx * g.x + fy * g.y);
+    const float q1 = w * (fx * g.z + fy * g.w);
+    sflux[3 * i + 0] = q0;
+    sflux[3 * i + 1] = q1;
+    sflux[3 * i + 2] = -(q0 + q1);
+    return make_float2(fx, fy);
+}
+
+// Momentum update of slot s (substep m >= 1) from its corner eta_AM, then (vertex) its
+// transport; the levels shift in global memory.
+template <int NONLIN>
+__device__ __forceinline__ void sesm_slot(const QArgs &A, int s, int i, bool owned, bool vertex, float e0, float e1,
+                                          float e2, float dt, float *sflux)
+{
+    const PArgs &P = A.P;
+    const StepArgs &a = P.a;
+    const float4 g = __ldg(P.sg + s), c = __ldg(P.sc + s);
+    const float2 r = __ldg(P.R + s);
+    const float2 u1 = P.U[s], u2 = A.U2[s], uab = A.UAB[s];
+    const float d0 = e0 - e2, d1 = e1 - e2;
+    const float gx = d0 * g.x + d1 * g.z;
+    const float gy = d0 * g.y + d1 * g.w;
+    float H = c.y;
+    if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
+    const float gH = a.g * H;
+    // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
+    float2 u0;
+    u0.x = u1.x + dt * (c.z * uab.y - gH * gx + r.x);
+    u0.y = u1.y + dt * (-c.z * uab.x - gH * gy + r.y);
+    if (vertex) {
+        A.UAB[s] = sesm_transport(A, s, i, owned, false, u0, u1, u2, g, c.x, dt, sflux);
+        A.U2[s] = u1;
+    }
+    P.U[s] = u0;
+}
+
+template <int NONLIN>
+__global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_stream(QArgs A)
+{
+    const PArgs &P = A.P;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_abort;
+    const int p = P.pack_patch[P.pack_base + blockIdx.x];
+    const int T = blockDim.x;
+    const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
+    const int nown_s = P.patch_own[p], nint = P.patch_int[p];
+    const int v0 = P.patch_v[p], nown = P.patch_v[p + 1] - v0;
+    const StepArgs a = P.a;
+    const float dt = P.patch_dt[p];
+    unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
+    unsigned *exit_count = base_word + kFlagStride;
+    const unsigned base = ld_relaxed_gpu(base_word);
+    const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
+
+    float *sem = reinterpret_cast<float *>(smem_raw);   // eta_AM of own and halo vertices
+    float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
+    float *h0 = reinterpret_cast<float *>(smem_raw + A.off_hist);   // eta^m, eta^{m-1}, eta^{m-2} of own vertices
+    float *h1 = h0 + A.vmax, *h2 = h1 + A.vmax;
+    for (int i = threadIdx.x; i < nown; i += T) {
+        const float x = __ldg(P.eta_in + v0 + i);
+        h0[i] = x;
+        h1[i] = x;
+        h2[i] = x;
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+
+    const int *hid = P.halo_v + P.patch_halo[p];
+    bool ok = true;
+    for (int m = 0; m <= P.M; m++) {
+        const bool vertex = m < P.M;
+        if (m == 0) {
+            // no momentum update: U_AB^0 from level 0 and its aliases
+#pragma unroll 8
+            for (int i = threadIdx.x; i < ns; i += T) {
+                const int s = s0 + i;
+                const float2 u = P.U[s];
+                A.UAB[s] = sesm_transport(A, s, i, i < nown_s, true, u, u, u, __ldg(P.sg + s), __ldg(P.sc + s).x, dt,
+                                          sflux);
+                A.U2[s] = u;
+            }
+        } else {
+            const unsigned tag = base + (unsigned)m;
+            const unsigned long long *xs = P.xb[m & 1];
+#pragma unroll 8
+            for (int i = threadIdx.x; i < nint; i += T) {
+                const ushort4 l = __ldg(P.sl + s0 + i);
+                sesm_slot<NONLIN>(A, s0 + i, i, i < nown_s, vertex, sem[l.x], sem[l.y], sem[l.z], dt, sflux);
+            }
+#pragma unroll 8
+            for (int i = nint + threadIdx.x; i < ns; i += T) {
+                const ushort4 l = __ldg(P.sl + s0 + i);
+                const int q0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), q1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
+                          q2 = l.z < nown ? -1 : __ldg(hid + l.z - nown);
+                const unsigned long long w0 = q0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q0);
+                const unsigned long long w1 = q1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q1);
+                const unsigned long long w2 = q2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q2);
+                const float e0 = q0 < 0 ? sem[l.x] : halo_eta(P, xs, q0, w0, tag, abort_val, ok);
+                const float e1 = q1 < 0 ? sem[l.y] : halo_eta(P, xs, q1, w1, tag, abort_val, ok);
+                const float e2 = q2 < 0 ? sem[l.z] : halo_eta(P, xs, q2, w2, tag, abort_val, ok);
+                sesm_slot<NONLIN>(A, s0 + i, i, i < nown_s, vertex, e0, e1, e2, dt, sflux);
+            }
+            if (!ok) s_abort = 1;
+        }
+        if (!vertex) break;
+        __syncthreads();
+        if (s_abort) break;
+
+        // vertex pass: eta^{m+1}, then eta_AM^{m+1} for the own slots and the neighbours
+        unsigned long long *xout = P.xb[(m + 1) & 1];
+        const unsigned long long tag_out = (unsigned long long)(base + (unsigned)(m + 1)) << 32;
+        const bool publish = p != a.silent_patch;
+        bool bad = false;
+        for (int i = threadIdx.x; i < nown; i += T) {
+            float sum = 0.0f;
+            const int k1 = __ldg(P.vcsr_off + v0 + i + 1);
+            for (int k = __ldg(P.vcsr_off + v0 + i); k < k1; k++) {
+                const uint32_t q = __ldg(P.vcsr + k);
+                sum += sflux[3 * (q >> 2) + (q & 3u)];
+            }
+            float e = h0[i] + sum * __ldg(P.inv_av + v0 + i);
+            if (P.W) e -= dt * __ldg(P.W + v0 + i);
+            const float em = a.am0 * e + a.am1 * h0[i] + a.am2 * h1[i] + a.am3 * h2[i];
+            h2[i] = h1[i];
+            h1[i] = h0[i];
+            h0[i] = e;
+            sem[i] = em;
+            if (publish) st_relaxed_gpu_u64(xout + v0 + i, tag_out | __float_as_uint(em));
+            bad |= !(fabsf(e) <= a.eta_bound);
+        }
+        if (bad) atomicOr(P.status, 1u);
+        __syncthreads();
+    }
+    __syncthreads();
+
+    for (int i = threadIdx.x; i < nown; i += T) P.eta_out[v0 + i] = h0[i];
+    for (int i = threadIdx.x; i < nown_s; i += T) {
+        const int s = s0 + i;
+        const int w = P.sv[s].w;
+        const float2 hi = A.Shi[s], lo = A.Slo[s];
+        P.Umean[w] = make_float2((hi.x + lo.x) * a.inv_M, (hi.y + lo.y) * a.inv_M);
+    }
+    // the last block of the pack to leave (every block has read the base by then) sets
+    // the next launch's base
+    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == gridDim.x - 1) {
+        *exit_count = 0u;
+        *base_word = base + (unsigned)P.M + 1u;
+    }
+}
+
+void *sesm_stream_kernel(int nonlin)
+{
+    return nonlin ? (void *)k_persistent_sesm_stream<1> : (void *)k_persistent_sesm_stream<0>;
+}
+
+size_t hist_offset(const SmemLayout &L) { return align16(L.total_plain); }
+
+size_t sesm_stream_smem(const PatchMax &m)
+{
+    const SmemLayout L = smem_layout(m);
+    return hist_offset(L) + align16(3 * sizeof(float) * (size_t)m.vertices);
+}
+
+}  // namespace
+
+PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm)
+{
+    PersistentPlan plan;
+    int dev = 0, smem_optin = 0, smem_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return plan;
+    }
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    const int t =
+        std::min(std::min(kSesmStreamThreads, 1024 / blocks_per_sm), std::max(32, ((m.slots + 31) / 32) * 32));
+    const size_t smem = sesm_stream_smem(m);
+    size_t budget = (size_t)smem_optin - 1024;
+    const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
+    if (share < 2048) return plan;
+    budget = std::min(budget, share - 2048);
+    if (smem > budget) return plan;
+    for (int nonlin = 0; nonlin < 2; nonlin++) {
+        void *fn = sesm_stream_kernel(nonlin);
+        int occ = 0;
+        if (!fn || raise_smem_limit(fn) < (int)smem ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, smem) != cudaSuccess || occ < blocks_per_sm) {
+            cudaGetLastError();
+            return plan;
+        }
+    }
+    plan.slots_per_thread = (m.slots + t - 1) / t;   // rounds of the slot loop (not registers)
+    plan.threads = t;
+    plan.cached = 0;
+    plan.stream = 1;
+    plan.blocks_per_sm = blocks_per_sm;
+    plan.smem = smem;
+    return plan;
+}
+
+cudaError_t persistent_prepare_sesm_stream(const PersistentPlan &plan)
+{
+    for (int nonlin = 0; nonlin < 2; nonlin++) {
+        void *fn = sesm_stream_kernel(nonlin);
+        if (!fn || raise_smem_limit(fn) < (int)plan.smem) return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_persistent_sesm_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M,
+                                               int parity, const PackPlan &pk, int pack_index, cudaStream_t stream)
+{
+    if (!s.U_x[0] || !s.U_x[1]) return cudaErrorInvalidValue;
+    QArgs A;
+    A.P = make_pargs(m, s, a, M, parity, pk.mx);
+    A.P.pack_base = pk.base;
+    A.P.pack_index = pack_index;
+    A.U2 = s.U_x[0];
+    A.UAB = s.U_x[1];
+    A.Shi = s.S_hi;
+    A.Slo = s.S_lo;
+    A.off_hist = (int)hist_offset(smem_layout(pk.mx));
+    A.vmax = pk.mx.vertices;
+    void *fn = sesm_stream_kernel(a.nonlinear_h);
+    void *args[] = {&A};
+    return cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan_sesm.threads), args, pk.plan_sesm.smem,
+                                       stream);
+}
+
+}  // namespace sesw

@@ -164,3 +164,13 @@ def test_sesm_persistent_batch_in_packs(S):
     ie = np.cumsum([c.mesh.ne for c in cases])[:-1]
     for c, coef, e, u, um in zip(cases, coefs, np.split(eta, iv), np.split(U, ie), np.split(Um, ie)):
         _check(c, coef, (e, u, um), 2, f"{c.name} packs={info['npack']}")
+
+
+def test_sesm_streamed_on_the_sphere_matches_oracle(S):
+    """The level-8 sphere's patches are too large for the SESM kernel's on-chip state, so the
+    persistent layout streams the transport levels and sums from L2; 2 steps against the oracle."""
+    case = I.sphere_case(level=8, nsteps=2)
+    coef = _sesm(case)
+    (got, info) = _run(S, case, 2, PERSISTENT)
+    assert info["mode"] == PERSISTENT and info["streamed"] == 1, info
+    _check(case, coef, got, 2, "sphere8 SESM streamed")
