@@ -110,8 +110,8 @@ def test_sesm_summation_identity_and_volume(S, mode):
 def test_sesm_rules(S):
     case = I.tiny_jittered_case()
     _sesm(case)
-    # persistent SESM needs patches of at most 4 x 384 slots: one block per SM on the
-    # channel gives patches of ~1300 vertices, which it refuses (the SE kernel takes them)
+    # the on-chip SESM kernel takes patches of at most 4 x 384 slots: one block per SM on
+    # the channel gives patches of ~1300 vertices, whose state the layout then streams
     big = I.channel_case(nsteps=1)
     _sesm(big)
     with S.Subcycle() as s:
@@ -119,8 +119,8 @@ def test_sesm_rules(S):
         s.sesw_set_blocks_per_sm(1)
         s.sesw_mesh_upload(big.mesh)
         assert s.sesw_get_info()["mode"] == PERSISTENT
-        with pytest.raises(S.SeswError, match="SESW_MODE_GRAPH"):
-            s.sesw_set_params(big.params)
+        s.sesw_set_params(big.params)
+        assert s.sesw_get_info()["streamed"] == 1
     with S.Subcycle() as s:
         s.sesw_set_mode(PERSISTENT)
         s.sesw_mesh_upload(big.mesh)
