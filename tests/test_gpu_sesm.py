@@ -174,3 +174,26 @@ def test_sesm_streamed_on_the_sphere_matches_oracle(S):
     (got, info) = _run(S, case, 2, PERSISTENT)
     assert info["mode"] == PERSISTENT and info["streamed"] == 1, info
     _check(case, coef, got, 2, "sphere8 SESM streamed")
+
+
+def test_sesm_batch_mixes_streamed_and_cached_packs(S):
+    """One SESM step launching different kernels per pack: the level-8 sphere (streamed) batched
+    with small basins (on-chip SESM kernel). Every basin against the oracle."""
+    sphere = I.sphere_case(level=8, nsteps=2)
+    small = I.ensemble_cases(nbasins=3, vmin=5000, vmax=20000, M=sphere.params.M, nsteps=2, seed=5)
+    cases = small + [sphere]
+    coefs = [_sesm(c) for c in cases]
+    with S.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload_batch([c.mesh for c in cases])
+        s.sesw_set_params_batch([c.params for c in cases])
+        s.sesw_set_forcing(np.concatenate([c.R for c in cases]))
+        s.sesw_set_state(np.concatenate([c.eta0 for c in cases]), np.concatenate([c.U0 for c in cases]))
+        s.sesw_advance(2)
+        info = s.sesw_get_info()
+        eta, U, Um = s.sesw_get_state()
+    assert info["mode"] == PERSISTENT and info["npack"] >= 2 and info["streamed"] == 0, info
+    iv = np.cumsum([c.mesh.nv for c in cases])[:-1]
+    ie = np.cumsum([c.mesh.ne for c in cases])[:-1]
+    for c, coef, e, u, um in zip(cases, coefs, np.split(eta, iv), np.split(U, ie), np.split(Um, ie)):
+        _check(c, coef, (e, u, um), 2, f"{c.name} in a mixed SESM batch")
