@@ -98,8 +98,10 @@ typedef struct sesw_mesh {
  *                1: AB3-AM4 with dissipative coefficients (Eqs. 4.7-4.8, "SESM"); levels
  *                   before the start of a subcycle are taken equal to level 0 and <<U>> is the
  *                   mean of the AB3 transports, which keeps Eq. 4.11 exact. In
- *                   SESW_MODE_PERSISTENT it needs patches of at most 1536 slots and 768 own
- *                   vertices (SESW_EINVAL otherwise: upload in SESW_MODE_GRAPH instead)
+ *                   SESW_MODE_PERSISTENT, patches of at most 1536 slots and 768 own vertices
+ *                   keep its state on chip and larger ones stream it from L2; patches too
+ *                   large for the streaming kernel's shared memory give SESW_EINVAL (upload
+ *                   in SESW_MODE_GRAPH instead)
  *   flags        bit 0 (SESW_FLAG_NO_STABILITY_CHECK): accept parameters whose Courant
  *                bound exceeds the stability limit (the bound is conservative);
  *                bit 1 (SESW_FLAG_TEST_FORCE_TIMEOUT, for testing failure detection):
@@ -167,8 +169,10 @@ typedef struct sesw_info {
     int64_t device_bytes;    /* device memory held by the context */
     int32_t npack;           /* persistent mode: cooperative launches per step (packs of meshes
                                 that together fit the resident grid) */
-    int32_t streamed;        /* persistent mode: 1 when the (first) pack streams its transport, sums
-                                and static slot data from L2, for patches too large for registers */
+    int32_t streamed;        /* persistent mode: nonzero when the (first) pack streams its transport,
+                                sums and static slot data from L2, for patches too large for
+                                registers: 1 with the slots' corner indices held in shared memory,
+                                2 with them read from L2 too (the largest patches) */
     double visc_number;      /* viscous number of the barotropic viscosity (see sesw_params;
                                 0 until parameters are set) */
     double visc_stiffness;   /* max_e 2 sum_edges (H0_edge/H0_e)(L/d)/A_e (1/m^2): visc_number =

@@ -233,7 +233,8 @@ struct PersistentPlan {
     int slots_per_thread = 0;   // 0: not possible for this mesh
     int threads = 0;
     int cached = 0;             // 1: the patch's static data lives in shared memory
-    int stream = 0;             // 1: k_persistent_stream (state and static data in global memory)
+    int stream = 0;             // state and static data in global memory (the streaming kernels):
+                                // 1 with the corner indices in shared memory, 2 without
     int blocks_per_sm = 1;
     size_t smem = 0;
 };

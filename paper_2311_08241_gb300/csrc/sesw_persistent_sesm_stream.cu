@@ -4,8 +4,9 @@
 // Eq. (4.12) and the freshwater flux of Eq. (4.5). The transport levels U^{m-1} and
 // U^{m-2}, the AB3 transport U_AB^{m-1}, the compensated sum and the static slot data
 // stay in global memory (L2-resident across the substeps) and are read and written slot
-// by slot; the AM4 elevation of the own and halo vertices, the corner fluxes and the
-// three-level elevation history of the own vertices live in shared memory. The owner of
+// by slot; the AM4 elevation of the own and halo vertices, the corner fluxes, the
+// three-level elevation history of the own vertices and the slots' corner indices (loaded
+// once per launch) live in shared memory. The owner of
 // a vertex exchanges its AM4 elevation as in k_persistent_sesm.
 #include "sesw_persistent.cuh"
 
@@ -20,6 +21,7 @@ struct QArgs {
     float2 *U2, *UAB;     // per slot: U^{m-2} and U_AB^{m-1}
     float2 *Shi, *Slo;    // per slot: the compensated sum of the AB3 transports
     int off_hist;         // shared-memory offset of the elevation history (bytes)
+    int off_idx;          // IDX: shared-memory offset of the cached corner indices (ushort4 per slot)
     int vmax;             // own vertices of the largest patch (stride of the history)
 };
 
@@ -79,7 +81,9 @@ __device__ __forceinline__ void sesm_slot(const QArgs &A, int s, int i, bool own
     P.U[s] = u0;
 }
 
-template <int NONLIN>
+// IDX = 1 keeps the slots' corner indices in shared memory; IDX = 0 (patches too large for
+// that) reads them from global memory every substep.
+template <int NONLIN, int IDX>
 __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_stream(QArgs A)
 {
     const PArgs &P = A.P;
@@ -101,6 +105,9 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
     float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
     float *h0 = reinterpret_cast<float *>(smem_raw + A.off_hist);   // eta^m, eta^{m-1}, eta^{m-2} of own vertices
     float *h1 = h0 + A.vmax, *h2 = h1 + A.vmax;
+    ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + A.off_idx);
+    if (IDX)
+        for (int i = threadIdx.x; i < ns; i += T) s_l[i] = __ldg(P.sl + s0 + i);
     for (int i = threadIdx.x; i < nown; i += T) {
         const float x = __ldg(P.eta_in + v0 + i);
         h0[i] = x;
@@ -129,12 +136,12 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
             const unsigned long long *xs = P.xb[m & 1];
 #pragma unroll 8
             for (int i = threadIdx.x; i < nint; i += T) {
-                const ushort4 l = __ldg(P.sl + s0 + i);
+                const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
                 sesm_slot<NONLIN>(A, s0 + i, i, i < nown_s, vertex, sem[l.x], sem[l.y], sem[l.z], dt, sflux);
             }
 #pragma unroll 8
             for (int i = nint + threadIdx.x; i < ns; i += T) {
-                const ushort4 l = __ldg(P.sl + s0 + i);
+                const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
                 const int q0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), q1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
                           q2 = l.z < nown ? -1 : __ldg(hid + l.z - nown);
                 const unsigned long long w0 = q0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q0);
@@ -193,17 +200,19 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
     }
 }
 
-void *sesm_stream_kernel(int nonlin)
+void *sesm_stream_kernel(int nonlin, int idx)
 {
-    return nonlin ? (void *)k_persistent_sesm_stream<1> : (void *)k_persistent_sesm_stream<0>;
+    if (idx) return nonlin ? (void *)k_persistent_sesm_stream<1, 1> : (void *)k_persistent_sesm_stream<0, 1>;
+    return nonlin ? (void *)k_persistent_sesm_stream<1, 0> : (void *)k_persistent_sesm_stream<0, 0>;
 }
 
 size_t hist_offset(const SmemLayout &L) { return align16(L.total_plain); }
 
-size_t sesm_stream_smem(const PatchMax &m)
+size_t idx_offset(const PatchMax &m) { return hist_offset(smem_layout(m)) + align16(3 * sizeof(float) * (size_t)m.vertices); }
+
+size_t sesm_stream_smem(const PatchMax &m, int idx)
 {
-    const SmemLayout L = smem_layout(m);
-    return hist_offset(L) + align16(3 * sizeof(float) * (size_t)m.vertices);
+    return idx ? idx_offset(m) + sizeof(ushort4) * (size_t)m.slots : idx_offset(m);
 }
 
 }  // namespace
@@ -221,14 +230,20 @@ PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm)
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     const int t =
         std::min(std::min(kSesmStreamThreads, 1024 / blocks_per_sm), std::max(32, ((m.slots + 31) / 32) * 32));
-    const size_t smem = sesm_stream_smem(m);
     size_t budget = (size_t)smem_optin - 1024;
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
+    // the corner indices join the shared memory when they fit
+    int idx = 1;
+    size_t smem = sesm_stream_smem(m, 1);
+    if (smem > budget) {
+        idx = 0;
+        smem = sesm_stream_smem(m, 0);
+    }
     if (smem > budget) return plan;
     for (int nonlin = 0; nonlin < 2; nonlin++) {
-        void *fn = sesm_stream_kernel(nonlin);
+        void *fn = sesm_stream_kernel(nonlin, idx);
         int occ = 0;
         if (!fn || raise_smem_limit(fn) < (int)smem ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, smem) != cudaSuccess || occ < blocks_per_sm) {
@@ -239,7 +254,7 @@ PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm)
     plan.slots_per_thread = (m.slots + t - 1) / t;   // rounds of the slot loop (not registers)
     plan.threads = t;
     plan.cached = 0;
-    plan.stream = 1;
+    plan.stream = idx ? 1 : 2;
     plan.blocks_per_sm = blocks_per_sm;
     plan.smem = smem;
     return plan;
@@ -248,7 +263,7 @@ PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm)
 cudaError_t persistent_prepare_sesm_stream(const PersistentPlan &plan)
 {
     for (int nonlin = 0; nonlin < 2; nonlin++) {
-        void *fn = sesm_stream_kernel(nonlin);
+        void *fn = sesm_stream_kernel(nonlin, plan.stream == 1);
         if (!fn || raise_smem_limit(fn) < (int)plan.smem) return cudaErrorInvalidValue;
     }
     return cudaSuccess;
@@ -267,8 +282,9 @@ cudaError_t launch_persistent_sesm_stream_pack(const DevMesh &m, const DevState 
     A.Shi = s.S_hi;
     A.Slo = s.S_lo;
     A.off_hist = (int)hist_offset(smem_layout(pk.mx));
+    A.off_idx = (int)idx_offset(pk.mx);
     A.vmax = pk.mx.vertices;
-    void *fn = sesm_stream_kernel(a.nonlinear_h);
+    void *fn = sesm_stream_kernel(a.nonlinear_h, pk.plan_sesm.stream == 1);
     void *args[] = {&A};
     return cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan_sesm.threads), args, pk.plan_sesm.smem,
                                        stream);

@@ -3,8 +3,9 @@
 // baroclinic step, with the time-mean transport of Eq. (4.12) and the freshwater flux of
 // Eq. (4.5), like k_persistent, but the transport, the compensated sum and the static
 // slot data stay in global memory (L2-resident across the substeps) and are read and
-// written slot by slot. Only the elevation of the patch's own and halo vertices and the
-// per-corner fluxes live in shared memory. With no per-slot registers carried between
+// written slot by slot. The elevation of the patch's own and halo vertices, the
+// per-corner fluxes and the slots' corner indices (loaded once per launch) live in shared
+// memory. With no per-slot registers carried between
 // substeps, a block holds any number of slots per thread without spilling, and every
 // load of a slot depends only on the slot's index, so it costs one L2 round trip.
 #include "sesw_persistent.cuh"
@@ -18,6 +19,7 @@ constexpr int kStreamThreads = 1024;   // 64 registers per thread at any residen
 struct SArgs {
     PArgs P;
     float2 *Shi, *Slo;
+    int off_idx;    // IDX: shared-memory offset of the cached corner indices (ushort4 per slot)
 };
 
 // Element update of one slot (Eq. 4.10, first row, and the theta-weighted flux) from its
@@ -65,7 +67,9 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
 }
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set.
-template <int NONLIN, int EXTRA>
+// IDX = 1 keeps the slots' corner indices in shared memory; IDX = 0 (patches too large for
+// that) reads them from global memory every substep.
+template <int NONLIN, int EXTRA, int IDX>
 __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A)
 {
     const PArgs &P = A.P;
@@ -86,6 +90,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
 
     float *seta = reinterpret_cast<float *>(smem_raw);
     float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
+    ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + A.off_idx);
+    if (IDX)
+        for (int i = threadIdx.x; i < ns; i += T) s_l[i] = __ldg(P.sl + s0 + i);
     for (int i = threadIdx.x; i < nown; i += T) seta[i] = P.eta_in[v0 + i];
     for (int i = threadIdx.x; i < nhalo; i += T) seta[nown + i] = P.eta_in[P.halo_v[hb + i]];
     if (threadIdx.x == 0) s_abort = 0;
@@ -103,12 +110,12 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
         const int nfirst = first ? ns : nint;
 #pragma unroll 8
         for (int i = threadIdx.x; i < nfirst; i += T) {
-            const ushort4 l = __ldg(P.sl + s0 + i);
+            const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
             stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, first, seta[l.x], seta[l.y], seta[l.z], dt, sflux);
         }
 #pragma unroll 8
         for (int i = nfirst + threadIdx.x; i < ns; i += T) {
-            const ushort4 l = __ldg(P.sl + s0 + i);
+            const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
             const int h0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), h1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
                       h2 = l.z < nown ? -1 : __ldg(hid + l.z - nown);
             const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
@@ -166,10 +173,16 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
     }
 }
 
-void *stream_kernel(int nonlin, int extra)
+template <int IDX>
+void *stream_kernel_of(int nonlin, int extra)
 {
-    if (extra) return nonlin ? (void *)k_persistent_stream<1, 1> : (void *)k_persistent_stream<0, 1>;
-    return nonlin ? (void *)k_persistent_stream<1, 0> : (void *)k_persistent_stream<0, 0>;
+    if (extra) return nonlin ? (void *)k_persistent_stream<1, 1, IDX> : (void *)k_persistent_stream<0, 1, IDX>;
+    return nonlin ? (void *)k_persistent_stream<1, 0, IDX> : (void *)k_persistent_stream<0, 0, IDX>;
+}
+
+void *stream_kernel(int nonlin, int extra, int idx)
+{
+    return idx ? stream_kernel_of<1>(nonlin, extra) : stream_kernel_of<0>(nonlin, extra);
 }
 
 }  // namespace
@@ -192,13 +205,20 @@ PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm)
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
-    if (L.total_plain > budget) return plan;
+    // the corner indices join the shared memory when they fit
+    int idx = 1;
+    size_t need = align16(L.total_plain) + sizeof(ushort4) * (size_t)m.slots;
+    if (need > budget) {
+        idx = 0;
+        need = L.total_plain;
+    }
+    if (need > budget) return plan;
     for (int nonlin = 0; nonlin < 2; nonlin++)
         for (int extra = 0; extra < 2; extra++) {
-            void *fn = stream_kernel(nonlin, extra);
+            void *fn = stream_kernel(nonlin, extra, idx);
             int occ = 0;
-            if (!fn || raise_smem_limit(fn) < (int)L.total_plain ||
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, L.total_plain) != cudaSuccess ||
+            if (!fn || raise_smem_limit(fn) < (int)need ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, t, need) != cudaSuccess ||
                 occ < blocks_per_sm) {
                 cudaGetLastError();
                 return plan;
@@ -207,9 +227,9 @@ PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm)
     plan.slots_per_thread = (m.slots + t - 1) / t;   // rounds of the slot loop (not registers)
     plan.threads = t;
     plan.cached = 0;
-    plan.stream = 1;
+    plan.stream = idx ? 1 : 2;
     plan.blocks_per_sm = blocks_per_sm;
-    plan.smem = L.total_plain;
+    plan.smem = need;
     return plan;
 }
 
@@ -217,7 +237,7 @@ cudaError_t persistent_prepare_stream(const PersistentPlan &plan)
 {
     for (int nonlin = 0; nonlin < 2; nonlin++)
         for (int extra = 0; extra < 2; extra++) {
-            void *fn = stream_kernel(nonlin, extra);
+            void *fn = stream_kernel(nonlin, extra, plan.stream == 1);
             if (!fn || raise_smem_limit(fn) < (int)plan.smem) return cudaErrorInvalidValue;
         }
     return cudaSuccess;
@@ -232,7 +252,8 @@ cudaError_t launch_persistent_stream_pack(const DevMesh &m, const DevState &s, c
     A.P.pack_index = pack_index;
     A.Shi = s.S_hi;
     A.Slo = s.S_lo;
-    void *fn = stream_kernel(a.nonlinear_h, s.W != nullptr || s.eta_sum != nullptr);
+    A.off_idx = (int)align16(smem_layout(pk.mx).total_plain);
+    void *fn = stream_kernel(a.nonlinear_h, s.W != nullptr || s.eta_sum != nullptr, pk.plan.stream == 1);
     if (!fn) return cudaErrorInvalidValue;
     void *args[] = {&A};
     return cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan.threads), args, pk.plan.smem, stream);

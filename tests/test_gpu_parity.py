@@ -339,6 +339,30 @@ def test_streaming_layout_with_freshwater_and_step_mean(sesw):
     assert _maxabs(eb - eb_ref) <= ETA_ABS_TOL
 
 
+def test_streaming_without_the_index_cache(sesw):
+    """Patches that fit the streaming kernel's shared memory only without the slots' corner indices
+    (an 816k-vertex channel at the benchmark channel's resolution, one patch per block) read the
+    indices from L2 every substep; 2 steps against the oracle."""
+    case = I.channel_case(nx=1200, ny=680, Lx=4000e3 * 1200 / 588, Ly=2000e3 * 680 / 340, nsteps=2)
+    with sesw.Subcycle() as s:
+        s.sesw_set_mode(PERSISTENT)
+        s.sesw_mesh_upload(case.mesh)
+        info = s.sesw_get_info()
+        assert info["streamed"] == 2, info
+        s.sesw_set_params(case.params)
+        s.sesw_set_forcing(case.R)
+        s.sesw_set_state(case.eta0, case.U0)
+        s.sesw_advance(2)
+        assert s.sesw_status() == sesw.SESW_OK
+        got = s.sesw_get_state()
+    ref = orc.OracleMesh(case.mesh).advance(case.R, case.params, 2, case.eta0, case.U0)[:3]
+    r32 = orc.OracleMesh(case.mesh, orc.lib_fp32()).advance(case.R, case.params, 2, case.eta0, case.U0)[:3]
+    for k, name in enumerate(("eta", "U", "<<U>>")):
+        tol = ENVELOPE_FACTOR * _maxabs(r32[k] - ref[k]) + ULP_FLOOR * _maxabs(ref[k])
+        assert _maxabs(got[k] - ref[k]) <= tol, name
+    assert _maxabs(got[0] - ref[0]) <= ETA_ABS_TOL
+
+
 def test_contexts_with_different_layouts_coexist(sesw):
     """Kernel attributes are process-wide: a context with large patches keeps working after a
     context with small patches has been set up (and the other way round)."""

@@ -176,6 +176,17 @@ def test_sesm_streamed_on_the_sphere_matches_oracle(S):
     _check(case, coef, got, 2, "sphere8 SESM streamed")
 
 
+def test_sesm_streamed_without_the_index_cache(S):
+    """Patches that fit the streaming SESM kernel's shared memory only without the slots' corner
+    indices (a 704k-vertex channel at the benchmark channel's resolution) read the indices from L2
+    every substep; 2 steps against the oracle."""
+    case = I.channel_case(nx=1100, ny=640, Lx=4000e3 * 1100 / 588, Ly=2000e3 * 640 / 340, nsteps=2)
+    coef = _sesm(case)
+    (got, info) = _run(S, case, 2, PERSISTENT)
+    assert info["mode"] == PERSISTENT and info["streamed"] == 2, info
+    _check(case, coef, got, 2, "channel 704k SESM streamed, indices from L2")
+
+
 def test_sesm_batch_mixes_streamed_and_cached_packs(S):
     """One SESM step launching different kernels per pack: the level-8 sphere (streamed) batched
     with small basins (on-chip SESM kernel). Every basin against the oracle."""
