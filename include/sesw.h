@@ -204,12 +204,32 @@ int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
  *                         elevation with neighbouring blocks as tagged words through L2
  *                         with bounded waits (a wait that gives up sets SESW_ETIMEOUT)
  *   SESW_MODE_AUTO        persistent when the mesh fits it, else graph (default)
- * Results are the same to FP32 rounding; the summation order per vertex depends on
- * the patch layout. Takes effect at the next mesh upload. */
+ * Both modes, every patch size and every batch give bitwise the same results for the SE
+ * scheme: each triangle's update is one fixed sequence of FP32 roundings, and each vertex
+ * adds its incident triangles' contributions in the order of the caller's triangle ids.
+ * Takes effect at the next mesh upload. */
 #define SESW_MODE_AUTO       0
 #define SESW_MODE_GRAPH      1
 #define SESW_MODE_PERSISTENT 2
 int sesw_set_mode(sesw_ctx *ctx, int32_t mode);
+
+/* Persistent mode: which kernel form each pack (one cooperative launch) runs.
+ *   SESW_FORM_AUTO             the register form where a thread holds at most 6 slots, else
+ *                              the streaming form (default)
+ *   SESW_FORM_REGISTERS        transports and sums in registers, static slot data in shared
+ *                              memory when it fits (sesw_info.streamed = 0)
+ *   SESW_FORM_STREAM           transports, sums and static data read from L2 slot by slot,
+ *                              corner indices in shared memory when they fit (streamed = 1, else 2)
+ *   SESW_FORM_STREAM_UNCACHED  the streaming form with the corner indices read from L2 too
+ *                              (streamed = 2)
+ * All forms give bitwise the same results (the per-vertex sums run in a fixed order). A mesh
+ * that does not fit the requested form falls back to graph mode (SESW_MODE_AUTO) or is refused
+ * (SESW_MODE_PERSISTENT). Takes effect at the next mesh upload. */
+#define SESW_FORM_AUTO            0
+#define SESW_FORM_REGISTERS       1
+#define SESW_FORM_STREAM          2
+#define SESW_FORM_STREAM_UNCACHED 3
+int sesw_set_persistent_form(sesw_ctx *ctx, int32_t form);
 
 /* Persistent mode: resident blocks (patches) per SM, 1, 2 or 4; 0 (default) tries 2
  * and falls back to 1. Takes effect at the next mesh upload. */
@@ -336,9 +356,9 @@ int sesw_diagnostics_batch(sesw_ctx *ctx, double *volume, double *energy);
  * area_v and eta [nv], area_e and h_e (water depth H of each triangle, > 0) [ne],
  * U [ne][2], out [2]; g > 0; cuda_stream a cudaStream_t (NULL = legacy default).
  * Work is enqueued on the stream and the call returns without waiting.
- * Limits: 0 <= nv, ne <= SESW_NOALLOC_MAX_ITEMS (33,554,432); larger sizes and NULL
- * pointers return SESW_EINVAL before anything is launched; a failed launch returns
- * SESW_ECUDA.
+ * Limits: 0 <= nv, ne <= SESW_NOALLOC_MAX_ITEMS (33,554,432); larger sizes, NULL
+ * pointers and a g that is not positive return SESW_EINVAL before anything is launched
+ * (the device data, such as h_e > 0, is not checked); a failed launch returns SESW_ECUDA.
  * Scratch: one fixed 128 KiB array of partial sums (SESW_NOALLOC_MAX_CHUNKS pairs of
  * doubles) that lives in the library's device memory on every GPU that loads the
  * library, until the process exits. Nothing is allocated or freed by the call. Every
@@ -346,7 +366,9 @@ int sesw_diagnostics_batch(sesw_ctx *ctx, double *volume, double *energy);
  * start at zero); calls that overlap on the GPU (several streams or threads at once)
  * race on it and must be ordered by the caller.
  * The first call on a device looks up the array's device address with that device
- * current (cudaGetSymbolAddress); make that first call before any stream capture. */
+ * current (cudaGetSymbolAddress) and keeps it for the rest of the process; make that first
+ * call before any stream capture, and do not call this after a cudaDeviceReset of the
+ * device in the same process (the kept address would be stale). */
 #define SESW_NOALLOC_MAX_CHUNKS 8192
 #define SESW_NOALLOC_MAX_ITEMS (SESW_NOALLOC_MAX_CHUNKS * 4096)
 int sesw_diagnostics_noalloc(int64_t nv, int64_t ne, const double *area_v, const double *eta,

@@ -334,7 +334,10 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
         out.slot_c[s] = make_float4((float)A[e], (float)h0, (float)m.coriolis[e], 0.0f);
     }
 
-    // ---- per-vertex incidence (local slot, corner), ordered by vertex then slot
+    // ---- per-vertex incidence (local slot, corner), grouped by vertex. Within a vertex the
+    // entries are ordered by the caller's element id, so that the sum of a vertex's corner
+    // fluxes runs in the same order whatever the patch layout: a mesh then gives bitwise
+    // the same result in every execution mode, patch size and batch it is uploaded in.
     {
         std::vector<int> cnt(nv + 1, 0);
         for (int p = 0; p < npatch; p++)
@@ -356,6 +359,13 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
                     if (vpatch[cv[k]] == p)
                         out.vcsr[fill[cv[k]]++] = ((uint32_t)(s - patch_slot[p]) << 2) | (uint32_t)k;
             }
+        auto caller_elem = [&](int v, uint32_t q) {
+            const int w = out.slot_v[patch_slot[vpatch[v]] + (int)(q >> 2)].w;
+            return eperm[w >= 0 ? w : -1 - w];
+        };
+        for (int v = 0; v < nv; v++)
+            std::sort(out.vcsr.begin() + cnt[v], out.vcsr.begin() + cnt[v + 1],
+                      [&](uint32_t a, uint32_t b) { return caller_elem(v, a) < caller_elem(v, b); });
     }
 
     out.inv_av.resize(nv);

@@ -334,6 +334,15 @@ int sesw_set_blocks_per_sm(sesw_ctx *c, int32_t k)
     return SESW_OK;
 }
 
+int sesw_set_persistent_form(sesw_ctx *c, int32_t form)
+{
+    if (!c) return SESW_EINVAL;
+    if (form < SESW_FORM_AUTO || form > SESW_FORM_STREAM_UNCACHED)
+        return fail(c, SESW_EINVAL, "form must be one of SESW_FORM_AUTO, _REGISTERS, _STREAM, _STREAM_UNCACHED");
+    c->form = form;
+    return SESW_OK;
+}
+
 int sesw_set_mode(sesw_ctx *c, int32_t mode)
 {
     if (!c) return SESW_EINVAL;
@@ -389,7 +398,7 @@ static int persistent_patch_sizes(const sesw_mesh *meshes, int n, int nblk, int 
 // patches are packed separately (first fit, largest first), so that a pack's plan is not
 // set by a larger class; each pack gets the plans of its largest patch. Leaves `packs`
 // empty when some pack does not fit the persistent kernel.
-static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int base, int nblk, int bps,
+static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int base, int nblk, int bps, int form,
                        std::vector<sesw::PackPlan> &packs, std::vector<std::vector<int>> &pack_basins)
 {
     packs.clear();
@@ -426,13 +435,19 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                     pk.mx.local = std::max(pk.mx.local, nvq + nhq);
                     pk.mx.csr = std::max(pk.mx.csr, hm.vcsr_off[hm.patch_v[q + 1]] - hm.vcsr_off[hm.patch_v[q]]);
                 }
-            pk.plan = sesw::persistent_plan(pk.mx, bps);
-            // patches whose state does not fit in registers without heavy spills (8 or more
-            // slots per thread) stream it from global memory; measured on the sphere at
-            // level 8 this is faster, and with 6 slots per thread the register kernel is
-            if (pk.plan.slots_per_thread == 0 || pk.plan.slots_per_thread >= 8) {
-                const sesw::PersistentPlan st = sesw::persistent_plan_stream(pk.mx, bps);
-                if (st.slots_per_thread > 0) pk.plan = st;
+            const bool streamed = form == SESW_FORM_STREAM || form == SESW_FORM_STREAM_UNCACHED;
+            const int idx_mode = form == SESW_FORM_STREAM_UNCACHED ? 0 : -1;
+            if (streamed) {
+                pk.plan = sesw::persistent_plan_stream(pk.mx, bps, idx_mode);
+            } else {
+                pk.plan = sesw::persistent_plan(pk.mx, bps);
+                // patches whose state does not fit in registers without heavy spills (8 or more
+                // slots per thread) stream it from global memory; measured on the sphere at
+                // level 8 this is faster, and with 6 slots per thread the register kernel is
+                if (form == SESW_FORM_AUTO && (pk.plan.slots_per_thread == 0 || pk.plan.slots_per_thread >= 8)) {
+                    const sesw::PersistentPlan st = sesw::persistent_plan_stream(pk.mx, bps);
+                    if (st.slots_per_thread > 0) pk.plan = st;
+                }
             }
             if (pk.plan.slots_per_thread == 0) {
                 packs.clear();
@@ -440,8 +455,13 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                 return;
             }
             pk.plan.blocks_per_sm = bps;
-            pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, bps);
-            if (pk.plan_sesm.slots_per_thread == 0) pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, bps);
+            if (streamed) {
+                pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, bps, idx_mode);
+            } else {
+                pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, bps);
+                if (form == SESW_FORM_AUTO && pk.plan_sesm.slots_per_thread == 0)
+                    pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, bps);
+            }
             packs.push_back(pk);
             pack_basins.push_back(bn);
         }
@@ -480,7 +500,8 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
                 const int base = persistent_patch_sizes(meshes, n, nblk, bps, pv);
                 rc = prepare_parts(c, meshes, n, pv, hm, err);
                 if (rc != SESW_OK) return fail(c, rc, err);
-                if (sesw::build_halos(hm, err) == SESW_OK) make_packs(hm, pv, base, nblk, bps, packs, pack_basins);
+                if (sesw::build_halos(hm, err) == SESW_OK)
+                    make_packs(hm, pv, base, nblk, bps, c->form, packs, pack_basins);
             }
             if (!packs.empty()) {
                 plan = packs[0].plan;
@@ -540,6 +561,8 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     TRY(upload(c, &d.inv_av, hm.inv_av, "inv_av"));
     TRY(upload(c, &d.h0_v, hm.h0_v, "h0_v"));
     TRY(upload(c, &d.area_v, hm.area_v, "area_v"));
+    TRY(upload(c, &d.area_e, hm.area_e, "area_e"));
+    TRY(upload(c, &d.h0_e, hm.h0_e, "h0_e"));
     TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
     TRY(zalloc(c, &d.patch_dt, hm.npatch, "patch_dt"));

@@ -19,6 +19,90 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
     lo = __fadd_rn(lo, err);
 }
 
+// Element update of one slot in the dissipative forward-backward substep (Eq. 4.10, first
+// row) and the theta-weighted transport that the continuity row and the time mean of
+// Eq. (4.12) use. Every SE kernel calls this one function, and its roundings are spelled
+// out, so that the same inputs give bitwise the same transport and flux whichever kernel
+// or launch layout computes them.
+//   e0, e1, e2  corner elevations; grad eta = (e0 - e2) dphi0 + (e1 - e2) dphi1
+//   g           (dphi0/dx, dphi0/dy, dphi1/dx, dphi1/dy)
+//   gH0         g H0_e; NONLIN adds g (e0 + e1 + e2) / 3 (H = H0 + eta)
+//   aa, inv     f dt / 2 and 1 / (1 + aa^2) (Crank-Nicolson Coriolis)
+//   r           frozen forcing R (m^2/s^2)
+//   u           in: U^m, out: U^{m+1}
+// Returns F = (1 + theta) U^{m+1} - theta U^m.
+template <int NONLIN>
+__device__ __forceinline__ float2 se_transport(float e0, float e1, float e2, float4 g, float gH0, float gconst,
+                                               float aa, float inv, float dt, float2 r, float one_p_theta,
+                                               float theta, float2 &u)
+{
+    const float d0 = __fsub_rn(e0, e2), d1 = __fsub_rn(e1, e2);
+    const float gx = __fmaf_rn(d1, g.z, __fmul_rn(d0, g.x));
+    const float gy = __fmaf_rn(d1, g.w, __fmul_rn(d0, g.y));
+    float gH = gH0;
+    if (NONLIN) gH = __fmaf_rn(gconst, __fmul_rn(__fadd_rn(__fadd_rn(e0, e1), e2), 1.0f / 3.0f), gH0);
+    const float rx = __fmaf_rn(dt, __fmaf_rn(-gH, gx, r.x), __fmaf_rn(aa, u.y, u.x));
+    const float ry = __fmaf_rn(dt, __fmaf_rn(-gH, gy, r.y), __fmaf_rn(-aa, u.x, u.y));
+    const float nx = __fmul_rn(__fmaf_rn(aa, ry, rx), inv);
+    const float ny = __fmul_rn(__fmaf_rn(-aa, rx, ry), inv);
+    const float2 F = make_float2(__fmaf_rn(one_p_theta, nx, __fmul_rn(-theta, u.x)),
+                                 __fmaf_rn(one_p_theta, ny, __fmul_rn(-theta, u.y)));
+    u = make_float2(nx, ny);
+    return F;
+}
+
+// Contributions of the transport F of a triangle to the median-dual cells of its three
+// corners: c_k = w F . dphi_k with w = dt A_e (k = 0, 1), c_2 = -(c_0 + c_1).
+__device__ __forceinline__ void corner_fluxes(float2 F, float4 g, float w, float *out3)
+{
+    const float c0 = __fmul_rn(w, __fmaf_rn(F.y, g.y, __fmul_rn(F.x, g.x)));
+    const float c1 = __fmul_rn(w, __fmaf_rn(F.y, g.w, __fmul_rn(F.x, g.z)));
+    out3[0] = c0;
+    out3[1] = c1;
+    out3[2] = -__fadd_rn(c0, c1);
+}
+
+// The vertex update of Eq. (4.10), second row: eta + (sum of the corner contributions,
+// added in the vertex's incidence order) / A_v.
+__device__ __forceinline__ float vertex_eta(float eta, float sum, float inv_area)
+{
+    return __fmaf_rn(sum, inv_area, eta);
+}
+
+// The SESM substep (Eqs. 4.7-4.8) in one form for every kernel, with its roundings
+// spelled out like se_transport's.
+// Momentum: U^m = U^{m-1} + dt (-f e_z x U_AB^{m-1} - g H_AM grad(eta_AM) + R), from the
+// corner values of eta_AM; H_AM = H0_e (+ the corner mean of eta_AM with NONLIN).
+template <int NONLIN>
+__device__ __forceinline__ float2 sesm_momentum(float e0, float e1, float e2, float4 g, float H0, float gconst,
+                                                float f, float dt, float2 r, float2 u1, float2 uab)
+{
+    const float d0 = __fsub_rn(e0, e2), d1 = __fsub_rn(e1, e2);
+    const float gx = __fmaf_rn(d1, g.z, __fmul_rn(d0, g.x));
+    const float gy = __fmaf_rn(d1, g.w, __fmul_rn(d0, g.y));
+    float H = H0;
+    if (NONLIN) H = __fadd_rn(H0, __fmul_rn(__fadd_rn(__fadd_rn(e0, e1), e2), 1.0f / 3.0f));
+    const float gH = __fmul_rn(gconst, H);
+    // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
+    const float tx = __fadd_rn(__fmaf_rn(-gH, gx, __fmul_rn(f, uab.y)), r.x);
+    const float ty = __fadd_rn(__fmaf_rn(-gH, gy, __fmul_rn(-f, uab.x)), r.y);
+    return make_float2(__fmaf_rn(dt, tx, u1.x), __fmaf_rn(dt, ty, u1.y));
+}
+
+// AB3 transport ab0 U^m + ab1 U^{m-1} + ab2 U^{m-2} (Eq. 4.7).
+__device__ __forceinline__ float2 sesm_ab3(float2 u0, float2 ua, float2 ub, float ab0, float ab1, float ab2)
+{
+    return make_float2(__fmaf_rn(ab2, ub.x, __fmaf_rn(ab1, ua.x, __fmul_rn(ab0, u0.x))),
+                       __fmaf_rn(ab2, ub.y, __fmaf_rn(ab1, ua.y, __fmul_rn(ab0, u0.y))));
+}
+
+// AM4 elevation am0 eta^{m+1} + am1 eta^m + am2 eta^{m-1} + am3 eta^{m-2} (Eq. 4.7).
+__device__ __forceinline__ float sesm_am4(float e, float e1, float e2, float e3, float am0, float am1, float am2,
+                                          float am3)
+{
+    return __fmaf_rn(am3, e3, __fmaf_rn(am2, e2, __fmaf_rn(am1, e1, __fmul_rn(am0, e))));
+}
+
 // The device's opt-in shared-memory limit per block (0 when it cannot be read).
 int optin_smem();
 

@@ -107,6 +107,8 @@ struct DevMesh {
     float *inv_av = nullptr;
     float *h0_v = nullptr;
     double *area_v = nullptr;
+    double *area_e = nullptr;      // FP64 element area and rest depth (new element order), for the
+    double *h0_e = nullptr;        // FP64 diagnostics
     int *vperm = nullptr;
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
@@ -256,13 +258,14 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
                               const std::vector<PackPlan> &packs, cudaStream_t stream);
 // The SESM scheme for patches too large for its on-chip state (k_persistent_sesm_stream):
 // two more slot arrays (DevState::U_x) hold U^{m-2} and U_AB^{m-1}.
-PersistentPlan persistent_plan_sesm_stream(const PatchMax &mx, int blocks_per_sm);
+// idx_mode: -1 keeps the slots' corner indices in shared memory when they fit, 0 never.
+PersistentPlan persistent_plan_sesm_stream(const PatchMax &mx, int blocks_per_sm, int idx_mode = -1);
 cudaError_t persistent_prepare_sesm_stream(const PersistentPlan &plan);
 cudaError_t launch_persistent_sesm_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M,
                                                int parity, const PackPlan &pk, int pack_index, cudaStream_t stream);
 // Patches too large for the on-chip state (k_persistent_stream): transport, sums and
 // static data stay in global memory; only the elevation and the fluxes are on chip.
-PersistentPlan persistent_plan_stream(const PatchMax &mx, int blocks_per_sm);
+PersistentPlan persistent_plan_stream(const PatchMax &mx, int blocks_per_sm, int idx_mode = -1);
 cudaError_t persistent_prepare_stream(const PersistentPlan &plan);
 cudaError_t launch_persistent_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                                           const PackPlan &pk, int pack_index, cudaStream_t stream);
@@ -301,6 +304,7 @@ struct sesw_ctx {
     int block_threads = 256;
     int mode_req = SESW_MODE_AUTO, mode = SESW_MODE_GRAPH;
     int blocks_per_sm = 0;         // persistent mode; 0 = try 2, then 1
+    int form = SESW_FORM_AUTO;     // persistent mode: which kernel a pack runs (sesw_set_persistent_form)
     sesw::PersistentPlan plan;
     sesw::PersistentPlan plan_sesm;   // the SESM scheme's plan (empty: graph mode only)
     std::vector<sesw::PackPlan> packs;   // persistent mode: the launches of a step

@@ -123,11 +123,11 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
 {
     extern __shared__ float sflux[];
     const int p = blockIdx.x;
-    const float dt = patch_dt[p], half_dt = 0.5f * dt;
+    const float dt = patch_dt[p], half_dt = __fmul_rn(0.5f, dt);
     const int s0 = patch_slot[p];
     const int n = patch_slot[p + 1] - s0;
     const int nown = patch_own[p];
-    const float one_p_theta = 1.0f + a.theta;
+    const float one_p_theta = __fadd_rn(1.0f, a.theta);
 
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int s = s0 + i;
@@ -137,12 +137,9 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
         float2 r = R[s];
         const float2 u = U_in[s];
         const float e0 = eta_in[v.x], e1 = eta_in[v.y], e2 = eta_in[v.z];
-        const float d0 = e0 - e2, d1 = e1 - e2;
-        const float gx = d0 * g.x + d1 * g.z;
-        const float gy = d0 * g.y + d1 * g.w;
-        float H = c.y;
-        if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
         if (VISC) {
+            float H = c.y;
+            if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
             const float ev[3] = {e0, e1, e2};
             const float2 V = visc_of<VISC == 2>(s, H, u, ev, c.x, vis.T, U_in, eta_in, vis.va);
             if (vis.start) {
@@ -152,29 +149,20 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
                 r = make_float2(r.x + (V.x - z.x), r.y + (V.y - z.y));
             }
         }
-        const float gH = a.g * H;
-        const float aa = c.z * half_dt;
-        const float rx = u.x + aa * u.y + dt * (r.x - gH * gx);
-        const float ry = u.y - aa * u.x + dt * (r.y - gH * gy);
-        const float inv = 1.0f / (1.0f + aa * aa);
-        const float nx = (rx + aa * ry) * inv;
-        const float ny = (ry - aa * rx) * inv;
-        U_out[s] = make_float2(nx, ny);
-        const float fx = one_p_theta * nx - a.theta * u.x;
-        const float fy = one_p_theta * ny - a.theta * u.y;
+        const float aa = __fmul_rn(c.z, half_dt);
+        const float inv = __frcp_rn(__fmaf_rn(aa, aa, 1.0f));
+        float2 un = u;
+        const float2 F = se_transport<NONLIN>(e0, e1, e2, g, __fmul_rn(a.g, c.y), a.g, aa, inv, dt, r, one_p_theta,
+                                              a.theta, un);
+        U_out[s] = un;
         if (i < nown) {
             float2 hi = Shi[s], lo = Slo[s];
-            two_sum_acc(hi.x, lo.x, fx);
-            two_sum_acc(hi.y, lo.y, fy);
+            two_sum_acc(hi.x, lo.x, F.x);
+            two_sum_acc(hi.y, lo.y, F.y);
             Shi[s] = hi;
             Slo[s] = lo;
         }
-        const float w = dt * c.x;
-        const float c0 = w * (fx * g.x + fy * g.y);
-        const float c1 = w * (fx * g.z + fy * g.w);
-        sflux[3 * i + 0] = c0;
-        sflux[3 * i + 1] = c1;
-        sflux[3 * i + 2] = -(c0 + c1);
+        corner_fluxes(F, g, __fmul_rn(dt, c.x), sflux + 3 * i);
     }
     __syncthreads();
 
@@ -187,8 +175,8 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
             const uint32_t q = vcsr[k];
             sum += sflux[3 * (q >> 2) + (q & 3u)];
         }
-        float e = eta_in[v] + sum * inv_av[v];
-        if (W) e -= dt * W[v];
+        float e = vertex_eta(eta_in[v], sum, inv_av[v]);
+        if (W) e = __fmaf_rn(-dt, W[v], e);
         if (eta_sum) eta_sum[v] += eta_in[v];     // sum of eta^0 .. eta^{M-1} (time mean of the step)
         eta_out[v] = e;
         bad |= !(fabsf(e) <= a.eta_bound);
@@ -238,42 +226,27 @@ k_sesm(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 
         if (L.update) {
             const float4 c = sc[s];
             const float2 u3 = L.u3[s], r = R[s];
-            const float abx = a.ab0 * u1.x + a.ab1 * u2.x + a.ab2 * u3.x;
-            const float aby = a.ab0 * u1.y + a.ab1 * u2.y + a.ab2 * u3.y;
+            const float2 uab = sesm_ab3(u1, u2, u3, a.ab0, a.ab1, a.ab2);
             float em[3];
             const int vv[3] = {v.x, v.y, v.z};
 #pragma unroll
             for (int k = 0; k < 3; k++)
-                em[k] = a.am0 * L.e0[vv[k]] + a.am1 * L.e1[vv[k]] + a.am2 * L.e2[vv[k]] + a.am3 * L.e3[vv[k]];
-            const float d0 = em[0] - em[2], d1 = em[1] - em[2];
-            const float gx = d0 * g.x + d1 * g.z;
-            const float gy = d0 * g.y + d1 * g.w;
-            float H = c.y;
-            if (NONLIN) H += (em[0] + em[1] + em[2]) * (1.0f / 3.0f);
-            const float gH = a.g * H;
-            // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
-            u0.x = u1.x + dt * (c.z * aby - gH * gx + r.x);
-            u0.y = u1.y + dt * (-c.z * abx - gH * gy + r.y);
+                em[k] = sesm_am4(L.e0[vv[k]], L.e1[vv[k]], L.e2[vv[k]], L.e3[vv[k]], a.am0, a.am1, a.am2, a.am3);
+            u0 = sesm_momentum<NONLIN>(em[0], em[1], em[2], g, c.y, a.g, c.z, dt, r, u1, uab);
             L.u0[s] = u0;
         } else {
             u0 = L.u0[s];
         }
         if (!L.vertex) continue;
-        const float fx = a.ab0 * u0.x + a.ab1 * u1.x + a.ab2 * u2.x;
-        const float fy = a.ab0 * u0.y + a.ab1 * u1.y + a.ab2 * u2.y;
+        const float2 F = sesm_ab3(u0, u1, u2, a.ab0, a.ab1, a.ab2);
         if (i < nown) {
             float2 hi = Shi[s], lo = Slo[s];
-            two_sum_acc(hi.x, lo.x, fx);
-            two_sum_acc(hi.y, lo.y, fy);
+            two_sum_acc(hi.x, lo.x, F.x);
+            two_sum_acc(hi.y, lo.y, F.y);
             Shi[s] = hi;
             Slo[s] = lo;
         }
-        const float w = dt * sc[s].x;
-        const float c0 = w * (fx * g.x + fy * g.y);
-        const float c1 = w * (fx * g.z + fy * g.w);
-        sflux[3 * i + 0] = c0;
-        sflux[3 * i + 1] = c1;
-        sflux[3 * i + 2] = -(c0 + c1);
+        corner_fluxes(F, g, __fmul_rn(dt, sc[s].x), sflux + 3 * i);
     }
     if (!L.vertex) return;
     __syncthreads();
@@ -286,8 +259,8 @@ k_sesm(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 
             const uint32_t q = vcsr[k];
             sum += sflux[3 * (q >> 2) + (q & 3u)];
         }
-        float e = L.e0[v] + sum * inv_av[v];
-        if (W) e -= dt * W[v];
+        float e = vertex_eta(L.e0[v], sum, inv_av[v]);
+        if (W) e = __fmaf_rn(-dt, W[v], e);
         L.enew[v] = e;
         bad |= !(fabsf(e) <= a.eta_bound);
     }
@@ -404,9 +377,9 @@ __device__ __forceinline__ void block_sum2(double &x, double &y, double (*sh)[N]
 // Per-block partial sums of volume and energy (FP64). Fixed grid and order, so the
 // result is reproducible run to run.
 __global__ void __launch_bounds__(kAuxThreads)
-k_diag_partial(const int4 *__restrict__ sv, const float4 *__restrict__ sc, const float2 *__restrict__ U,
-               const double *__restrict__ area_v, const float *__restrict__ eta, int nv, int nslot, double g,
-               int nonlinear_h, double *__restrict__ part)
+k_diag_partial(const int4 *__restrict__ sv, const double *__restrict__ area_e, const double *__restrict__ h0_e,
+               const float2 *__restrict__ U, const double *__restrict__ area_v, const float *__restrict__ eta, int nv,
+               int nslot, double g, int nonlinear_h, double *__restrict__ part)
 {
     __shared__ double sh[2][32];
     double vol = 0.0, en = 0.0;
@@ -419,11 +392,10 @@ k_diag_partial(const int4 *__restrict__ sv, const float4 *__restrict__ sc, const
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslot; s += stride) {
         const int4 c = sv[s];
         if (c.w < 0) continue;
-        const float4 k = sc[s];
-        double H = (double)k.y;
+        double H = h0_e[c.w];
         if (nonlinear_h) H += ((double)eta[c.x] + (double)eta[c.y] + (double)eta[c.z]) / 3.0;
         const float2 u = U[s];
-        en += (double)k.x * ((double)u.x * u.x + (double)u.y * u.y) / (2.0 * H);
+        en += area_e[c.w] * ((double)u.x * u.x + (double)u.y * u.y) / (2.0 * H);
     }
     block_sum2<32>(vol, en, sh);
     if (threadIdx.x == 0) {
@@ -435,8 +407,9 @@ k_diag_partial(const int4 *__restrict__ sv, const float4 *__restrict__ sc, const
 // One block per basin: volume and energy of its vertex and owned-slot ranges.
 __global__ void __launch_bounds__(kAuxThreads)
 k_diag_basins(const int *__restrict__ basin_v, const int *__restrict__ basin_slot, const int4 *__restrict__ sv,
-              const float4 *__restrict__ sc, const float2 *__restrict__ U, const double *__restrict__ area_v,
-              const float *__restrict__ eta, double g, int nonlinear_h, double *__restrict__ out)
+              const double *__restrict__ area_e, const double *__restrict__ h0_e, const float2 *__restrict__ U,
+              const double *__restrict__ area_v, const float *__restrict__ eta, double g, int nonlinear_h,
+              double *__restrict__ out)
 {
     __shared__ double sh[2][32];
     const int b = blockIdx.x;
@@ -449,11 +422,10 @@ k_diag_basins(const int *__restrict__ basin_v, const int *__restrict__ basin_slo
     for (int s = basin_slot[b] + threadIdx.x; s < basin_slot[b + 1]; s += blockDim.x) {
         const int4 c = sv[s];
         if (c.w < 0) continue;
-        const float4 k = sc[s];
-        double H = (double)k.y;
+        double H = h0_e[c.w];
         if (nonlinear_h) H += ((double)eta[c.x] + (double)eta[c.y] + (double)eta[c.z]) / 3.0;
         const float2 u = U[s];
-        en += (double)k.x * ((double)u.x * u.x + (double)u.y * u.y) / (2.0 * H);
+        en += area_e[c.w] * ((double)u.x * u.x + (double)u.y * u.y) / (2.0 * H);
     }
     block_sum2<32>(vol, en, sh);
     if (threadIdx.x == 0) {
@@ -649,8 +621,8 @@ cudaError_t launch_gather_state(const DevMesh &m, const DevState &s, int parity,
 cudaError_t launch_diagnostics_basins(const DevMesh &m, const DevState &s, const StepArgs &a, int parity,
                                       double *out, cudaStream_t stream)
 {
-    k_diag_basins<<<m.nbasin, kAuxThreads, 0, stream>>>(m.basin_v, m.basin_slot, m.slot_v, m.slot_c, s.U, m.area_v,
-                                                       s.eta[parity], a.g64, a.nonlinear_h, out);
+    k_diag_basins<<<m.nbasin, kAuxThreads, 0, stream>>>(m.basin_v, m.basin_slot, m.slot_v, m.area_e, m.h0_e, s.U,
+                                                       m.area_v, s.eta[parity], a.g64, a.nonlinear_h, out);
     return cudaGetLastError();
 }
 
@@ -666,8 +638,8 @@ int diagnostics_blocks(const DevMesh &m)
 cudaError_t launch_diagnostics(const DevMesh &m, const DevState &s, const StepArgs &a, int parity, int nblocks,
                                cudaStream_t stream)
 {
-    k_diag_partial<<<nblocks, kAuxThreads, 0, stream>>>(m.slot_v, m.slot_c, s.U, m.area_v, s.eta[parity], m.nv,
-                                                        m.nslot, a.g64, a.nonlinear_h, s.diag_part);
+    k_diag_partial<<<nblocks, kAuxThreads, 0, stream>>>(m.slot_v, m.area_e, m.h0_e, s.U, m.area_v, s.eta[parity],
+                                                        m.nv, m.nslot, a.g64, a.nonlinear_h, s.diag_part);
     k_diag_final<<<1, kAuxThreads, 0, stream>>>(s.diag_part, nblocks, s.diag_out);
     return cudaGetLastError();
 }

@@ -24,7 +24,8 @@ constexpr int64_t kItemsPerBlock = (int64_t)kThreads * kItemsPerThread;   // 409
 // Scratch: one (volume, energy) partial pair per chunk of 4096 items.
 static __device__ __align__(256) double g_partials[2 * SESW_NOALLOC_MAX_CHUNKS];
 
-// Host-side view of the scratch: its device address, looked up once per device.
+// Host-side view of the scratch: its device address, looked up once per device and kept
+// for the life of the process (a cudaDeviceReset would invalidate it).
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 double *g_scratch[kMaxDevices] = {nullptr};
@@ -101,7 +102,8 @@ extern "C" int sesw_diagnostics_noalloc(int64_t nv, int64_t ne, const double *ar
                                         const double *area_e, const double *h_e, const double *U, double g,
                                         double *out, void *cuda_stream)
 {
-    if (nv < 0 || ne < 0 || !out || (nv > 0 && (!area_v || !eta)) || (ne > 0 && (!area_e || !h_e || !U)))
+    if (nv < 0 || ne < 0 || !out || !(g > 0.0) || (nv > 0 && (!area_v || !eta)) ||
+        (ne > 0 && (!area_e || !h_e || !U)))
         return SESW_EINVAL;
     const int64_t n = nv > ne ? nv : ne;
     const int64_t nchunks = (n + kItemsPerBlock - 1) / kItemsPerBlock;

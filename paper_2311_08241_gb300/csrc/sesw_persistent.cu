@@ -33,34 +33,18 @@ __device__ __forceinline__ void element_update(const float e0, const float e1, c
                                                float2 &slo, bool owned, float *flux3, float theta,
                                                float one_p_theta, float dt, float gconst)
 {
-    const float d0 = e0 - e2, d1 = e1 - e2;
-    const float gx = d0 * g.x + d1 * g.z;
-    const float gy = d0 * g.y + d1 * g.w;
-    float gH = coef.y;
-    if (NONLIN) gH += gconst * ((e0 + e1 + e2) * (1.0f / 3.0f));
-    const float aa = coef.z;
-    const float rx = u.x + aa * u.y + dt * (r.x - gH * gx);
-    const float ry = u.y - aa * u.x + dt * (r.y - gH * gy);
-    const float nx = (rx + aa * ry) * coef.w;
-    const float ny = (ry - aa * rx) * coef.w;
-    const float fx = one_p_theta * nx - theta * u.x;
-    const float fy = one_p_theta * ny - theta * u.y;
-    u = make_float2(nx, ny);
+    const float2 F = se_transport<NONLIN>(e0, e1, e2, g, coef.y, gconst, coef.z, coef.w, dt, r, one_p_theta, theta, u);
     if (owned) {
-        two_sum_acc(shi.x, slo.x, fx);
-        two_sum_acc(shi.y, slo.y, fy);
+        two_sum_acc(shi.x, slo.x, F.x);
+        two_sum_acc(shi.y, slo.y, F.y);
     }
-    const float c0 = coef.x * (fx * g.x + fy * g.y);
-    const float c1 = coef.x * (fx * g.z + fy * g.w);
-    flux3[0] = c0;
-    flux3[1] = c1;
-    flux3[2] = -(c0 + c1);
+    corner_fluxes(F, g, coef.x, flux3);
 }
 
 __device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a, float dt)
 {
-    const float aa = c.z * (0.5f * dt);
-    return make_float4(dt * c.x, a.g * c.y, aa, 1.0f / (1.0f + aa * aa));
+    const float aa = __fmul_rn(c.z, __fmul_rn(0.5f, dt));
+    return make_float4(__fmul_rn(dt, c.x), __fmul_rn(a.g, c.y), aa, __frcp_rn(__fmaf_rn(aa, aa, 1.0f)));
 }
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set;
@@ -124,7 +108,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     }
     __syncthreads();
 
-    const float one_p_theta = 1.0f + a.theta;
+    const float one_p_theta = __fadd_rn(1.0f, a.theta);
     // Element update of the slots with local index in [lo, hi). Corner elevations of
     // own vertices come from shared memory; with `halo_src` set, those of halo vertices
     // are read from that exchange buffer with tag `tag`. Used for the first substep (all
@@ -284,9 +268,9 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                 }
                 inv = P.inv_av[v0 + i];
             }
-            float e = seta[i] + sum * inv;
+            float e = vertex_eta(seta[i], sum, inv);
             if (EXTRA) {
-                if (P.W) e -= dt * __ldg(P.W + v0 + i);
+                if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
                 if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
             }
             seta[i] = e;

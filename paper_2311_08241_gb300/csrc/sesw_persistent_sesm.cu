@@ -92,34 +92,20 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
 
     // U_AB of a slot, its flux contributions and (owned slots) the compensated sum
     auto transport = [&](int j, int i, float2 u0, float2 ua, float2 ub, float4 g, float area) {
-        const float fx = a.ab0 * u0.x + a.ab1 * ua.x + a.ab2 * ub.x;
-        const float fy = a.ab0 * u0.y + a.ab1 * ua.y + a.ab2 * ub.y;
+        const float2 F = sesm_ab3(u0, ua, ub, a.ab0, a.ab1, a.ab2);
         if (i < nown_s) {
-            two_sum_acc(shi[j].x, slo[j].x, fx);
-            two_sum_acc(shi[j].y, slo[j].y, fy);
+            two_sum_acc(shi[j].x, slo[j].x, F.x);
+            two_sum_acc(shi[j].y, slo[j].y, F.y);
         }
-        const float w = dt * area;
-        const float q0 = w * (fx * g.x + fy * g.y);
-        const float q1 = w * (fx * g.z + fy * g.w);
-        sflux[3 * i + 0] = q0;
-        sflux[3 * i + 1] = q1;
-        sflux[3 * i + 2] = -(q0 + q1);
-        uab[j] = make_float2(fx, fy);
+        corner_fluxes(F, g, __fmul_rn(dt, area), sflux + 3 * i);
+        uab[j] = F;
     };
     bool ok = true;
     // momentum update of slot i (round j) from its corner eta_AM
     auto slot = [&](int j, int i, float e0, float e1, float e2, bool vertex) {
         const float4 g = s_g[i], c = s_c[i];
         const float2 r = s_r[i];
-        const float d0 = e0 - e2, d1 = e1 - e2;
-        const float gx = d0 * g.x + d1 * g.z;
-        const float gy = d0 * g.y + d1 * g.w;
-        float H = c.y;
-        if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
-        const float gH = a.g * H;
-        float2 u0;
-        u0.x = u1[j].x + dt * (c.z * uab[j].y - gH * gx + r.x);
-        u0.y = u1[j].y + dt * (-c.z * uab[j].x - gH * gy + r.y);
+        const float2 u0 = sesm_momentum<NONLIN>(e0, e1, e2, g, c.y, a.g, c.z, dt, r, u1[j], uab[j]);
         if (vertex) transport(j, i, u0, u1[j], u2[j], g, c.x);
         u2[j] = u1[j];
         u1[j] = u0;
@@ -200,9 +186,9 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
                 float sum = 0.0f;
                 const int k1 = s_off[i + 1];
                 for (int q = s_off[i]; q < k1; q++) sum += sflux[s_csr[q]];
-                float e = eh0[k] + sum * s_inv[i];
-                if (P.W) e -= dt * __ldg(P.W + v0 + i);
-                const float em = a.am0 * e + a.am1 * eh0[k] + a.am2 * eh1[k] + a.am3 * eh2[k];
+                float e = vertex_eta(eh0[k], sum, s_inv[i]);
+                if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
+                const float em = sesm_am4(e, eh0[k], eh1[k], eh2[k], a.am0, a.am1, a.am2, a.am3);
                 eh2[k] = eh1[k];
                 eh1[k] = eh0[k];
                 eh0[k] = e;

@@ -31,26 +31,20 @@ __device__ __forceinline__ float2 sesm_transport(const QArgs &A, int s, int i, b
                                                  float2 ua, float2 ub, float4 g, float area, float dt, float *sflux)
 {
     const StepArgs &a = A.P.a;
-    const float fx = a.ab0 * u0.x + a.ab1 * ua.x + a.ab2 * ub.x;
-    const float fy = a.ab0 * u0.y + a.ab1 * ua.y + a.ab2 * ub.y;
+    const float2 F = sesm_ab3(u0, ua, ub, a.ab0, a.ab1, a.ab2);
     if (owned) {
         float2 hi = make_float2(0.0f, 0.0f), lo = hi;
         if (!first) {
             hi = A.Shi[s];
             lo = A.Slo[s];
         }
-        two_sum_acc(hi.x, lo.x, fx);
-        two_sum_acc(hi.y, lo.y, fy);
+        two_sum_acc(hi.x, lo.x, F.x);
+        two_sum_acc(hi.y, lo.y, F.y);
         A.Shi[s] = hi;
         A.Slo[s] = lo;
     }
-    const float w = dt * area;
-    const float q0 = w * (fx * g.x + fy * g.y);
-    const float q1 = w * (fx * g.z + fy * g.w);
-    sflux[3 * i + 0] = q0;
-    sflux[3 * i + 1] = q1;
-    sflux[3 * i + 2] = -(q0 + q1);
-    return make_float2(fx, fy);
+    corner_fluxes(F, g, __fmul_rn(dt, area), sflux + 3 * i);
+    return F;
 }
 
 // Momentum update of slot s (substep m >= 1) from its corner eta_AM, then (vertex) its
@@ -64,16 +58,7 @@ __device__ __forceinline__ void sesm_slot(const QArgs &A, int s, int i, bool own
     const float4 g = __ldg(P.sg + s), c = __ldg(P.sc + s);
     const float2 r = __ldg(P.R + s);
     const float2 u1 = P.U[s], u2 = A.U2[s], uab = A.UAB[s];
-    const float d0 = e0 - e2, d1 = e1 - e2;
-    const float gx = d0 * g.x + d1 * g.z;
-    const float gy = d0 * g.y + d1 * g.w;
-    float H = c.y;
-    if (NONLIN) H += (e0 + e1 + e2) * (1.0f / 3.0f);
-    const float gH = a.g * H;
-    // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
-    float2 u0;
-    u0.x = u1.x + dt * (c.z * uab.y - gH * gx + r.x);
-    u0.y = u1.y + dt * (-c.z * uab.x - gH * gy + r.y);
+    const float2 u0 = sesm_momentum<NONLIN>(e0, e1, e2, g, c.y, a.g, c.z, dt, r, u1, uab);
     if (vertex) {
         A.UAB[s] = sesm_transport(A, s, i, owned, false, u0, u1, u2, g, c.x, dt, sflux);
         A.U2[s] = u1;
@@ -170,9 +155,9 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
                 const uint32_t q = __ldg(P.vcsr + k);
                 sum += sflux[3 * (q >> 2) + (q & 3u)];
             }
-            float e = h0[i] + sum * __ldg(P.inv_av + v0 + i);
-            if (P.W) e -= dt * __ldg(P.W + v0 + i);
-            const float em = a.am0 * e + a.am1 * h0[i] + a.am2 * h1[i] + a.am3 * h2[i];
+            float e = vertex_eta(h0[i], sum, __ldg(P.inv_av + v0 + i));
+            if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
+            const float em = sesm_am4(e, h0[i], h1[i], h2[i], a.am0, a.am1, a.am2, a.am3);
             h2[i] = h1[i];
             h1[i] = h0[i];
             h0[i] = e;
@@ -217,7 +202,7 @@ size_t sesm_stream_smem(const PatchMax &m, int idx)
 
 }  // namespace
 
-PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm)
+PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm, int idx_mode)
 {
     PersistentPlan plan;
     int dev = 0, smem_optin = 0, smem_sm = 0;
@@ -234,10 +219,10 @@ PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm)
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
-    // the corner indices join the shared memory when they fit
+    // the corner indices join the shared memory when they fit (idx_mode 0: never)
     int idx = 1;
     size_t smem = sesm_stream_smem(m, 1);
-    if (smem > budget) {
+    if (smem > budget || idx_mode == 0) {
         idx = 0;
         smem = sesm_stream_smem(m, 0);
     }

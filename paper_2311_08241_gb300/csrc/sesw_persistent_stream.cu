@@ -38,32 +38,18 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
         shi = A.Shi[s];
         slo = A.Slo[s];
     }
-    const float d0 = e0 - e2, d1 = e1 - e2;
-    const float gx = d0 * g.x + d1 * g.z;
-    const float gy = d0 * g.y + d1 * g.w;
-    float gH = a.g * c.y;
-    if (NONLIN) gH += a.g * ((e0 + e1 + e2) * (1.0f / 3.0f));
-    const float aa = c.z * (0.5f * dt);
-    const float inv = 1.0f / (1.0f + aa * aa);
-    const float rx = u.x + aa * u.y + dt * (r.x - gH * gx);
-    const float ry = u.y - aa * u.x + dt * (r.y - gH * gy);
-    const float nx = (rx + aa * ry) * inv;
-    const float ny = (ry - aa * rx) * inv;
-    const float fx = (1.0f + a.theta) * nx - a.theta * u.x;
-    const float fy = (1.0f + a.theta) * ny - a.theta * u.y;
-    P.U[s] = make_float2(nx, ny);
+    const float aa = __fmul_rn(c.z, __fmul_rn(0.5f, dt));
+    const float inv = __frcp_rn(__fmaf_rn(aa, aa, 1.0f));
+    const float2 F = se_transport<NONLIN>(e0, e1, e2, g, __fmul_rn(a.g, c.y), a.g, aa, inv, dt, r,
+                                          __fadd_rn(1.0f, a.theta), a.theta, u);
+    P.U[s] = u;
     if (owned) {
-        two_sum_acc(shi.x, slo.x, fx);
-        two_sum_acc(shi.y, slo.y, fy);
+        two_sum_acc(shi.x, slo.x, F.x);
+        two_sum_acc(shi.y, slo.y, F.y);
         A.Shi[s] = shi;
         A.Slo[s] = slo;
     }
-    const float w = dt * c.x;
-    const float q0 = w * (fx * g.x + fy * g.y);
-    const float q1 = w * (fx * g.z + fy * g.w);
-    sflux[3 * i + 0] = q0;
-    sflux[3 * i + 1] = q1;
-    sflux[3 * i + 2] = -(q0 + q1);
+    corner_fluxes(F, g, __fmul_rn(dt, c.x), sflux + 3 * i);
 }
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set.
@@ -143,9 +129,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
                 const uint32_t q = __ldg(P.vcsr + k);
                 sum += sflux[3 * (q >> 2) + (q & 3u)];
             }
-            float e = seta[i] + sum * __ldg(P.inv_av + v0 + i);
+            float e = vertex_eta(seta[i], sum, __ldg(P.inv_av + v0 + i));
             if (EXTRA) {
-                if (P.W) e -= dt * __ldg(P.W + v0 + i);
+                if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
                 if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
             }
             seta[i] = e;
@@ -187,7 +173,7 @@ void *stream_kernel(int nonlin, int extra, int idx)
 
 }  // namespace
 
-PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm)
+PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm, int idx_mode)
 {
     PersistentPlan plan;
     int dev = 0, smem_optin = 0, smem_sm = 0;
@@ -205,10 +191,10 @@ PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm)
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
-    // the corner indices join the shared memory when they fit
+    // the corner indices join the shared memory when they fit (idx_mode 0: never)
     int idx = 1;
     size_t need = align16(L.total_plain) + sizeof(ushort4) * (size_t)m.slots;
-    if (need > budget) {
+    if (need > budget || idx_mode == 0) {
         idx = 0;
         need = L.total_plain;
     }

@@ -30,12 +30,17 @@ SESW_FLAG_TEST_FORCE_TIMEOUT = 2
 SESW_MODE_AUTO = 0
 SESW_MODE_GRAPH = 1
 SESW_MODE_PERSISTENT = 2
+SESW_FORM_AUTO = 0
+SESW_FORM_REGISTERS = 1
+SESW_FORM_STREAM = 2
+SESW_FORM_STREAM_UNCACHED = 3
 
 _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", -4: "SESW_ETIMEOUT",
           -5: "SESW_EUNSTABLE", -6: "SESW_ENOMEM"}
 
 # every symbol include/sesw.h declares
-EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_blocks_per_sm", "sesw_set_patch_vertices",
+EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_persistent_form", "sesw_set_blocks_per_sm",
+           "sesw_set_patch_vertices",
            "sesw_set_block_threads",
            "sesw_mesh_upload", "sesw_mesh_upload_batch", "sesw_set_params_batch", "sesw_diagnostics_batch",
            "sesw_set_params", "sesw_set_state", "sesw_set_forcing", "sesw_set_freshwater", "sesw_viscosity",
@@ -110,6 +115,7 @@ def load(build_if_missing: bool = True):
         L.sesw_set_block_threads.argtypes = [P, ctypes.c_int32]
         L.sesw_set_mode.argtypes = [P, ctypes.c_int32]
         L.sesw_set_blocks_per_sm.argtypes = [P, ctypes.c_int32]
+        L.sesw_set_persistent_form.argtypes = [P, ctypes.c_int32]
         L.sesw_mesh_upload.argtypes = [P, ctypes.POINTER(sesw_mesh)]
         L.sesw_set_params.argtypes = [P, ctypes.POINTER(sesw_params)]
         L.sesw_mesh_upload_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(sesw_mesh)]
@@ -253,6 +259,9 @@ class Subcycle:
 
     def sesw_set_blocks_per_sm(self, k: int):
         return self._check(self._L.sesw_set_blocks_per_sm(self._h, int(k)))
+
+    def sesw_set_persistent_form(self, form: int):
+        return self._check(self._L.sesw_set_persistent_form(self._h, int(form)))
 
     def sesw_set_block_threads(self, n: int):
         return self._check(self._L.sesw_set_block_threads(self._h, int(n)))
@@ -470,7 +479,17 @@ def sesw_mesh_check(mesh, patch_vertices: int = 512):
 def sesw_diagnostics_noalloc(nv, ne, area_v, eta, area_e, h_e, U, g, out, stream=None):
     """Allocation-free volume/energy of caller-held device arrays (torch float64 CUDA
     tensors); writes out[0:2] on the stream and returns the status code."""
+    import torch
+
     L = load()
+    dev = torch.cuda.current_device()
+    need = {"area_v": (area_v, int(nv)), "eta": (eta, int(nv)), "area_e": (area_e, int(ne)),
+            "h_e": (h_e, int(ne)), "U": (U, 2 * int(ne)), "out": (out, 2)}
+    for name, (t, n) in need.items():
+        if not (isinstance(t, torch.Tensor) and t.dtype == torch.float64 and t.is_contiguous()
+                and t.is_cuda and t.device.index == dev and t.numel() >= n):
+            raise TypeError(f"{name} must be a contiguous torch.float64 tensor on cuda:{dev} "
+                            f"with at least {n} elements")
     sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
     return L.sesw_diagnostics_noalloc(int(nv), int(ne), _ptr(area_v), _ptr(eta), _ptr(area_e), _ptr(h_e),
                                       _ptr(U), float(g), _ptr(out), sp)
@@ -488,11 +507,15 @@ def _as_f64(x):
     return x
 
 
-def run_case(case, nsteps=None, device=0, patch_vertices=None, mode=None):
+def run_case(case, nsteps=None, device=0, patch_vertices=None, mode=None, form=None, blocks_per_sm=None):
     """Upload a case, advance it and return (eta, U, Umean) as numpy arrays."""
     with Subcycle(device) as s:
         if mode is not None:
             s.sesw_set_mode(mode)
+        if form is not None:
+            s.sesw_set_persistent_form(form)
+        if blocks_per_sm is not None:
+            s.sesw_set_blocks_per_sm(blocks_per_sm)
         if patch_vertices:
             s.sesw_set_patch_vertices(patch_vertices)
         s.sesw_mesh_upload(case.mesh)
