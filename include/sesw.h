@@ -77,7 +77,20 @@ typedef void (*sesw_free_fn)(void *ptr, void *user);
  *              space-filling curve (a 2-D curve when every z is 0, else 3-D);
  *              NULL keeps the caller's order
  *   depth      [nv] rest depth H0 (m), > 0; H0 on a triangle is the corner mean
- *   coriolis   [ne] Coriolis parameter f (1/s) of each triangle */
+ *   coriolis   [ne] Coriolis parameter f (1/s) of each triangle
+ * Optional connectivity and areas. The library derives all of them from tri and xy (the
+ * edges from the triangles' sides, A_e as the area of the triangle's corners in its frame,
+ * A_v = sum of A_e/3 over the triangles at v, the median-dual cell of Eq. 4.10's divergence).
+ * A caller that keeps its own tables may pass them; each one given is checked against the
+ * derived one and a mismatch gives SESW_EINVAL naming the first bad item. NULL (or ned = 0
+ * with both edge pointers NULL) means "derive". Zero-initialise the struct so that fields
+ * a caller does not know of stay NULL.
+ *   ned        number of edges (each side shared by one or two triangles counts once)
+ *   edge_v     [ned][2] the edge's two vertices, any order
+ *   edge_e     [ned][2] the triangles on either side, any order, -1 for a coast side
+ *   area_v     [nv] median-dual cell areas (m^2), equal to the derived ones within 1e-12
+ *              relative
+ *   area_e     [ne] triangle areas (m^2), within 1e-12 relative */
 typedef struct sesw_mesh {
     int32_t nv;
     int32_t ne;
@@ -86,6 +99,11 @@ typedef struct sesw_mesh {
     const double *pos;
     const double *depth;
     const double *coriolis;
+    int32_t ned;
+    const int32_t *edge_v;
+    const int32_t *edge_e;
+    const double *area_v;
+    const double *area_e;
 } sesw_mesh;
 
 /* Scheme parameters (Eq. 4.10).
@@ -113,6 +131,10 @@ typedef struct sesw_mesh {
  *                SESM coefficients of Eq. (4.7); all zero selects beta = 0.281105 and, with
  *                chi = theta/2, gamma = 0.083 - 0.514 chi, zeta = 0.010 - 0.135 chi,
  *                delta = 2 chi + gamma + 2 zeta + 1/2 (Eqs. dp_4, dp_6)
+ *   precision    arithmetic of the substeps: SESW_PRECISION_FP32 (0, the only one): eta, U and
+ *                R in FP32 with the geometry rounded once from FP64, the time mean in a
+ *                compensated FP32 pair (about 48 significant bits), volume and energy in FP64;
+ *                any other value gives SESW_EINVAL
  *   visc_background, visc_flow
  *                barotropic viscous regularisation R_hV = div(H A grad(U/H)) of Eq.
  *                (viscosity_BT), added to the momentum forcing with its start-of-step value
@@ -130,6 +152,7 @@ typedef struct sesw_mesh {
  *                by 1 (reported in sesw_info.visc_number). */
 #define SESW_FLAG_NO_STABILITY_CHECK 1
 #define SESW_FLAG_TEST_FORCE_TIMEOUT 2
+#define SESW_PRECISION_FP32 0
 typedef struct sesw_params {
     double g;
     double theta;
@@ -145,6 +168,8 @@ typedef struct sesw_params {
     double sesm_zeta;
     double visc_background;
     double visc_flow;
+    int32_t precision;
+    int32_t reserved;        /* 0 */
 } sesw_params;
 
 /* Read-only facts about the uploaded mesh and its device layout. */

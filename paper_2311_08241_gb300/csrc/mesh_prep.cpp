@@ -161,6 +161,39 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
             koff[pair % (uint64_t)nv] += fabs(kab);
             i = j;
         }
+        // the caller's edge table, when given, must list exactly these edges with their triangles
+        if (m.edge_v || m.edge_e || m.ned != 0) {
+            if (!m.edge_v || !m.edge_e) { err = "edge_v and edge_e must be given together"; return SESW_EINVAL; }
+            std::vector<uint64_t> keys;
+            std::vector<std::pair<int, int>> sides;
+            for (size_t i = 0; i < he.size();) {
+                size_t j = i + 1;
+                while (j < he.size() && (he[j].key >> 1) == (he[i].key >> 1)) j++;
+                const int a = he[i].ek / 3, b = j - i == 2 ? he[i + 1].ek / 3 : -1;
+                keys.push_back(he[i].key >> 1);
+                sides.push_back({std::min(a, b), std::max(a, b)});
+                i = j;
+            }
+            if ((size_t)m.ned != keys.size()) {
+                fmt(err, "the edge table lists %lld edges; the triangles have %.0f", m.ned, (double)keys.size());
+                return SESW_EINVAL;
+            }
+            std::vector<char> seen(keys.size(), 0);
+            for (int k = 0; k < m.ned; k++) {
+                const int a = m.edge_v[2 * (size_t)k], b = m.edge_v[2 * (size_t)k + 1];
+                if (a < 0 || a >= nv || b < 0 || b >= nv || a == b) { fmt(err, "edge %lld has a bad vertex", k); return SESW_EINVAL; }
+                const uint64_t key = (uint64_t)std::min(a, b) * (uint64_t)nv + (uint64_t)std::max(a, b);
+                const size_t q = std::lower_bound(keys.begin(), keys.end(), key) - keys.begin();
+                if (q == keys.size() || keys[q] != key) { fmt(err, "edge %lld is not a side of any triangle", k); return SESW_EINVAL; }
+                if (seen[q]) { fmt(err, "edge %lld is listed twice", k); return SESW_EINVAL; }
+                seen[q] = 1;
+                const int ea = m.edge_e[2 * (size_t)k], eb = m.edge_e[2 * (size_t)k + 1];
+                if (std::make_pair(std::min(ea, eb), std::max(ea, eb)) != sides[q]) {
+                    fmt(err, "edge %lld does not list the triangles on its two sides", k);
+                    return SESW_EINVAL;
+                }
+            }
+        }
     }
 
     // ---- median-dual areas; every vertex must be a corner of some triangle
@@ -169,6 +202,20 @@ int prepare_mesh(const sesw_mesh &m, int patch_vertices, HostMesh &out, std::str
         for (int k = 0; k < 3; k++) Av[m.tri[3 * (size_t)e + k]] += A[e] / 3.0;
     for (int v = 0; v < nv; v++)
         if (!(Av[v] > 0.0)) { fmt(err, "vertex %lld is not a corner of any triangle", v); return SESW_EINVAL; }
+    // the caller's areas, when given, must be the derived ones
+    auto area_ok = [](double given, double want) { return fabs(given - want) <= 1e-12 * want; };
+    if (m.area_e)
+        for (int e = 0; e < ne; e++)
+            if (!area_ok(m.area_e[e], A[e])) {
+                fmt(err, "area_e[%lld] differs from the area of the triangle's corners (%.17g)", e, A[e]);
+                return SESW_EINVAL;
+            }
+    if (m.area_v)
+        for (int v = 0; v < nv; v++)
+            if (!area_ok(m.area_v[v], Av[v])) {
+                fmt(err, "area_v[%lld] differs from the median-dual area (%.17g)", v, Av[v]);
+                return SESW_EINVAL;
+            }
 
     // ---- vertex order along a Hilbert curve
     std::vector<int> vperm(nv);

@@ -6,6 +6,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <system_error>
+#include <thread>
 #include <cstdio>
 #include <new>
 #include <string>
@@ -352,17 +355,39 @@ int sesw_set_mode(sesw_ctx *c, int32_t mode)
     return SESW_OK;
 }
 
+// Prepare every mesh of a batch (each on its own, in parallel over the host's cores: the
+// preparation of one mesh touches nothing but its own input and output), then concatenate.
 static int prepare_parts(sesw_ctx *c, const sesw_mesh *meshes, int n, const std::vector<int> &pv, sesw::HostMesh &hm,
                          std::string &err)
 {
     std::vector<sesw::HostMesh> parts(n);
-    for (int b = 0; b < n; b++) {
-        int rc = sesw::prepare_mesh(meshes[b], pv[b], parts[b], err);
-        if (rc != SESW_OK) {
-            if (n > 1) err = "basin " + std::to_string(b) + ": " + err;
-            return rc;
+    std::vector<int> rcs(n, SESW_OK);
+    std::vector<std::string> errs(n);
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int b = next++; b < n; b = next++) {
+            try {
+                rcs[b] = sesw::prepare_mesh(meshes[b], pv[b], parts[b], errs[b]);
+            } catch (const std::bad_alloc &) {
+                rcs[b] = SESW_ENOMEM;
+                errs[b] = "host allocation failed during mesh preparation";
+            }
         }
+    };
+    const int nthreads = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    try {
+        for (int t = 1; t < nthreads; t++) pool.emplace_back(work);
+    } catch (const std::system_error &) {
+        // fewer threads: the ones that started and this one share the work
     }
+    work();
+    for (auto &t : pool) t.join();
+    for (int b = 0; b < n; b++)
+        if (rcs[b] != SESW_OK) {
+            err = n > 1 ? "basin " + std::to_string(b) + ": " + errs[b] : errs[b];
+            return rcs[b];
+        }
     if (n == 1)
         hm = std::move(parts[0]);
     else
@@ -752,6 +777,8 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
         if (q.M < 1 || q.M > 65536) return fail(c, SESW_EINVAL, "M must be in [1, 65536]");
         if (q.nonlinear_h != 0 && q.nonlinear_h != 1) return fail(c, SESW_EINVAL, "nonlinear_h must be 0 or 1");
         if (q.scheme != 0 && q.scheme != 1) return fail(c, SESW_EINVAL, "scheme must be 0 (SE) or 1 (SESM)");
+        if (q.precision != SESW_PRECISION_FP32)
+            return fail(c, SESW_EINVAL, "precision must be SESW_PRECISION_FP32 (FP32 substeps, FP64 diagnostics)");
         if (q.scheme == 1 && c->mode == SESW_MODE_PERSISTENT && c->plan_sesm.slots_per_thread == 0)
             return fail(c, SESW_EINVAL, "the patches of this mesh do not fit the persistent SESM kernel; set "
                                         "SESW_MODE_GRAPH before the upload");

@@ -27,6 +27,7 @@ SESW_HOST = 0
 SESW_DEVICE = 1
 SESW_FLAG_NO_STABILITY_CHECK = 1
 SESW_FLAG_TEST_FORCE_TIMEOUT = 2
+SESW_PRECISION_FP32 = 0
 SESW_MODE_AUTO = 0
 SESW_MODE_GRAPH = 1
 SESW_MODE_PERSISTENT = 2
@@ -65,7 +66,8 @@ class SeswError(RuntimeError):
 class sesw_mesh(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("ne", ctypes.c_int32), ("tri", ctypes.c_void_p),
                 ("xy", ctypes.c_void_p), ("pos", ctypes.c_void_p), ("depth", ctypes.c_void_p),
-                ("coriolis", ctypes.c_void_p)]
+                ("coriolis", ctypes.c_void_p), ("ned", ctypes.c_int32), ("edge_v", ctypes.c_void_p),
+                ("edge_e", ctypes.c_void_p), ("area_v", ctypes.c_void_p), ("area_e", ctypes.c_void_p)]
 
 
 class sesw_params(ctypes.Structure):
@@ -73,7 +75,8 @@ class sesw_params(ctypes.Structure):
                 ("M", ctypes.c_int32), ("nonlinear_h", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("eta_bound", ctypes.c_double), ("sesm_beta", ctypes.c_double),
                 ("sesm_delta", ctypes.c_double), ("sesm_gamma", ctypes.c_double), ("sesm_zeta", ctypes.c_double),
-                ("visc_background", ctypes.c_double), ("visc_flow", ctypes.c_double)]
+                ("visc_background", ctypes.c_double), ("visc_flow", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sesw_info(ctypes.Structure):
@@ -266,8 +269,8 @@ class Subcycle:
     def sesw_set_block_threads(self, n: int):
         return self._check(self._L.sesw_set_block_threads(self._h, int(n)))
 
-    def sesw_mesh_upload(self, mesh):
-        m, keep = _mesh_struct(mesh)
+    def sesw_mesh_upload(self, mesh, edges=None, areas=None):
+        m, keep = _mesh_struct(mesh, edges, areas)
         rc = self._check(self._L.sesw_mesh_upload(self._h, ctypes.byref(m)))
         del keep
         self.nv, self.ne = int(mesh.nv), int(mesh.ne)
@@ -449,24 +452,34 @@ def _params_struct(p, flags=0, eta_bound=0.0):
     visc = getattr(p, "visc", None) or (0.0, 0.0)
     return sesw_params(float(p.g), float(p.theta), float(p.tau), int(p.M), int(p.nonlinear_h),
                        int(getattr(p, "scheme", 0)), int(flags), float(eta_bound), *(float(x) for x in coef),
-                       *(float(x) for x in visc))
+                       *(float(x) for x in visc), int(getattr(p, "precision", SESW_PRECISION_FP32)), 0)
 
 
-def _mesh_struct(mesh):
+def _mesh_struct(mesh, edges=None, areas=None):
+    """The C mesh description; edges = (edge_v [ned][2], edge_e [ned][2]) and areas = (area_v, area_e)
+    are the optional caller tables (None: the library derives them)."""
+    def opt(x, dt):
+        return None if x is None else np.ascontiguousarray(x, dtype=dt)
+
+    ev, ee = edges if edges is not None else (None, None)
+    av, ae = areas if areas is not None else (None, None)
     keep = [np.ascontiguousarray(mesh.tri, dtype=np.int32),
             np.ascontiguousarray(mesh.xy, dtype=np.float64),
             None if mesh.pos is None else np.ascontiguousarray(mesh.pos, dtype=np.float64),
             np.ascontiguousarray(mesh.depth, dtype=np.float64),
-            np.ascontiguousarray(mesh.coriolis, dtype=np.float64)]
-    t, xy, pos, d, f = keep
-    m = sesw_mesh(int(mesh.nv), int(t.shape[0]), _ptr(t), _ptr(xy), _ptr(pos), _ptr(d), _ptr(f))
+            np.ascontiguousarray(mesh.coriolis, dtype=np.float64),
+            opt(ev, np.int32), opt(ee, np.int32), opt(av, np.float64), opt(ae, np.float64)]
+    t, xy, pos, d, f, kv, ke, kav, kae = keep
+    ned = 0 if kv is None else int(kv.shape[0])
+    m = sesw_mesh(int(mesh.nv), int(t.shape[0]), _ptr(t), _ptr(xy), _ptr(pos), _ptr(d), _ptr(f), ned, _ptr(kv),
+                  _ptr(ke), _ptr(kav), _ptr(kae))
     return m, keep
 
 
-def sesw_mesh_check(mesh, patch_vertices: int = 512):
+def sesw_mesh_check(mesh, patch_vertices: int = 512, edges=None, areas=None):
     """Host-only validation and layout of a mesh (no GPU needed). Returns the layout facts."""
     L = load()
-    m, keep = _mesh_struct(mesh)
+    m, keep = _mesh_struct(mesh, edges, areas)
     info = sesw_info()
     buf = ctypes.create_string_buffer(512)
     rc = L.sesw_mesh_check(ctypes.byref(m), int(patch_vertices), ctypes.byref(info), buf, 512)

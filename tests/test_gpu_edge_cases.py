@@ -104,3 +104,25 @@ def test_viscosity_without_neighbours_and_uniform_freshwater(S):
             eta, U, _ = s.sesw_get_state()
         assert np.max(np.abs(eta + 5 * 40.0 * 3e-5)) <= 1e-6
         assert np.max(np.abs(U)) <= 1e-9
+
+
+@MODES
+def test_upload_with_caller_edges_and_areas(S, mode):
+    """A mesh uploaded with the caller's edge connectivity and areas (here the oracle's own tables)
+    gives bitwise the result of the same mesh with the tables derived by the library."""
+    case = I.basin_case(nsteps=3)
+    om = orc.OracleMesh(case.mesh)
+    edges, areas = om.edges(), om.areas()
+    out = []
+    for tables in ((None, None), (edges, areas)):
+        with S.Subcycle() as s:
+            s.sesw_set_mode(mode)
+            s.sesw_mesh_upload(case.mesh, edges=tables[0], areas=tables[1])
+            s.sesw_set_params(case.params)
+            s.sesw_set_forcing(case.R)
+            s.sesw_set_state(case.eta0, case.U0)
+            s.sesw_advance(case.nsteps)
+            out.append(s.sesw_get_state())
+    for k in range(3):
+        assert np.array_equal(out[0][k], out[1][k])
+    _assert_close(case, out[1], f"basin with caller tables mode={mode}")

@@ -167,3 +167,57 @@ def test_courant_bound_is_an_upper_bound(maker):
     lam = sla.eigsh(Dm @ K @ Dm, k=1, which="LA", return_eigenvectors=False)[0]
     assert lam <= info["stiffness_bound"] * (1 + 1e-9)
     assert info["stiffness_bound"] <= 2.0 * lam
+
+
+# ---------------------------------------------------------------- optional caller tables
+
+def _tables(mesh):
+    """Edges and areas from the oracle's own mesh preparation (an independent derivation)."""
+    from oracle import runner as orc
+
+    om = orc.OracleMesh(mesh)
+    ev, ee = om.edges()
+    av, ae = om.areas()
+    return (ev, ee), (av, ae)
+
+
+def test_caller_edges_and_areas_are_accepted():
+    m = I.tiny_jittered_case(nx=9, ny=7, seed=4).mesh
+    edges, areas = _tables(m)
+    base = S.sesw_mesh_check(m, 64)
+    info = S.sesw_mesh_check(m, 64, edges=edges, areas=areas)
+    assert info == base
+    # any order of an edge's vertices and of its two triangles
+    ev, ee = (x.copy() for x in edges)
+    perm = np.random.default_rng(0).permutation(len(ev))
+    S.sesw_mesh_check(m, 64, edges=(ev[perm][:, ::-1], ee[perm][:, ::-1]), areas=areas)
+
+
+@pytest.mark.parametrize("what,needle", [
+    ("area_e", "area_e"), ("area_v", "area_v"), ("edge_side", "triangles on its two sides"),
+    ("edge_missing", "lists"), ("edge_twice", "listed twice"), ("edge_bogus", "not a side"),
+    ("edge_half", "given together")])
+def test_caller_tables_that_disagree_are_refused(what, needle):
+    m = I.tiny_jittered_case(nx=9, ny=7, seed=4).mesh
+    (ev, ee), (av, ae) = _tables(m)
+    ev, ee, av, ae = ev.copy(), ee.copy(), av.copy(), ae.copy()
+    edges, areas = (ev, ee), (av, ae)
+    if what == "area_e":
+        ae[5] *= 1.0 + 1e-9
+    elif what == "area_v":
+        av[3] *= 1.0 - 1e-9
+    elif what == "edge_side":
+        k = int(np.argmax(ee[:, 1] >= 0))
+        ee[k, 1] = (ee[k, 1] + 1) % m.ne
+    elif what == "edge_missing":
+        edges = (ev[1:], ee[1:])
+    elif what == "edge_twice":
+        ev[1], ee[1] = ev[0], ee[0]
+    elif what == "edge_bogus":
+        a, b = ev[0]
+        ev[0] = (a, next(v for v in range(m.nv) if v != a and not np.any(np.all(np.sort(ev, 1) == sorted((a, v)), 1))))
+    elif what == "edge_half":
+        edges = (ev, None)
+    with pytest.raises(S.SeswError, match=needle) as e:
+        S.sesw_mesh_check(m, 64, edges=edges, areas=areas)
+    assert e.value.code == S.SESW_EINVAL
