@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """Throughput of the split-explicit barotropic subcycle on GB300.
 
-One benchmark step is one baroclinic step of the wind-driven zonal channel
-(4000 x 2000 km, jittered Delaunay mesh with 199,920 vertices and 398,664 triangles,
-beta plane, Gaussian ridge, M = 40 substeps of tau/M = 12 s): every row of the hot
-path (element pass, vertex pass, time-mean accumulation, step epilogue) runs once
-per substep. Metric: vertex-substeps per second, whole job.
+Default workload: the batched ensemble, 64 closed basins of uneven size (jittered Delaunay
+meshes, log-uniform 2e4-4e5 vertices, 8.59 M vertices and 17.1 M triangles in total, M = 40,
+per-basin dt), advanced together: one upload, and one sesw_advance per benchmark step for the
+whole batch in the layout the autotuner picks. One benchmark step is one baroclinic step of
+every basin: every row of the hot path (element pass, vertex pass, time-mean accumulation,
+step epilogue) runs once per substep. Metric: vertex-substeps per second, whole job.
+Other workloads: --workload channel (the 200k-vertex wind-driven channel), sphere (the
+level-8 icosahedral sphere), surrogate (the learned surrogate on the sphere).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
 With N > 1 (launched by torchrun) every rank advances its own copy of the
 workload (independent ensemble members, no data exchange); the reported value is
@@ -61,10 +64,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-substeps", type=int, default=4,
                     help="substeps of the channel per reference-arm step (a bounded sample)")
-    ap.add_argument("--workload", choices=["channel", "sphere", "ensemble", "surrogate"], default="channel",
-                    help="channel: the headline workload; sphere: the global-like level-8 sphere "
-                         "(458,683 wet vertices); ensemble: 64 basins of uneven size, batched; "
-                         "surrogate: train and evaluate the learned surrogate on the sphere")
+    ap.add_argument("--workload", choices=["channel", "sphere", "ensemble", "surrogate"], default="ensemble",
+                    help="ensemble: 64 basins of uneven size, batched (the headline workload); channel: the "
+                         "200k-vertex wind-driven channel; sphere: the global-like level-8 sphere (458,683 wet "
+                         "vertices); surrogate: train and evaluate the learned surrogate on the sphere")
+    ap.add_argument("--autotune", choices=["quick", "full", "none"], default="quick",
+                    help="ensemble layouts timed before the run: quick (persistent forms and two graph "
+                         "layouts), full (every candidate), none (persistent, one block per SM)")
     ap.add_argument("--surrogate-level", type=int, default=8)
     ap.add_argument("--surrogate-traj", type=int, default=40)
     ap.add_argument("--surrogate-steps", type=int, default=50)
@@ -135,27 +141,84 @@ KERNEL_SOURCE = {"k_persistent": ("sesw_persistent.cu", "sesw_persistent.cuh", "
                                               "sesw_device.cuh")}
 
 
-def kernel_source_hash(kernel="k_persistent"):
-    """Hash of the source files of `kernel` (its profile is stale once one of them changes)."""
+def kernel_source_hash(kernels=("k_persistent",)):
+    """Hash of the source files of the given kernels (a profile is stale once one of them changes)."""
+    if isinstance(kernels, str):
+        kernels = (kernels,)
+    names = []
+    for k in kernels:
+        for name in KERNEL_SOURCE.get(k, ("sesw_kernels.cu",)):
+            if name not in names:
+                names.append(name)
     h = hashlib.sha256()
-    for name in KERNEL_SOURCE.get(kernel, ("sesw_kernels.cu",)):
+    for name in names:
         with open(os.path.join(ROOT, "paper_2311_08241_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic_for(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
-    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+def profile_figures(profile, kernels):
+    """Counters of a committed ncu summary (profiles/<profile>.md): DRAM bytes and warp instructions
+    per launch (or per step, as the summary states), or None where the summary is missing or was
+    taken on other kernel sources than the ones built now."""
+    p = os.path.join(ROOT, "profiles", f"{profile}.md")
     try:
         txt = open(p).read()
     except OSError:
         return None
-    m1 = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    m2 = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-    if not m1 or not m2 or m1.group(1) != kernel_source_hash(kernel):
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_source_hash(kernels):
         return None
-    return float(m2.group(1))
+    out = {"profile": f"profiles/{profile}.md"}
+    for key in ("dram_bytes_per_launch", "warp_instructions_per_launch", "dram_bytes_per_step",
+                "warp_instructions_per_step"):
+        v = re.search(key + r":\s*([0-9.eE+]+)", txt)
+        if v:
+            out[key] = float(v.group(1))
+    return out
+
+
+def profiled_traffic_for(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel source."""
+    f = profile_figures(f"{kernel}_{workload}", (kernel,))
+    return None if f is None else f.get("dram_bytes_per_launch")
+
+
+def issue_peak(device_sms, sm_max_mhz):
+    """Warp instructions per second the SMs can issue: 4 schedulers per SM, one warp instruction
+    each per cycle, at the largest SM clock."""
+    return device_sms * 4 * sm_max_mhz * 1e6
+
+
+def roofline_issue(kernel, seconds, inst, dram, alg_bytes, sms, sm_max_mhz, per="launch"):
+    """Roofline of an on-chip kernel: bound by instruction issue (warp instructions from the committed
+    ncu capture / CUDA-event time, against the issue peak), with the DRAM rate of the same capture and
+    the algorithmic-byte rate of the scope table beside it."""
+    peak, src = measured_hbm_peak()
+    ipk = issue_peak(sms, sm_max_mhz)
+    achieved = None if inst is None else inst / seconds
+    dram_gbs = None if dram is None else dram / seconds / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": ipk, "unit": "warp-instructions/s",
+            "frac": None if achieved is None else achieved / ipk, "traffic": dram, "traffic_per": per,
+            "kernel": kernel, "seconds_per_" + per: seconds,
+            "peak_from": f"{sms} SMs x 4 schedulers x {sm_max_mhz:g} MHz",
+            "warp_instructions_per_" + per: inst,
+            "dram": {"achieved_gbs": dram_gbs, "peak_gbs": peak, "frac": None if dram_gbs is None else dram_gbs / peak,
+                     "peak_source": src},
+            "algorithmic": {"bytes_per_" + per: alg_bytes, "gbs": alg_bytes / seconds / 1e9,
+                            "frac_of_hbm": alg_bytes / seconds / 1e9 / peak,
+                            "note": "scope-table bytes (12 V + 92 E per substep); the state stays on chip "
+                                    "for the M substeps of a launch, so this is not a DRAM rate"}}
+
+
+def sm_max_mhz_of(clk):
+    if clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"])
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["sm_max_mhz"])
+    except Exception:
+        return 2070.0
 
 
 class ClockSampler:
@@ -310,29 +373,90 @@ def barrier(world):
         dist.barrier()
 
 
+def ensemble_workload(rank=0, nbasins=64, scale=1.0):
+    """The batched ensemble (the scope table's batched configuration): seeded basins, per-basin dt."""
+    from paper_2311_08241_gb300 import inputs as I
+
+    cases = I.ensemble_cases(nbasins=nbasins, scale=scale, seed=20231118 + rank)
+    V = sum(c.mesh.nv for c in cases)
+    E = sum(c.mesh.ne for c in cases)
+    M = cases[0].params.M
+    desc = {"workload": f"batched ensemble of {len(cases)} closed basins (jittered Delaunay, log-uniform "
+                        f"2e4-4e5 vertices x {scale:g}, seeded depths 1000-5000 m, eta bumps 0.5 m), M={M}, "
+                        f"per-basin dt from the stability rule, one upload and one advance per step",
+            "V": V, "E": E, "M": M, "nbasin": len(cases)}
+    return cases, desc
+
+
+def ensemble_oracle_sample(cases, substeps, budget_s=None, rounds=None, oms=None):
+    """The FP64 oracle on the ensemble: `substeps` substeps (dt = tau/M of each basin) of every basin
+    in turn, for budget_s seconds or `rounds` passes over the basins. Returns (vertex-substeps, s)."""
+    from oracle import runner as orc
+    from paper_2311_08241_gb300 import inputs as I
+
+    oms = oms or [orc.OracleMesh(c.mesh) for c in cases]
+    state = [(c.eta0.copy(), c.U0.copy()) for c in cases]
+    work, t0, n = 0, time.perf_counter(), 0
+    while True:
+        for b, (c, om) in enumerate(zip(cases, oms)):
+            p = c.params
+            sp = I.Params(g=p.g, theta=p.theta, tau=p.tau / p.M * substeps, M=substeps, nonlinear_h=p.nonlinear_h)
+            eta, U, _, _ = om.advance(c.R, sp, 1, *state[b])
+            state[b] = (eta, U)
+            work += c.mesh.nv * substeps
+            if budget_s is not None and time.perf_counter() - t0 >= budget_s:
+                return work, time.perf_counter() - t0
+        n += 1
+        if rounds is not None and n >= rounds:
+            return work, time.perf_counter() - t0
+
+
+def cpu_baseline_ensemble(cases, seconds):
+    """The FP64 oracle, as it stands, on the host cores, on a bounded sample of the batched workload:
+    4 substeps of each basin in turn until `seconds` elapse (all cores), then a shorter single-thread
+    sample."""
+    from oracle import runner as orc
+
+    oms = [orc.OracleMesh(c.mesh) for c in cases]
+    cores = orc.set_threads(0)
+    work, dt = ensemble_oracle_sample(cases, 4, budget_s=seconds, oms=oms)
+    orc.set_threads(1)
+    work1, dt1 = ensemble_oracle_sample(cases, 4, budget_s=max(1.0, seconds / 4), oms=oms)
+    orc.set_threads(cores)
+    for om in oms:
+        om.close()
+    return {"value": work / dt, "unit": METRIC, "cores": cores, "kind": "oracle",
+            "single_thread_value": work1 / dt1, "cpu_model": cpu_model(),
+            "sample": f"{work:.4g} vertex-substeps: 4 substeps of each basin of the batch in turn for {dt:.1f} s "
+                      f"wall, FP64, OpenMP over {cores} threads; single thread: {work1:.4g} in {dt1:.1f} s"}
+
+
 def run_ensemble(args, world, rank, local):
     """Batched ensemble: every basin in one upload and one advance per step (layout picked by the
-    autotuner), against advancing each basin in its own context one after another."""
+    autotuner), timed on the device; the same through the public API with host buffers; against
+    advancing each basin in its own context one after another (bitwise the same results)."""
     import torch
 
     from paper_2311_08241_gb300 import autotune as AT
-    from paper_2311_08241_gb300 import inputs as I
     from paper_2311_08241_gb300 import sesw as S
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    cases = I.ensemble_cases(nbasins=args.ensemble_basins, scale=args.ensemble_scale, seed=20231118 + rank)
+    cases, desc = ensemble_workload(rank, args.ensemble_basins, args.ensemble_scale)
     meshes = [c.mesh for c in cases]
     params = [c.params for c in cases]
-    M = params[0].M
-    V = sum(m.nv for m in meshes)
-    E = sum(m.ne for m in meshes)
+    V, E, M = desc["V"], desc["E"], desc["M"]
     R = np.concatenate([c.R for c in cases])
     eta0 = np.concatenate([c.eta0 for c in cases])
     U0 = np.concatenate([c.U0 for c in cases])
-    best, table = AT.autotune(meshes, params, forcing=R, steps=3, warmup=1, device=local,
-                              graph_patches=(256, 1024), graph_threads=(256, 512))
+    if args.autotune == "none":
+        best, table = AT.Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=1), []
+    elif args.autotune == "quick":
+        best, table = AT.autotune(meshes, params, forcing=R, steps=3, warmup=1, device=local,
+                                  graph_patches=(1024,), graph_threads=(512,), wave_sizes=False)
+    else:
+        best, table = AT.autotune(meshes, params, forcing=R, steps=3, warmup=1, device=local)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def timed(advance, nsteps):
@@ -353,6 +477,7 @@ def run_ensemble(args, world, rank, local):
     sim.sesw_set_state(eta0, U0)
     info = sim.sesw_get_info()
     for _ in range(args.warmup):
+        flush.zero_()
         sim.sesw_advance(1)
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -365,6 +490,31 @@ def run_ensemble(args, world, rank, local):
         raise RuntimeError("batched run flagged a device status")
     total_ms = reduce_max(sum(step_ms), world, dev)
     value = whole_job_value(V, M, args.steps, world, total_ms)
+
+    # End to end through the public API with pinned host buffers: each step uploads its forcing
+    # (every basin), advances the batch, and reads back eta and <<U>> of every basin; the
+    # asynchronous calls pipeline the transfers on the library's copy streams.
+    R_h = torch.from_numpy(np.ascontiguousarray(R)).pin_memory()
+    outs = [(torch.empty(V, dtype=torch.float64).pin_memory(), torch.empty((E, 2), dtype=torch.float64).pin_memory())
+            for _ in range(2)]
+    n_e2e = max(1, min(args.e2e_steps, args.steps))
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    tickets = [0, 0]
+    for n in range(n_e2e):
+        k = n & 1
+        if n >= 2:
+            sim.sesw_wait(tickets[k])
+        sim.sesw_set_forcing_async(R_h)
+        sim.sesw_advance(1)
+        tickets[k] = sim.sesw_get_state_async(outs[k][0], None, outs[k][1])
+    sim.sesw_wait(0)
+    e2e_s = reduce_max(time.perf_counter() - t0, world, dev)
+    e2e = {"value": world * V * M * n_e2e / e2e_s, "unit": METRIC, "h2d_bytes_per_step": int(R_h.numel() * 8),
+           "d2h_bytes_per_step": int(outs[0][0].numel() * 8 + outs[0][1].numel() * 8), "steps": n_e2e,
+           "calls": "sesw_set_forcing_async, sesw_advance, sesw_get_state_async on the whole batch "
+                    "(pipelined, pinned host buffers)"}
 
     # the same basins advanced one context after another (each as the library runs a single mesh)
     singles = []
@@ -381,7 +531,7 @@ def run_ensemble(args, world, rank, local):
     seq_ms = timed(lambda: [s1.sesw_advance(1) for s1 in singles], nseq)
     speedup = statistics.mean(seq_ms) / statistics.mean(step_ms)
 
-    # SSH agreement of the two forms after the same steps from the same start
+    # SSH of the two forms after the same steps from the same start: bitwise equal
     nchk = 5
     sim.sesw_set_state(eta0, U0)
     sim.sesw_advance(nchk)
@@ -392,36 +542,49 @@ def run_ensemble(args, world, rank, local):
         s1.sesw_advance(nchk)
         eta_s.append(s1.sesw_get_state()[0])
         s1.close()
-    ssh_diff = float(np.max(np.abs(eta_b - np.concatenate(eta_s))))
+    eta_s = np.concatenate(eta_s)
+    ssh_diff = float(np.max(np.abs(eta_b - eta_s)))
 
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
-    b_alg = algorithmic_bytes_per_substep(V, E)
     mean_step_s = statistics.mean(step_ms) * 1e-3
-    # persistent: a step is one launch per pack, each doing M substeps of its basins
-    # (averaged over packs); graph: M substep launches of the whole batch
+    b_alg_step = algorithmic_bytes_per_substep(V, E) * M
     launches_per_step = max(1, info["npack"]) if persistent else M + 1
-    per_launch = b_alg * M / launches_per_step if persistent else b_alg
-    launch_s = mean_step_s / launches_per_step if persistent else mean_step_s / M
-    achieved = per_launch / launch_s / 1e9
-    peak, peak_src = measured_hbm_peak()
-    kname = "k_persistent" if persistent else "k_substep"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if persistent:
+        kernels = ("k_persistent", "k_persistent_stream")
+        fig = profile_figures("k_persistent_ensemble", kernels)
+        if fig is not None and f"layout: {best.label()}\n" not in open(os.path.join(ROOT, fig["profile"])).read():
+            fig = None
+        roofline = roofline_issue(f"k_persistent + k_persistent_stream ({launches_per_step} pack launches per step)",
+                                  mean_step_s, fig and fig.get("warp_instructions_per_step"),
+                                  fig and fig.get("dram_bytes_per_step"), b_alg_step, sms, sm_max_mhz_of(clk),
+                                  per="step")
+        if fig:
+            roofline["profile"] = fig["profile"]
+    else:
+        achieved = b_alg_step / mean_step_s / 1e9
+        peak, src = measured_hbm_peak()
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "peak_source": src, "kernel": "k_substep", "bytes_per_step": b_alg_step}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"batched ensemble of {len(cases)} closed basins (jittered Delaunay, "
-                                   f"log-uniform 2e4-4e5 vertices x {args.ensemble_scale:g}), M={M}, per-basin dt",
-                       "V": V, "E": E, "M": M, "nbasin": len(cases), "layout": best.label(),
-                       "npatch": info["npatch"], "nslot": info["nslot"], "npack": info["npack"],
-                       "l2": "flushed between timed steps (256 MiB write)",
-                       "autotune_ms_per_step": {c.label(): t for c, t in table}},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic_for(kname, "ensemble"),
-                         "peak_source": peak_src, "kernel": kname, "bytes_per_launch": per_launch},
+            "config": dict(desc, layout=best.label(), npatch=info["npatch"], nslot=info["nslot"],
+                           npack=info["npack"], streamed_first_pack=info["streamed"],
+                           l2="flushed between timed steps (256 MiB write)", parallelism=f"replicas{world}",
+                           autotune=args.autotune,
+                           autotune_ms_per_step={c.label(): t for c, t in table}),
+            "roofline": roofline, "e2e": e2e,
             "batched_vs_sequential": {"speedup": speedup, "sequential_ms_per_step": statistics.mean(seq_ms),
                                       "batched_ms_per_step": statistics.mean(step_ms),
-                                      "max_ssh_difference_m": ssh_diff, "after_steps": nchk},
-            "gpu_launches": args.steps * launches_per_step, "clocks": clk}
+                                      "max_ssh_difference_m": ssh_diff,
+                                      "bitwise_equal": bool(np.array_equal(eta_b, eta_s)), "after_steps": nchk},
+            "gpu_launches": args.steps * launches_per_step,
+            "graph_launches_per_step": 1 if sim.sesw_get_info()["step_graph"] else 0,
+            "clocks": clk}
     sim.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_ensemble(cases, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -491,6 +654,26 @@ def run_reference(args, world, rank):
     from oracle import runner as orc
     from paper_2311_08241_gb300 import inputs as I
 
+    if args.workload == "ensemble":
+        cases, desc = ensemble_workload(0, args.ensemble_basins, args.ensemble_scale)
+        S = max(1, args.ref_substeps)
+        oms = [orc.OracleMesh(c.mesh) for c in cases]
+        cores = orc.set_threads(0)
+        ensemble_oracle_sample(cases, S, rounds=args.warmup, oms=oms) if args.warmup else None
+        work, dt = ensemble_oracle_sample(cases, S, rounds=args.steps, oms=oms)
+        value = work / dt
+        sample_txt = (f"each step: {S} substeps (dt = tau/M of each basin) of every basin of the batch, FP64 "
+                      f"oracle, OpenMP over {cores} threads")
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": dict(desc, sample_substeps_per_step=S),
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                 "sample": sample_txt},
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "gpu_launches": 0}
+        print(json.dumps(line), flush=True)
+        return
     case, desc = workload(args.workload)
     S = max(1, args.ref_substeps)
     p = case.params
@@ -629,9 +812,18 @@ def run_ours(args, world, rank, local):
         kname = ("k_persistent_stream" if info["streamed"] else "k_persistent") if persistent else "k_substep"
     if args.visc:
         kname = "k_substep (viscosity fused)"
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": profiled_traffic_for(kname, args.workload), "peak_source": peak_src, "kernel": kname,
-                "bytes_per_launch": per_launch}
+    if persistent:
+        # on chip for the M substeps of a launch: bound by instruction issue, not by DRAM
+        fig = profile_figures(f"{kname}_{args.workload}", (kname,))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        roofline = roofline_issue(kname, launch_s, fig and fig.get("warp_instructions_per_launch"),
+                                  fig and fig.get("dram_bytes_per_launch"), per_launch, sms, sm_max_mhz_of(clk))
+        if fig:
+            roofline["profile"] = fig["profile"]
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": profiled_traffic_for(kname, args.workload), "peak_source": peak_src,
+                    "kernel": kname, "bytes_per_launch": per_launch}
 
     # End to end through the public API with pinned host buffers: each step uploads its
     # forcing, advances, and reads back eta and <<U>>. The asynchronous calls pipeline the

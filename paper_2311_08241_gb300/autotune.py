@@ -1,7 +1,8 @@
 """Pick the execution layout of a mesh (or batch) by timing it on the GPU.
 
-Candidates are the persistent kernel with 1, 2 or 4 resident blocks per SM and
-the per-substep graph with several patch sizes and block sizes. Each candidate is
+Candidates are the persistent kernel with 1, 2 or 4 resident blocks per SM, in
+its automatic form and with every pack streamed, and the per-substep graph with
+several patch sizes and block sizes. Each candidate is
 uploaded through the C-ABI and timed with CUDA events on a few baroclinic steps
 of the actual workload. A layout the mesh does not fit is skipped. The result
 is the fastest candidate, plus the whole table so callers can report it.
@@ -28,6 +29,10 @@ def wave_patch_sizes(nv_max, nsm, blocks_per_sm=WAVE_BLOCKS_PER_SM):
     return tuple(sorted({max(32, -(-int(nv_max) // (nsm * k))) for k in blocks_per_sm}))
 
 
+FORM_NAMES = {S.SESW_FORM_AUTO: "", S.SESW_FORM_REGISTERS: " registers", S.SESW_FORM_STREAM: " streamed",
+              S.SESW_FORM_STREAM_UNCACHED: " streamed-uncached"}
+
+
 @dataclasses.dataclass
 class Choice:
     mode: int
@@ -35,16 +40,18 @@ class Choice:
     patch_vertices: int = 256
     block_threads: int = 256
     ms_per_step: float = float("inf")
+    form: int = S.SESW_FORM_AUTO
 
     def apply(self, sim):
         sim.sesw_set_mode(self.mode)
         sim.sesw_set_blocks_per_sm(self.blocks_per_sm)
         sim.sesw_set_patch_vertices(self.patch_vertices)
         sim.sesw_set_block_threads(self.block_threads)
+        sim.sesw_set_persistent_form(self.form)
 
     def label(self):
         if self.mode == S.SESW_MODE_PERSISTENT:
-            return f"persistent bps={self.blocks_per_sm}"
+            return f"persistent bps={self.blocks_per_sm}{FORM_NAMES[self.form]}"
         return f"graph pv={self.patch_vertices} bt={self.block_threads}"
 
 
@@ -63,10 +70,14 @@ def _time_steps(sim, steps, warmup, stream):
 
 
 def autotune(meshes, params, forcing=None, steps=5, warmup=2, device=0, include_graph=True, include_persistent=True,
-             graph_patches=GRAPH_PATCHES, graph_threads=GRAPH_THREADS, verbose=False):
+             graph_patches=GRAPH_PATCHES, graph_threads=GRAPH_THREADS, verbose=False,
+             persistent_forms=(S.SESW_FORM_AUTO, S.SESW_FORM_STREAM), wave_sizes=True):
     """Time every candidate layout on the meshes (a list: one mesh, or the basins of a batch).
 
     params: one Params per mesh. forcing: optional concatenated [sum E][2] array.
+    Persistent candidates: every blocks-per-SM count with every kernel form of persistent_forms.
+    Graph candidates: graph_patches (plus, with wave_sizes, the one-wave patch sizes) with every
+    block size of graph_threads.
     Returns (best Choice, list of (Choice, ms_per_step or None)).
     """
     import torch
@@ -105,18 +116,20 @@ def autotune(meshes, params, forcing=None, steps=5, warmup=2, device=0, include_
 
     if include_persistent:
         for k in PERSISTENT_BLOCKS:
-            c = Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=k)
-            try:
-                t = run(c)
-            except S.SeswError:
-                t = None
-            c.ms_per_step = t if t is not None else float("inf")
-            table.append((c, t))
-            if verbose:
-                print(c.label(), t)
+            for form in persistent_forms:
+                c = Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=k, form=form)
+                try:
+                    t = run(c)
+                except S.SeswError:
+                    t = None
+                c.ms_per_step = t if t is not None else float("inf")
+                table.append((c, t))
+                if verbose:
+                    print(c.label(), t)
     if include_graph:
         nsm = torch.cuda.get_device_properties(device).multi_processor_count
-        patches = tuple(sorted(set(graph_patches) | set(wave_patch_sizes(max(m.nv for m in meshes), nsm))))
+        waves = set(wave_patch_sizes(max(m.nv for m in meshes), nsm)) if wave_sizes else set()
+        patches = tuple(sorted(set(graph_patches) | waves))
         for pv in patches:
             try:
                 res = run(Choice(S.SESW_MODE_GRAPH, patch_vertices=pv))

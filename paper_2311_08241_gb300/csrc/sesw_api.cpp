@@ -1227,6 +1227,7 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->npack = c->mode == SESW_MODE_PERSISTENT ? (int32_t)c->packs.size() : 0;
     info->visc_number = c->have_params ? c->visc_number : 0.0;
     for (double v : c->basin_visc_stiffness) info->visc_stiffness = std::max(info->visc_stiffness, v);
+    info->step_graph = c->mode == SESW_MODE_PERSISTENT && !c->persist_graph_ok ? 0 : 1;
     return SESW_OK;
 }
 
