@@ -641,7 +641,9 @@ def run_surrogate(args, world, rank, local):
             "surrogate": {"held_out_loss": test_loss, "persistence_loss": baseline, "untrained_loss": untrained,
                           "loss_ratio_vs_persistence": test_loss / baseline, "train_loss_per_epoch": hist,
                           "generate_s": t_gen, "train_s": t_train,
-                          "speedup_vs_plain": plain_ms / sur_ms, "rollout": roll},
+                          "speedup_vs_plain": plain_ms / sur_ms, "rollout": roll,
+                          "gain_over_plain": SG.gain_summary(roll),
+                          "ssh_signal_m": roll["max_ssh_reference_m"]},
             "gpu_launches": roll["surrogate"]["gpu_launches"]}
     if rank == 0:
         print(json.dumps(line), flush=True)

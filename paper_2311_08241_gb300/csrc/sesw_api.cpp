@@ -459,6 +459,8 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                     pk.mx.halo = std::max(pk.mx.halo, nhq);
                     pk.mx.local = std::max(pk.mx.local, nvq + nhq);
                     pk.mx.csr = std::max(pk.mx.csr, hm.vcsr_off[hm.patch_v[q + 1]] - hm.vcsr_off[hm.patch_v[q]]);
+                    for (int v = hm.patch_v[q]; v < hm.patch_v[q + 1]; v++)
+                        pk.mx.deg = std::max(pk.mx.deg, hm.vcsr_off[v + 1] - hm.vcsr_off[v]);
                 }
             const bool streamed = form == SESW_FORM_STREAM || form == SESW_FORM_STREAM_UNCACHED;
             const int idx_mode = form == SESW_FORM_STREAM_UNCACHED ? 0 : -1;

@@ -6,6 +6,14 @@
 
 namespace sesw {
 
+// Packed FP32 pairs. Blackwell issues one instruction for an (x, y) pair of FP32 additions,
+// multiplications or fused multiply-adds (FADD2/FMUL2/FFMA2), each lane rounded exactly as
+// the scalar __fadd_rn/__fmul_rn/__fmaf_rn would round it. The vector quantities of the
+// substep (gradients, transports, sums) are (x, y) pairs, so they take half the instructions.
+__device__ __forceinline__ float2 pair(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
 // Error-free accumulation of x into the pair (hi, lo): after the call hi + lo equals
 // the old hi + lo + x up to the rounding of lo (Knuth's two-sum). The explicit
 // round-to-nearest intrinsics keep the compiler from fusing or reassociating.
@@ -17,6 +25,24 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
     float err = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(x, bp));
     hi = s;
     lo = __fadd_rn(lo, err);
+}
+
+// The same two-sum on both components of a pair at once (per lane identical to two_sum_acc;
+// PACKED = 0 runs the two scalar ones).
+template <int PACKED = 1>
+__device__ __forceinline__ void two_sum_acc2(float2 &hi, float2 &lo, float2 x)
+{
+    if (!PACKED) {
+        two_sum_acc(hi.x, lo.x, x.x);
+        two_sum_acc(hi.y, lo.y, x.y);
+        return;
+    }
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bp = __fadd2_rn(s, neg2(hi));
+    const float2 ap = __fadd2_rn(s, neg2(bp));
+    const float2 err = __fadd2_rn(__fadd2_rn(hi, neg2(ap)), __fadd2_rn(x, neg2(bp)));
+    hi = s;
+    lo = __fadd2_rn(lo, err);
 }
 
 // Element update of one slot in the dissipative forward-backward substep (Eq. 4.10, first
@@ -31,35 +57,58 @@ __device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
 //   r           frozen forcing R (m^2/s^2)
 //   u           in: U^m, out: U^{m+1}
 // Returns F = (1 + theta) U^{m+1} - theta U^m.
-template <int NONLIN>
+// PACKED = 0 computes the same roundings with scalar instructions (bitwise the same result).
+template <int NONLIN, int PACKED = 1>
 __device__ __forceinline__ float2 se_transport(float e0, float e1, float e2, float4 g, float gH0, float gconst,
                                                float aa, float inv, float dt, float2 r, float one_p_theta,
                                                float theta, float2 &u)
 {
     const float d0 = __fsub_rn(e0, e2), d1 = __fsub_rn(e1, e2);
-    const float gx = __fmaf_rn(d1, g.z, __fmul_rn(d0, g.x));
-    const float gy = __fmaf_rn(d1, g.w, __fmul_rn(d0, g.y));
+    if (!PACKED) {
+        const float gx = __fmaf_rn(d1, g.z, __fmul_rn(d0, g.x));
+        const float gy = __fmaf_rn(d1, g.w, __fmul_rn(d0, g.y));
+        float gH = gH0;
+        if (NONLIN) gH = __fmaf_rn(gconst, __fmul_rn(__fadd_rn(__fadd_rn(e0, e1), e2), 1.0f / 3.0f), gH0);
+        const float rx = __fmaf_rn(dt, __fmaf_rn(-gH, gx, r.x), __fmaf_rn(aa, u.y, u.x));
+        const float ry = __fmaf_rn(dt, __fmaf_rn(-gH, gy, r.y), __fmaf_rn(-aa, u.x, u.y));
+        const float nx = __fmul_rn(__fmaf_rn(aa, ry, rx), inv);
+        const float ny = __fmul_rn(__fmaf_rn(-aa, rx, ry), inv);
+        const float2 F = make_float2(__fmaf_rn(one_p_theta, nx, __fmul_rn(-theta, u.x)),
+                                     __fmaf_rn(one_p_theta, ny, __fmul_rn(-theta, u.y)));
+        u = make_float2(nx, ny);
+        return F;
+    }
+    const float2 grad = __ffma2_rn(splat(d1), pair(g.z, g.w), __fmul2_rn(splat(d0), pair(g.x, g.y)));
     float gH = gH0;
     if (NONLIN) gH = __fmaf_rn(gconst, __fmul_rn(__fadd_rn(__fadd_rn(e0, e1), e2), 1.0f / 3.0f), gH0);
-    const float rx = __fmaf_rn(dt, __fmaf_rn(-gH, gx, r.x), __fmaf_rn(aa, u.y, u.x));
-    const float ry = __fmaf_rn(dt, __fmaf_rn(-gH, gy, r.y), __fmaf_rn(-aa, u.x, u.y));
-    const float nx = __fmul_rn(__fmaf_rn(aa, ry, rx), inv);
-    const float ny = __fmul_rn(__fmaf_rn(-aa, rx, ry), inv);
-    const float2 F = make_float2(__fmaf_rn(one_p_theta, nx, __fmul_rn(-theta, u.x)),
-                                 __fmaf_rn(one_p_theta, ny, __fmul_rn(-theta, u.y)));
-    u = make_float2(nx, ny);
+    // right-hand side: U + aa (U_y, -U_x) + dt (R - g H grad eta)
+    const float2 t = __ffma2_rn(splat(-gH), grad, r);
+    const float2 w = __ffma2_rn(pair(aa, -aa), pair(u.y, u.x), u);
+    const float2 rr = __ffma2_rn(splat(dt), t, w);
+    // Crank-Nicolson solve: U' = (rr + aa (rr_y, -rr_x)) / (1 + aa^2)
+    const float2 n = __fmul2_rn(__ffma2_rn(pair(aa, -aa), pair(rr.y, rr.x), rr), splat(inv));
+    const float2 F = __ffma2_rn(splat(one_p_theta), n, __fmul2_rn(splat(-theta), u));
+    u = n;
     return F;
 }
 
 // Contributions of the transport F of a triangle to the median-dual cells of its three
 // corners: c_k = w F . dphi_k with w = dt A_e (k = 0, 1), c_2 = -(c_0 + c_1).
+template <int PACKED = 1>
 __device__ __forceinline__ void corner_fluxes(float2 F, float4 g, float w, float *out3)
 {
-    const float c0 = __fmul_rn(w, __fmaf_rn(F.y, g.y, __fmul_rn(F.x, g.x)));
-    const float c1 = __fmul_rn(w, __fmaf_rn(F.y, g.w, __fmul_rn(F.x, g.z)));
-    out3[0] = c0;
-    out3[1] = c1;
-    out3[2] = -__fadd_rn(c0, c1);
+    if (!PACKED) {
+        const float c0 = __fmul_rn(w, __fmaf_rn(F.y, g.y, __fmul_rn(F.x, g.x)));
+        const float c1 = __fmul_rn(w, __fmaf_rn(F.y, g.w, __fmul_rn(F.x, g.z)));
+        out3[0] = c0;
+        out3[1] = c1;
+        out3[2] = -__fadd_rn(c0, c1);
+        return;
+    }
+    const float2 c = __fmul2_rn(splat(w), __ffma2_rn(splat(F.y), pair(g.y, g.w), __fmul2_rn(splat(F.x), pair(g.x, g.z))));
+    out3[0] = c.x;
+    out3[1] = c.y;
+    out3[2] = -__fadd_rn(c.x, c.y);
 }
 
 // The vertex update of Eq. (4.10), second row: eta + (sum of the corner contributions,
@@ -78,22 +127,19 @@ __device__ __forceinline__ float2 sesm_momentum(float e0, float e1, float e2, fl
                                                 float f, float dt, float2 r, float2 u1, float2 uab)
 {
     const float d0 = __fsub_rn(e0, e2), d1 = __fsub_rn(e1, e2);
-    const float gx = __fmaf_rn(d1, g.z, __fmul_rn(d0, g.x));
-    const float gy = __fmaf_rn(d1, g.w, __fmul_rn(d0, g.y));
+    const float2 grad = __ffma2_rn(splat(d1), pair(g.z, g.w), __fmul2_rn(splat(d0), pair(g.x, g.y)));
     float H = H0;
     if (NONLIN) H = __fadd_rn(H0, __fmul_rn(__fadd_rn(__fadd_rn(e0, e1), e2), 1.0f / 3.0f));
     const float gH = __fmul_rn(gconst, H);
     // -f e_z x U_AB = (f U_AB_y, -f U_AB_x)
-    const float tx = __fadd_rn(__fmaf_rn(-gH, gx, __fmul_rn(f, uab.y)), r.x);
-    const float ty = __fadd_rn(__fmaf_rn(-gH, gy, __fmul_rn(-f, uab.x)), r.y);
-    return make_float2(__fmaf_rn(dt, tx, u1.x), __fmaf_rn(dt, ty, u1.y));
+    const float2 t = __fadd2_rn(__ffma2_rn(splat(-gH), grad, __fmul2_rn(pair(f, -f), pair(uab.y, uab.x))), r);
+    return __ffma2_rn(splat(dt), t, u1);
 }
 
 // AB3 transport ab0 U^m + ab1 U^{m-1} + ab2 U^{m-2} (Eq. 4.7).
 __device__ __forceinline__ float2 sesm_ab3(float2 u0, float2 ua, float2 ub, float ab0, float ab1, float ab2)
 {
-    return make_float2(__fmaf_rn(ab2, ub.x, __fmaf_rn(ab1, ua.x, __fmul_rn(ab0, u0.x))),
-                       __fmaf_rn(ab2, ub.y, __fmaf_rn(ab1, ua.y, __fmul_rn(ab0, u0.y))));
+    return __ffma2_rn(splat(ab2), ub, __ffma2_rn(splat(ab1), ua, __fmul2_rn(splat(ab0), u0)));
 }
 
 // AM4 elevation am0 eta^{m+1} + am1 eta^m + am2 eta^{m-1} + am3 eta^{m-2} (Eq. 4.7).

@@ -243,6 +243,7 @@ struct PersistentPlan {
 // Largest patch of a pack: what its shared-memory layout and its plan depend on.
 struct PatchMax {
     int slots = 0, local = 0, vertices = 0, halo = 0, csr = 0;
+    int deg = 0;   // most incidences (triangle corners) of one vertex
 };
 // One cooperative launch of a step: blocks [base, base + nblocks) of pack_patch, with the
 // plans of both schemes for its largest patch (the SESM plan may be empty).

@@ -157,8 +157,7 @@ k_substep(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const floa
         U_out[s] = un;
         if (i < nown) {
             float2 hi = Shi[s], lo = Slo[s];
-            two_sum_acc(hi.x, lo.x, F.x);
-            two_sum_acc(hi.y, lo.y, F.y);
+            two_sum_acc2(hi, lo, F);
             Shi[s] = hi;
             Slo[s] = lo;
         }
@@ -241,8 +240,7 @@ k_sesm(const int4 *__restrict__ sv, const float4 *__restrict__ sg, const float4 
         const float2 F = sesm_ab3(u0, u1, u2, a.ab0, a.ab1, a.ab2);
         if (i < nown) {
             float2 hi = Shi[s], lo = Slo[s];
-            two_sum_acc(hi.x, lo.x, F.x);
-            two_sum_acc(hi.y, lo.y, F.y);
+            two_sum_acc2(hi, lo, F);
             Shi[s] = hi;
             Slo[s] = lo;
         }

@@ -27,18 +27,19 @@ namespace {
 
 // Element update of one slot (Eq. 4.10, first row, and the theta-weighted flux);
 // coef = (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)).
-template <int NONLIN>
+// Packed FP32 pairs in the element update of the cached kernels (UNCACHED: kUncachedPacked).
+constexpr int kUncachedPacked = 0;
+
+template <int NONLIN, int PACKED>
 __device__ __forceinline__ void element_update(const float e0, const float e1, const float e2, const float4 g,
                                                const float4 coef, const float2 r, float2 &u, float2 &shi,
                                                float2 &slo, bool owned, float *flux3, float theta,
                                                float one_p_theta, float dt, float gconst)
 {
-    const float2 F = se_transport<NONLIN>(e0, e1, e2, g, coef.y, gconst, coef.z, coef.w, dt, r, one_p_theta, theta, u);
-    if (owned) {
-        two_sum_acc(shi.x, slo.x, F.x);
-        two_sum_acc(shi.y, slo.y, F.y);
-    }
-    corner_fluxes(F, g, coef.x, flux3);
+    const float2 F =
+        se_transport<NONLIN, PACKED>(e0, e1, e2, g, coef.y, gconst, coef.z, coef.w, dt, r, one_p_theta, theta, u);
+    if (owned) two_sum_acc2<PACKED>(shi, slo, F);
+    corner_fluxes<PACKED>(F, g, coef.x, flux3);
 }
 
 __device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a, float dt)
@@ -60,7 +61,6 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     const int nown_s = P.patch_own[p], nint = P.patch_int[p];
     const int v0 = P.patch_v[p], nown = P.patch_v[p + 1] - v0;
     const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
-    const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
     const StepArgs a = P.a;
     const float dt = P.patch_dt[p];
     unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
@@ -74,8 +74,6 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     float4 *s_c = reinterpret_cast<float4 *>(smem_raw + P.off_c);
     float2 *s_r = reinterpret_cast<float2 *>(smem_raw + P.off_r);
     ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + P.off_l);
-    unsigned short *s_off = reinterpret_cast<unsigned short *>(smem_raw + P.off_off);
-    unsigned short *s_csr = reinterpret_cast<unsigned short *>(smem_raw + P.off_csr);
     float *s_inv = reinterpret_cast<float *>(smem_raw + P.off_inv);
     int *s_halo = reinterpret_cast<int *>(smem_raw + P.off_halo);
 
@@ -88,12 +86,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
             s_r[i] = P.R[s0 + i];
             s_l[i] = P.sl[s0 + i];
         }
-        for (int i = threadIdx.x; i <= nown; i += T) s_off[i] = (unsigned short)(P.vcsr_off[v0 + i] - c0);
-        // cached incidence entries hold the flux index 3 * slot + corner directly
-        for (int k = threadIdx.x; k < ncsr; k += T) {
-            const uint32_t q = P.vcsr[c0 + k];
-            s_csr[k] = (unsigned short)(3u * (q >> 2) + (q & 3u));
-        }
+        cache_incidences(P, smem_raw, v0, nown);
         for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
         for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
     }
@@ -149,7 +142,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
                     e1 = seta[l.y];
                     e2 = seta[l.z];
                 }
-                element_update<NONLIN>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
+                element_update<NONLIN, CACHED ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
                                        a.theta, one_p_theta, dt, a.g);
             }
         }
@@ -173,7 +166,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
 #pragma unroll
         for (int q = 1; q < SPT; q++)
             if (q == j) { uu = u[q]; sh = shi[q]; sl = slo[q]; }
-        element_update<NONLIN>(e0, e1, e2, g, coef, r, uu, sh, sl, i < nown_s, sflux + 3 * i, a.theta,
+        element_update<NONLIN, CACHED ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, uu, sh, sl, i < nown_s, sflux + 3 * i, a.theta,
                                one_p_theta, dt, a.g);
 #pragma unroll
         for (int q = 0; q < SPT; q++)
@@ -257,8 +250,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
         for (int i = threadIdx.x; i < nown; i += T) {
             float sum = 0.0f, inv;
             if (CACHED) {
-                const int k1 = s_off[i + 1];
-                for (int k = s_off[i]; k < k1; k++) sum += sflux[s_csr[k]];
+                sum = cached_flux_sum(P, smem_raw, i);
                 inv = s_inv[i];
             } else {
                 const int k1 = P.vcsr_off[v0 + i + 1];

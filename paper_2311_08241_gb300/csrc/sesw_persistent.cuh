@@ -37,6 +37,9 @@ namespace {
 // and the buffers need no clearing. Tags wrap modulo 2^32; a wrapped tag could only
 // match a word that no launch has rewritten since, and every launch rewrites every word
 // that is read.
+// Incidences of a vertex in the padded form (PArgs::inc8): at most this many per vertex.
+constexpr int kIncWidth = 8;
+
 struct PArgs {
     const int *patch_slot, *patch_own, *patch_int, *patch_v, *patch_halo, *halo_v;
     const int *vcsr_off;
@@ -61,6 +64,10 @@ struct PArgs {
     int M, npatch;
     // shared-memory carve-up (CACHED), in bytes from the dynamic shared base
     int off_flux, off_g, off_c, off_r, off_l, off_off, off_csr, off_inv, off_halo;
+    // inc8: the cached incidences are one row of 8 16-bit byte offsets per own vertex (into the
+    // dynamic shared memory: the corner fluxes, padded with a zero word) at off_off, in place of
+    // the CSR (offsets at off_off, entries at off_csr); zero_off: the zero word's byte offset
+    int inc8, zero_off;
 };
 
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p)
@@ -111,11 +118,71 @@ __device__ __forceinline__ float halo_eta(const PArgs &P, const unsigned long lo
 }
 
 
+// Copy the incidences of a patch's own vertices into shared memory (cached layouts): with
+// P.inc8, one row of kIncWidth 16-bit byte offsets per vertex, pointing at its corner fluxes
+// in incidence order and padded with the zero word; else the CSR with flux indices
+// 3 * slot + corner. Also clears the zero word. The caller synchronises the block afterwards.
+__device__ __forceinline__ void cache_incidences(const PArgs &P, unsigned char *smem_raw, int v0, int nown)
+{
+    const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
+    if (P.inc8) {
+        uint4 *rows = reinterpret_cast<uint4 *>(smem_raw + P.off_off);
+        for (int i = threadIdx.x; i < nown; i += blockDim.x) {
+            const int k0 = P.vcsr_off[v0 + i], deg = P.vcsr_off[v0 + i + 1] - k0;
+            unsigned h[kIncWidth];
+#pragma unroll
+            for (int k = 0; k < kIncWidth; k++) {
+                unsigned off = (unsigned)P.zero_off;
+                if (k < deg) {
+                    const uint32_t q = P.vcsr[k0 + k];
+                    off = (unsigned)P.off_flux + 4u * (3u * (q >> 2) + (q & 3u));
+                }
+                h[k] = off;
+            }
+            rows[i] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        }
+        if (threadIdx.x == 0) *reinterpret_cast<float *>(smem_raw + P.zero_off) = 0.0f;
+    } else {
+        unsigned short *s_off = reinterpret_cast<unsigned short *>(smem_raw + P.off_off);
+        unsigned short *s_csr = reinterpret_cast<unsigned short *>(smem_raw + P.off_csr);
+        for (int i = threadIdx.x; i <= nown; i += blockDim.x) s_off[i] = (unsigned short)(P.vcsr_off[v0 + i] - c0);
+        for (int k = threadIdx.x; k < ncsr; k += blockDim.x) {
+            const uint32_t q = P.vcsr[c0 + k];
+            s_csr[k] = (unsigned short)(3u * (q >> 2) + (q & 3u));
+        }
+    }
+}
+
+// Sum of the corner fluxes of own vertex i in its incidence order (cached layouts; see
+// cache_incidences). The padded form adds zeros after the last incidence, which leaves the
+// sum unchanged.
+__device__ __forceinline__ float cached_flux_sum(const PArgs &P, const unsigned char *smem_raw, int i)
+{
+    float sum = 0.0f;
+    if (P.inc8) {
+        const uint4 q = reinterpret_cast<const uint4 *>(smem_raw + P.off_off)[i];
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            sum = __fadd_rn(sum, *reinterpret_cast<const float *>(smem_raw + (w[k] & 0xffffu)));
+            sum = __fadd_rn(sum, *reinterpret_cast<const float *>(smem_raw + (w[k] >> 16)));
+        }
+    } else {
+        const unsigned short *s_off = reinterpret_cast<const unsigned short *>(smem_raw + P.off_off);
+        const unsigned short *s_csr = reinterpret_cast<const unsigned short *>(smem_raw + P.off_csr);
+        const float *sflux = reinterpret_cast<const float *>(smem_raw + P.off_flux);
+        const int k1 = s_off[i + 1];
+        for (int k = s_off[i]; k < k1; k++) sum = __fadd_rn(sum, sflux[s_csr[k]]);
+    }
+    return sum;
+}
+
 inline size_t flag_bytes(int npatch) { return sizeof(unsigned) * (2 * (size_t)npatch + 1) * kFlagStride; }
 
 
 struct SmemLayout {
     int off_flux, off_g, off_c, off_r, off_l, off_off, off_csr, off_inv, off_halo;
+    int inc8, zero_off;
     size_t total_plain, total_cached;
 };
 
@@ -126,7 +193,9 @@ inline SmemLayout smem_layout(const PatchMax &m)
     SmemLayout L;
     size_t o = align16(sizeof(float) * (size_t)m.local);
     L.off_flux = (int)o;
-    o = align16(o + sizeof(float) * 3 * (size_t)m.slots);
+    // the corner fluxes, then one zero word (the padding target of the padded incidence rows)
+    L.zero_off = (int)(o + sizeof(float) * 3 * (size_t)m.slots);
+    o = align16(o + sizeof(float) * (3 * (size_t)m.slots + 1));
     L.total_plain = o;
     L.off_g = (int)o;
     o += sizeof(float4) * (size_t)m.slots;
@@ -141,9 +210,14 @@ inline SmemLayout smem_layout(const PatchMax &m)
     L.off_halo = (int)o;
     o = align16(o + sizeof(int) * (size_t)m.halo);
     L.off_off = (int)o;
-    o = align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1));
-    L.off_csr = (int)o;
-    o = align16(o + sizeof(unsigned short) * (size_t)m.csr);
+    const size_t csr_end = align16(align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1)) +
+                                   sizeof(unsigned short) * (size_t)m.csr);
+    L.off_csr = (int)align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1));
+    // padded rows when every vertex has at most kIncWidth incidences and every flux byte offset
+    // fits 16 bits; they take the place of the CSR
+    L.inc8 = m.deg <= kIncWidth && L.zero_off + 4 <= 65535 ? 1 : 0;
+    const size_t inc_end = o + sizeof(unsigned short) * kIncWidth * (size_t)m.vertices;
+    o = L.inc8 ? align16(inc_end) : csr_end;
     L.total_cached = o;
     return L;
 }
@@ -190,6 +264,8 @@ inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, 
     P.off_csr = L.off_csr;
     P.off_inv = L.off_inv;
     P.off_halo = L.off_halo;
+    P.inc8 = L.inc8;
+    P.zero_off = L.zero_off;
     P.pack_patch = m.pack_patch;
     P.pack_base = 0;
     P.pack_index = 0;

@@ -35,7 +35,6 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
     const int nown_s = P.patch_own[p], nint = P.patch_int[p];
     const int v0 = P.patch_v[p], nown = P.patch_v[p + 1] - v0;
     const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
-    const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
     const StepArgs a = P.a;
     const float dt = P.patch_dt[p];
     unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
@@ -49,8 +48,6 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
     float4 *s_c = reinterpret_cast<float4 *>(smem_raw + P.off_c);
     float2 *s_r = reinterpret_cast<float2 *>(smem_raw + P.off_r);
     ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + P.off_l);
-    unsigned short *s_off = reinterpret_cast<unsigned short *>(smem_raw + P.off_off);
-    unsigned short *s_csr = reinterpret_cast<unsigned short *>(smem_raw + P.off_csr);
     float *s_inv = reinterpret_cast<float *>(smem_raw + P.off_inv);
     int *s_halo = reinterpret_cast<int *>(smem_raw + P.off_halo);
 
@@ -60,11 +57,7 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
         s_r[i] = P.R[s0 + i];
         s_l[i] = P.sl[s0 + i];
     }
-    for (int i = threadIdx.x; i <= nown; i += T) s_off[i] = (unsigned short)(P.vcsr_off[v0 + i] - c0);
-    for (int k = threadIdx.x; k < ncsr; k += T) {
-        const uint32_t q = P.vcsr[c0 + k];
-        s_csr[k] = (unsigned short)(3u * (q >> 2) + (q & 3u));
-    }
+    cache_incidences(P, smem_raw, v0, nown);
     for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
     for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
     if (threadIdx.x == 0) s_abort = 0;
@@ -94,8 +87,7 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
     auto transport = [&](int j, int i, float2 u0, float2 ua, float2 ub, float4 g, float area) {
         const float2 F = sesm_ab3(u0, ua, ub, a.ab0, a.ab1, a.ab2);
         if (i < nown_s) {
-            two_sum_acc(shi[j].x, slo[j].x, F.x);
-            two_sum_acc(shi[j].y, slo[j].y, F.y);
+            two_sum_acc2(shi[j], slo[j], F);
         }
         corner_fluxes(F, g, __fmul_rn(dt, area), sflux + 3 * i);
         uab[j] = F;
@@ -183,9 +175,7 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
         for (int k = 0; k < kSesmVpt; k++) {
             const int i = threadIdx.x + k * T;
             if (i < nown) {
-                float sum = 0.0f;
-                const int k1 = s_off[i + 1];
-                for (int q = s_off[i]; q < k1; q++) sum += sflux[s_csr[q]];
+                const float sum = cached_flux_sum(P, smem_raw, i);
                 float e = vertex_eta(eh0[k], sum, s_inv[i]);
                 if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
                 const float em = sesm_am4(e, eh0[k], eh1[k], eh2[k], a.am0, a.am1, a.am2, a.am3);

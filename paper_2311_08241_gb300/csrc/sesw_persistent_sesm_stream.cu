@@ -38,8 +38,7 @@ __device__ __forceinline__ float2 sesm_transport(const QArgs &A, int s, int i, b
             hi = A.Shi[s];
             lo = A.Slo[s];
         }
-        two_sum_acc(hi.x, lo.x, F.x);
-        two_sum_acc(hi.y, lo.y, F.y);
+        two_sum_acc2(hi, lo, F);
         A.Shi[s] = hi;
         A.Slo[s] = lo;
     }

@@ -15,6 +15,7 @@ namespace sesw {
 namespace {
 
 constexpr int kStreamThreads = 1024;   // 64 registers per thread at any residency
+constexpr int kStreamPacked = 0;       // packed FP32 pairs in the element update
 
 struct SArgs {
     PArgs P;
@@ -40,16 +41,15 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
     }
     const float aa = __fmul_rn(c.z, __fmul_rn(0.5f, dt));
     const float inv = __frcp_rn(__fmaf_rn(aa, aa, 1.0f));
-    const float2 F = se_transport<NONLIN>(e0, e1, e2, g, __fmul_rn(a.g, c.y), a.g, aa, inv, dt, r,
+    const float2 F = se_transport<NONLIN, kStreamPacked>(e0, e1, e2, g, __fmul_rn(a.g, c.y), a.g, aa, inv, dt, r,
                                           __fadd_rn(1.0f, a.theta), a.theta, u);
     P.U[s] = u;
     if (owned) {
-        two_sum_acc(shi.x, slo.x, F.x);
-        two_sum_acc(shi.y, slo.y, F.y);
+        two_sum_acc2<kStreamPacked>(shi, slo, F);
         A.Shi[s] = shi;
         A.Slo[s] = slo;
     }
-    corner_fluxes(F, g, __fmul_rn(dt, c.x), sflux + 3 * i);
+    corner_fluxes<kStreamPacked>(F, g, __fmul_rn(dt, c.x), sflux + 3 * i);
 }
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set.

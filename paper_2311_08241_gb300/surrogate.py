@@ -156,6 +156,19 @@ def rollout_error(case, R, params_ref, weights, scales, nsteps, resid_tol, coars
     return out
 
 
+def gain_summary(roll):
+    """What each cheaper form gains over the plain subcycle at M: its speedup (plain time per step
+    over its own) and the SSH error it pays for it, from a rollout_error result."""
+    plain_ms = roll["plain"]["ms_per_step"]
+    out = {}
+    for name, r in roll.items():
+        if name == "plain" or not isinstance(r, dict) or "ms_per_step" not in r:
+            continue
+        out[name] = {"speedup_vs_plain": plain_ms / r["ms_per_step"], "max_ssh_error_m": r["max_ssh_error_m"],
+                     "ms_per_step": r["ms_per_step"]}
+    return out
+
+
 def sphere_forcing(case, seed):
     """Smooth random forcing of the sphere workload (new seed per trajectory)."""
     H0e = case.mesh.depth[case.mesh.tri].mean(axis=1)

@@ -94,10 +94,19 @@ def test_sphere_matches_oracle(sesw, mode):
 
 @MODES
 def test_sphere_level8_full_size(sesw, mode):
-    """Global-like sphere at full size (level 8: ~460k wet vertices), 5 steps of 50 substeps."""
-    case = I.sphere_case(level=8, nsteps=5)
+    """Global-like sphere at full size and length (level 8: ~460k wet vertices), 50 steps of 50
+    substeps, the workload's own length."""
+    case = I.sphere_case(level=8, nsteps=50)
     got = sesw.run_case(case, mode=mode)
-    _assert_close(case, got, f"sphere-l8 mode={mode}")
+    _assert_close(case, got, f"sphere-l8-50 mode={mode}")
+
+
+def test_channel_matches_oracle_200_steps(sesw):
+    """The channel over its full length of 200 steps (8000 substeps) in the benchmark's launch
+    configuration (the other layouts give bitwise the same result, tests/test_gpu_bitwise.py)."""
+    case = I.channel_case(nsteps=200)
+    got = sesw.run_case(case, mode=PERSISTENT)
+    _assert_close(case, got, "channel-200 persistent")
 
 
 def test_modes_agree(sesw):

@@ -179,3 +179,43 @@ def test_trained_surrogate_gains_over_persistence_on_held_out_data(S):
         test = s.sesw_surrogate_loss(sp.test)
     print("held-out loss", test, "persistence", base)
     assert test < 0.5 * base
+
+
+def test_surrogate_against_plain_and_reduced_M_on_held_out_forcing(S):
+    """The three ways to take a baroclinic step, on a held-out forcing of a small sphere after
+    training: the surrogate with its fallback, the plain subcycle at M (the reference) and the
+    plain subcycle at M/2. Each reports its time per step and its SSH error against the
+    reference; the test checks that the numbers are produced and consistent, and states them
+    (a surrogate slower or less accurate than halving M is a valid outcome)."""
+    from paper_2311_08241_gb300 import surrogate as SG
+
+    case = I.sphere_case(level=4, nsteps=10)
+    forcing = lambda k: SG.sphere_forcing(case, 700 + k)
+    ntraj, nst = 10, 10
+    with S.Subcycle() as s:
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_params(case.params)
+        s.sesw_surrogate_init(ntraj * nst, seed=1)
+        SG.generate(s, case.mesh, forcing, ntraj, nst)
+        sp = SG.split(ntraj, nst, test_fraction=0.2)
+        s.sesw_surrogate_fit_scales(ntraj * nst, 2e5)
+        SG.train(s, sp.train, 12, lr=3e-3)
+        weights = s.sesw_surrogate_weights()
+        scales = s.sesw_surrogate_scales()
+    held_out = forcing(ntraj - 1)      # the last trajectory's forcing is in the test split
+    M = case.params.M
+    roll = SG.rollout_error(case, held_out, case.params, weights, scales, nst, 0.1, coarse_M=(M // 2,))
+    gain = SG.gain_summary(roll)
+    print("gain over the plain subcycle:", gain)
+    for form in ("plain", f"plain_M{M // 2}", "surrogate", "surrogate_no_fallback"):
+        assert roll[form]["ms_per_step"] > 0 and np.isfinite(roll[form]["max_ssh_error_m"]), form
+    assert roll["plain"]["max_ssh_error_m"] == 0.0
+    assert roll[f"plain_M{M // 2}"]["max_ssh_error_m"] > 0.0
+    sur = roll["surrogate"]
+    assert 0 <= sur["fallback_steps"] <= nst
+    if sur["fallback_steps"] == nst:
+        # every step rejected: the fallback is the plain step itself, bit for bit
+        assert sur["max_ssh_error_m"] == 0.0
+    assert set(gain) >= {"surrogate", f"plain_M{M // 2}"}
+    for v in gain.values():
+        assert v["speedup_vs_plain"] > 0
