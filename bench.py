@@ -69,8 +69,13 @@ def parse():
                          "200k-vertex wind-driven channel; sphere: the global-like level-8 sphere (458,683 wet "
                          "vertices); surrogate: train and evaluate the learned surrogate on the sphere")
     ap.add_argument("--autotune", choices=["quick", "full", "none"], default="quick",
-                    help="ensemble layouts timed before the run: quick (persistent forms and two graph "
-                         "layouts), full (every candidate), none (persistent, one block per SM)")
+                    help="ensemble layouts timed before the run: quick (persistent forms, large-basin "
+                         "layouts and one graph layout), full (every candidate), none (the layout of "
+                         "--blocks-per-sm (default 1), --large-bps and --large-form)")
+    ap.add_argument("--large-bps", type=int, default=0,
+                    help="with --autotune none: blocks per SM of the large basins' packs (0: the same)")
+    ap.add_argument("--large-form", choices=["same", "auto", "registers", "stream", "stream-uncached"],
+                    default="same", help="with --autotune none: kernel form of the large basins' packs")
     ap.add_argument("--surrogate-level", type=int, default=8)
     ap.add_argument("--surrogate-traj", type=int, default=40)
     ap.add_argument("--surrogate-steps", type=int, default=50)
@@ -78,7 +83,8 @@ def parse():
     ap.add_argument("--resid-tol", type=float, default=0.1)
     ap.add_argument("--ensemble-basins", type=int, default=64)
     ap.add_argument("--ensemble-scale", type=float, default=1.0)
-    ap.add_argument("--sequential-steps", type=int, default=10)
+    ap.add_argument("--sequential-steps", type=int, default=10,
+                    help="ensemble: steps of the one-basin-after-another comparison (0: skip it)")
     return ap.parse_args()
 
 
@@ -451,7 +457,10 @@ def run_ensemble(args, world, rank, local):
     eta0 = np.concatenate([c.eta0 for c in cases])
     U0 = np.concatenate([c.U0 for c in cases])
     if args.autotune == "none":
-        best, table = AT.Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=1), []
+        forms = {"same": -1, "auto": S.SESW_FORM_AUTO, "registers": S.SESW_FORM_REGISTERS,
+                 "stream": S.SESW_FORM_STREAM, "stream-uncached": S.SESW_FORM_STREAM_UNCACHED}
+        best, table = AT.Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=args.blocks_per_sm or 1,
+                                large_bps=args.large_bps, large_form=forms[args.large_form]), []
     elif args.autotune == "quick":
         best, table = AT.autotune(meshes, params, forcing=R, steps=3, warmup=1, device=local,
                                   graph_patches=(1024,), graph_threads=(512,), wave_sizes=False)
@@ -517,33 +526,38 @@ def run_ensemble(args, world, rank, local):
                     "(pipelined, pinned host buffers)"}
 
     # the same basins advanced one context after another (each as the library runs a single mesh)
+    compare = args.sequential_steps > 0
     singles = []
-    for c in cases:
+    for c in cases if compare else []:
         s1 = S.Subcycle(local, stream=stream)
         s1.sesw_mesh_upload(c.mesh)
         s1.sesw_set_params(c.params)
         s1.sesw_set_forcing(c.R)
         s1.sesw_set_state(c.eta0, c.U0)
         singles.append(s1)
-    for s1 in singles:
-        s1.sesw_advance(1)
-    nseq = max(1, min(args.sequential_steps, args.steps))
-    seq_ms = timed(lambda: [s1.sesw_advance(1) for s1 in singles], nseq)
-    speedup = statistics.mean(seq_ms) / statistics.mean(step_ms)
-
-    # SSH of the two forms after the same steps from the same start: bitwise equal
-    nchk = 5
-    sim.sesw_set_state(eta0, U0)
-    sim.sesw_advance(nchk)
-    eta_b = sim.sesw_get_state()[0]
-    eta_s = []
-    for c, s1 in zip(cases, singles):
-        s1.sesw_set_state(c.eta0, c.U0)
-        s1.sesw_advance(nchk)
-        eta_s.append(s1.sesw_get_state()[0])
-        s1.close()
-    eta_s = np.concatenate(eta_s)
-    ssh_diff = float(np.max(np.abs(eta_b - eta_s)))
+    batched_vs_sequential = None
+    if compare:
+        for s1 in singles:
+            s1.sesw_advance(1)
+        nseq = max(1, min(args.sequential_steps, args.steps))
+        seq_ms = timed(lambda: [s1.sesw_advance(1) for s1 in singles], nseq)
+        speedup = statistics.mean(seq_ms) / statistics.mean(step_ms)
+        # SSH of the two forms after the same steps from the same start: bitwise equal
+        nchk = 5
+        sim.sesw_set_state(eta0, U0)
+        sim.sesw_advance(nchk)
+        eta_b = sim.sesw_get_state()[0]
+        eta_s = []
+        for c, s1 in zip(cases, singles):
+            s1.sesw_set_state(c.eta0, c.U0)
+            s1.sesw_advance(nchk)
+            eta_s.append(s1.sesw_get_state()[0])
+            s1.close()
+        eta_s = np.concatenate(eta_s)
+        batched_vs_sequential = {"speedup": speedup, "sequential_ms_per_step": statistics.mean(seq_ms),
+                                 "batched_ms_per_step": statistics.mean(step_ms),
+                                 "max_ssh_difference_m": float(np.max(np.abs(eta_b - eta_s))),
+                                 "bitwise_equal": bool(np.array_equal(eta_b, eta_s)), "after_steps": nchk}
 
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
     mean_step_s = statistics.mean(step_ms) * 1e-3
@@ -575,10 +589,7 @@ def run_ensemble(args, world, rank, local):
                            autotune=args.autotune,
                            autotune_ms_per_step={c.label(): t for c, t in table}),
             "roofline": roofline, "e2e": e2e,
-            "batched_vs_sequential": {"speedup": speedup, "sequential_ms_per_step": statistics.mean(seq_ms),
-                                      "batched_ms_per_step": statistics.mean(step_ms),
-                                      "max_ssh_difference_m": ssh_diff,
-                                      "bitwise_equal": bool(np.array_equal(eta_b, eta_s)), "after_steps": nchk},
+            "batched_vs_sequential": batched_vs_sequential,
             "gpu_launches": args.steps * launches_per_step,
             "graph_launches_per_step": 1 if sim.sesw_get_info()["step_graph"] else 0,
             "clocks": clk}

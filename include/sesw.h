@@ -260,6 +260,17 @@ int sesw_set_mode(sesw_ctx *ctx, int32_t mode);
 #define SESW_FORM_STREAM_UNCACHED 3
 int sesw_set_persistent_form(sesw_ctx *ctx, int32_t form);
 
+/* Persistent mode, batches: the residency and kernel form of the packs of "large" basins,
+ * those too large for one grid of patches of the common size (the largest patch whose static
+ * data fits shared memory at the batch's blocks per SM, 1280 vertices at one block per SM).
+ * Such a basin fills its own grid of blocks_per_sm x SMs patches; blocks_per_sm 0 (default)
+ * takes the batch's own value, and form -1 (default) the form of sesw_set_persistent_form.
+ * With two blocks per SM and the streaming form, for example, a 400k-vertex basin runs 304
+ * patches of ~1300 vertices streamed from L2 while the small basins of the same batch keep one
+ * block per SM and their static data in shared memory. Results do not depend on this choice
+ * (bitwise). Takes effect at the next mesh upload. */
+int sesw_set_large_basins(sesw_ctx *ctx, int32_t blocks_per_sm, int32_t form);
+
 /* Persistent mode: resident blocks (patches) per SM, 1, 2 or 4; 0 (default) tries 2
  * and falls back to 1. Takes effect at the next mesh upload. */
 int sesw_set_blocks_per_sm(sesw_ctx *ctx, int32_t blocks_per_sm);
@@ -278,12 +289,13 @@ int sesw_mesh_upload(sesw_ctx *ctx, const sesw_mesh *mesh);
 /* Upload a batch of independent meshes ("basins", e.g. ensemble members of uneven
  * size) that advance together in every sesw_advance. Each mesh is validated and
  * prepared exactly as sesw_mesh_upload would prepare it alone (its own space-filling
- * curve order and patches), and the layouts are concatenated, so with SESW_MODE_GRAPH a
- * basin's results are bitwise those of its own upload with the same patch size. In
- * SESW_MODE_PERSISTENT one patch size is used for all meshes (the smallest that puts
- * the largest mesh into one grid of resident blocks); the meshes are packed, largest
- * first, into packs that each fill at most that grid, and a step runs one cooperative
- * launch per pack. Caller order of every state,
+ * curve order and patches), and the layouts are concatenated; a basin's results are
+ * bitwise those of its own upload in any mode and layout. In SESW_MODE_PERSISTENT each basin
+ * gets the larger of its one-grid patch size and a common size whose static data fits shared
+ * memory (basins larger than one grid of those are cut by sesw_set_large_basins); the meshes
+ * are packed, largest first, into packs that each fill at most one grid of resident blocks,
+ * a step runs one cooperative launch per pack, and the launches of a step are one CUDA graph.
+ * Caller order of every state,
  * forcing and output array is the concatenation of the meshes in order. Errors name
  * the first bad basin. */
 int sesw_mesh_upload_batch(sesw_ctx *ctx, int32_t nmesh, const sesw_mesh *meshes);

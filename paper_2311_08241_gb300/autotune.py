@@ -41,6 +41,8 @@ class Choice:
     block_threads: int = 256
     ms_per_step: float = float("inf")
     form: int = S.SESW_FORM_AUTO
+    large_bps: int = 0          # batches: blocks per SM of the large basins' packs (0: blocks_per_sm)
+    large_form: int = -1        # batches: their kernel form (-1: form)
 
     def apply(self, sim):
         sim.sesw_set_mode(self.mode)
@@ -48,10 +50,15 @@ class Choice:
         sim.sesw_set_patch_vertices(self.patch_vertices)
         sim.sesw_set_block_threads(self.block_threads)
         sim.sesw_set_persistent_form(self.form)
+        sim.sesw_set_large_basins(self.large_bps, self.large_form)
 
     def label(self):
         if self.mode == S.SESW_MODE_PERSISTENT:
-            return f"persistent bps={self.blocks_per_sm}{FORM_NAMES[self.form]}"
+            lab = f"persistent bps={self.blocks_per_sm}{FORM_NAMES[self.form]}"
+            if self.large_bps or self.large_form >= 0:
+                lf = self.form if self.large_form < 0 else self.large_form
+                lab += f" large bps={self.large_bps or self.blocks_per_sm}{FORM_NAMES[lf]}"
+            return lab
         return f"graph pv={self.patch_vertices} bt={self.block_threads}"
 
 
@@ -71,11 +78,14 @@ def _time_steps(sim, steps, warmup, stream):
 
 def autotune(meshes, params, forcing=None, steps=5, warmup=2, device=0, include_graph=True, include_persistent=True,
              graph_patches=GRAPH_PATCHES, graph_threads=GRAPH_THREADS, verbose=False,
-             persistent_forms=(S.SESW_FORM_AUTO, S.SESW_FORM_STREAM), wave_sizes=True):
+             persistent_forms=(S.SESW_FORM_AUTO, S.SESW_FORM_STREAM), wave_sizes=True,
+             large_layouts=((2, S.SESW_FORM_AUTO), (2, S.SESW_FORM_STREAM), (4, S.SESW_FORM_STREAM))):
     """Time every candidate layout on the meshes (a list: one mesh, or the basins of a batch).
 
     params: one Params per mesh. forcing: optional concatenated [sum E][2] array.
-    Persistent candidates: every blocks-per-SM count with every kernel form of persistent_forms.
+    Persistent candidates: every blocks-per-SM count with every kernel form of persistent_forms;
+    for a batch also one block per SM for the common basins with each (blocks per SM, form) of
+    large_layouts for the large ones.
     Graph candidates: graph_patches (plus, with wave_sizes, the one-wave patch sizes) with every
     block size of graph_threads.
     Returns (best Choice, list of (Choice, ms_per_step or None)).
@@ -115,17 +125,20 @@ def autotune(meshes, params, forcing=None, steps=5, warmup=2, device=0, include_
             return _time_steps(sim, steps, warmup, stream)
 
     if include_persistent:
-        for k in PERSISTENT_BLOCKS:
-            for form in persistent_forms:
-                c = Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=k, form=form)
-                try:
-                    t = run(c)
-                except S.SeswError:
-                    t = None
-                c.ms_per_step = t if t is not None else float("inf")
-                table.append((c, t))
-                if verbose:
-                    print(c.label(), t)
+        cands = [Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=k, form=form)
+                 for k in PERSISTENT_BLOCKS for form in persistent_forms]
+        if len(meshes) > 1:
+            cands += [Choice(S.SESW_MODE_PERSISTENT, blocks_per_sm=1, large_bps=lb, large_form=lf)
+                      for lb, lf in large_layouts]
+        for c in cands:
+            try:
+                t = run(c)
+            except S.SeswError:
+                t = None
+            c.ms_per_step = t if t is not None else float("inf")
+            table.append((c, t))
+            if verbose:
+                print(c.label(), t)
     if include_graph:
         nsm = torch.cuda.get_device_properties(device).multi_processor_count
         waves = set(wave_patch_sizes(max(m.nv for m in meshes), nsm)) if wave_sizes else set()

@@ -346,6 +346,18 @@ int sesw_set_persistent_form(sesw_ctx *c, int32_t form)
     return SESW_OK;
 }
 
+int sesw_set_large_basins(sesw_ctx *c, int32_t blocks_per_sm, int32_t form)
+{
+    if (!c) return SESW_EINVAL;
+    if (blocks_per_sm != 0 && blocks_per_sm != 1 && blocks_per_sm != 2 && blocks_per_sm != 4)
+        return fail(c, SESW_EINVAL, "blocks_per_sm must be 0, 1, 2 or 4");
+    if (form < -1 || form > SESW_FORM_STREAM_UNCACHED)
+        return fail(c, SESW_EINVAL, "form must be -1 or one of SESW_FORM_AUTO, _REGISTERS, _STREAM, _STREAM_UNCACHED");
+    c->large_bps = blocks_per_sm;
+    c->large_form = form;
+    return SESW_OK;
+}
+
 int sesw_set_mode(sesw_ctx *c, int32_t mode)
 {
     if (!c) return SESW_EINVAL;
@@ -401,10 +413,14 @@ static int prepare_parts(sesw_ctx *c, const sesw_mesh *meshes, int n, const std:
 // packs of at most nblk patches, one cooperative launch each: a basin gets the larger of
 // its one-grid size and a common size `base`, the largest patch whose static data fits
 // shared memory (so most basins run the cached kernel), or a smaller one when the whole
-// batch then fits a single pack. Returns base.
-static int persistent_patch_sizes(const sesw_mesh *meshes, int n, int nblk, int bps, std::vector<int> &pv)
+// batch then fits a single pack. Basins whose one-grid size exceeds `base` ("large") are
+// cut into one grid of nblk_large patches instead (their own residency, see
+// sesw_set_large_basins) and marked in `large`. Returns base.
+static int persistent_patch_sizes(const sesw_mesh *meshes, int n, int nblk, int bps, int nblk_large,
+                                  std::vector<int> &pv, std::vector<char> &large)
 {
     pv.assign(n, 32);
+    large.assign(n, 0);
     long long total = 0;
     for (int b = 0; b < n; b++) {
         total += meshes[b].nv;
@@ -415,31 +431,45 @@ static int persistent_patch_sizes(const sesw_mesh *meshes, int n, int nblk, int 
     long long base = cached;
     if (nblk > n) base = std::min<long long>(base, (total + (nblk - n) - 1) / (nblk - n));
     base = std::max<long long>(32, base);
-    for (int b = 0; b < n; b++) pv[b] = std::max<int>(pv[b], (int)base);
+    for (int b = 0; b < n; b++) {
+        if (pv[b] > base) {
+            large[b] = 1;
+            pv[b] = (int)std::max<long long>(32, (meshes[b].nv + nblk_large - 1) / nblk_large);
+        } else {
+            pv[b] = (int)base;
+        }
+    }
     return (int)base;
 }
 
-// Packs of a persistent batch: basins of the common patch size and basins of larger
-// patches are packed separately (first fit, largest first), so that a pack's plan is not
-// set by a larger class; each pack gets the plans of its largest patch. Leaves `packs`
-// empty when some pack does not fit the persistent kernel.
-static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int base, int nblk, int bps, int form,
-                       std::vector<sesw::PackPlan> &packs, std::vector<std::vector<int>> &pack_basins)
+// Packs of a persistent batch: basins of the common patch size and large basins are packed
+// separately (first fit, largest first), so that a pack's plan is not set by a larger class;
+// each pack gets the plans of its largest patch. The common class packs at most nblk patches
+// per launch with bps resident blocks per SM and kernel form `form`; the large class nblk_large,
+// bps_large and form_large. Leaves `packs` empty when some pack does not fit the persistent kernel.
+static void make_packs(const sesw::HostMesh &hm, const std::vector<char> &large, int nblk, int bps, int form,
+                       int nblk_large, int bps_large, int form_large, std::vector<sesw::PackPlan> &packs,
+                       std::vector<std::vector<int>> &pack_basins)
 {
     packs.clear();
     pack_basins.clear();
     auto np_of = [&](int b) { return hm.basin_patch[b + 1] - hm.basin_patch[b]; };
     for (int cls = 0; cls < 2; cls++) {
+        const int cap = cls ? nblk_large : nblk, kbps = cls ? bps_large : bps, kform = cls ? form_large : form;
         std::vector<int> order;
         for (int b = 0; b < hm.nbasin; b++)
-            if ((pv[b] > base) == (cls == 1)) order.push_back(b);
+            if ((large[b] != 0) == (cls == 1)) order.push_back(b);
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return np_of(x) > np_of(y); });
         std::vector<std::vector<int>> bins;
         std::vector<int> fill;
         for (int b : order) {
-            if (np_of(b) > nblk) return;
+            if (np_of(b) > cap) {
+                packs.clear();
+                pack_basins.clear();
+                return;
+            }
             size_t k = 0;
-            while (k < bins.size() && fill[k] + np_of(b) > nblk) k++;
+            while (k < bins.size() && fill[k] + np_of(b) > cap) k++;
             if (k == bins.size()) {
                 bins.emplace_back();
                 fill.push_back(0);
@@ -462,17 +492,17 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                     for (int v = hm.patch_v[q]; v < hm.patch_v[q + 1]; v++)
                         pk.mx.deg = std::max(pk.mx.deg, hm.vcsr_off[v + 1] - hm.vcsr_off[v]);
                 }
-            const bool streamed = form == SESW_FORM_STREAM || form == SESW_FORM_STREAM_UNCACHED;
-            const int idx_mode = form == SESW_FORM_STREAM_UNCACHED ? 0 : -1;
+            const bool streamed = kform == SESW_FORM_STREAM || kform == SESW_FORM_STREAM_UNCACHED;
+            const int idx_mode = kform == SESW_FORM_STREAM_UNCACHED ? 0 : -1;
             if (streamed) {
-                pk.plan = sesw::persistent_plan_stream(pk.mx, bps, idx_mode);
+                pk.plan = sesw::persistent_plan_stream(pk.mx, kbps, idx_mode);
             } else {
-                pk.plan = sesw::persistent_plan(pk.mx, bps);
+                pk.plan = sesw::persistent_plan(pk.mx, kbps);
                 // patches whose state does not fit in registers without heavy spills (8 or more
                 // slots per thread) stream it from global memory; measured on the sphere at
                 // level 8 this is faster, and with 6 slots per thread the register kernel is
-                if (form == SESW_FORM_AUTO && (pk.plan.slots_per_thread == 0 || pk.plan.slots_per_thread >= 8)) {
-                    const sesw::PersistentPlan st = sesw::persistent_plan_stream(pk.mx, bps);
+                if (kform == SESW_FORM_AUTO && (pk.plan.slots_per_thread == 0 || pk.plan.slots_per_thread >= 8)) {
+                    const sesw::PersistentPlan st = sesw::persistent_plan_stream(pk.mx, kbps);
                     if (st.slots_per_thread > 0) pk.plan = st;
                 }
             }
@@ -481,13 +511,13 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<int> &pv, int
                 pack_basins.clear();
                 return;
             }
-            pk.plan.blocks_per_sm = bps;
+            pk.plan.blocks_per_sm = kbps;
             if (streamed) {
-                pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, bps, idx_mode);
+                pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, kbps, idx_mode);
             } else {
-                pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, bps);
-                if (form == SESW_FORM_AUTO && pk.plan_sesm.slots_per_thread == 0)
-                    pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, bps);
+                pk.plan_sesm = sesw::persistent_plan_sesm(pk.mx, kbps);
+                if (kform == SESW_FORM_AUTO && pk.plan_sesm.slots_per_thread == 0)
+                    pk.plan_sesm = sesw::persistent_plan_sesm_stream(pk.mx, kbps);
             }
             packs.push_back(pk);
             pack_basins.push_back(bn);
@@ -523,12 +553,16 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
             for (int bps : tries) {
                 if (bps <= 0 || !packs.empty()) continue;
                 const int nblk = nsm * bps;
+                const int bps_large = c->large_bps > 0 ? c->large_bps : bps;
+                const int form_large = c->large_form >= 0 ? c->large_form : c->form;
+                const int nblk_large = nsm * bps_large;
                 std::vector<int> pv;
-                const int base = persistent_patch_sizes(meshes, n, nblk, bps, pv);
+                std::vector<char> large;
+                persistent_patch_sizes(meshes, n, nblk, bps, nblk_large, pv, large);
                 rc = prepare_parts(c, meshes, n, pv, hm, err);
                 if (rc != SESW_OK) return fail(c, rc, err);
                 if (sesw::build_halos(hm, err) == SESW_OK)
-                    make_packs(hm, pv, base, nblk, bps, c->form, packs, pack_basins);
+                    make_packs(hm, large, nblk, bps, c->form, nblk_large, bps_large, form_large, packs, pack_basins);
             }
             if (!packs.empty()) {
                 plan = packs[0].plan;

@@ -306,6 +306,8 @@ struct sesw_ctx {
     int mode_req = SESW_MODE_AUTO, mode = SESW_MODE_GRAPH;
     int blocks_per_sm = 0;         // persistent mode; 0 = try 2, then 1
     int form = SESW_FORM_AUTO;     // persistent mode: which kernel a pack runs (sesw_set_persistent_form)
+    int large_bps = 0;             // batches: resident blocks per SM of the large basins' packs (0: blocks_per_sm)
+    int large_form = -1;           // batches: kernel form of the large basins' packs (-1: form)
     sesw::PersistentPlan plan;
     sesw::PersistentPlan plan_sesm;   // the SESM scheme's plan (empty: graph mode only)
     std::vector<sesw::PackPlan> packs;   // persistent mode: the launches of a step

@@ -40,7 +40,8 @@ _NAMES = {0: "SESW_OK", -1: "SESW_EINVAL", -2: "SESW_ECUDA", -3: "SESW_ESTATE", 
           -5: "SESW_EUNSTABLE", -6: "SESW_ENOMEM"}
 
 # every symbol include/sesw.h declares
-EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_persistent_form", "sesw_set_blocks_per_sm",
+EXPORTS = ("sesw_create", "sesw_set_stream", "sesw_set_mode", "sesw_set_persistent_form", "sesw_set_large_basins",
+           "sesw_set_blocks_per_sm",
            "sesw_set_patch_vertices",
            "sesw_set_block_threads",
            "sesw_mesh_upload", "sesw_mesh_upload_batch", "sesw_set_params_batch", "sesw_diagnostics_batch",
@@ -120,6 +121,7 @@ def load(build_if_missing: bool = True):
         L.sesw_set_mode.argtypes = [P, ctypes.c_int32]
         L.sesw_set_blocks_per_sm.argtypes = [P, ctypes.c_int32]
         L.sesw_set_persistent_form.argtypes = [P, ctypes.c_int32]
+        L.sesw_set_large_basins.argtypes = [P, ctypes.c_int32, ctypes.c_int32]
         L.sesw_mesh_upload.argtypes = [P, ctypes.POINTER(sesw_mesh)]
         L.sesw_set_params.argtypes = [P, ctypes.POINTER(sesw_params)]
         L.sesw_mesh_upload_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(sesw_mesh)]
@@ -266,6 +268,9 @@ class Subcycle:
 
     def sesw_set_persistent_form(self, form: int):
         return self._check(self._L.sesw_set_persistent_form(self._h, int(form)))
+
+    def sesw_set_large_basins(self, blocks_per_sm: int = 0, form: int = -1):
+        return self._check(self._L.sesw_set_large_basins(self._h, int(blocks_per_sm), int(form)))
 
     def sesw_set_block_threads(self, n: int):
         return self._check(self._L.sesw_set_block_threads(self._h, int(n)))

@@ -125,3 +125,29 @@ def test_persistent_batch_in_packs_is_bitwise_the_single_runs(S):
         _same(single, (e, u, um), f"basin {b} persistent")
         if b % 5 == 0:
             _same(_run(S, c, 2, GRAPH)[0], (e, u, um), f"basin {b} graph")
+
+
+def test_batch_with_large_basins_on_their_own_residency(S):
+    """A batch whose large basins (above one grid of 1280-vertex patches) run at two blocks per SM,
+    streamed or in registers, next to small basins at one block per SM with cached static data:
+    every basin bitwise equals its own single upload."""
+    big = I.ensemble_cases(nbasins=2, vmin=2.1e5, vmax=2.4e5, seed=31, nsteps=2)
+    small = I.ensemble_cases(nbasins=3, vmin=5e3, vmax=2e4, seed=32, nsteps=2, M=big[0].params.M)
+    cases = small + big
+    singles = [_run(S, c, 2, PERSISTENT)[0] for c in cases]
+    for lform in (S.SESW_FORM_AUTO, S.SESW_FORM_STREAM):
+        with S.Subcycle() as s:
+            s.sesw_set_mode(PERSISTENT)
+            s.sesw_set_blocks_per_sm(1)
+            s.sesw_set_large_basins(2, lform)
+            s.sesw_mesh_upload_batch([c.mesh for c in cases])
+            s.sesw_set_params_batch([c.params for c in cases])
+            s.sesw_set_forcing(np.concatenate([c.R for c in cases]))
+            s.sesw_set_state(np.concatenate([c.eta0 for c in cases]), np.concatenate([c.U0 for c in cases]))
+            s.sesw_advance(2)
+            info = s.sesw_get_info()
+            eta, U, Um = s.sesw_get_state()
+        assert info["mode"] == PERSISTENT and info["npack"] >= 3, info
+        parts = zip(cases, singles, _split(cases, eta, "v"), _split(cases, U, "e"), _split(cases, Um, "e"))
+        for b, (c, single, e, u, um) in enumerate(parts):
+            _same(single, (e, u, um), f"basin {b} large form {lform}")
