@@ -562,14 +562,15 @@ def run_ensemble(args, world, rank, local):
     persistent = info["mode"] == S.SESW_MODE_PERSISTENT
     mean_step_s = statistics.mean(step_ms) * 1e-3
     b_alg_step = algorithmic_bytes_per_substep(V, E) * M
-    launches_per_step = max(1, info["npack"]) if persistent else M + 1
+    launches_per_step = max(1, sim.sesw_get_info()["launches"])
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if persistent:
         kernels = ("k_persistent", "k_persistent_stream")
         fig = profile_figures("k_persistent_ensemble", kernels)
         if fig is not None and f"layout: {best.label()}\n" not in open(os.path.join(ROOT, fig["profile"])).read():
             fig = None
-        roofline = roofline_issue(f"k_persistent + k_persistent_stream ({launches_per_step} pack launches per step)",
+        roofline = roofline_issue(f"k_persistent + k_persistent_stream ({info['npack']} packs in "
+                                  f"{launches_per_step} launches per step)",
                                   mean_step_s, fig and fig.get("warp_instructions_per_step"),
                                   fig and fig.get("dram_bytes_per_step"), b_alg_step, sms, sm_max_mhz_of(clk),
                                   per="step")

@@ -203,9 +203,11 @@ typedef struct sesw_info {
     double visc_stiffness;   /* max_e 2 sum_edges (H0_edge/H0_e)(L/d)/A_e (1/m^2): visc_number =
                                 (tau/M) visc_background visc_stiffness */
     int32_t step_graph;      /* 1 when a baroclinic step is enqueued as one CUDA graph launch (all of its
-                                kernels: one per pack in persistent mode, M + 1 in graph mode); 0 when
-                                the cooperative launches could not be captured and are issued directly */
-    int32_t reserved;
+                                kernels); 0 when the cooperative launches could not be captured and are
+                                issued directly */
+    int32_t launches;        /* kernel launches of one step: persistent SE, one per group of packs that
+                                run the same kernel (a launch runs its packs one after another);
+                                persistent SESM, one per pack; graph mode, M + 1 (SE) */
 } sesw_info;
 
 /* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a

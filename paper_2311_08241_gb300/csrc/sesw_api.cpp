@@ -123,7 +123,7 @@ int capture_step_graph(sesw_ctx *c, int parity, cudaGraphExec_t *out)
     } else if (c->mode == SESW_MODE_PERSISTENT) {
         e = c->params.scheme == 1
                 ? sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, parity, c->packs, c->cap_stream)
-                : sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->packs, c->cap_stream);
+                : sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, parity, c->groups, c->cap_stream);
     } else if (c->params.scheme == 1) {
         // SESM: level rings, U^m in B[m % 3] (B[0] holds U^0 and, at the end, U^M) and
         // eta^m in Er[m % 5] (Er[0] holds eta^0 and, at the end, eta^M); levels before
@@ -201,7 +201,7 @@ int enqueue_step(sesw_ctx *c)
         if (c->params.scheme == 1)
             CK(c, sesw::launch_persistent_sesm(c->dm, c->ds, c->args, c->params.M, c->parity, c->packs, c->stream));
         else
-            CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->packs, c->stream));
+            CK(c, sesw::launch_persistent(c->dm, c->ds, c->args, c->params.M, c->parity, c->groups, c->stream));
         c->parity ^= 1;
         return SESW_OK;
     }
@@ -525,6 +525,52 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<char> &large,
     }
 }
 
+// Launch groups of an SE step: consecutive packs that run the same kernel (same form, slots
+// per thread, cached or streamed static data, residency) share one cooperative launch, planned
+// for their common largest patch; a pack for which the merged plan would pick another kernel,
+// or no longer fit, starts a new group.
+static std::vector<sesw::PackGroup> make_groups(const std::vector<sesw::PackPlan> &packs)
+{
+    std::vector<sesw::PackGroup> groups;
+    auto same_kernel = [](const sesw::PersistentPlan &x, const sesw::PersistentPlan &y) {
+        return x.slots_per_thread == y.slots_per_thread && x.cached == y.cached && x.stream == y.stream &&
+               x.blocks_per_sm == y.blocks_per_sm;
+    };
+    for (size_t k = 0; k < packs.size(); k++) {
+        const sesw::PackPlan &pk = packs[k];
+        if (!groups.empty() && same_kernel(groups.back().plan, pk.plan)) {
+            sesw::PackGroup &g = groups.back();
+            sesw::PatchMax mx = g.mx;
+            mx.slots = std::max(mx.slots, pk.mx.slots);
+            mx.local = std::max(mx.local, pk.mx.local);
+            mx.vertices = std::max(mx.vertices, pk.mx.vertices);
+            mx.halo = std::max(mx.halo, pk.mx.halo);
+            mx.csr = std::max(mx.csr, pk.mx.csr);
+            mx.deg = std::max(mx.deg, pk.mx.deg);
+            const int bps = pk.plan.blocks_per_sm;
+            sesw::PersistentPlan np = pk.plan.stream ? sesw::persistent_plan_stream(mx, bps, pk.plan.stream == 2 ? 0 : -1)
+                                                     : sesw::persistent_plan(mx, bps);
+            np.blocks_per_sm = bps;
+            if (np.slots_per_thread > 0 && (pk.plan.stream || np.slots_per_thread == pk.plan.slots_per_thread) &&
+                same_kernel(np, pk.plan)) {
+                g.mx = mx;
+                g.plan = np;
+                g.last = (int)k + 1;
+                g.nblocks = std::max(g.nblocks, pk.nblocks);
+                continue;
+            }
+        }
+        sesw::PackGroup g;
+        g.first = (int)k;
+        g.last = (int)k + 1;
+        g.nblocks = pk.nblocks;
+        g.mx = pk.mx;
+        g.plan = pk.plan;
+        groups.push_back(g);
+    }
+    return groups;
+}
+
 static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
 {
     if (!c) return SESW_EINVAL;
@@ -543,6 +589,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     int mode = SESW_MODE_GRAPH;
     sesw::PersistentPlan plan, plan_sesm;
     std::vector<sesw::PackPlan> packs;
+    std::vector<sesw::PackGroup> groups;
     std::vector<std::vector<int>> pack_basins;
     try {
         if (c->mode_req != SESW_MODE_GRAPH) {
@@ -639,6 +686,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
             d.pack_off.push_back((int)pp.size());
         }
         TRY(upload(c, &d.pack_patch, pp, "pack_patch"));
+        TRY(upload(c, &d.pack_off_d, d.pack_off, "pack_off"));
     }
     {
         std::vector<int> bslot(hm.nbasin + 1);
@@ -676,6 +724,9 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
         TRY(zalloc(c, &s.xbuf[0], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.xbuf[1], 2 * (size_t)hm.nv, "xbuf"));
         TRY(zalloc(c, &s.flags, sesw::persistent_flag_bytes(hm.npatch) / sizeof(unsigned), "flags"));
+        groups = make_groups(packs);
+        for (const auto &g : groups)
+            CK(c, g.plan.stream ? sesw::persistent_prepare_stream(g.plan) : sesw::persistent_prepare(g.plan));
         for (const auto &pk : packs) {
             CK(c, pk.plan.stream ? sesw::persistent_prepare_stream(pk.plan) : sesw::persistent_prepare(pk.plan));
             if (plan_sesm.slots_per_thread > 0)
@@ -740,6 +791,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     c->plan = plan;
     c->plan_sesm = plan_sesm;
     c->packs = packs;
+    c->groups = groups;
     c->persist_graph_ok = true;
     c->grad_gram_max_h = hm.grad_gram_max_h;
     c->nbasin = hm.nbasin;
@@ -1264,6 +1316,10 @@ int sesw_get_info(sesw_ctx *c, sesw_info *info)
     info->visc_number = c->have_params ? c->visc_number : 0.0;
     for (double v : c->basin_visc_stiffness) info->visc_stiffness = std::max(info->visc_stiffness, v);
     info->step_graph = c->mode == SESW_MODE_PERSISTENT && !c->persist_graph_ok ? 0 : 1;
+    if (c->mode == SESW_MODE_PERSISTENT)
+        info->launches = (int32_t)(c->have_params && c->params.scheme == 1 ? c->packs.size() : c->groups.size());
+    else
+        info->launches = (c->have_params ? c->params.M : 0) + 1;
     return SESW_OK;
 }
 

@@ -130,6 +130,7 @@ struct DevMesh {
     // step launches the packs one after another
     int *pack_patch = nullptr;     // [npatch] patch ids, pack by pack
     std::vector<int> pack_off;     // [npack+1] ranges into pack_patch (host)
+    int *pack_off_d = nullptr;     // the same on the device
     // persistent kernel
     int *patch_halo = nullptr;
     int *halo_v = nullptr;
@@ -252,11 +253,19 @@ struct PackPlan {
     PatchMax mx;
     PersistentPlan plan, plan_sesm;
 };
+// Consecutive packs [first, last) that one cooperative launch of the SE kernels runs one after
+// another: they share the kernel, with the plan and shared-memory layout of their common
+// largest patch (mx) and as many blocks as the largest of them.
+struct PackGroup {
+    int first = 0, last = 0, nblocks = 0;
+    PatchMax mx;
+    PersistentPlan plan;
+};
 PersistentPlan persistent_plan(const PatchMax &mx, int blocks_per_sm);
 cudaError_t persistent_prepare(const PersistentPlan &plan);
 size_t persistent_flag_bytes(int npatch);
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                              const std::vector<PackPlan> &packs, cudaStream_t stream);
+                              const std::vector<PackGroup> &groups, cudaStream_t stream);
 // The SESM scheme for patches too large for its on-chip state (k_persistent_sesm_stream):
 // two more slot arrays (DevState::U_x) hold U^{m-2} and U_AB^{m-1}.
 // idx_mode: -1 keeps the slots' corner indices in shared memory when they fit, 0 never.
@@ -268,8 +277,8 @@ cudaError_t launch_persistent_sesm_stream_pack(const DevMesh &m, const DevState 
 // static data stay in global memory; only the elevation and the fluxes are on chip.
 PersistentPlan persistent_plan_stream(const PatchMax &mx, int blocks_per_sm, int idx_mode = -1);
 cudaError_t persistent_prepare_stream(const PersistentPlan &plan);
-cudaError_t launch_persistent_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                                          const PackPlan &pk, int pack_index, cudaStream_t stream);
+cudaError_t launch_persistent_stream_group(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                                           const PackGroup &g, cudaStream_t stream);
 // The SESM scheme in the persistent form (k_persistent_sesm): cached patches of at most
 // 4 x 384 slots and 2 x 384 own vertices; an empty plan when the patches do not fit.
 PersistentPlan persistent_plan_sesm(const PatchMax &mx, int blocks_per_sm);
@@ -310,7 +319,8 @@ struct sesw_ctx {
     int large_form = -1;           // batches: kernel form of the large basins' packs (-1: form)
     sesw::PersistentPlan plan;
     sesw::PersistentPlan plan_sesm;   // the SESM scheme's plan (empty: graph mode only)
-    std::vector<sesw::PackPlan> packs;   // persistent mode: the launches of a step
+    std::vector<sesw::PackPlan> packs;   // persistent mode: the packs of a step (one launch each for SESM)
+    std::vector<sesw::PackGroup> groups; // persistent mode: the launches of an SE step
     bool persist_graph_ok = true;
     bool have_mesh = false, have_params = false;
     sesw::DevMesh dm;

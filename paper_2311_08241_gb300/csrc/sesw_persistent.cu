@@ -50,12 +50,12 @@ __device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a, f
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set;
 // the instantiation without them carries neither load nor branch.
+// One baroclinic step of patch p, the block's patch in pack `pack` (npb blocks take part).
 template <int SPT, int NONLIN, int CACHED, int EXTRA>
-__global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
+__device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, const int pack, const int npb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_abort;
-    const int p = P.pack_patch[P.pack_base + blockIdx.x];
     const int T = blockDim.x;
     const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
     const int nown_s = P.patch_own[p], nint = P.patch_int[p];
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
     const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
     const StepArgs a = P.a;
     const float dt = P.patch_dt[p];
-    unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
+    unsigned *base_word = P.flags + (size_t)(1 + 2 * pack) * kFlagStride;
     unsigned *exit_count = base_word + kFlagStride;
     const unsigned base = ld_relaxed_gpu(base_word);
     const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
@@ -287,11 +287,26 @@ __global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
             }
         }
     }
-    // the last block of the pack to leave (every block has read the base by then) sets
-    // the next launch's base
-    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == gridDim.x - 1) {
+    // the last block of the pack to leave (every block of the pack has read the base by
+    // then) sets the base of the pack's next step
+    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == (unsigned)npb - 1u) {
         *exit_count = 0u;
         *base_word = base + (unsigned)P.M + 1u;
+    }
+}
+
+// A launch runs packs [P.pack_first, P.pack_last) one after another: block b takes patch b of
+// each pack that has more than b patches. Packs exchange nothing with each other (a pack holds
+// whole basins), so a block goes on to its next pack as soon as it is done with the last
+// one, while other blocks still finish theirs; every block of a pack is resident, so the
+// waits of a pack always end.
+template <int SPT, int NONLIN, int CACHED, int EXTRA>
+__global__ void __launch_bounds__(1024, 1) k_persistent(PArgs P)
+{
+    for (int k = P.pack_first; k < P.pack_last; k++) {
+        const int b0 = P.pack_off[k], npb = P.pack_off[k + 1] - b0;
+        if ((int)blockIdx.x < npb) persistent_patch<SPT, NONLIN, CACHED, EXTRA>(P, P.pack_patch[b0 + blockIdx.x], k, npb);
+        __syncthreads();   // the next pack reuses the shared memory
     }
 }
 
@@ -396,22 +411,21 @@ cudaError_t persistent_prepare(const PersistentPlan &plan)
 }
 
 cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                              const std::vector<PackPlan> &packs, cudaStream_t stream)
+                              const std::vector<PackGroup> &groups, cudaStream_t stream)
 {
     const int extra = s.W != nullptr || s.eta_sum != nullptr;
-    for (size_t k = 0; k < packs.size(); k++) {
-        const PackPlan &pk = packs[k];
+    for (const PackGroup &g : groups) {
         cudaError_t e;
-        if (pk.plan.stream) {
-            e = launch_persistent_stream_pack(m, s, a, M, parity, pk, (int)k, stream);
+        if (g.plan.stream) {
+            e = launch_persistent_stream_group(m, s, a, M, parity, g, stream);
         } else {
-            void *fn = persistent_kernel(pk.plan.slots_per_thread, a.nonlinear_h, pk.plan.cached, extra);
+            void *fn = persistent_kernel(g.plan.slots_per_thread, a.nonlinear_h, g.plan.cached, extra);
             if (!fn) return cudaErrorInvalidValue;
-            PArgs P = make_pargs(m, s, a, M, parity, pk.mx);
-            P.pack_base = pk.base;
-            P.pack_index = (int)k;
+            PArgs P = make_pargs(m, s, a, M, parity, g.mx);
+            P.pack_first = g.first;
+            P.pack_last = g.last;
             void *args[] = {&P};
-            e = cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan.threads), args, pk.plan.smem, stream);
+            e = cudaLaunchCooperativeKernel(fn, dim3(g.nblocks), dim3(g.plan.threads), args, g.plan.smem, stream);
         }
         if (e != cudaSuccess) return e;
     }

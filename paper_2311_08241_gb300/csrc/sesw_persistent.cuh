@@ -59,7 +59,9 @@ struct PArgs {
     unsigned *flags;        // line 0: abort word; line 1 + 2k: tag base of pack k; line 2 + 2k: its exit count
     unsigned *status;
     const int *pack_patch;  // patch of each block: pack_patch[pack_base + blockIdx.x]
-    int pack_base, pack_index;
+    int pack_base, pack_index;   // launches of one pack (the SESM kernels)
+    const int *pack_off;         // [npack + 1] ranges of pack_patch
+    int pack_first, pack_last;   // launches of a group of packs (the SE kernels)
     StepArgs a;
     int M, npatch;
     // shared-memory carve-up (CACHED), in bytes from the dynamic shared base
@@ -269,6 +271,9 @@ inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, 
     P.pack_patch = m.pack_patch;
     P.pack_base = 0;
     P.pack_index = 0;
+    P.pack_off = m.pack_off_d;
+    P.pack_first = 0;
+    P.pack_last = 0;
     return P;
 }
 

@@ -56,12 +56,11 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
 // IDX = 1 keeps the slots' corner indices in shared memory; IDX = 0 (patches too large for
 // that) reads them from global memory every substep.
 template <int NONLIN, int EXTRA, int IDX>
-__global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A)
+__device__ __forceinline__ void stream_patch(const SArgs &A, const int p, const int pack, const int npb)
 {
     const PArgs &P = A.P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_abort;
-    const int p = P.pack_patch[P.pack_base + blockIdx.x];
     const int T = blockDim.x;
     const int s0 = P.patch_slot[p], ns = P.patch_slot[p + 1] - s0;
     const int nown_s = P.patch_own[p], nint = P.patch_int[p];
@@ -69,7 +68,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
     const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
     const StepArgs a = P.a;
     const float dt = P.patch_dt[p];
-    unsigned *base_word = P.flags + (size_t)(1 + 2 * P.pack_index) * kFlagStride;
+    unsigned *base_word = P.flags + (size_t)(1 + 2 * pack) * kFlagStride;
     unsigned *exit_count = base_word + kFlagStride;
     const unsigned base = ld_relaxed_gpu(base_word);
     const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
@@ -151,11 +150,23 @@ __global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A
         const float2 hi = A.Shi[s], lo = A.Slo[s];
         P.Umean[w] = make_float2((hi.x + lo.x) * a.inv_M, (hi.y + lo.y) * a.inv_M);
     }
-    // the last block of the pack to leave (every block has read the base by then) sets
-    // the next launch's base
-    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == gridDim.x - 1) {
+    // the last block of the pack to leave (every block of the pack has read the base by
+    // then) sets the base of the pack's next step
+    if (threadIdx.x == 0 && atomicAdd(exit_count, 1u) == (unsigned)npb - 1u) {
         *exit_count = 0u;
         *base_word = base + (unsigned)P.M + 1u;
+    }
+}
+
+// The packs [P.pack_first, P.pack_last) one after another, as in k_persistent.
+template <int NONLIN, int EXTRA, int IDX>
+__global__ void __launch_bounds__(kStreamThreads, 1) k_persistent_stream(SArgs A)
+{
+    const PArgs &P = A.P;
+    for (int k = P.pack_first; k < P.pack_last; k++) {
+        const int b0 = P.pack_off[k], npb = P.pack_off[k + 1] - b0;
+        if ((int)blockIdx.x < npb) stream_patch<NONLIN, EXTRA, IDX>(A, P.pack_patch[b0 + blockIdx.x], k, npb);
+        __syncthreads();   // the next pack reuses the shared memory
     }
 }
 
@@ -229,20 +240,20 @@ cudaError_t persistent_prepare_stream(const PersistentPlan &plan)
     return cudaSuccess;
 }
 
-cudaError_t launch_persistent_stream_pack(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
-                                          const PackPlan &pk, int pack_index, cudaStream_t stream)
+cudaError_t launch_persistent_stream_group(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
+                                           const PackGroup &g, cudaStream_t stream)
 {
     SArgs A;
-    A.P = make_pargs(m, s, a, M, parity, pk.mx);
-    A.P.pack_base = pk.base;
-    A.P.pack_index = pack_index;
+    A.P = make_pargs(m, s, a, M, parity, g.mx);
+    A.P.pack_first = g.first;
+    A.P.pack_last = g.last;
     A.Shi = s.S_hi;
     A.Slo = s.S_lo;
-    A.off_idx = (int)align16(smem_layout(pk.mx).total_plain);
-    void *fn = stream_kernel(a.nonlinear_h, s.W != nullptr || s.eta_sum != nullptr, pk.plan.stream == 1);
+    A.off_idx = (int)align16(smem_layout(g.mx).total_plain);
+    void *fn = stream_kernel(a.nonlinear_h, s.W != nullptr || s.eta_sum != nullptr, g.plan.stream == 1);
     if (!fn) return cudaErrorInvalidValue;
     void *args[] = {&A};
-    return cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan.threads), args, pk.plan.smem, stream);
+    return cudaLaunchCooperativeKernel(fn, dim3(g.nblocks), dim3(g.plan.threads), args, g.plan.smem, stream);
 }
 
 }  // namespace sesw

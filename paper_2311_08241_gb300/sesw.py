@@ -89,7 +89,7 @@ class sesw_info(ctypes.Structure):
                 ("courant_limit", ctypes.c_double), ("stiffness_bound", ctypes.c_double),
                 ("device_bytes", ctypes.c_int64), ("npack", ctypes.c_int32), ("streamed", ctypes.c_int32),
                 ("visc_number", ctypes.c_double), ("visc_stiffness", ctypes.c_double),
-                ("step_graph", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("step_graph", ctypes.c_int32), ("launches", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
