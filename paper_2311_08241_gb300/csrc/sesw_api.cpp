@@ -11,6 +11,8 @@
 #include <thread>
 #include <cstdio>
 #include <new>
+#include <numeric>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -522,6 +524,24 @@ static void make_packs(const sesw::HostMesh &hm, const std::vector<char> &large,
             packs.push_back(pk);
             pack_basins.push_back(bn);
         }
+        // packs of one class that run the same kernel next to each other, so that one launch
+        // takes them all (make_groups)
+        const size_t first = packs.size() - bins.size();
+        std::vector<size_t> korder(bins.size());
+        std::iota(korder.begin(), korder.end(), first);
+        auto key = [&](size_t k) {
+            const sesw::PersistentPlan &q = packs[k].plan;
+            return std::make_tuple(q.stream, q.cached, q.slots_per_thread);
+        };
+        std::stable_sort(korder.begin(), korder.end(), [&](size_t x, size_t y) { return key(x) < key(y); });
+        std::vector<sesw::PackPlan> sp;
+        std::vector<std::vector<int>> sb;
+        for (size_t k : korder) {
+            sp.push_back(packs[k]);
+            sb.push_back(pack_basins[k]);
+        }
+        std::copy(sp.begin(), sp.end(), packs.begin() + first);
+        std::copy(sb.begin(), sb.end(), pack_basins.begin() + first);
     }
 }
 

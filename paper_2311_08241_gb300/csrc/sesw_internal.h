@@ -298,6 +298,14 @@ size_t linear_tc_packed_elems(int K);
 cudaError_t pack_linear_tc(int K, const __nv_bfloat16 *W, __nv_bfloat16 *packed, cudaStream_t st);
 cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *packed, const float *bias, int act,
                              float *Y, unsigned *status, cudaStream_t st);
+// Backward of such a layer on the tensor cores, dA (FP32) split into two bfloat16 parts:
+// partial sums of the weight gradient sum_n Z[n][i] dA[n][j] and of the bias gradient over
+// rows_per_cta rows each (a multiple of 64; layout of k_reduce_partials), and the input
+// gradient dZ[n][i] = sum_j dA[n][j] W[i][j] (W: K x 64 bfloat16, row-major). K = 128 or 192.
+cudaError_t launch_wgrad_tc(int N, int K, int rows_per_cta, const float *Z, const float *dA, float *partial,
+                            unsigned *status, cudaStream_t st);
+cudaError_t launch_dgrad_tc(int N, int K, const float *dA, const __nv_bfloat16 *W, float *dZ, unsigned *status,
+                            cudaStream_t st);
 
 }  // namespace sesw
 

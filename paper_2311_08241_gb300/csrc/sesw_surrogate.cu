@@ -706,13 +706,17 @@ cudaError_t pack_tc(Surrogate &S, cudaStream_t st)
     return cudaSuccess;
 }
 
-// gradient of layer l's matrix and bias from its input Z [N][K] and dA [N][C]
+// gradient of layer l's matrix and bias from its input Z [N][K] and dA [N][C]; the message
+// layers (inputs rounded to bfloat16 values, 64 outputs) on the tensor cores
 cudaError_t wgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const float *Z, const float *dA)
 {
     const int rows = 2048;
     const int nb = std::max(1, (N + rows - 1) / rows);
     const int len = ly.K * ly.C + ly.C;
-    if (ly.K <= 16)
+    if (ly.tc >= 0) {
+        const cudaError_t e = launch_wgrad_tc(N, ly.K, rows, Z, dA, S.partial, S.status, st);
+        if (e != cudaSuccess) return e;
+    } else if (ly.K <= 16)
         k_mm_wgrad<1><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
     else if (ly.K <= 64)
         k_mm_wgrad<4><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
@@ -722,6 +726,13 @@ cudaError_t wgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const f
         k_mm_wgrad<12><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
     k_reduce_partials<<<grid1(len), 256, 0, st>>>(S.partial, nb, len, S.grad + ly.w, S.grad + ly.b, ly.K * ly.C);
     return cudaGetLastError();
+}
+
+// dZ = dA W^T of a message layer (the gradient with respect to its inputs), on the tensor cores
+cudaError_t dgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const float *dA, float *dZ)
+{
+    if (ly.tc >= 0) return launch_dgrad_tc(N, ly.K, dA, S.w16 + ly.w, dZ, S.status, st);
+    return mm(S, st, N, ly.C, ly.K, dA, S.w16 + ly.w, 1, nullptr, 0, nullptr, dZ);
 }
 
 // forward of one sample whose features are in S.xv, S.xe
@@ -772,14 +783,14 @@ cudaError_t backward(Surrogate &S, cudaStream_t st)
         k_msg_vert<<<grid1((size_t)S.V * HC), 256, 0, st>>>(S.V, S.voff, S.vinc, S.earea, S.vinvA, S.hv[l], S.he[l + 1],
                                                             S.zv);
         if ((e = wgrad(S, st, lv, S.V, S.zv, S.dav)) != cudaSuccess) return e;
-        if ((e = mm(S, st, S.V, HC, 2 * HC, S.dav, S.w16 + lv.w, 1, nullptr, 0, nullptr, S.dzv)) != cudaSuccess) return e;
+        if ((e = dgrad(S, st, lv, S.V, S.dav, S.dzv)) != cudaSuccess) return e;
         k_msg_vert_adj_v<<<grid1((size_t)S.V * HC), 256, 0, st>>>(S.V, S.dzv, S.dhv);
         k_msg_vert_adj_e<<<grid1((size_t)S.E * HC), 256, 0, st>>>(S.E, S.etri, S.earea, S.vinvA, S.dzv, S.dhe);
         // element update of layer l
         k_tanh_bwd<<<grid1((size_t)S.E * HC), 256, 0, st>>>((size_t)S.E * HC, S.dhe, S.ye[l], S.dae);
         k_msg_elem<<<grid1((size_t)S.E * HC), 256, 0, st>>>(S.E, S.etri, S.egrad, Ls, S.he[l], S.hv[l], S.ze);
         if ((e = wgrad(S, st, le, S.E, S.ze, S.dae)) != cudaSuccess) return e;
-        if ((e = mm(S, st, S.E, HC, 3 * HC, S.dae, S.w16 + le.w, 1, nullptr, 0, nullptr, S.dze)) != cudaSuccess) return e;
+        if ((e = dgrad(S, st, le, S.E, S.dae, S.dze)) != cudaSuccess) return e;
         k_msg_elem_adj_e<<<grid1((size_t)S.E * HC), 256, 0, st>>>(S.E, S.dze, S.dhe);
         k_msg_elem_adj_v<<<grid1((size_t)S.V * HC), 256, 0, st>>>(S.V, S.voff, S.vinc, S.egrad, Ls, S.dze, S.dhv);
     }

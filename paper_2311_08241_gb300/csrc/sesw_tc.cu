@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "sesw_device.cuh"
 #include "sesw_internal.h"
 
@@ -227,9 +229,396 @@ cudaError_t launch_k(int N, const float *X, const uint4 *Wp, const float *bias, 
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------
+// The two backward contractions of a message layer (inputs Z [N][K] holding bfloat16 values,
+// K = 128 or 192; weights W [K][64]; dA = dL/d(pre-activation) [N][64], FP32):
+//   weight gradient  G[i][j] = sum_n Z[n][i] dA[n][j]           (k_wgrad_tc)
+//   input gradient   dZ[n][i] = sum_j dA[n][j] W[i][j]           (k_dgrad_tc)
+// dA is not a bfloat16 value, so each of its elements is split into two bfloat16 parts,
+// hi = bf16(dA) and lo = bf16(dA - hi), which carry 16 significant bits, and both parts
+// are multiplied: the products accumulate in FP32 in tensor memory. Operand tiles are
+// staged in the same K-major layout without swizzle as k_linear_tc's (core matrices of 8
+// rows x 16 bytes, 128 bytes apart along K, KC * 128 bytes apart along M or N).
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, int accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait on phase `parity` of an mbarrier; false when the budget ran out.
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, long long budget)
+{
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
+// Read 16 FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 16; t++) v[t] = __uint_as_float(r[t]);
+}
+
+constexpr int WG_THREADS = 256;
+constexpr int WG_NC = 64;          // rows n of one staged chunk: 4 MMA steps of 16
+constexpr int WG_KC = WG_NC / 8;   // core matrices along the reduction in a chunk
+
+// Weight gradient: CTA b sums rows [b R, b R + R) of Z^T dA into partial[b][i * 64 + j], and
+// the bias gradient (the column sums of dA) into partial[b][K * 64 + j]. D is one (K = 128)
+// or two (K = 192: rows 128..191 and 64 rows of zeros) tiles of 128 x 64 in TMEM.
+template <int K>
+__global__ void __launch_bounds__(WG_THREADS)
+k_wgrad_tc(int N, int rows_per_cta, const float *__restrict__ Z, const float *__restrict__ dA,
+           float *__restrict__ partial, unsigned *__restrict__ status, long long wait_cycles)
+{
+    constexpr int MT = (K + 127) / 128;
+    constexpr int A_CHUNKS = MT * 128 * WG_KC;     // 16-byte chunks of the A tile (rows i, K-major)
+    constexpr int B_CHUNKS = TC_N * WG_KC;         // of each B tile (rows j)
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint4 *As = reinterpret_cast<uint4 *>(smem);
+    uint4 *Bh = As + A_CHUNKS;
+    uint4 *Bl = Bh + B_CHUNKS;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    __shared__ float s_bias[WG_KC][TC_N];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * rows_per_cta, r1 = min(N, r0 + rows_per_cta);
+    const int nchunk = r1 > r0 ? (r1 - r0 + WG_NC - 1) / WG_NC : 0;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(MT * TC_N));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    // rows K .. MT * 128 - 1 of A stay zero
+    for (int c = tid; c < A_CHUNKS; c += WG_THREADS) As[c] = make_uint4(0u, 0u, 0u, 0u);
+    // bias: thread t < 128 owns row octet t / 16 and columns 4 (t % 16) .. + 3 of every chunk
+    float bsum[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    __syncthreads();
+    const uint32_t tmem = tmem_base;
+    const uint32_t bar = smem_u32(&mbar);
+    const uint32_t a0 = smem_u32(As), bh0 = smem_u32(Bh), bl0 = smem_u32(Bl);
+    constexpr uint32_t idesc = idesc_bf16_f32(128, TC_N);
+
+    for (int ch = 0; ch < nchunk; ch++) {
+        const int n0 = r0 + ch * WG_NC;
+        // A: unit (octet oc, feature quad fq) reads Z[n0 + 8 oc + t][4 fq .. 4 fq + 3], t < 8,
+        // and writes the core-matrix rows of features 4 fq .. 4 fq + 3
+        for (int u = tid; u < WG_KC * (K / 4); u += WG_THREADS) {
+            const int oc = u / (K / 4), fq = u % (K / 4);
+            float4 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int n = n0 + 8 * oc + t;
+                v[t] = n < r1 ? *reinterpret_cast<const float4 *>(Z + (size_t)n * K + 4 * fq)
+                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            const float *f = reinterpret_cast<const float *>(v);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int i = 4 * fq + q;
+                uint32_t w[4];
+#pragma unroll
+                for (int t = 0; t < 8; t += 2)
+                    w[t / 2] = bf16x2_bits(__float2bfloat16_rn(f[4 * t + q]), __float2bfloat16_rn(f[4 * (t + 1) + q]));
+                As[((i >> 3) * WG_KC + oc) * 8 + (i & 7)] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        // B: the same for dA, split into hi and lo parts
+        if (tid < WG_KC * (TC_N / 4)) {
+            const int oc = tid / (TC_N / 4), jq = tid % (TC_N / 4);
+            float4 v[8];
+#pragma unroll
+            for (int t = 0; t < 8; t++) {
+                const int n = n0 + 8 * oc + t;
+                v[t] = n < r1 ? *reinterpret_cast<const float4 *>(dA + (size_t)n * TC_N + 4 * jq)
+                              : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            const float *f = reinterpret_cast<const float *>(v);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int j = 4 * jq + q;
+                uint32_t wh[4], wl[4];
+#pragma unroll
+                for (int t = 0; t < 8; t += 2) {
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    split_bf16(f[4 * t + q], h0, l0);
+                    split_bf16(f[4 * (t + 1) + q], h1, l1);
+                    wh[t / 2] = bf16x2_bits(h0, h1);
+                    wl[t / 2] = bf16x2_bits(l0, l1);
+                }
+                const int c = ((j >> 3) * WG_KC + oc) * 8 + (j & 7);
+                Bh[c] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+                Bl[c] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+#pragma unroll
+                for (int t = 0; t < 8; t++) bsum[q] += f[4 * t + q];
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int ks = 0; ks < WG_KC / 2; ks++) {
+                const uint64_t bdh = umma_desc(bh0 + ks * 256, 128, WG_KC * 128);
+                const uint64_t bdl = umma_desc(bl0 + ks * 256, 128, WG_KC * 128);
+#pragma unroll
+                for (int mt = 0; mt < MT; mt++) {
+                    const uint64_t ad = umma_desc(a0 + mt * 16 * WG_KC * 128 + ks * 256, 128, WG_KC * 128);
+                    mma_bf16(tmem + mt * TC_N, ad, bdh, idesc, ch > 0 || ks > 0);
+                    mma_bf16(tmem + mt * TC_N, ad, bdl, idesc, 1);
+                }
+            }
+            mma_commit(bar);
+            // the tiles are overwritten by the next chunk only after the products have read them
+            if (!mbar_wait_parity(bar, ch & 1, wait_cycles)) {
+                atomicOr(status, 2u);
+                mbar_wait_parity(bar, ch & 1, wait_cycles);
+                s_ok = 0;
+            }
+        }
+        __syncthreads();
+        if (!s_ok) break;
+    }
+
+    // bias partial: the 8 row octets' sums in a fixed order
+    if (tid < WG_KC * (TC_N / 4)) {
+        const int oc = tid / (TC_N / 4), jq = tid % (TC_N / 4);
+#pragma unroll
+        for (int q = 0; q < 4; q++) s_bias[oc][4 * jq + q] = bsum[q];
+    }
+    __syncthreads();
+    float *out = partial + (size_t)blockIdx.x * ((size_t)K * TC_N + TC_N);
+    if (tid < TC_N) {
+        float b = 0.0f;
+        for (int oc = 0; oc < WG_KC; oc++) b += s_bias[oc][tid];
+        out[(size_t)K * TC_N + tid] = b;
+    }
+    // G rows i = 128 mt + 32 (warp % 4) + lane, columns 32 (warp / 4) .. + 31
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int quarter = warp & 3, half = warp >> 2;
+#pragma unroll
+    for (int mt = 0; mt < MT; mt++) {
+        const int i = mt * 128 + quarter * 32 + lane;
+#pragma unroll
+        for (int q = 2 * half; q < 2 * half + 2; q++) {
+            float v[16];
+            if (nchunk > 0 && s_ok) {
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + mt * TC_N + q * 16, v);
+            } else {
+#pragma unroll
+                for (int t = 0; t < 16; t++) v[t] = 0.0f;
+            }
+            if (i < K) {
+                float4 *dst = reinterpret_cast<float4 *>(out + (size_t)i * TC_N + q * 16);
+#pragma unroll
+                for (int t = 0; t < 16; t += 4) dst[t / 4] = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(MT * TC_N));
+    }
+}
+
+// Input gradient: dZ[n][i] = sum_j dA[n][j] W[i][j] for 128 rows n per CTA; the reduction is
+// over the 64 output channels j (4 MMA steps, each on the hi and the lo part of dA), the MMA's
+// N is the layer's K (128 or 192 TMEM columns). W (K x 64 bfloat16, row-major) is already the
+// K-major image of the B operand: row i holds W[i][0 .. 63].
+template <int K>
+__global__ void __launch_bounds__(WG_THREADS)
+k_dgrad_tc(int N, const float *__restrict__ dA, const __nv_bfloat16 *__restrict__ W, float *__restrict__ dZ,
+           unsigned *__restrict__ status, long long wait_cycles)
+{
+    constexpr int KC = TC_N / 8;                   // core matrices along the reduction (8)
+    constexpr int TCOLS = K <= 128 ? 128 : 256;    // TMEM allocation (a power of two)
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint4 *Ah = reinterpret_cast<uint4 *>(smem);   // 128 x 64 bf16
+    uint4 *Al = Ah + TC_M * KC;
+    uint4 *Bs = Al + TC_M * KC;                    // K x 64 bf16
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n0 = blockIdx.x * TC_M;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // A: chunk (row r = 8 rg + rl, channels 8 kc .. + 7) of dA, split into hi and lo
+    for (int c = tid; c < TC_M * KC; c += WG_THREADS) {
+        const int rl = c & 7, kc = (c >> 3) % KC, rg = (c >> 3) / KC;
+        const int n = n0 + rg * 8 + rl;
+        float4 va = make_float4(0.0f, 0.0f, 0.0f, 0.0f), vb = va;
+        if (n < N) {
+            va = *reinterpret_cast<const float4 *>(dA + (size_t)n * TC_N + kc * 8);
+            vb = *reinterpret_cast<const float4 *>(dA + (size_t)n * TC_N + kc * 8 + 4);
+        }
+        const float f[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+        uint32_t wh[4], wl[4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            __nv_bfloat16 h0, l0, h1, l1;
+            split_bf16(f[t], h0, l0);
+            split_bf16(f[t + 1], h1, l1);
+            wh[t / 2] = bf16x2_bits(h0, h1);
+            wl[t / 2] = bf16x2_bits(l0, l1);
+        }
+        Ah[(rg * KC + kc) * 8 + rl] = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        Al[(rg * KC + kc) * 8 + rl] = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    }
+    // B: chunk (row i = 8 ig + il, channels 8 kc .. + 7) is 16 contiguous bytes of W
+    const uint4 *Wv = reinterpret_cast<const uint4 *>(W);
+    for (int c = tid; c < K * KC; c += WG_THREADS) {
+        const int il = c & 7, kc = (c >> 3) % KC, ig = (c >> 3) / KC;
+        Bs[c] = Wv[(size_t)(ig * 8 + il) * KC + kc];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    const uint32_t tmem = tmem_base;
+    if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t ah = smem_u32(Ah), al = smem_u32(Al), b0 = smem_u32(Bs);
+        constexpr uint32_t idesc = idesc_bf16_f32(TC_M, K);
+#pragma unroll
+        for (int ks = 0; ks < KC / 2; ks++) {
+            const uint64_t bd = umma_desc(b0 + ks * 256, 128, KC * 128);
+            mma_bf16(tmem, umma_desc(ah + ks * 256, 128, KC * 128), bd, idesc, ks > 0);
+            mma_bf16(tmem, umma_desc(al + ks * 256, 128, KC * 128), bd, idesc, 1);
+        }
+        mma_commit(smem_u32(&mbar));
+        bool ok = mbar_wait_parity(smem_u32(&mbar), 0, wait_cycles);
+        if (!ok) {
+            atomicOr(status, 2u);
+            mbar_wait_parity(smem_u32(&mbar), 0, wait_cycles);
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const int quarter = warp & 3, half = warp >> 2;
+        const int n = n0 + quarter * 32 + lane;
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
+        constexpr int GROUPS = K / 16;             // 16-column groups, split between the two halves
+        for (int q = half; q < GROUPS; q += 2) {
+            float v[16];
+            tmem_ld16(taddr + q * 16, v);
+            if (n < N) {
+                float4 *dst = reinterpret_cast<float4 *>(dZ + (size_t)n * K + q * 16);
+#pragma unroll
+                for (int t = 0; t < 16; t += 4) dst[t / 4] = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+    }
+}
+
 }  // namespace
 
 bool linear_tc_supported(int K, int P) { return P == TC_N && (K == 128 || K == 192); }
+
+size_t wgrad_tc_smem(int K) { return (size_t)((K + 127) / 128) * 128 * WG_NC * 2 + 2 * (size_t)TC_N * WG_NC * 2; }
+
+cudaError_t launch_wgrad_tc(int N, int K, int rows_per_cta, const float *Z, const float *dA, float *partial,
+                            unsigned *status, cudaStream_t st)
+{
+    if (rows_per_cta <= 0 || rows_per_cta % WG_NC) return cudaErrorInvalidValue;
+    const int grid = std::max(1, (N + rows_per_cta - 1) / rows_per_cta);
+    const size_t smem = wgrad_tc_smem(K);
+    cudaError_t e;
+    if (K == 128) {
+        if ((e = cudaFuncSetAttribute(k_wgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        k_wgrad_tc<128><<<grid, WG_THREADS, smem, st>>>(N, rows_per_cta, Z, dA, partial, status, 2000000000ll);
+    } else if (K == 192) {
+        if ((e = cudaFuncSetAttribute(k_wgrad_tc<192>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        k_wgrad_tc<192><<<grid, WG_THREADS, smem, st>>>(N, rows_per_cta, Z, dA, partial, status, 2000000000ll);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dgrad_tc(int N, int K, const float *dA, const __nv_bfloat16 *W, float *dZ, unsigned *status,
+                            cudaStream_t st)
+{
+    const int grid = (N + TC_M - 1) / TC_M;
+    if (grid == 0) return cudaSuccess;
+    const size_t smem = 2 * (size_t)TC_M * TC_N * 2 + (size_t)K * TC_N * 2;
+    cudaError_t e;
+    if (K == 128) {
+        if ((e = cudaFuncSetAttribute(k_dgrad_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        k_dgrad_tc<128><<<grid, WG_THREADS, smem, st>>>(N, dA, W, dZ, status, 2000000000ll);
+    } else if (K == 192) {
+        if ((e = cudaFuncSetAttribute(k_dgrad_tc<192>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        k_dgrad_tc<192><<<grid, WG_THREADS, smem, st>>>(N, dA, W, dZ, status, 2000000000ll);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 size_t linear_tc_packed_elems(int K) { return (size_t)TC_N * K; }
 
