@@ -103,62 +103,49 @@ k_mm(int N, int Kin, int P, const float *__restrict__ X, const __nv_bfloat16 *__
     }
 }
 
-// partial[b][i * C + c] = sum_{n in chunk b} Z[n][i] dA[n][c];  partial[b][K * C + c] = sum dA[n][c].
-// Thread (kg, cg) owns rows i = kg + 16 j (j < KJ) and columns 4 cg .. 4 cg + 3.
-template <int KJ>
+// Weight gradient of the small layers (the input layers, K = 2 or 6 and C = 64; the output
+// layers, K = 64 and C = 4 or 1; the message layers run on the tensor cores):
+//   partial[b][i * C + c] = sum_{n in rows of block b} Z[n][i] dA[n][c],
+//   partial[b][K * C + c] = sum_{n in rows of block b} dA[n][c].
+// A chunk of WG_ROWS rows of Z and dA is staged in shared memory with coalesced loads; thread t
+// owns outputs t, t + 256, ... of the K * C + C and adds the chunk's rows in order.
 __global__ void __launch_bounds__(256)
-k_mm_wgrad(int N, int K, int C, const float *__restrict__ Z, const float *__restrict__ dA, int rows_per_block,
-           float *__restrict__ partial)
+k_wgrad_small(int N, int K, int C, const float *__restrict__ Z, const float *__restrict__ dA, int rows_per_block,
+              float *__restrict__ partial)
 {
-    __shared__ float Zs[WG_ROWS][16 * KJ + 1];
-    __shared__ float Ds[WG_ROWS][HC + 1];
-    const int kg = threadIdx.x >> 4, cg = threadIdx.x & 15;
-    float acc[KJ][4], bacc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-    for (int j = 0; j < KJ; j++)
-#pragma unroll
-        for (int q = 0; q < 4; q++) acc[j][q] = 0.0f;
+    __shared__ float Zs[WG_ROWS * HC];
+    __shared__ float Ds[WG_ROWS * HC];
+    constexpr int MAXO = 2;                      // outputs per thread: (K * C + C) <= 512
+    float acc[MAXO] = {0.0f, 0.0f};
+    const int nout = K * C + C;
     const int nb = blockIdx.x * rows_per_block, ne = min(N, nb + rows_per_block);
     for (int t0 = nb; t0 < ne; t0 += WG_ROWS) {
+        const int nr = min(WG_ROWS, ne - t0);
         __syncthreads();
-        for (int t = threadIdx.x; t < WG_ROWS * K; t += blockDim.x) {
-            const int r = t / K, i = t % K;
-            Zs[r][i] = t0 + r < ne ? Z[(size_t)(t0 + r) * K + i] : 0.0f;
-        }
-        for (int t = threadIdx.x; t < WG_ROWS * C; t += blockDim.x) {
-            const int r = t / C, c = t % C;
-            Ds[r][c] = t0 + r < ne ? dA[(size_t)(t0 + r) * C + c] : 0.0f;
-        }
+        for (int t = threadIdx.x; t < nr * K; t += blockDim.x) Zs[t] = Z[(size_t)t0 * K + t];
+        for (int t = threadIdx.x; t < nr * C; t += blockDim.x) Ds[t] = dA[(size_t)t0 * C + t];
         __syncthreads();
-        for (int r = 0; r < WG_ROWS; r++) {
-            float d[4];
 #pragma unroll
-            for (int q = 0; q < 4; q++) d[q] = (4 * cg + q < C) ? Ds[r][4 * cg + q] : 0.0f;
-#pragma unroll
-            for (int j = 0; j < KJ; j++) {
-                const int i = kg + 16 * j;
-                const float z = i < K ? Zs[r][i] : 0.0f;
-#pragma unroll
-                for (int q = 0; q < 4; q++) acc[j][q] = fmaf(z, d[q], acc[j][q]);
+        for (int q = 0; q < MAXO; q++) {
+            const int o = threadIdx.x + q * 256;
+            if (o >= nout) continue;
+            float a = acc[q];
+            if (o < K * C) {
+                const int i = o / C, c = o % C;
+                for (int r = 0; r < nr; r++) a = fmaf(Zs[r * K + i], Ds[r * C + c], a);
+            } else {
+                const int c = o - K * C;
+                for (int r = 0; r < nr; r++) a += Ds[r * C + c];
             }
-            if (kg == 0)
-#pragma unroll
-                for (int q = 0; q < 4; q++) bacc[q] += d[q];
+            acc[q] = a;
         }
     }
-    float *out = partial + (size_t)blockIdx.x * ((size_t)K * C + C);
+    float *out = partial + (size_t)blockIdx.x * nout;
 #pragma unroll
-    for (int j = 0; j < KJ; j++) {
-        const int i = kg + 16 * j;
-        if (i >= K) continue;
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (4 * cg + q < C) out[(size_t)i * C + 4 * cg + q] = acc[j][q];
+    for (int q = 0; q < MAXO; q++) {
+        const int o = threadIdx.x + q * 256;
+        if (o < nout) out[o] = acc[q];
     }
-    if (kg == 0)
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (4 * cg + q < C) out[(size_t)K * C + 4 * cg + q] = bacc[q];
 }
 
 // Sum the partials of nb blocks in block order into gW (K*C) and gb (C).
@@ -716,14 +703,11 @@ cudaError_t wgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const f
     if (ly.tc >= 0) {
         const cudaError_t e = launch_wgrad_tc(N, ly.K, rows, Z, dA, S.partial, S.status, st);
         if (e != cudaSuccess) return e;
-    } else if (ly.K <= 16)
-        k_mm_wgrad<1><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
-    else if (ly.K <= 64)
-        k_mm_wgrad<4><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
-    else if (ly.K <= 128)
-        k_mm_wgrad<8><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
-    else
-        k_mm_wgrad<12><<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
+    } else {
+        // the staged tiles hold WG_ROWS rows of at most HC values; a thread owns at most 2 outputs
+        if (ly.K > HC || ly.C > HC || ly.K * ly.C + ly.C > 512) return cudaErrorInvalidValue;
+        k_wgrad_small<<<nb, 256, 0, st>>>(N, ly.K, ly.C, Z, dA, rows, S.partial);
+    }
     k_reduce_partials<<<grid1(len), 256, 0, st>>>(S.partial, nb, len, S.grad + ly.w, S.grad + ly.b, ly.K * ly.C);
     return cudaGetLastError();
 }
