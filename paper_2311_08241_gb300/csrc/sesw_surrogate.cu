@@ -697,9 +697,13 @@ cudaError_t pack_tc(Surrogate &S, cudaStream_t st)
 // layers (inputs rounded to bfloat16 values, 64 outputs) on the tensor cores
 cudaError_t wgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const float *Z, const float *dA)
 {
-    const int rows = 2048;
-    const int nb = std::max(1, (N + rows - 1) / rows);
+    // the small layers have few outputs per block, so their blocks take fewer rows (more blocks
+    // in flight); the partial buffer holds ceil(N / 2048) partials of the largest layer
     const int len = ly.K * ly.C + ly.C;
+    int rows = 2048;
+    if (ly.tc < 0)
+        while (rows > 128 && (size_t)((N + rows / 2 - 1) / (rows / 2)) * len <= S.partial_len) rows /= 2;
+    const int nb = std::max(1, (N + rows - 1) / rows);
     if (ly.tc >= 0) {
         const cudaError_t e = launch_wgrad_tc(N, ly.K, rows, Z, dA, S.partial, S.status, st);
         if (e != cudaSuccess) return e;
