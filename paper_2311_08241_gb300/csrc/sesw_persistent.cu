@@ -12,8 +12,9 @@ namespace {
 // resident (cooperative launch). A block keeps the elevation of its own and halo
 // vertices and the per-corner fluxes in shared memory, and the transport and the
 // compensated flux sum of its slots in registers, for all M substeps. When it fits
-// (CACHED), the patch's static slot data, incidence lists, 1/A_v and halo index list
-// are also copied to shared memory once per step.
+// (CACHED = 1), the patch's static slot data, incidence lists, 1/A_v and halo index list
+// are also copied to shared memory once per step; with CACHED = 2 (patches whose static slot
+// data do not fit) only the incidences, 1/A_v and the halo index list.
 //
 // Substep m: update the interior slots (corners all own vertices); update the other
 // slots, reading the halo elevation from the exchange buffer of parity m; vertex pass;
@@ -79,13 +80,15 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
 
     for (int i = threadIdx.x; i < nown; i += T) seta[i] = P.eta_in[v0 + i];
     for (int i = threadIdx.x; i < nhalo; i += T) seta[nown + i] = P.eta_in[P.halo_v[hb + i]];
-    if (CACHED) {
+    if (CACHED == 1) {
         for (int i = threadIdx.x; i < ns; i += T) {
             s_g[i] = P.sg[s0 + i];
             s_c[i] = slot_coef(P.sc[s0 + i], a, dt);
             s_r[i] = P.R[s0 + i];
             s_l[i] = P.sl[s0 + i];
         }
+    }
+    if (CACHED) {
         cache_incidences(P, smem_raw, v0, nown);
         for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
         for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
@@ -115,7 +118,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                 float4 g, coef;
                 float2 r;
                 ushort4 l;
-                if (CACHED) {
+                if (CACHED == 1) {
                     g = s_g[i];
                     coef = s_c[i];
                     r = s_r[i];
@@ -142,7 +145,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                     e1 = seta[l.y];
                     e2 = seta[l.z];
                 }
-                element_update<NONLIN, CACHED ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
+                element_update<NONLIN, CACHED == 1 ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
                                        a.theta, one_p_theta, dt, a.g);
             }
         }
@@ -153,7 +156,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
     auto slot_update = [&](int j, int i, float e0, float e1, float e2) {
         float4 g, coef;
         float2 r;
-        if (CACHED) {
+        if (CACHED == 1) {
             g = s_g[i];
             coef = s_c[i];
             r = s_r[i];
@@ -166,7 +169,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
 #pragma unroll
         for (int q = 1; q < SPT; q++)
             if (q == j) { uu = u[q]; sh = shi[q]; sl = slo[q]; }
-        element_update<NONLIN, CACHED ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, uu, sh, sl, i < nown_s, sflux + 3 * i, a.theta,
+        element_update<NONLIN, CACHED == 1 ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, uu, sh, sl, i < nown_s, sflux + 3 * i, a.theta,
                                one_p_theta, dt, a.g);
 #pragma unroll
         for (int q = 0; q < SPT; q++)
@@ -200,7 +203,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                 const int i = threadIdx.x + j * T;
                 if (j == SPT - 1) {
                     if (early) {
-                        const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                        const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                         const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
                                   h2 = l.z < nown ? -1 : hid[l.z - nown];
                         const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, q0, base + (unsigned)m, abort_val, ok);
@@ -208,11 +211,11 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                         const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, q2, base + (unsigned)m, abort_val, ok);
                         slot_update(j, i, e0, e1, e2);
                     } else if (i < npre) {
-                        const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                        const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                         slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                     }
                 } else if (i < ns) {
-                    const ushort4 l = CACHED ? s_l[i] : P.sl[s0 + i];
+                    const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                     if (i < npre) {
                         slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                     } else {
@@ -228,7 +231,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                     }
                 }
                 if (j == 0 && early) {
-                    const ushort4 l = CACHED ? s_l[ilast] : P.sl[s0 + ilast];
+                    const ushort4 l = CACHED == 1 ? s_l[ilast] : P.sl[s0 + ilast];
                     const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
                               h2 = l.z < nown ? -1 : hid[l.z - nown];
                     if (h0 >= 0) q0 = ld_relaxed_gpu_u64(xs + h0);
@@ -320,12 +323,20 @@ void *persistent_fn(int nonlin, int extra)
 
 void *persistent_kernel(int spt, int nonlin, int cached, int extra)
 {
-    if (cached) {
+    if (cached == 1) {
         switch (spt) {
         case 1: return persistent_fn<1, 1>(nonlin, extra);
         case 2: return persistent_fn<2, 1>(nonlin, extra);
         case 3: return persistent_fn<3, 1>(nonlin, extra);
         case 4: return persistent_fn<4, 1>(nonlin, extra);
+        default: return nullptr;
+        }
+    }
+    if (cached == 2) {
+        switch (spt) {
+        case 4: return persistent_fn<4, 2>(nonlin, extra);
+        case 6: return persistent_fn<6, 2>(nonlin, extra);
+        case 8: return persistent_fn<8, 2>(nonlin, extra);
         default: return nullptr;
         }
     }
@@ -377,9 +388,17 @@ PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
-    // the cached variant indexes incidence entries and offsets with 16 bits
-    int cached = (spt <= 4 && L.total_cached <= budget && m.csr < 65536 && m.slots < 16384) ? 1 : 0;
-    const size_t smem = cached ? L.total_cached : L.total_plain;
+    // the cached variants index incidence entries and offsets with 16 bits; the slots' static
+    // data join the vertices' data in shared memory when they fit (cached = 1), else only the
+    // vertices' data (cached = 2, with 4 or more slots per thread)
+    int cached = 0;
+    if (m.csr < 65536 && 3 * (size_t)m.slots < 65536) {
+        if (spt <= 4 && L.total_cached <= budget && m.slots < 16384)
+            cached = 1;
+        else if (spt >= 4 && L.total_vcached <= budget && persistent_kernel(spt, 0, 2, 0))
+            cached = 2;
+    }
+    const size_t smem = cached == 1 ? L.total_cached : cached == 2 ? L.total_vcached : L.total_plain;
     if (smem > budget) return plan;
     // every variant the plan may launch must reach blocks_per_sm resident blocks
     for (int nonlin = 0; nonlin < 2; nonlin++)

@@ -121,9 +121,9 @@ __device__ __forceinline__ float halo_eta(const PArgs &P, const unsigned long lo
 
 
 // Copy the incidences of a patch's own vertices into shared memory (cached layouts): with
-// P.inc8, one row of kIncWidth 16-bit byte offsets per vertex, pointing at its corner fluxes
-// in incidence order and padded with the zero word; else the CSR with flux indices
-// 3 * slot + corner. Also clears the zero word. The caller synchronises the block afterwards.
+// P.inc8, one row of kIncWidth 16-bit byte offsets (inc8 = 1) or word indices (inc8 = 2) per
+// vertex, pointing at its corner fluxes in incidence order and padded with the zero word; else
+// the CSR with flux indices 3 * slot + corner. Also clears the zero word. The caller synchronises the block afterwards.
 __device__ __forceinline__ void cache_incidences(const PArgs &P, unsigned char *smem_raw, int v0, int nown)
 {
     const int c0 = P.vcsr_off[v0], ncsr = P.vcsr_off[v0 + nown] - c0;
@@ -139,7 +139,7 @@ __device__ __forceinline__ void cache_incidences(const PArgs &P, unsigned char *
                     const uint32_t q = P.vcsr[k0 + k];
                     off = (unsigned)P.off_flux + 4u * (3u * (q >> 2) + (q & 3u));
                 }
-                h[k] = off;
+                h[k] = P.inc8 == 2 ? off >> 2 : off;
             }
             rows[i] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
         }
@@ -161,13 +161,22 @@ __device__ __forceinline__ void cache_incidences(const PArgs &P, unsigned char *
 __device__ __forceinline__ float cached_flux_sum(const PArgs &P, const unsigned char *smem_raw, int i)
 {
     float sum = 0.0f;
-    if (P.inc8) {
+    if (P.inc8 == 1) {
         const uint4 q = reinterpret_cast<const uint4 *>(smem_raw + P.off_off)[i];
         const unsigned w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             sum = __fadd_rn(sum, *reinterpret_cast<const float *>(smem_raw + (w[k] & 0xffffu)));
             sum = __fadd_rn(sum, *reinterpret_cast<const float *>(smem_raw + (w[k] >> 16)));
+        }
+    } else if (P.inc8 == 2) {
+        const uint4 q = reinterpret_cast<const uint4 *>(smem_raw + P.off_off)[i];
+        const unsigned w[4] = {q.x, q.y, q.z, q.w};
+        const float *words = reinterpret_cast<const float *>(smem_raw);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            sum = __fadd_rn(sum, words[w[k] & 0xffffu]);
+            sum = __fadd_rn(sum, words[w[k] >> 16]);
         }
     } else {
         const unsigned short *s_off = reinterpret_cast<const unsigned short *>(smem_raw + P.off_off);
@@ -185,11 +194,18 @@ inline size_t flag_bytes(int npatch) { return sizeof(unsigned) * (2 * (size_t)np
 struct SmemLayout {
     int off_flux, off_g, off_c, off_r, off_l, off_off, off_csr, off_inv, off_halo;
     int inc8, zero_off;
-    size_t total_plain, total_cached;
+    size_t total_plain;     // elevation, corner fluxes and the zero word
+    size_t total_vcached;   // ... and the vertices' data: 1/A_v, halo ids, incidences
+    size_t total_cached;    // ... and the slots' static data
 };
 
 inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Shared-memory layout of a patch: [elevation of own and halo vertices | corner fluxes, zero
+// word | 1/A_v, halo ids, incidences | per slot: gradients, coefficients, forcing, corners].
+// The kernels that keep everything on chip use the whole layout (CACHED = 1), those for larger
+// patches the part up to the incidences (CACHED = 2: the slots' static data then come from L2),
+// the streaming kernels only the first part.
 inline SmemLayout smem_layout(const PatchMax &m)
 {
     SmemLayout L;
@@ -199,14 +215,6 @@ inline SmemLayout smem_layout(const PatchMax &m)
     L.zero_off = (int)(o + sizeof(float) * 3 * (size_t)m.slots);
     o = align16(o + sizeof(float) * (3 * (size_t)m.slots + 1));
     L.total_plain = o;
-    L.off_g = (int)o;
-    o += sizeof(float4) * (size_t)m.slots;
-    L.off_c = (int)o;
-    o += sizeof(float4) * (size_t)m.slots;
-    L.off_r = (int)o;
-    o = align16(o + sizeof(float2) * (size_t)m.slots);
-    L.off_l = (int)o;
-    o = align16(o + sizeof(ushort4) * (size_t)m.slots);
     L.off_inv = (int)o;
     o = align16(o + sizeof(float) * (size_t)m.vertices);
     L.off_halo = (int)o;
@@ -215,11 +223,21 @@ inline SmemLayout smem_layout(const PatchMax &m)
     const size_t csr_end = align16(align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1)) +
                                    sizeof(unsigned short) * (size_t)m.csr);
     L.off_csr = (int)align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1));
-    // padded rows when every vertex has at most kIncWidth incidences and every flux byte offset
-    // fits 16 bits; they take the place of the CSR
-    L.inc8 = m.deg <= kIncWidth && L.zero_off + 4 <= 65535 ? 1 : 0;
+    // padded rows when every vertex has at most kIncWidth incidences: 16-bit byte offsets of the
+    // corner fluxes when they fit 16 bits (inc8 = 1), else 16-bit word indices (inc8 = 2); they
+    // take the place of the CSR
+    L.inc8 = m.deg > kIncWidth ? 0 : (L.zero_off + 4 <= 65535 ? 1 : (L.zero_off / 4 + 1 <= 65535 ? 2 : 0));
     const size_t inc_end = o + sizeof(unsigned short) * kIncWidth * (size_t)m.vertices;
     o = L.inc8 ? align16(inc_end) : csr_end;
+    L.total_vcached = o;
+    L.off_g = (int)o;
+    o += sizeof(float4) * (size_t)m.slots;
+    L.off_c = (int)o;
+    o += sizeof(float4) * (size_t)m.slots;
+    L.off_r = (int)o;
+    o = align16(o + sizeof(float2) * (size_t)m.slots);
+    L.off_l = (int)o;
+    o = align16(o + sizeof(ushort4) * (size_t)m.slots);
     L.total_cached = o;
     return L;
 }
