@@ -235,9 +235,7 @@ cudaError_t launch_diagnostics_basins(const DevMesh &m, const DevState &s, const
 struct PersistentPlan {
     int slots_per_thread = 0;   // 0: not possible for this mesh
     int threads = 0;
-    int cached = 0;             // 1: the patch's static data lives in shared memory; 2: the
-                                // vertices' data does, and the static data of the first ncache slots
-    int ncache = 0;             // cached = 2: slots whose static data is in shared memory (whole rounds)
+    int cached = 0;             // 1: the patch's static data lives in shared memory
     int stream = 0;             // state and static data in global memory (the streaming kernels):
                                 // 1 with the corner indices in shared memory, 2 without
     int blocks_per_sm = 1;

@@ -80,9 +80,8 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
 
     for (int i = threadIdx.x; i < nown; i += T) seta[i] = P.eta_in[v0 + i];
     for (int i = threadIdx.x; i < nhalo; i += T) seta[nown + i] = P.eta_in[P.halo_v[hb + i]];
-    if (CACHED) {
-        const int nst = CACHED == 1 ? ns : min(ns, P.ncache);
-        for (int i = threadIdx.x; i < nst; i += T) {
+    if (CACHED == 1) {
+        for (int i = threadIdx.x; i < ns; i += T) {
             s_g[i] = P.sg[s0 + i];
             s_c[i] = slot_coef(P.sc[s0 + i], a, dt);
             s_r[i] = P.R[s0 + i];
@@ -119,7 +118,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                 float4 g, coef;
                 float2 r;
                 ushort4 l;
-                if (CACHED == 1 || (CACHED == 2 && j * T < P.ncache)) {
+                if (CACHED == 1) {
                     g = s_g[i];
                     coef = s_c[i];
                     r = s_r[i];
@@ -157,7 +156,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
     auto slot_update = [&](int j, int i, float e0, float e1, float e2) {
         float4 g, coef;
         float2 r;
-        if (CACHED == 1 || (CACHED == 2 && j * T < P.ncache)) {
+        if (CACHED == 1) {
             g = s_g[i];
             coef = s_c[i];
             r = s_r[i];
@@ -204,7 +203,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                 const int i = threadIdx.x + j * T;
                 if (j == SPT - 1) {
                     if (early) {
-                        const ushort4 l = CACHED == 1 || (CACHED == 2 && j * T < P.ncache) ? s_l[i] : P.sl[s0 + i];
+                        const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                         const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
                                   h2 = l.z < nown ? -1 : hid[l.z - nown];
                         const float e0 = h0 < 0 ? seta[l.x] : halo_eta(P, xs, h0, q0, base + (unsigned)m, abort_val, ok);
@@ -212,11 +211,11 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                         const float e2 = h2 < 0 ? seta[l.z] : halo_eta(P, xs, h2, q2, base + (unsigned)m, abort_val, ok);
                         slot_update(j, i, e0, e1, e2);
                     } else if (i < npre) {
-                        const ushort4 l = CACHED == 1 || (CACHED == 2 && j * T < P.ncache) ? s_l[i] : P.sl[s0 + i];
+                        const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                         slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                     }
                 } else if (i < ns) {
-                    const ushort4 l = CACHED == 1 || (CACHED == 2 && j * T < P.ncache) ? s_l[i] : P.sl[s0 + i];
+                    const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                     if (i < npre) {
                         slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                     } else {
@@ -232,7 +231,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                     }
                 }
                 if (j == 0 && early) {
-                    const ushort4 l = CACHED == 1 || (CACHED == 2 && (SPT - 1) * T < P.ncache) ? s_l[ilast] : P.sl[s0 + ilast];
+                    const ushort4 l = CACHED == 1 ? s_l[ilast] : P.sl[s0 + ilast];
                     const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
                               h2 = l.z < nown ? -1 : hid[l.z - nown];
                     if (h0 >= 0) q0 = ld_relaxed_gpu_u64(xs + h0);
@@ -399,17 +398,7 @@ PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
         else if (spt >= 4 && L.total_vcached <= budget && persistent_kernel(spt, 0, 2, 0))
             cached = 2;
     }
-    // cached = 2: whole rounds of slots whose static data also fits (the remaining rounds read it
-    // from L2)
-    int ncache = 0;
-    if (cached == 2) {
-        const int rounds = (int)std::min<size_t>((size_t)spt, (budget - L.total_vcached) / (kSlotStaticBytes * t + 64));
-        ncache = std::max(0, rounds) * t;
-    }
-    const size_t smem = cached == 1   ? L.total_cached
-                        : cached == 2 ? smem_layout(m, ncache).total_cached
-                                      : L.total_plain;
-    if (cached == 2 && smem > budget) return plan;
+    const size_t smem = cached == 1 ? L.total_cached : cached == 2 ? L.total_vcached : L.total_plain;
     if (smem > budget) return plan;
     // every variant the plan may launch must reach blocks_per_sm resident blocks
     for (int nonlin = 0; nonlin < 2; nonlin++)
@@ -426,7 +415,6 @@ PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
     plan.slots_per_thread = spt;
     plan.threads = t;
     plan.cached = cached;
-    plan.ncache = ncache;
     plan.smem = smem;
     return plan;
 }
@@ -452,7 +440,7 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
         } else {
             void *fn = persistent_kernel(g.plan.slots_per_thread, a.nonlinear_h, g.plan.cached, extra);
             if (!fn) return cudaErrorInvalidValue;
-            PArgs P = make_pargs(m, s, a, M, parity, g.mx, g.plan.cached == 2 ? g.plan.ncache : -1);
+            PArgs P = make_pargs(m, s, a, M, parity, g.mx);
             P.pack_first = g.first;
             P.pack_last = g.last;
             void *args[] = {&P};

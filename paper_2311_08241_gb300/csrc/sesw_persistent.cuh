@@ -70,7 +70,6 @@ struct PArgs {
     // dynamic shared memory: the corner fluxes, padded with a zero word) at off_off, in place of
     // the CSR (offsets at off_off, entries at off_csr); zero_off: the zero word's byte offset
     int inc8, zero_off;
-    int ncache;      // CACHED = 2: slots [0, ncache) have their static data in shared memory
 };
 
 __device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p)
@@ -207,10 +206,8 @@ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 // The kernels that keep everything on chip use the whole layout (CACHED = 1), those for larger
 // patches the part up to the incidences (CACHED = 2: the slots' static data then come from L2),
 // the streaming kernels only the first part.
-// nslot_static: slots whose static data has room in the last part (default: all of them).
-inline SmemLayout smem_layout(const PatchMax &m, int nslot_static = -1)
+inline SmemLayout smem_layout(const PatchMax &m)
 {
-    const size_t nst = nslot_static < 0 ? (size_t)m.slots : (size_t)nslot_static;
     SmemLayout L;
     size_t o = align16(sizeof(float) * (size_t)m.local);
     L.off_flux = (int)o;
@@ -234,23 +231,19 @@ inline SmemLayout smem_layout(const PatchMax &m, int nslot_static = -1)
     o = L.inc8 ? align16(inc_end) : csr_end;
     L.total_vcached = o;
     L.off_g = (int)o;
-    o += sizeof(float4) * nst;
+    o += sizeof(float4) * (size_t)m.slots;
     L.off_c = (int)o;
-    o += sizeof(float4) * nst;
+    o += sizeof(float4) * (size_t)m.slots;
     L.off_r = (int)o;
-    o = align16(o + sizeof(float2) * nst);
+    o = align16(o + sizeof(float2) * (size_t)m.slots);
     L.off_l = (int)o;
-    o = align16(o + sizeof(ushort4) * nst);
+    o = align16(o + sizeof(ushort4) * (size_t)m.slots);
     L.total_cached = o;
     return L;
 }
 
-// Bytes of the static data of one slot in the layout above.
-constexpr size_t kSlotStaticBytes = sizeof(float4) + sizeof(float4) + sizeof(float2) + sizeof(ushort4);
 
-
-inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity, const PatchMax &mx,
-                        int ncache = -1)
+inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity, const PatchMax &mx)
 {
     PArgs P;
     P.patch_slot = m.patch_slot;
@@ -281,8 +274,7 @@ inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, 
     P.a = a;
     P.M = M;
     P.npatch = m.npatch;
-    const SmemLayout L = smem_layout(mx, ncache);
-    P.ncache = ncache < 0 ? mx.slots : ncache;
+    const SmemLayout L = smem_layout(mx);
     P.off_flux = L.off_flux;
     P.off_g = L.off_g;
     P.off_c = L.off_c;
