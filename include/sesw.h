@@ -184,7 +184,10 @@ typedef struct sesw_info {
     int32_t blocks_per_sm;   /* persistent mode: resident blocks per SM */
     int32_t slots_per_thread;/* persistent mode: element slots per thread (held in registers,
                                 or slot-loop rounds when streamed) */
-    int32_t cached;          /* persistent mode: 1 when static slot data lives in shared memory */
+    int32_t cached;          /* persistent mode, register kernels: 1 when the static slot data lives in
+                                shared memory, 2 when the vertices' data does and the static data of
+                                the first rounds of slots (large patches); streaming kernels
+                                (streamed != 0): 1 when the vertices' data lives in shared memory */
     int32_t nbasin;          /* meshes in the uploaded batch (1 for sesw_mesh_upload) */
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
                                 (0 until parameters are set) */

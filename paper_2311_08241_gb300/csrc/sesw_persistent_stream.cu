@@ -21,7 +21,35 @@ struct SArgs {
     PArgs P;
     float2 *Shi, *Slo;
     int off_idx;    // IDX: shared-memory offset of the cached corner indices (ushort4 per slot)
+    int vcache;     // 1: the vertices' data (1/A_v, halo ids, incidences) is in shared memory at
+                    // P.off_inv, P.off_halo and P.off_off / P.off_csr
 };
+
+// Shared-memory layout of the streaming kernel: the plain part (elevation, corner fluxes, zero
+// word), the slots' corner indices (idx), then, when vc, the vertices' data laid out like the
+// register kernel's. Returns the total; fills the offsets into P when P is given.
+size_t stream_layout(const PatchMax &m, int idx, int vc, PArgs *P)
+{
+    const SmemLayout L = smem_layout(m);
+    size_t o = align16(L.total_plain) + (idx ? sizeof(ushort4) * (size_t)m.slots : 0);
+    if (!vc) return o;
+    o = align16(o);
+    const size_t off_inv = o;
+    o = align16(o + sizeof(float) * (size_t)m.vertices);
+    const size_t off_halo = o;
+    o = align16(o + sizeof(int) * (size_t)m.halo);
+    const size_t off_off = o;
+    const size_t off_csr = align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1));
+    const size_t end = L.inc8 ? align16(o + sizeof(unsigned short) * kIncWidth * (size_t)m.vertices)
+                              : align16(off_csr + sizeof(unsigned short) * (size_t)m.csr);
+    if (P) {
+        P->off_inv = (int)off_inv;
+        P->off_halo = (int)off_halo;
+        P->off_off = (int)off_off;
+        P->off_csr = (int)off_csr;
+    }
+    return end;
+}
 
 // Element update of one slot (Eq. 4.10, first row, and the theta-weighted flux) from its
 // corner elevations, with everything else read from and written back to global memory.
@@ -76,14 +104,21 @@ __device__ __forceinline__ void stream_patch(const SArgs &A, const int p, const 
     float *seta = reinterpret_cast<float *>(smem_raw);
     float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
     ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + A.off_idx);
+    float *s_inv = reinterpret_cast<float *>(smem_raw + P.off_inv);
+    int *s_halo = reinterpret_cast<int *>(smem_raw + P.off_halo);
     if (IDX)
         for (int i = threadIdx.x; i < ns; i += T) s_l[i] = __ldg(P.sl + s0 + i);
     for (int i = threadIdx.x; i < nown; i += T) seta[i] = P.eta_in[v0 + i];
     for (int i = threadIdx.x; i < nhalo; i += T) seta[nown + i] = P.eta_in[P.halo_v[hb + i]];
+    if (A.vcache) {
+        cache_incidences(P, smem_raw, v0, nown);
+        for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
+        for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
+    }
     if (threadIdx.x == 0) s_abort = 0;
     __syncthreads();
 
-    const int *hid = P.halo_v + hb;
+    const int *hid = A.vcache ? s_halo : P.halo_v + hb;
     bool ok = true;
     for (int m = 0; m < P.M; m++) {
         const unsigned tag = base + (unsigned)m;
@@ -101,8 +136,8 @@ __device__ __forceinline__ void stream_patch(const SArgs &A, const int p, const 
 #pragma unroll 8
         for (int i = nfirst + threadIdx.x; i < ns; i += T) {
             const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
-            const int h0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), h1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
-                      h2 = l.z < nown ? -1 : __ldg(hid + l.z - nown);
+            const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
+                      h2 = l.z < nown ? -1 : hid[l.z - nown];
             const unsigned long long w0 = h0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h0);
             const unsigned long long w1 = h1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h1);
             const unsigned long long w2 = h2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + h2);
@@ -122,13 +157,19 @@ __device__ __forceinline__ void stream_patch(const SArgs &A, const int p, const 
         const bool publish = more && p != a.silent_patch;
         bool bad = false;
         for (int i = threadIdx.x; i < nown; i += T) {
-            float sum = 0.0f;
-            const int k1 = __ldg(P.vcsr_off + v0 + i + 1);
-            for (int k = __ldg(P.vcsr_off + v0 + i); k < k1; k++) {
-                const uint32_t q = __ldg(P.vcsr + k);
-                sum += sflux[3 * (q >> 2) + (q & 3u)];
+            float sum = 0.0f, inv;
+            if (A.vcache) {
+                sum = cached_flux_sum(P, smem_raw, i);
+                inv = s_inv[i];
+            } else {
+                const int k1 = __ldg(P.vcsr_off + v0 + i + 1);
+                for (int k = __ldg(P.vcsr_off + v0 + i); k < k1; k++) {
+                    const uint32_t q = __ldg(P.vcsr + k);
+                    sum += sflux[3 * (q >> 2) + (q & 3u)];
+                }
+                inv = __ldg(P.inv_av + v0 + i);
             }
-            float e = vertex_eta(seta[i], sum, __ldg(P.inv_av + v0 + i));
+            float e = vertex_eta(seta[i], sum, inv);
             if (EXTRA) {
                 if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
                 if (P.eta_sum) P.eta_sum[v0 + i] += seta[i];
@@ -202,14 +243,20 @@ PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm, int 
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
-    // the corner indices join the shared memory when they fit (idx_mode 0: never)
+    // the corner indices join the shared memory when they fit (idx_mode 0: never), and then the
+    // vertices' data when it fits too (the cached incidences index the fluxes with 16 bits)
     int idx = 1;
-    size_t need = align16(L.total_plain) + sizeof(ushort4) * (size_t)m.slots;
+    size_t need = stream_layout(m, 1, 0, nullptr);
     if (need > budget || idx_mode == 0) {
         idx = 0;
         need = L.total_plain;
     }
     if (need > budget) return plan;
+    int vc = 0;
+    if (m.csr < 65536 && 3 * (size_t)m.slots < 65536 && stream_layout(m, idx, 1, nullptr) <= budget) {
+        vc = 1;
+        need = stream_layout(m, idx, 1, nullptr);
+    }
     for (int nonlin = 0; nonlin < 2; nonlin++)
         for (int extra = 0; extra < 2; extra++) {
             void *fn = stream_kernel(nonlin, extra, idx);
@@ -223,7 +270,7 @@ PersistentPlan persistent_plan_stream(const PatchMax &m, int blocks_per_sm, int 
         }
     plan.slots_per_thread = (m.slots + t - 1) / t;   // rounds of the slot loop (not registers)
     plan.threads = t;
-    plan.cached = 0;
+    plan.cached = vc;    // streaming kernels: 1 when the vertices' data is in shared memory
     plan.stream = idx ? 1 : 2;
     plan.blocks_per_sm = blocks_per_sm;
     plan.smem = need;
@@ -250,6 +297,8 @@ cudaError_t launch_persistent_stream_group(const DevMesh &m, const DevState &s, 
     A.Shi = s.S_hi;
     A.Slo = s.S_lo;
     A.off_idx = (int)align16(smem_layout(g.mx).total_plain);
+    A.vcache = g.plan.cached;
+    if (A.vcache) stream_layout(g.mx, g.plan.stream == 1, 1, &A.P);
     void *fn = stream_kernel(a.nonlinear_h, s.W != nullptr || s.eta_sum != nullptr, g.plan.stream == 1);
     if (!fn) return cudaErrorInvalidValue;
     void *args[] = {&A};
