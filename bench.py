@@ -163,10 +163,11 @@ def kernel_source_hash(kernels=("k_persistent",)):
     return h.hexdigest()[:16]
 
 
-def profile_figures(profile, kernels):
+def profile_figures(profile, kernels, layout=None):
     """Counters of a committed ncu summary (profiles/<profile>.md): DRAM bytes and warp instructions
     per launch (or per step, as the summary states), or None where the summary is missing or was
-    taken on other kernel sources than the ones built now."""
+    taken on other kernel sources than the ones built now. With `layout`, the figures of the block
+    that starts with the line "layout: <layout>" (None if the summary has no such block)."""
     p = os.path.join(ROOT, "profiles", f"{profile}.md")
     try:
         txt = open(p).read()
@@ -175,6 +176,12 @@ def profile_figures(profile, kernels):
     m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
     if not m or m.group(1) != kernel_source_hash(kernels):
         return None
+    if layout is not None:
+        blocks = re.split(r"(?m)^layout: ", txt)[1:]
+        block = next((b for b in blocks if b.split("\n", 1)[0].strip() == layout), None)
+        if block is None:
+            return None
+        txt = block
     out = {"profile": f"profiles/{profile}.md"}
     for key in ("dram_bytes_per_launch", "warp_instructions_per_launch", "dram_bytes_per_step",
                 "warp_instructions_per_step"):
@@ -566,9 +573,7 @@ def run_ensemble(args, world, rank, local):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     if persistent:
         kernels = ("k_persistent", "k_persistent_stream")
-        fig = profile_figures("k_persistent_ensemble", kernels)
-        if fig is not None and f"layout: {best.label()}\n" not in open(os.path.join(ROOT, fig["profile"])).read():
-            fig = None
+        fig = profile_figures("k_persistent_ensemble", kernels, layout=best.label())
         roofline = roofline_issue(f"k_persistent + k_persistent_stream ({info['npack']} packs in "
                                   f"{launches_per_step} launches per step)",
                                   mean_step_s, fig and fig.get("warp_instructions_per_step"),
