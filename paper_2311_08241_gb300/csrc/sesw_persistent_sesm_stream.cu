@@ -23,6 +23,8 @@ struct QArgs {
     int off_hist;         // shared-memory offset of the elevation history (bytes)
     int off_idx;          // IDX: shared-memory offset of the cached corner indices (ushort4 per slot)
     int vmax;             // own vertices of the largest patch (stride of the history)
+    int vcache;           // 1: the vertices' data (1/A_v, halo ids, incidences) is in shared memory
+                          // at P.off_inv, P.off_halo and P.off_off / P.off_csr
 };
 
 // U_AB of slot s from its levels, its flux contributions and (owned) the compensated sum;
@@ -90,6 +92,9 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
     float *h0 = reinterpret_cast<float *>(smem_raw + A.off_hist);   // eta^m, eta^{m-1}, eta^{m-2} of own vertices
     float *h1 = h0 + A.vmax, *h2 = h1 + A.vmax;
     ushort4 *s_l = reinterpret_cast<ushort4 *>(smem_raw + A.off_idx);
+    float *s_inv = reinterpret_cast<float *>(smem_raw + P.off_inv);
+    int *s_halo = reinterpret_cast<int *>(smem_raw + P.off_halo);
+    const int hb = P.patch_halo[p], nhalo = P.patch_halo[p + 1] - hb;
     if (IDX)
         for (int i = threadIdx.x; i < ns; i += T) s_l[i] = __ldg(P.sl + s0 + i);
     for (int i = threadIdx.x; i < nown; i += T) {
@@ -98,10 +103,15 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
         h1[i] = x;
         h2[i] = x;
     }
+    if (A.vcache) {
+        cache_incidences(P, smem_raw, v0, nown);
+        for (int i = threadIdx.x; i < nown; i += T) s_inv[i] = P.inv_av[v0 + i];
+        for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
+    }
     if (threadIdx.x == 0) s_abort = 0;
     __syncthreads();
 
-    const int *hid = P.halo_v + P.patch_halo[p];
+    const int *hid = A.vcache ? s_halo : P.halo_v + hb;
     bool ok = true;
     for (int m = 0; m <= P.M; m++) {
         const bool vertex = m < P.M;
@@ -148,13 +158,19 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
         const bool publish = p != a.silent_patch;
         bool bad = false;
         for (int i = threadIdx.x; i < nown; i += T) {
-            float sum = 0.0f;
-            const int k1 = __ldg(P.vcsr_off + v0 + i + 1);
-            for (int k = __ldg(P.vcsr_off + v0 + i); k < k1; k++) {
-                const uint32_t q = __ldg(P.vcsr + k);
-                sum += sflux[3 * (q >> 2) + (q & 3u)];
+            float sum = 0.0f, inv;
+            if (A.vcache) {
+                sum = cached_flux_sum(P, smem_raw, i);
+                inv = s_inv[i];
+            } else {
+                const int k1 = __ldg(P.vcsr_off + v0 + i + 1);
+                for (int k = __ldg(P.vcsr_off + v0 + i); k < k1; k++) {
+                    const uint32_t q = __ldg(P.vcsr + k);
+                    sum += sflux[3 * (q >> 2) + (q & 3u)];
+                }
+                inv = __ldg(P.inv_av + v0 + i);
             }
-            float e = vertex_eta(h0[i], sum, __ldg(P.inv_av + v0 + i));
+            float e = vertex_eta(h0[i], sum, inv);
             if (P.W) e = __fmaf_rn(-dt, __ldg(P.W + v0 + i), e);
             const float em = sesm_am4(e, h0[i], h1[i], h2[i], a.am0, a.am1, a.am2, a.am3);
             h2[i] = h1[i];
@@ -194,9 +210,30 @@ size_t hist_offset(const SmemLayout &L) { return align16(L.total_plain); }
 
 size_t idx_offset(const PatchMax &m) { return hist_offset(smem_layout(m)) + align16(3 * sizeof(float) * (size_t)m.vertices); }
 
-size_t sesm_stream_smem(const PatchMax &m, int idx)
+// Shared memory of the SESM streaming kernel: the plain part, the elevation history, the
+// corner indices (idx), then, when vc, the vertices' data laid out like the register kernel's
+// (offsets into P when P is given).
+size_t sesm_stream_smem(const PatchMax &m, int idx, int vc = 0, PArgs *P = nullptr)
 {
-    return idx ? idx_offset(m) + sizeof(ushort4) * (size_t)m.slots : idx_offset(m);
+    size_t o = idx ? idx_offset(m) + sizeof(ushort4) * (size_t)m.slots : idx_offset(m);
+    if (!vc) return o;
+    const SmemLayout L = smem_layout(m);
+    o = align16(o);
+    const size_t off_inv = o;
+    o = align16(o + sizeof(float) * (size_t)m.vertices);
+    const size_t off_halo = o;
+    o = align16(o + sizeof(int) * (size_t)m.halo);
+    const size_t off_off = o;
+    const size_t off_csr = align16(o + sizeof(unsigned short) * ((size_t)m.vertices + 1));
+    const size_t end = L.inc8 ? align16(o + sizeof(unsigned short) * kIncWidth * (size_t)m.vertices)
+                              : align16(off_csr + sizeof(unsigned short) * (size_t)m.csr);
+    if (P) {
+        P->off_inv = (int)off_inv;
+        P->off_halo = (int)off_halo;
+        P->off_off = (int)off_off;
+        P->off_csr = (int)off_csr;
+    }
+    return end;
 }
 
 }  // namespace
@@ -226,6 +263,12 @@ PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm,
         smem = sesm_stream_smem(m, 0);
     }
     if (smem > budget) return plan;
+    // the vertices' data joins when it fits (its cached incidences index the fluxes with 16 bits)
+    int vc = 0;
+    if (m.csr < 65536 && 3 * (size_t)m.slots < 65536 && sesm_stream_smem(m, idx, 1) <= budget) {
+        vc = 1;
+        smem = sesm_stream_smem(m, idx, 1);
+    }
     for (int nonlin = 0; nonlin < 2; nonlin++) {
         void *fn = sesm_stream_kernel(nonlin, idx);
         int occ = 0;
@@ -237,7 +280,7 @@ PersistentPlan persistent_plan_sesm_stream(const PatchMax &m, int blocks_per_sm,
     }
     plan.slots_per_thread = (m.slots + t - 1) / t;   // rounds of the slot loop (not registers)
     plan.threads = t;
-    plan.cached = 0;
+    plan.cached = vc;    // streaming kernels: 1 when the vertices' data is in shared memory
     plan.stream = idx ? 1 : 2;
     plan.blocks_per_sm = blocks_per_sm;
     plan.smem = smem;
@@ -268,6 +311,8 @@ cudaError_t launch_persistent_sesm_stream_pack(const DevMesh &m, const DevState 
     A.off_hist = (int)hist_offset(smem_layout(pk.mx));
     A.off_idx = (int)idx_offset(pk.mx);
     A.vmax = pk.mx.vertices;
+    A.vcache = pk.plan_sesm.cached;
+    if (A.vcache) sesm_stream_smem(pk.mx, pk.plan_sesm.stream == 1, 1, &A.P);
     void *fn = sesm_stream_kernel(a.nonlinear_h, pk.plan_sesm.stream == 1);
     void *args[] = {&A};
     return cudaLaunchCooperativeKernel(fn, dim3(pk.nblocks), dim3(pk.plan_sesm.threads), args, pk.plan_sesm.smem,
