@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(kSesmStreamThreads, 1) k_persistent_sesm_strea
 #pragma unroll 8
             for (int i = nint + threadIdx.x; i < ns; i += T) {
                 const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
-                const int q0 = l.x < nown ? -1 : __ldg(hid + l.x - nown), q1 = l.y < nown ? -1 : __ldg(hid + l.y - nown),
-                          q2 = l.z < nown ? -1 : __ldg(hid + l.z - nown);
+                const int q0 = l.x < nown ? -1 : hid[l.x - nown], q1 = l.y < nown ? -1 : hid[l.y - nown],
+                          q2 = l.z < nown ? -1 : hid[l.z - nown];
                 const unsigned long long w0 = q0 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q0);
                 const unsigned long long w1 = q1 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q1);
                 const unsigned long long w2 = q2 < 0 ? 0ull : ld_relaxed_gpu_u64(xs + q2);
