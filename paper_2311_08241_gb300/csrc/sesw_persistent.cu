@@ -30,6 +30,11 @@ namespace {
 // coef = (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)).
 // Packed FP32 pairs in the element update of the cached kernels (UNCACHED: kUncachedPacked).
 constexpr int kUncachedPacked = 0;
+// Cached kernel: each substep, one thread per halo vertex fetches its tagged word into shared
+// memory after the interior rounds, and every other slot then reads its corners from shared
+// memory (one extra block barrier per substep; patches with more halo vertices than threads
+// keep the per-slot halo reads).
+constexpr int kHaloPrefetch = 1;
 
 template <int NONLIN, int PACKED>
 __device__ __forceinline__ void element_update(const float e0, const float e1, const float e2, const float4 g,
@@ -180,8 +185,33 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
     // no thread does more rounds in total than ceil(ns / T); the interior slots left over
     // go with the boundary slots, whose halo reads may have to wait for a neighbour.
     const int npre = nint >= T ? (nint / T) * T : nint;
+    const bool hpre = kHaloPrefetch && CACHED == 1 && nhalo <= T;
     for (int m = 0; m < P.M; m++) {
-        if (m == 0 || SPT == 1) {
+        if (hpre && m > 0) {
+            // this thread's halo word is requested before the interior rounds and stored to
+            // shared memory after them; the other slots follow a barrier
+            const unsigned long long *xs = P.xb[m & 1];
+            const int hv = (int)threadIdx.x < nhalo ? s_halo[threadIdx.x] : -1;
+            const unsigned long long hw = hv >= 0 ? ld_relaxed_gpu_u64(xs + hv) : 0ull;
+#pragma unroll
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (i < npre) {
+                    const ushort4 l = s_l[i];
+                    slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
+                }
+            }
+            if (hv >= 0) seta[nown + threadIdx.x] = halo_eta(P, xs, hv, hw, base + (unsigned)m, abort_val, ok);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (i >= npre && i < ns) {
+                    const ushort4 l = s_l[i];
+                    slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
+                }
+            }
+        } else if (m == 0 || SPT == 1) {
             if (m == 0) {
                 elements(0, ns, nullptr, 0u);
             } else {
