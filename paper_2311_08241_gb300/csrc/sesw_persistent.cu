@@ -30,10 +30,11 @@ namespace {
 // coef = (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)).
 // Packed FP32 pairs in the element update of the cached kernels (UNCACHED: kUncachedPacked).
 constexpr int kUncachedPacked = 0;
-// Cached kernel: each substep, one thread per halo vertex fetches its tagged word into shared
-// memory after the interior rounds, and every other slot then reads its corners from shared
-// memory (one extra block barrier per substep; patches with more halo vertices than threads
-// keep the per-slot halo reads).
+// Cached kernels (CACHED = 1 or 2, the halo ids in shared memory): each substep, one thread per
+// halo vertex requests its tagged word before the interior rounds and stores its value to
+// shared memory after them, and every other slot then reads its corners from shared memory
+// (one extra block barrier per substep; patches with more halo vertices than threads keep the
+// per-slot halo reads).
 constexpr int kHaloPrefetch = 1;
 
 template <int NONLIN, int PACKED>
@@ -185,7 +186,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
     // no thread does more rounds in total than ceil(ns / T); the interior slots left over
     // go with the boundary slots, whose halo reads may have to wait for a neighbour.
     const int npre = nint >= T ? (nint / T) * T : nint;
-    const bool hpre = kHaloPrefetch && CACHED == 1 && nhalo <= T;
+    const bool hpre = kHaloPrefetch && CACHED != 0 && nhalo <= T;
     for (int m = 0; m < P.M; m++) {
         if (hpre && m > 0) {
             // this thread's halo word is requested before the interior rounds and stored to
@@ -197,7 +198,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
             for (int j = 0; j < SPT; j++) {
                 const int i = threadIdx.x + j * T;
                 if (i < npre) {
-                    const ushort4 l = s_l[i];
+                    const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                     slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                 }
             }
@@ -207,7 +208,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
             for (int j = 0; j < SPT; j++) {
                 const int i = threadIdx.x + j * T;
                 if (i >= npre && i < ns) {
-                    const ushort4 l = s_l[i];
+                    const ushort4 l = CACHED == 1 ? s_l[i] : P.sl[s0 + i];
                     slot_update(j, i, seta[l.x], seta[l.y], seta[l.z]);
                 }
             }

@@ -128,13 +128,28 @@ __device__ __forceinline__ void stream_patch(const SArgs &A, const int p, const 
         // reads may have to wait for a neighbour; every halo value is in shared memory
         // at m = 0
         const int nfirst = first ? ns : nint;
+        // with the halo ids in shared memory, one thread per halo vertex requests its tagged
+        // word now and stores its value to shared memory after the interior slots; the other
+        // slots then read all corners from shared memory
+        const bool hpre = !first && A.vcache && nhalo <= T;
+        const int hv = hpre && (int)threadIdx.x < nhalo ? hid[threadIdx.x] : -1;
+        const unsigned long long hw = hv >= 0 ? ld_relaxed_gpu_u64(xs + hv) : 0ull;
 #pragma unroll 8
         for (int i = threadIdx.x; i < nfirst; i += T) {
             const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
             stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, first, seta[l.x], seta[l.y], seta[l.z], dt, sflux);
         }
+        if (hpre) {
+            if (hv >= 0) seta[nown + threadIdx.x] = halo_eta(P, xs, hv, hw, tag, abort_val, ok);
+            __syncthreads();
 #pragma unroll 8
-        for (int i = nfirst + threadIdx.x; i < ns; i += T) {
+            for (int i = nfirst + threadIdx.x; i < ns; i += T) {
+                const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
+                stream_slot<NONLIN>(A, s0 + i, i, i < nown_s, false, seta[l.x], seta[l.y], seta[l.z], dt, sflux);
+            }
+        }
+#pragma unroll 8
+        for (int i = nfirst + threadIdx.x; !hpre && i < ns; i += T) {
             const ushort4 l = IDX ? s_l[i] : __ldg(P.sl + s0 + i);
             const int h0 = l.x < nown ? -1 : hid[l.x - nown], h1 = l.y < nown ? -1 : hid[l.y - nown],
                       h2 = l.z < nown ? -1 : hid[l.z - nown];
