@@ -37,10 +37,11 @@ __device__ __forceinline__ void two_sum_acc2(float2 &hi, float2 &lo, float2 x)
         two_sum_acc(hi.y, lo.y, x.y);
         return;
     }
+    const float2 m1 = splat(-1.0f);
     const float2 s = __fadd2_rn(hi, x);
-    const float2 bp = __fadd2_rn(s, neg2(hi));
-    const float2 ap = __fadd2_rn(s, neg2(bp));
-    const float2 err = __fadd2_rn(__fadd2_rn(hi, neg2(ap)), __fadd2_rn(x, neg2(bp)));
+    const float2 bp = __ffma2_rn(hi, m1, s);
+    const float2 ap = __ffma2_rn(bp, m1, s);
+    const float2 err = __fadd2_rn(__ffma2_rn(ap, m1, hi), __ffma2_rn(bp, m1, x));
     hi = s;
     lo = __fadd2_rn(lo, err);
 }
@@ -105,10 +106,11 @@ __device__ __forceinline__ void corner_fluxes(float2 F, float4 g, float w, float
         out3[2] = -__fadd_rn(c0, c1);
         return;
     }
-    const float2 c = __fmul2_rn(splat(w), __ffma2_rn(splat(F.y), pair(g.y, g.w), __fmul2_rn(splat(F.x), pair(g.x, g.z))));
-    out3[0] = c.x;
-    out3[1] = c.y;
-    out3[2] = -__fadd_rn(c.x, c.y);
+    const float c0 = __fmul_rn(w, __fmaf_rn(F.y, g.y, __fmul_rn(F.x, g.x)));
+    const float c1 = __fmul_rn(w, __fmaf_rn(F.y, g.w, __fmul_rn(F.x, g.z)));
+    out3[0] = c0;
+    out3[1] = c1;
+    out3[2] = -__fadd_rn(c0, c1);
 }
 
 // The vertex update of Eq. (4.10), second row: eta + (sum of the corner contributions,
