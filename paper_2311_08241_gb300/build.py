@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libsesw.so")
 SOURCES = ["sesw_kernels.cu", "sesw_persistent.cu", "sesw_persistent_sesm.cu", "sesw_persistent_stream.cu",
            "sesw_persistent_sesm_stream.cu", "sesw_tc.cu", "sesw_noalloc.cu", "sesw_surrogate.cu",
            "sesw_api.cpp", "mesh_prep.cpp"]
-HEADERS = [os.path.join(CSRC, "sesw_internal.h"), os.path.join(CSRC, "sesw_device.cuh"),
+HEADERS = [os.path.join(CSRC, "sesw_internal.h"), os.path.join(CSRC, "sesw_device.cuh"), os.path.join(CSRC, "sesw_msg.cuh"),
            os.path.join(CSRC, "sesw_persistent.cuh"),
            os.path.join(ROOT, "include", "sesw.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -289,15 +289,32 @@ cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const St
 struct Surrogate;
 void surrogate_release(sesw_ctx *c);
 
-// Dense layer on the tensor cores (sesw_tc.cu): Y[n][j] = act(sum_k X[n][k] W[k][j] + b[j])
-// for N rows, K inputs holding bfloat16 values, 64 outputs. W (K x 64 row-major bf16) is
-// first packed by pack_linear_tc into linear_tc_packed_elems(K) elements (the shared-memory
-// image of W^T), which launch_linear_tc then reads.
+// Message layers on the tensor cores (sesw_tc.cu): K inputs holding bfloat16 values (K = 128
+// or 192), 64 outputs. W (K x 64 row-major bf16) is first packed by pack_linear_tc into
+// linear_tc_packed_elems(K) elements (the shared-memory image of W^T), which
+// launch_msg_layer_tc then reads.
 bool linear_tc_supported(int K, int P);
 size_t linear_tc_packed_elems(int K);
 cudaError_t pack_linear_tc(int K, const __nv_bfloat16 *W, __nv_bfloat16 *packed, cudaStream_t st);
-cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *packed, const float *bias, int act,
-                             float *Y, unsigned *status, cudaStream_t st);
+// The inputs of a message layer, formed inside the tensor-core layer from the hidden states:
+// kind 0, element rows, Z_e = [h_e, L sum_k dphi_k/dx h_vk, L sum_k dphi_k/dy h_vk] (K = 192);
+// kind 1, vertex rows, Z_v = [h_v, sum A_e h_e / sum A_e over the vertex's triangles] (K = 128).
+// The layer writes Y = tanh(Z W + b) and h_next = h + Y ([N][64] each; h_next must not alias
+// the inputs).
+struct MsgLayerArgs {
+    int kind;                   // 0 element rows, 1 vertex rows
+    int N;                      // rows
+    const int4 *etri;           // element corners
+    const float4 *egrad;        // element basis gradients (dphi0/dx, dphi0/dy, dphi1/dx, dphi1/dy)
+    float L;                    // length scale of the element message
+    const int *voff, *vinc;     // vertex incidences (element << 2 | corner), CSR
+    const float *earea, *vinvA; // element areas; 1 / sum of each vertex's element areas
+    const float *hself;         // hidden state of the rows' own kind
+    const float *hother;        // hidden state of the other kind
+    float *Y, *hnext;
+};
+cudaError_t launch_msg_layer_tc(const MsgLayerArgs &a, const __nv_bfloat16 *packed, const float *bias,
+                                unsigned *status, cudaStream_t st);
 // Backward of such a layer on the tensor cores, dA (FP32) split into two bfloat16 parts:
 // partial sums of the weight gradient sum_n Z[n][i] dA[n][j] and of the bias gradient over
 // rows_per_cta rows each (a multiple of 64; layout of k_reduce_partials), and the input

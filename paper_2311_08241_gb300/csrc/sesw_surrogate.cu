@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "sesw_internal.h"
+#include "sesw_msg.cuh"
 
 namespace sesw {
 
@@ -169,20 +170,12 @@ __global__ void k_tanh_bwd(size_t n, const float *__restrict__ dY, const float *
         dA[i] = dY[i] * (1.0f - Y[i] * Y[i]);
 }
 
-__global__ void k_axpy(size_t n, const float *__restrict__ x, float *__restrict__ y)
-{
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        y[i] += x[i];
-}
-
 // ------------------------------------------------------------------------- messages
 // thread per (node, channel), 64 channels per node
 
-// Z_e = [h_e, L sum_k gx_k h_vk, L sum_k gy_k h_vk]
-// The message-layer inputs are rounded to bfloat16 values when they are formed: the
-// tensor-core layers read them as BF16 operands, and the weight gradients see the same values.
-__device__ __forceinline__ float bf16_value(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
+// Z_e = [h_e, L sum_k gx_k h_vk, L sum_k gy_k h_vk], rebuilt for the backward pass (the forward
+// pass forms it inside the tensor-core layer). The message-layer inputs are rounded to
+// bfloat16 values: the tensor-core layers read them as BF16 operands.
 __global__ void k_msg_elem(int E, const int4 *__restrict__ etri, const float4 *__restrict__ egrad, float L,
                            const float *__restrict__ he, const float *__restrict__ hv, float *__restrict__ Z)
 {
@@ -192,13 +185,11 @@ __global__ void k_msg_elem(int E, const int4 *__restrict__ etri, const float4 *_
         const int4 v = etri[e];
         const float4 g = egrad[e];
         const float h0 = hv[(size_t)v.x * HC + c], h1 = hv[(size_t)v.y * HC + c], h2 = hv[(size_t)v.z * HC + c];
-        // gradients of corner 2: -(g0 + g1)
-        const float gx = g.x * h0 + g.z * h1 - (g.x + g.z) * h2;
-        const float gy = g.y * h0 + g.w * h1 - (g.y + g.w) * h2;
+        const float2 m = msg_elem_grad(g, h0, h1, h2, L);
         float *z = Z + (size_t)e * 3 * HC;
         z[c] = bf16_value(he[t]);
-        z[HC + c] = bf16_value(L * gx);
-        z[2 * HC + c] = bf16_value(L * gy);
+        z[HC + c] = bf16_value(m.x);
+        z[2 * HC + c] = bf16_value(m.y);
     }
 }
 
@@ -233,7 +224,7 @@ __global__ void k_msg_elem_adj_v(int V, const int *__restrict__ voff, const int 
     }
 }
 
-// Z_v = [h_v, sum_{(e,k) at v} A_e h_e / sum A_e]
+// Z_v = [h_v, sum_{(e,k) at v} A_e h_e / sum A_e], rebuilt for the backward pass
 __global__ void k_msg_vert(int V, const int *__restrict__ voff, const int *__restrict__ vinc,
                            const float *__restrict__ earea, const float *__restrict__ vinvA,
                            const float *__restrict__ hv, const float *__restrict__ he, float *__restrict__ Z)
@@ -244,11 +235,11 @@ __global__ void k_msg_vert(int V, const int *__restrict__ voff, const int *__res
         float s = 0.0f;
         for (int q = voff[v]; q < voff[v + 1]; q++) {
             const int e = vinc[q] >> 2;
-            s += earea[e] * he[(size_t)e * HC + c];
+            s = msg_vert_acc(s, earea[e], he[(size_t)e * HC + c]);
         }
         float *z = Z + (size_t)v * 2 * HC;
         z[c] = bf16_value(hv[t]);
-        z[HC + c] = bf16_value(s * vinvA[v]);
+        z[HC + c] = bf16_value(msg_vert_mean(s, vinvA[v]));
     }
 }
 
@@ -673,13 +664,28 @@ cudaError_t mm(Surrogate &S, cudaStream_t st, int N, int Kin, int P, const float
     return cudaGetLastError();
 }
 
-// Forward of one layer, Y = act(X W + b): the message layers on the tensor cores (their
-// inputs hold bfloat16 values and their weights a packed copy), the others on k_mm.
-cudaError_t linear(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const float *X, int act, float *Y)
+// Forward of message layer ly (kind 0: element rows from h_e[l] and h_v[l]; kind 1: vertex rows
+// from h_v[l] and h_e[l + 1]) on the tensor cores, the message gather fused into the layer:
+// writes Y and h_next = h + Y.
+cudaError_t msg_layer(Surrogate &S, cudaStream_t st, const Layer &ly, int kind, const float *hself,
+                      const float *hother, float *Y, float *hnext)
 {
-    if (ly.tc >= 0)
-        return launch_linear_tc(N, ly.K, X, S.wtc + ly.tc, S.w32 + ly.b, act, Y, S.status, st);
-    return mm(S, st, N, ly.K, ly.C, X, S.w16 + ly.w, 0, S.w32 + ly.b, act, nullptr, Y);
+    if (ly.tc < 0) return cudaErrorInvalidValue;
+    MsgLayerArgs a;
+    a.kind = kind;
+    a.N = kind == 0 ? S.E : S.V;
+    a.etri = S.etri;
+    a.egrad = S.egrad;
+    a.L = (float)S.scales_h[S_L];
+    a.voff = S.voff;
+    a.vinc = S.vinc;
+    a.earea = S.earea;
+    a.vinvA = S.vinvA;
+    a.hself = hself;
+    a.hother = hother;
+    a.Y = Y;
+    a.hnext = hnext;
+    return launch_msg_layer_tc(a, S.wtc + ly.tc, S.w32 + ly.b, S.status, st);
 }
 
 // Refresh the packed tensor-core copies after the bfloat16 weights changed.
@@ -726,27 +732,15 @@ cudaError_t dgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const f
 // forward of one sample whose features are in S.xv, S.xe
 cudaError_t forward(Surrogate &S, cudaStream_t st)
 {
-    const float Ls = (float)S.scales_h[S_L];
     cudaError_t e;
     const Layer &lv0 = S.L[0], &le0 = S.L[1];
     if ((e = mm(S, st, S.V, 2, HC, S.xv, S.w16 + lv0.w, 0, S.w32 + lv0.b, 1, nullptr, S.hv[0])) != cudaSuccess) return e;
     if ((e = mm(S, st, S.E, 6, HC, S.xe, S.w16 + le0.w, 0, S.w32 + le0.b, 1, nullptr, S.he[0])) != cudaSuccess) return e;
     for (int l = 0; l < NL; l++) {
         const Layer &le = S.L[2 + 2 * l], &lv = S.L[3 + 2 * l];
-        k_msg_elem<<<grid1((size_t)S.E * HC), 256, 0, st>>>(S.E, S.etri, S.egrad, Ls, S.he[l], S.hv[l], S.ze);
-        if ((e = linear(S, st, le, S.E, S.ze, 1, S.ye[l])) != cudaSuccess) return e;
-        // h_e(l+1) = h_e(l) + y_e(l)
-        if ((e = cudaMemcpyAsync(S.he[l + 1], S.he[l], sizeof(float) * (size_t)S.E * HC, cudaMemcpyDeviceToDevice, st)) !=
-            cudaSuccess)
-            return e;
-        k_axpy<<<grid1((size_t)S.E * HC), 256, 0, st>>>((size_t)S.E * HC, S.ye[l], S.he[l + 1]);
-        k_msg_vert<<<grid1((size_t)S.V * HC), 256, 0, st>>>(S.V, S.voff, S.vinc, S.earea, S.vinvA, S.hv[l], S.he[l + 1],
-                                                            S.zv);
-        if ((e = linear(S, st, lv, S.V, S.zv, 1, S.yv[l])) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(S.hv[l + 1], S.hv[l], sizeof(float) * (size_t)S.V * HC, cudaMemcpyDeviceToDevice, st)) !=
-            cudaSuccess)
-            return e;
-        k_axpy<<<grid1((size_t)S.V * HC), 256, 0, st>>>((size_t)S.V * HC, S.yv[l], S.hv[l + 1]);
+        // h_e(l+1) = h_e(l) + y_e(l), then h_v(l+1) = h_v(l) + y_v(l) from h_e(l+1)
+        if ((e = msg_layer(S, st, le, 0, S.he[l], S.hv[l], S.ye[l], S.he[l + 1])) != cudaSuccess) return e;
+        if ((e = msg_layer(S, st, lv, 1, S.hv[l], S.he[l + 1], S.yv[l], S.hv[l + 1])) != cudaSuccess) return e;
     }
     const Layer &leo = S.L[2 + 2 * NL], &lvo = S.L[3 + 2 * NL];
     if ((e = mm(S, st, S.E, HC, 4, S.he[NL], S.w16 + leo.w, 0, S.w32 + leo.b, 0, nullptr, S.oe)) != cudaSuccess) return e;

@@ -1,16 +1,18 @@
-// Dense layer of the learned surrogate on the fifth-generation tensor cores (sm_103a):
-//     Y[n][j] = act( sum_k X[n][k] W[k][j] + b[j] ),  j < 64,
-// with X already rounded to bfloat16 values (stored as float) and W in bfloat16; the
-// products accumulate in FP32 in tensor memory.
+// Message layers of the learned surrogate on the fifth-generation tensor cores (sm_103a).
+// Forward (k_msg_layer_tc):
+//     Y[n][j] = tanh( sum_k Z[n][k] W[k][j] + b[j] ),  h_next[n][j] = h[n][j] + Y[n][j],  j < 64,
+// where the CTA forms its rows of Z (bfloat16 values) from the hidden states while staging
+// them, so Z never goes to memory; W is bfloat16 and the products accumulate in FP32 in
+// tensor memory.
 //
-// One CTA of 256 threads computes 128 rows. It stages its X tile and the whole W (as
-// W^T, from a copy packed once per weight update by k_pack_wt) in shared memory in the
-// K-major layout without swizzle that tcgen05.mma reads:
-// core matrices of 8 rows x 8 bf16 (16 bytes per row, 128 bytes each), core matrices
-// adjacent along K 128 bytes apart, along M (or N) K * 16 bytes apart. One thread
-// issues K/16 MMAs of shape 128 x 64 x 16 into a 64-column TMEM accumulator and commits
-// them to an mbarrier; after a bounded wait every warp reads 32 rows x 32 columns back
-// with tcgen05.ld, applies bias and activation, and stores.
+// One CTA of 256 threads computes 128 rows. It stages its Z tile and the whole W (as W^T,
+// from a copy packed once per weight update by k_pack_wt) in shared memory in the K-major
+// layout without swizzle that tcgen05.mma reads: core matrices of 8 rows x 8 bf16 (16 bytes
+// per row, 128 bytes each), core matrices adjacent along K 128 bytes apart, along M (or N)
+// K * 16 bytes apart. One thread issues K/16 MMAs of shape 128 x 64 x 16 into a 64-column
+// TMEM accumulator and commits them to an mbarrier; after a bounded wait every warp reads 32
+// rows x 32 columns back with tcgen05.ld, applies bias, activation and the residual, and
+// stores.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -19,6 +21,7 @@
 
 #include "sesw_device.cuh"
 #include "sesw_internal.h"
+#include "sesw_msg.cuh"
 
 namespace sesw {
 
@@ -68,7 +71,22 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, long long budget)
     }
 }
 
-// W (K x 64, row-major bf16) as the shared-memory image of W^T that k_linear_tc copies:
+// Read 16 FP32 columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int t = 0; t < 16; t++) v[t] = __uint_as_float(r[t]);
+}
+
+// W (K x 64, row-major bf16) as the shared-memory image of W^T that k_msg_layer_tc copies:
 // 16-byte chunk c = (jg * K/8 + kc) * 8 + jl holds W[8 kc .. 8 kc + 7][8 jg + jl].
 __global__ void k_pack_wt(int K, const __nv_bfloat16 *__restrict__ W, uint4 *__restrict__ out)
 {
@@ -84,12 +102,29 @@ __global__ void k_pack_wt(int K, const __nv_bfloat16 *__restrict__ W, uint4 *__r
     }
 }
 
-template <int K>
-__global__ void __launch_bounds__(TC_THREADS)
-k_linear_tc(int N, const float *__restrict__ X, const uint4 *__restrict__ Wp, const float *__restrict__ bias,
-            int act, float *__restrict__ Y, unsigned *__restrict__ status, long long wait_cycles)
+__device__ __forceinline__ uint4 pack_bf16x8(const float *v)
 {
-    static_assert(K % 16 == 0 && K <= 256, "K must be a multiple of 16");
+    return make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                      pack_bf16x2(v[6], v[7]));
+}
+
+__device__ __forceinline__ void load8(const float *p, float *v)
+{
+    const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+
+// One message layer of the surrogate's forward pass (KIND 0: element rows, K = 192; KIND 1:
+// vertex rows, K = 128): the CTA forms its 128 rows of Z from the hidden states while it
+// stages them as the A tile, so Z never goes to memory, then Y = tanh(Z W + b) and
+// h_next = h + Y in the epilogue.
+template <int KIND>
+__global__ void __launch_bounds__(TC_THREADS)
+k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *__restrict__ bias,
+               unsigned *__restrict__ status, long long wait_cycles)
+{
+    constexpr int K = KIND == 0 ? 3 * TC_N : 2 * TC_N;
     constexpr int KC = K / 8;    // core matrices along K
     extern __shared__ __align__(1024) unsigned char smem[];
     uint4 *As = reinterpret_cast<uint4 *>(smem);                              // 128 x K bf16
@@ -98,7 +133,7 @@ k_linear_tc(int N, const float *__restrict__ X, const uint4 *__restrict__ Wp, co
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n0 = blockIdx.x * TC_M;
+    const int N = a.N, n0 = blockIdx.x * TC_M;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -110,38 +145,55 @@ k_linear_tc(int N, const float *__restrict__ X, const uint4 *__restrict__ Wp, co
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // A tile: chunk c is row r = 8 rg + rl, columns 8 kc .. 8 kc + 7; consecutive threads
-    // fill consecutive 16-byte rows of one core matrix. Four chunks' loads are issued
-    // before any is converted, so that their latencies overlap.
-    constexpr int PER = TC_M * KC / TC_THREADS;
-    static_assert(PER % 4 == 0, "chunks per thread must be a multiple of 4");
-#pragma unroll
-    for (int b = 0; b < PER; b += 4) {
-        float4 va[4], vb[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int c = tid + (b + u) * TC_THREADS;
-            const int rl = c & 7, kc = (c >> 3) % KC, rg = (c >> 3) / KC;
-            const int n = n0 + rg * 8 + rl;
-            va[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            vb[u] = va[u];
-            if (n < N) {
-                va[u] = *reinterpret_cast<const float4 *>(X + (size_t)n * K + kc * 8);
-                vb[u] = *reinterpret_cast<const float4 *>(X + (size_t)n * K + kc * 8 + 4);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            const int c = tid + (b + u) * TC_THREADS;
-            const int rl = c & 7, kc = (c >> 3) % KC, rg = (c >> 3) / KC;
-            As[(rg * KC + kc) * 8 + rl] =
-                make_uint4(pack_bf16x2(va[u].x, va[u].y), pack_bf16x2(va[u].z, va[u].w),
-                           pack_bf16x2(vb[u].x, vb[u].y), pack_bf16x2(vb[u].z, vb[u].w));
-        }
-    }
-    // B tile: the packed image of W^T, copied as is
+    // B tile: the packed image of W^T, copied as is (its loads overlap the gathers below)
 #pragma unroll 4
     for (int c = tid; c < TC_N * KC; c += TC_THREADS) Bs[c] = Wp[c];
+    // A tile: item it is row r = 8 rg + rl and the 8 hidden channels 8 cg .. 8 cg + 7; it forms
+    // the row's 16-byte chunk of each block of Z for those channels (chunk kc of row r sits at
+    // (rg KC + kc) 8 + rl). Consecutive threads take consecutive rows of one core matrix, so
+    // the shared-memory stores do not conflict.
+    constexpr int PER = TC_M * (TC_N / 8) / TC_THREADS;
+#pragma unroll 2
+    for (int u = 0; u < PER; u++) {
+        const int it = tid + u * TC_THREADS;
+        const int rl = it & 7, cg = (it >> 3) & 7, rg = it >> 6;
+        const int n = n0 + rg * 8 + rl;
+        uint4 *chunk = As + (size_t)rg * KC * 8 + rl;    // chunk kc at chunk[kc * 8]
+        float hs[8] = {}, m0[8] = {}, m1[8] = {};
+        if (n < N) {
+            load8(a.hself + (size_t)n * TC_N + cg * 8, hs);
+            if (KIND == 0) {
+                const int4 v = a.etri[n];
+                const float4 g = a.egrad[n];
+                float h0[8], h1[8], h2[8];
+                load8(a.hother + (size_t)v.x * TC_N + cg * 8, h0);
+                load8(a.hother + (size_t)v.y * TC_N + cg * 8, h1);
+                load8(a.hother + (size_t)v.z * TC_N + cg * 8, h2);
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const float2 m = msg_elem_grad(g, h0[t], h1[t], h2[t], a.L);
+                    m0[t] = m.x;
+                    m1[t] = m.y;
+                }
+            } else {
+                const int q1 = a.voff[n + 1];
+                for (int q = a.voff[n]; q < q1; q++) {
+                    const int e = a.vinc[q] >> 2;
+                    const float ar = a.earea[e];
+                    float h[8];
+                    load8(a.hother + (size_t)e * TC_N + cg * 8, h);
+#pragma unroll
+                    for (int t = 0; t < 8; t++) m0[t] = msg_vert_acc(m0[t], ar, h[t]);
+                }
+                const float inv = a.vinvA[n];
+#pragma unroll
+                for (int t = 0; t < 8; t++) m0[t] = msg_vert_mean(m0[t], inv);
+            }
+        }
+        chunk[cg * 8] = pack_bf16x8(hs);
+        chunk[(8 + cg) * 8] = pack_bf16x8(m0);
+        if (KIND == 0) chunk[(16 + cg) * 8] = pack_bf16x8(m1);
+    }
     // make the generic-proxy writes of the tiles visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -181,27 +233,21 @@ k_linear_tc(int N, const float *__restrict__ X, const uint4 *__restrict__ Wp, co
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
         for (int q = 2 * half; q < 2 * half + 2; q++) {
-            uint32_t r[16];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15}, [%16];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                : "r"(taddr + q * 16));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float acc[16];
+            tmem_ld16(taddr + q * 16, acc);
             if (n < N) {
-                float4 *dst = reinterpret_cast<float4 *>(Y + (size_t)n * TC_N + q * 16);
+                const float4 *hsrc = reinterpret_cast<const float4 *>(a.hself + (size_t)n * TC_N + q * 16);
+                float4 *dy = reinterpret_cast<float4 *>(a.Y + (size_t)n * TC_N + q * 16);
+                float4 *dh = reinterpret_cast<float4 *>(a.hnext + (size_t)n * TC_N + q * 16);
 #pragma unroll
                 for (int t = 0; t < 16; t += 4) {
-                    float v[4];
+                    float y[4];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        float y = __uint_as_float(r[t + u]);
-                        if (bias) y += bias[q * 16 + t + u];
-                        if (act) y = tanhf(y);
-                        v[u] = y;
-                    }
-                    dst[t / 4] = make_float4(v[0], v[1], v[2], v[3]);
+                    for (int u = 0; u < 4; u++) y[u] = tanhf(__fadd_rn(acc[t + u], bias[q * 16 + t + u]));
+                    const float4 h = hsrc[t / 4];
+                    dy[t / 4] = make_float4(y[0], y[1], y[2], y[3]);
+                    dh[t / 4] = make_float4(__fadd_rn(h.x, y[0]), __fadd_rn(h.y, y[1]), __fadd_rn(h.z, y[2]),
+                                            __fadd_rn(h.w, y[3]));
                 }
             }
         }
@@ -214,21 +260,6 @@ k_linear_tc(int N, const float *__restrict__ X, const uint4 *__restrict__ Wp, co
     }
 }
 
-template <int K>
-cudaError_t launch_k(int N, const float *X, const uint4 *Wp, const float *bias, int act, float *Y,
-                     unsigned *status, cudaStream_t st)
-{
-    const size_t smem = (size_t)(TC_M + TC_N) * K * 2;
-    // a per-kernel, per-device attribute: set on every launch (cheap) so that any device works
-    cudaError_t e = cudaFuncSetAttribute(k_linear_tc<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int grid = (N + TC_M - 1) / TC_M;
-    if (grid == 0) return cudaSuccess;
-    // about one second of SM clock for the MMA completion wait
-    k_linear_tc<K><<<grid, TC_THREADS, smem, st>>>(N, X, Wp, bias, act, Y, status, 2000000000ll);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------------
 // The two backward contractions of a message layer (inputs Z [N][K] holding bfloat16 values,
 // K = 128 or 192; weights W [K][64]; dA = dL/d(pre-activation) [N][64], FP32):
@@ -237,7 +268,7 @@ cudaError_t launch_k(int N, const float *X, const uint4 *Wp, const float *bias, 
 // dA is not a bfloat16 value, so each of its elements is split into two bfloat16 parts,
 // hi = bf16(dA) and lo = bf16(dA - hi), which carry 16 significant bits, and both parts
 // are multiplied: the products accumulate in FP32 in tensor memory. Operand tiles are
-// staged in the same K-major layout without swizzle as k_linear_tc's (core matrices of 8
+// staged in the same K-major layout without swizzle as k_msg_layer_tc's (core matrices of 8
 // rows x 16 bytes, 128 bytes apart along K, KC * 128 bytes apart along M or N).
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
@@ -278,21 +309,6 @@ __device__ __forceinline__ bool mbar_wait_parity(uint32_t bar, uint32_t parity, 
         if (ok) return true;
         if (clock64() - t0 > budget) return false;
     }
-}
-
-// Read 16 FP32 columns of this warp's 32 TMEM lanes.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int t = 0; t < 16; t++) v[t] = __uint_as_float(r[t]);
 }
 
 constexpr int WG_THREADS = 256;
@@ -629,13 +645,25 @@ cudaError_t pack_linear_tc(int K, const __nv_bfloat16 *W, __nv_bfloat16 *packed,
     return cudaGetLastError();
 }
 
-cudaError_t launch_linear_tc(int N, int K, const float *X, const __nv_bfloat16 *packed, const float *bias, int act,
-                             float *Y, unsigned *status, cudaStream_t st)
+cudaError_t launch_msg_layer_tc(const MsgLayerArgs &a, const __nv_bfloat16 *packed, const float *bias,
+                                unsigned *status, cudaStream_t st)
 {
     const uint4 *Wp = reinterpret_cast<const uint4 *>(packed);
-    if (K == 128) return launch_k<128>(N, X, Wp, bias, act, Y, status, st);
-    if (K == 192) return launch_k<192>(N, X, Wp, bias, act, Y, status, st);
-    return cudaErrorInvalidValue;
+    if (a.kind != 0 && a.kind != 1) return cudaErrorInvalidValue;
+    const int grid = (a.N + TC_M - 1) / TC_M;
+    if (grid == 0) return cudaSuccess;
+    const int K = a.kind == 0 ? 3 * TC_N : 2 * TC_N;
+    const size_t smem = (size_t)(TC_M + TC_N) * K * 2;
+    const void *fn = a.kind == 0 ? (const void *)k_msg_layer_tc<0> : (const void *)k_msg_layer_tc<1>;
+    // a per-kernel, per-device attribute: set on every launch (cheap) so that any device works
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // about one second of SM clock for the MMA completion wait
+    if (a.kind == 0)
+        k_msg_layer_tc<0><<<grid, TC_THREADS, smem, st>>>(a, Wp, bias, status, 2000000000ll);
+    else
+        k_msg_layer_tc<1><<<grid, TC_THREADS, smem, st>>>(a, Wp, bias, status, 2000000000ll);
+    return cudaGetLastError();
 }
 
 }  // namespace sesw

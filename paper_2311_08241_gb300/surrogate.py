@@ -85,7 +85,7 @@ def persistence_loss(sim, idx):
         sim.sesw_surrogate_weights(set=w)
 
 
-SURROGATE_STEP_KERNELS = 27
+SURROGATE_STEP_KERNELS = 15
 
 
 def rollout_error(case, R, params_ref, weights, scales, nsteps, resid_tol, coarse_M=(), device=0,
@@ -142,7 +142,7 @@ def rollout_error(case, R, params_ref, weights, scales, nsteps, resid_tol, coars
         _, resid_nofb = s.sesw_surrogate_advance(nsteps, 1e30)
         eta_nofb = s.sesw_get_state()[0]
         t_nofb = (time.perf_counter() - t1) / nsteps
-    # kernels per surrogate step: state copy-in, features, 22 of the forward pass, apply to
+    # kernels per surrogate step: state copy-in, features, 10 of the forward pass, apply to
     # elements and vertices, residual; a fallback adds one plain step (one cooperative launch
     # per pack, or M substeps and the epilogue in graph mode)
     plain_launches = max(1, info["npack"]) if info["mode"] == S.SESW_MODE_PERSISTENT else params_ref.M + 1
