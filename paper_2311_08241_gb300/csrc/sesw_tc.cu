@@ -115,12 +115,28 @@ __device__ __forceinline__ void load8(const float *p, float *v)
     v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
+// Element incidences of a vertex-layer CTA's rows held in shared memory (more go through
+// global memory, in the same order).
+constexpr int MSG_INC_CAP = 1536;
+
+// Shared memory of k_msg_layer_tc: the A tile (128 x K bf16), W^T (64 x K bf16), then the
+// rows' graph data: KIND 0 the three corners of 128 elements (three CTAs of 75.3 KB fit an
+// SM); KIND 1 the 129 CSR offsets of the rows and the element ids and areas of up to
+// MSG_INC_CAP incidences.
+__host__ __device__ constexpr size_t msg_layer_smem(int kind)
+{
+    return (size_t)(TC_M + TC_N) * (kind == 0 ? 3 * TC_N : 2 * TC_N) * 2 +
+           (kind == 0 ? (size_t)TC_M * 12 : (size_t)(TC_M + 4) * 4 + (size_t)MSG_INC_CAP * 8);
+}
+
 // One message layer of the surrogate's forward pass (KIND 0: element rows, K = 192; KIND 1:
 // vertex rows, K = 128): the CTA forms its 128 rows of Z from the hidden states while it
 // stages them as the A tile, so Z never goes to memory, then Y = tanh(Z W + b) and
-// h_next = h + Y in the epilogue.
+// h_next = h + Y in the epilogue. The rows' graph data go to shared memory first, so that
+// every gather of the hidden states has its address at hand; each thread then gathers two
+// rows' inputs at a time.
 template <int KIND>
-__global__ void __launch_bounds__(TC_THREADS)
+__global__ void __launch_bounds__(TC_THREADS, 3)
 k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *__restrict__ bias,
                unsigned *__restrict__ status, long long wait_cycles)
 {
@@ -129,6 +145,11 @@ k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *
     extern __shared__ __align__(1024) unsigned char smem[];
     uint4 *As = reinterpret_cast<uint4 *>(smem);                              // 128 x K bf16
     uint4 *Bs = reinterpret_cast<uint4 *>(smem + (size_t)TC_M * K * 2);       // 64 x K bf16 (W^T)
+    unsigned char *gdata = smem + (size_t)(TC_M + TC_N) * K * 2;
+    int *s_tri = reinterpret_cast<int *>(gdata);                              // KIND 0: [3][128]
+    int *s_off = reinterpret_cast<int *>(gdata);                              // KIND 1
+    int *s_inc = s_off + TC_M + 4;
+    float *s_area = reinterpret_cast<float *>(s_inc + MSG_INC_CAP);
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
     __shared__ int s_ok;
@@ -145,59 +166,132 @@ k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // B tile: the packed image of W^T, copied as is (its loads overlap the gathers below)
+    // the rows' graph data (rows past N: element 0's corners; empty CSR rows)
+    if (KIND == 0) {
+        for (int r = tid; r < TC_M; r += TC_THREADS) {
+            const int4 v = n0 + r < N ? a.etri[n0 + r] : make_int4(0, 0, 0, 0);
+            s_tri[r] = v.x;
+            s_tri[TC_M + r] = v.y;
+            s_tri[2 * TC_M + r] = v.z;
+        }
+    } else {
+        for (int r = tid; r <= TC_M; r += TC_THREADS) s_off[r] = a.voff[min(n0 + r, N)];
+    }
+    // B tile: the packed image of W^T, copied as is
 #pragma unroll 4
     for (int c = tid; c < TC_N * KC; c += TC_THREADS) Bs[c] = Wp[c];
+    __syncthreads();
+    const int qbase = KIND == 1 ? s_off[0] : 0;
+    const bool inc_smem = KIND == 1 && s_off[TC_M] - qbase <= MSG_INC_CAP;
+    if (KIND == 1 && inc_smem) {
+        for (int t = tid; t < s_off[TC_M] - qbase; t += TC_THREADS) {
+            const int e = a.vinc[qbase + t] >> 2;
+            s_inc[t] = e;
+            s_area[t] = a.earea[e];
+        }
+        __syncthreads();
+    }
     // A tile: item it is row r = 8 rg + rl and the 8 hidden channels 8 cg .. 8 cg + 7; it forms
     // the row's 16-byte chunk of each block of Z for those channels (chunk kc of row r sits at
     // (rg KC + kc) 8 + rl). Consecutive threads take consecutive rows of one core matrix, so
     // the shared-memory stores do not conflict.
     constexpr int PER = TC_M * (TC_N / 8) / TC_THREADS;
-#pragma unroll 2
-    for (int u = 0; u < PER; u++) {
-        const int it = tid + u * TC_THREADS;
-        const int rl = it & 7, cg = (it >> 3) & 7, rg = it >> 6;
-        const int n = n0 + rg * 8 + rl;
-        uint4 *chunk = As + (size_t)rg * KC * 8 + rl;    // chunk kc at chunk[kc * 8]
-        float hs[8] = {}, m0[8] = {}, m1[8] = {};
-        if (n < N) {
-            load8(a.hself + (size_t)n * TC_N + cg * 8, hs);
-            if (KIND == 0) {
-                const int4 v = a.etri[n];
-                const float4 g = a.egrad[n];
-                float h0[8], h1[8], h2[8];
-                load8(a.hother + (size_t)v.x * TC_N + cg * 8, h0);
-                load8(a.hother + (size_t)v.y * TC_N + cg * 8, h1);
-                load8(a.hother + (size_t)v.z * TC_N + cg * 8, h2);
+    static_assert(PER % 2 == 0, "items per thread must be even");
+#pragma unroll 1
+    for (int u = 0; u < PER; u += 2) {
+        int r[2], cg[2], n[2];
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+            const int it = tid + (u + w) * TC_THREADS;
+            r[w] = (it >> 6) * 8 + (it & 7);
+            cg[w] = (it >> 3) & 7;
+            n[w] = n0 + r[w];
+        }
+        float hs[2][8], m0[2][8], m1[2][8];
+        if (KIND == 0) {
+            float h0[2][8], h1[2][8], h2[2][8];
+            float4 g[2];
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
+                const int c8 = cg[w] * 8, nc = min(n[w], N - 1);
+                g[w] = a.egrad[nc];
+                load8(a.hself + (size_t)nc * TC_N + c8, hs[w]);
+                load8(a.hother + (size_t)s_tri[r[w]] * TC_N + c8, h0[w]);
+                load8(a.hother + (size_t)s_tri[TC_M + r[w]] * TC_N + c8, h1[w]);
+                load8(a.hother + (size_t)s_tri[2 * TC_M + r[w]] * TC_N + c8, h2[w]);
+            }
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
 #pragma unroll
                 for (int t = 0; t < 8; t++) {
-                    const float2 m = msg_elem_grad(g, h0[t], h1[t], h2[t], a.L);
-                    m0[t] = m.x;
-                    m1[t] = m.y;
+                    const float2 m = msg_elem_grad(g[w], h0[w][t], h1[w][t], h2[w][t], a.L);
+                    m0[w][t] = m.x;
+                    m1[w][t] = m.y;
                 }
-            } else {
-                const int q1 = a.voff[n + 1];
-                for (int q = a.voff[n]; q < q1; q++) {
-                    const int e = a.vinc[q] >> 2;
-                    const float ar = a.earea[e];
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < 2; w++) load8(a.hself + (size_t)min(n[w], N - 1) * TC_N + cg[w] * 8, hs[w]);
+#pragma unroll
+            for (int w = 0; w < 2; w++) {
+                const int c8 = cg[w] * 8;
+                const int q0 = s_off[r[w]], q1 = s_off[r[w] + 1];
+#pragma unroll
+                for (int t = 0; t < 8; t++) m0[w][t] = 0.0f;
+                // four incidences' rows in flight, summed in incidence order
+                int q = q0;
+                for (; q + 4 <= q1; q += 4) {
+                    float h[4][8], ar[4];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const int e = inc_smem ? s_inc[q + j - qbase] : a.vinc[q + j] >> 2;
+                        ar[j] = inc_smem ? s_area[q + j - qbase] : a.earea[e];
+                        load8(a.hother + (size_t)e * TC_N + c8, h[j]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+#pragma unroll
+                        for (int t = 0; t < 8; t++) m0[w][t] = msg_vert_acc(m0[w][t], ar[j], h[j][t]);
+                }
+                for (; q < q1; q++) {
+                    const int e = inc_smem ? s_inc[q - qbase] : a.vinc[q] >> 2;
+                    const float ar = inc_smem ? s_area[q - qbase] : a.earea[e];
                     float h[8];
-                    load8(a.hother + (size_t)e * TC_N + cg * 8, h);
+                    load8(a.hother + (size_t)e * TC_N + c8, h);
 #pragma unroll
-                    for (int t = 0; t < 8; t++) m0[t] = msg_vert_acc(m0[t], ar, h[t]);
+                    for (int t = 0; t < 8; t++) m0[w][t] = msg_vert_acc(m0[w][t], ar, h[t]);
                 }
-                const float inv = a.vinvA[n];
+                const float inv = a.vinvA[min(n[w], N - 1)];
 #pragma unroll
-                for (int t = 0; t < 8; t++) m0[t] = msg_vert_mean(m0[t], inv);
+                for (int t = 0; t < 8; t++) m0[w][t] = msg_vert_mean(m0[w][t], inv);
             }
         }
-        chunk[cg * 8] = pack_bf16x8(hs);
-        chunk[(8 + cg) * 8] = pack_bf16x8(m0);
-        if (KIND == 0) chunk[(16 + cg) * 8] = pack_bf16x8(m1);
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+            if (n[w] >= N) {
+#pragma unroll
+                for (int t = 0; t < 8; t++) hs[w][t] = m0[w][t] = m1[w][t] = 0.0f;
+            }
+            uint4 *chunk = As + (size_t)(r[w] >> 3) * KC * 8 + (r[w] & 7);    // chunk kc at chunk[kc * 8]
+            chunk[cg[w] * 8] = pack_bf16x8(hs[w]);
+            chunk[(8 + cg[w]) * 8] = pack_bf16x8(m0[w]);
+            if (KIND == 0) chunk[(16 + cg[w]) * 8] = pack_bf16x8(m1[w]);
+        }
     }
     // make the generic-proxy writes of the tiles visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     const uint32_t tmem = tmem_base;
+    // the epilogue's residual rows, requested before the MMAs are issued: this thread's row and
+    // 32 columns (rows past N read row N - 1 and store nothing)
+    const int quarter = warp & 3, half = warp >> 2;
+    const int erow = n0 + quarter * 32 + lane;
+    float4 hres[8];
+    {
+        const float4 *hsrc = reinterpret_cast<const float4 *>(a.hself + (size_t)min(erow, N - 1) * TC_N + half * 32);
+#pragma unroll
+        for (int t = 0; t < 8; t++) hres[t] = hsrc[t];
+    }
 
     if (tid == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;");
@@ -227,16 +321,13 @@ k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *
 
     if (s_ok) {
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const int quarter = warp & 3, half = warp >> 2;
-        const int row = quarter * 32 + lane;
-        const int n = n0 + row;
+        const int n = erow;
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll
         for (int q = 2 * half; q < 2 * half + 2; q++) {
             float acc[16];
             tmem_ld16(taddr + q * 16, acc);
             if (n < N) {
-                const float4 *hsrc = reinterpret_cast<const float4 *>(a.hself + (size_t)n * TC_N + q * 16);
                 float4 *dy = reinterpret_cast<float4 *>(a.Y + (size_t)n * TC_N + q * 16);
                 float4 *dh = reinterpret_cast<float4 *>(a.hnext + (size_t)n * TC_N + q * 16);
 #pragma unroll
@@ -244,7 +335,7 @@ k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *
                     float y[4];
 #pragma unroll
                     for (int u = 0; u < 4; u++) y[u] = tanhf(__fadd_rn(acc[t + u], bias[q * 16 + t + u]));
-                    const float4 h = hsrc[t / 4];
+                    const float4 h = hres[(q - 2 * half) * 4 + t / 4];
                     dy[t / 4] = make_float4(y[0], y[1], y[2], y[3]);
                     dh[t / 4] = make_float4(__fadd_rn(h.x, y[0]), __fadd_rn(h.y, y[1]), __fadd_rn(h.z, y[2]),
                                             __fadd_rn(h.w, y[3]));
@@ -652,8 +743,7 @@ cudaError_t launch_msg_layer_tc(const MsgLayerArgs &a, const __nv_bfloat16 *pack
     if (a.kind != 0 && a.kind != 1) return cudaErrorInvalidValue;
     const int grid = (a.N + TC_M - 1) / TC_M;
     if (grid == 0) return cudaSuccess;
-    const int K = a.kind == 0 ? 3 * TC_N : 2 * TC_N;
-    const size_t smem = (size_t)(TC_M + TC_N) * K * 2;
+    const size_t smem = msg_layer_smem(a.kind);
     const void *fn = a.kind == 0 ? (const void *)k_msg_layer_tc<0> : (const void *)k_msg_layer_tc<1>;
     // a per-kernel, per-device attribute: set on every launch (cheap) so that any device works
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
