@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4000)
@@ -64,10 +64,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-substeps", type=int, default=4,
                     help="substeps of the channel per reference-arm step (a bounded sample)")
-    ap.add_argument("--workload", choices=["channel", "sphere", "ensemble", "surrogate"], default="ensemble",
-                    help="ensemble: 64 basins of uneven size, batched (the headline workload); channel: the "
-                         "200k-vertex wind-driven channel; sphere: the global-like level-8 sphere (458,683 wet "
-                         "vertices); surrogate: train and evaluate the learned surrogate on the sphere")
+    ap.add_argument("--workload", choices=["channel", "sphere", "ensemble", "surrogate"], default=None,
+                    help="ensemble (default): 64 basins of uneven size, batched (the headline workload); "
+                         "channel: the 200k-vertex wind-driven channel (the default with --scheme sesm, --visc "
+                         "or --freshwater); sphere: the global-like level-8 sphere (458,683 wet vertices); "
+                         "surrogate: train and evaluate the learned surrogate on the sphere")
     ap.add_argument("--autotune", choices=["quick", "full", "none"], default="quick",
                     help="ensemble layouts timed before the run: quick (persistent forms, large-basin "
                          "layouts and one graph layout), full (every candidate), none (the layout of "
@@ -85,7 +86,13 @@ def parse():
     ap.add_argument("--ensemble-scale", type=float, default=1.0)
     ap.add_argument("--sequential-steps", type=int, default=10,
                     help="ensemble: steps of the one-basin-after-another comparison (0: skip it)")
-    return ap.parse_args()
+    args = ap.parse_args(argv)
+    variant = args.scheme == "sesm" or bool(args.visc) or bool(args.freshwater)
+    if args.workload is None:
+        args.workload = "channel" if variant else "ensemble"
+    elif variant and args.workload in ("ensemble", "surrogate"):
+        ap.error("--scheme sesm, --visc and --freshwater run on the channel or sphere workloads")
+    return args
 
 
 def workload(name="channel"):

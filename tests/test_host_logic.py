@@ -221,3 +221,16 @@ def test_caller_tables_that_disagree_are_refused(what, needle):
     with pytest.raises(S.SeswError, match=needle) as e:
         S.sesw_mesh_check(m, 64, edges=edges, areas=areas)
     assert e.value.code == S.SESW_EINVAL
+
+
+def test_bench_variants_run_on_the_channel():
+    """The scheme and optional-term variants default to the channel workload; the batched
+    ensemble and the surrogate refuse them."""
+    import bench
+
+    assert bench.parse([]).workload == "ensemble"
+    assert bench.parse(["--scheme", "sesm"]).workload == "channel"
+    assert bench.parse(["--visc", "auto"]).workload == "channel"
+    assert bench.parse(["--freshwater", "2e-6", "--workload", "sphere"]).workload == "sphere"
+    with pytest.raises(SystemExit):
+        bench.parse(["--scheme", "sesm", "--workload", "ensemble"])
