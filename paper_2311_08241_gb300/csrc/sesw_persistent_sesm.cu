@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
     const unsigned base = ld_relaxed_gpu(base_word);
     const unsigned abort_val = base + 1u == 0u ? 1u : base + 1u;   // never 0, unique per launch
 
-    float *sem = reinterpret_cast<float *>(smem_raw);   // eta_AM of the own vertices
+    float *sem = reinterpret_cast<float *>(smem_raw);   // eta_AM of the own vertices, then of the halo
     float *sflux = reinterpret_cast<float *>(smem_raw + P.off_flux);
     float4 *s_g = reinterpret_cast<float4 *>(smem_raw + P.off_g);
     float4 *s_c = reinterpret_cast<float4 *>(smem_raw + P.off_c);
@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
     // requested right after the first round
     const int ilast = threadIdx.x + (SPT - 1) * T;
     const bool early = SPT > 1 && ilast >= npre && ilast < ns;
+    // one thread per halo vertex requests its tagged word before the interior rounds and stores
+    // the value after the eta_AM of the own vertices; the other slots then read every corner
+    // from shared memory (patches with more halo vertices than threads keep the reads per slot)
+    const bool hpre = nhalo <= T;
     for (int m = 0; m <= P.M; m++) {
         const bool vertex = m < P.M;
         if (m == 0) {
@@ -118,6 +122,29 @@ __global__ void __launch_bounds__(kSesmThreads, 2) k_persistent_sesm(PArgs P)
                 const int i = threadIdx.x + j * T;
                 if (i < ns) transport(j, i, u1[j], u1[j], u1[j], s_g[i], s_c[i].x);
             }
+        } else if (hpre) {
+            const unsigned long long *xs = P.xb[m & 1];
+            const int hv = (int)threadIdx.x < nhalo ? s_halo[threadIdx.x] : -1;
+            const unsigned long long hw = hv >= 0 ? ld_relaxed_gpu_u64(xs + hv) : 0ull;
+#pragma unroll
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (i < npre) {
+                    const ushort4 l = s_l[i];
+                    slot(j, i, sem[l.x], sem[l.y], sem[l.z], vertex);
+                }
+            }
+            if (hv >= 0) sem[nown + threadIdx.x] = halo_eta(P, xs, hv, hw, base + (unsigned)m, abort_val, ok);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < SPT; j++) {
+                const int i = threadIdx.x + j * T;
+                if (i >= npre && i < ns) {
+                    const ushort4 l = s_l[i];
+                    slot(j, i, sem[l.x], sem[l.y], sem[l.z], vertex);
+                }
+            }
+            if (!ok) s_abort = 1;
         } else {
             const unsigned tag = base + (unsigned)m;
             const unsigned long long *xs = P.xb[m & 1];
