@@ -210,7 +210,8 @@ def issue_peak(device_sms, sm_max_mhz):
     return device_sms * 4 * sm_max_mhz * 1e6
 
 
-def roofline_issue(kernel, seconds, inst, dram, alg_bytes, sms, sm_max_mhz, per="launch"):
+def roofline_issue(kernel, seconds, inst, dram, alg_bytes, sms, sm_max_mhz, per="launch",
+                   alg_model="12 V + 92 E per substep"):
     """Roofline of an on-chip kernel: bound by instruction issue (warp instructions from the committed
     ncu capture / CUDA-event time, against the issue peak), with the DRAM rate of the same capture and
     the algorithmic-byte rate of the scope table beside it."""
@@ -227,7 +228,7 @@ def roofline_issue(kernel, seconds, inst, dram, alg_bytes, sms, sm_max_mhz, per=
                      "peak_source": src},
             "algorithmic": {"bytes_per_" + per: alg_bytes, "gbs": alg_bytes / seconds / 1e9,
                             "frac_of_hbm": alg_bytes / seconds / 1e9 / peak,
-                            "note": "scope-table bytes (12 V + 92 E per substep); the state stays on chip "
+                            "note": f"scope-table bytes ({alg_model}); the state stays on chip "
                                     "for the M substeps of a launch, so this is not a DRAM rate"}}
 
 
@@ -842,8 +843,10 @@ def run_ours(args, world, rank, local):
         # on chip for the M substeps of a launch: bound by instruction issue, not by DRAM
         fig = profile_figures(f"{kname}_{args.workload}", (kname,))
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        model = "24 V + 108 E per substep" if args.scheme == "sesm" else "12 V + 92 E per substep"
         roofline = roofline_issue(kname, launch_s, fig and fig.get("warp_instructions_per_launch"),
-                                  fig and fig.get("dram_bytes_per_launch"), per_launch, sms, sm_max_mhz_of(clk))
+                                  fig and fig.get("dram_bytes_per_launch"), per_launch, sms, sm_max_mhz_of(clk),
+                                  alg_model=model)
         if fig:
             roofline["profile"] = fig["profile"]
     else:
