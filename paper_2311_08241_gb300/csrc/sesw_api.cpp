@@ -694,6 +694,7 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
     TRY(zalloc(c, &d.patch_dt, hm.npatch, "patch_dt"));
+    TRY(zalloc(c, &d.slot_k, hm.nslot, "slot_k"));
     if (mode == SESW_MODE_PERSISTENT) {
         // the packs chosen with the layout: their patches, pack by pack
         std::vector<int> pp;
@@ -967,6 +968,7 @@ static int set_params_impl(sesw_ctx *c, int n, const sesw_params *ps)
         c->patch_dt_host[q] = (float)(ps[c->patch_basin[q]].tau / ps[c->patch_basin[q]].M);
     CK(c, cudaMemcpyAsync(c->dm.patch_dt, c->patch_dt_host.data(), sizeof(float) * c->patch_dt_host.size(),
                           cudaMemcpyHostToDevice, c->stream));
+    CK(c, sesw::launch_slot_coef(c->dm, a.g, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     c->courant_max = cmax_all;
     c->courant_limit = limit;

@@ -113,6 +113,8 @@ struct DevMesh {
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
     float *patch_dt = nullptr;     // [npatch] substep length tau/M of the patch's basin
+    float4 *slot_k = nullptr;      // [nslot] the persistent kernels' step coefficients of each slot,
+                                   // (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)), set with the parameters
     // barotropic viscosity, per slot (graph mode): edge k joins corners k and k+1; q_k is
     // the neighbour's owner slot (-1: coast), c_k its corner opposite the edge, h_k its
     // H0, a_k = L/d, b_k = L^2/d, (cos, sin)_k the turn from its frame into this one
@@ -283,6 +285,8 @@ cudaError_t launch_persistent_stream_group(const DevMesh &m, const DevState &s, 
 // 4 x 384 slots and 2 x 384 own vertices; an empty plan when the patches do not fit.
 PersistentPlan persistent_plan_sesm(const PatchMax &mx, int blocks_per_sm);
 cudaError_t persistent_prepare_sesm(const PersistentPlan &plan);
+// Fill m.slot_k from the slots' static data, g and each patch's substep length.
+cudaError_t launch_slot_coef(const DevMesh &m, float g, cudaStream_t stream);
 cudaError_t launch_persistent_sesm(const DevMesh &m, const DevState &s, const StepArgs &a, int M, int parity,
                                    const std::vector<PackPlan> &packs, cudaStream_t stream);
 

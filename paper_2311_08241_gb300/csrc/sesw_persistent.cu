@@ -49,10 +49,21 @@ __device__ __forceinline__ void element_update(const float e0, const float e1, c
     corner_fluxes<PACKED>(F, g, coef.x, flux3);
 }
 
-__device__ __forceinline__ float4 slot_coef(const float4 c, const StepArgs &a, float dt)
+__device__ __forceinline__ float4 slot_coef(const float4 c, float g, float dt)
 {
     const float aa = __fmul_rn(c.z, __fmul_rn(0.5f, dt));
-    return make_float4(__fmul_rn(dt, c.x), __fmul_rn(a.g, c.y), aa, __frcp_rn(__fmaf_rn(aa, aa, 1.0f)));
+    return make_float4(__fmul_rn(dt, c.x), __fmul_rn(g, c.y), aa, __frcp_rn(__fmaf_rn(aa, aa, 1.0f)));
+}
+
+// The step coefficients of every slot, once per parameter change: the persistent kernels
+// read them instead of forming them each substep (or in each launch's prologue).
+__global__ void k_slot_coef(int npatch, const int *__restrict__ patch_slot, const float *__restrict__ patch_dt,
+                            const float4 *__restrict__ sc, float g, float4 *__restrict__ sk)
+{
+    for (int p = blockIdx.x; p < npatch; p += gridDim.x) {
+        const float dt = patch_dt[p];
+        for (int s = patch_slot[p] + threadIdx.x; s < patch_slot[p + 1]; s += blockDim.x) sk[s] = slot_coef(sc[s], g, dt);
+    }
 }
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set;
@@ -89,7 +100,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
     if (CACHED == 1) {
         for (int i = threadIdx.x; i < ns; i += T) {
             s_g[i] = P.sg[s0 + i];
-            s_c[i] = slot_coef(P.sc[s0 + i], a, dt);
+            s_c[i] = P.sk[s0 + i];
             s_r[i] = P.R[s0 + i];
             s_l[i] = P.sl[s0 + i];
         }
@@ -131,7 +142,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                     l = s_l[i];
                 } else {
                     g = P.sg[s0 + i];
-                    coef = slot_coef(P.sc[s0 + i], a, dt);
+                    coef = P.sk[s0 + i];
                     r = P.R[s0 + i];
                     l = P.sl[s0 + i];
                 }
@@ -168,7 +179,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
             r = s_r[i];
         } else {
             g = P.sg[s0 + i];
-            coef = slot_coef(P.sc[s0 + i], a, dt);
+            coef = P.sk[s0 + i];
             r = P.R[s0 + i];
         }
         float2 uu = u[0], sh = shi[0], sl = slo[0];
@@ -480,6 +491,14 @@ cudaError_t launch_persistent(const DevMesh &m, const DevState &s, const StepArg
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_slot_coef(const DevMesh &m, float g, cudaStream_t stream)
+{
+    if (m.npatch <= 0) return cudaSuccess;
+    k_slot_coef<<<std::min(m.npatch, 152 * 16), 256, 0, stream>>>(m.npatch, m.patch_slot, m.patch_dt, m.slot_c, g,
+                                                                 m.slot_k);
+    return cudaGetLastError();
 }
 
 }  // namespace sesw

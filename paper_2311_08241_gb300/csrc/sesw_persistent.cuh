@@ -47,6 +47,7 @@ struct PArgs {
     const int4 *sv;
     const ushort4 *sl;
     const float4 *sg, *sc;
+    const float4 *sk;          // step coefficients of each slot (DevMesh::slot_k)
     const float2 *R;
     float2 *U, *Umean;
     const float *inv_av;
@@ -258,6 +259,7 @@ inline PArgs make_pargs(const DevMesh &m, const DevState &s, const StepArgs &a, 
     P.sl = m.slot_l;
     P.sg = m.slot_g;
     P.sc = m.slot_c;
+    P.sk = m.slot_k;
     P.R = s.R;
     P.U = s.U;
     P.Umean = s.Umean;

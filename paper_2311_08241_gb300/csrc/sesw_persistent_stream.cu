@@ -59,7 +59,8 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
 {
     const PArgs &P = A.P;
     const StepArgs &a = P.a;
-    const float4 g = __ldg(P.sg + s), c = __ldg(P.sc + s);
+    // c = (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)), formed once per parameter change
+    const float4 g = __ldg(P.sg + s), c = __ldg(P.sk + s);
     const float2 r = __ldg(P.R + s);
     float2 u = P.U[s];
     float2 shi = make_float2(0.0f, 0.0f), slo = shi;
@@ -67,9 +68,7 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
         shi = A.Shi[s];
         slo = A.Slo[s];
     }
-    const float aa = __fmul_rn(c.z, __fmul_rn(0.5f, dt));
-    const float inv = __frcp_rn(__fmaf_rn(aa, aa, 1.0f));
-    const float2 F = se_transport<NONLIN, kStreamPacked>(e0, e1, e2, g, __fmul_rn(a.g, c.y), a.g, aa, inv, dt, r,
+    const float2 F = se_transport<NONLIN, kStreamPacked>(e0, e1, e2, g, c.y, a.g, c.z, c.w, dt, r,
                                           __fadd_rn(1.0f, a.theta), a.theta, u);
     P.U[s] = u;
     if (owned) {
@@ -77,7 +76,7 @@ __device__ __forceinline__ void stream_slot(const SArgs &A, int s, int i, bool o
         A.Shi[s] = shi;
         A.Slo[s] = slo;
     }
-    corner_fluxes<kStreamPacked>(F, g, __fmul_rn(dt, c.x), sflux + 3 * i);
+    corner_fluxes<kStreamPacked>(F, g, c.x, sflux + 3 * i);
 }
 
 // EXTRA: the optional per-vertex terms (freshwater flux, step-mean elevation) may be set.
