@@ -276,7 +276,7 @@ int sesw_set_persistent_form(sesw_ctx *ctx, int32_t form);
  * (bitwise). Takes effect at the next mesh upload. */
 int sesw_set_large_basins(sesw_ctx *ctx, int32_t blocks_per_sm, int32_t form);
 
-/* Persistent mode: resident blocks (patches) per SM, 1, 2 or 4; 0 (default) tries 2
+/* Persistent mode: resident blocks (patches) per SM, 1 to 4; 0 (default) tries 2
  * and falls back to 1. Takes effect at the next mesh upload. */
 int sesw_set_blocks_per_sm(sesw_ctx *ctx, int32_t blocks_per_sm);
 

@@ -334,7 +334,7 @@ int sesw_set_block_threads(sesw_ctx *c, int32_t threads)
 int sesw_set_blocks_per_sm(sesw_ctx *c, int32_t k)
 {
     if (!c) return SESW_EINVAL;
-    if (k != 0 && k != 1 && k != 2 && k != 4) return fail(c, SESW_EINVAL, "blocks_per_sm must be 0, 1, 2 or 4");
+    if (k < 0 || k > 4) return fail(c, SESW_EINVAL, "blocks_per_sm must be 0, 1, 2, 3 or 4");
     c->blocks_per_sm = k;
     return SESW_OK;
 }
@@ -351,8 +351,8 @@ int sesw_set_persistent_form(sesw_ctx *c, int32_t form)
 int sesw_set_large_basins(sesw_ctx *c, int32_t blocks_per_sm, int32_t form)
 {
     if (!c) return SESW_EINVAL;
-    if (blocks_per_sm != 0 && blocks_per_sm != 1 && blocks_per_sm != 2 && blocks_per_sm != 4)
-        return fail(c, SESW_EINVAL, "blocks_per_sm must be 0, 1, 2 or 4");
+    if (blocks_per_sm < 0 || blocks_per_sm > 4)
+        return fail(c, SESW_EINVAL, "blocks_per_sm must be 0, 1, 2, 3 or 4");
     if (form < -1 || form > SESW_FORM_STREAM_UNCACHED)
         return fail(c, SESW_EINVAL, "form must be -1 or one of SESW_FORM_AUTO, _REGISTERS, _STREAM, _STREAM_UNCACHED");
     c->large_bps = blocks_per_sm;

@@ -112,7 +112,7 @@ def full_ensemble():
     return cases, ref, r32
 
 
-@pytest.mark.parametrize("bps", [1, 2, 4])
+@pytest.mark.parametrize("bps", [1, 2, 3, 4])
 def test_full_size_ensemble_matches_oracle(S, full_ensemble, bps):
     """Every basin of the full-size ensemble, advanced as one batch in persistent packs (the layouts
     the benchmark's autotuner chooses among), against the oracle: within twice the FP32 oracle's
