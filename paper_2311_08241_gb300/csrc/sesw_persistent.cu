@@ -111,6 +111,9 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
         for (int i = threadIdx.x; i < nhalo; i += T) s_halo[i] = P.halo_v[hb + i];
     }
     if (threadIdx.x == 0) s_abort = 0;
+    // CACHED == 2: the low parts of the compensated sums live in shared memory (in the place
+    // of the static slot data, which this form does not cache), to spare registers
+    float2 *s_slo = reinterpret_cast<float2 *>(smem_raw + P.off_g);
     float2 u[SPT], shi[SPT], slo[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; j++) {
@@ -118,6 +121,7 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
         u[j] = i < ns ? P.U[s0 + i] : make_float2(0.0f, 0.0f);
         shi[j] = make_float2(0.0f, 0.0f);
         slo[j] = make_float2(0.0f, 0.0f);
+        if (CACHED == 2 && i < ns) s_slo[i] = make_float2(0.0f, 0.0f);
     }
     __syncthreads();
 
@@ -162,7 +166,8 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
                     e1 = seta[l.y];
                     e2 = seta[l.z];
                 }
-                element_update<NONLIN, CACHED == 1 ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, u[j], shi[j], slo[j], i < nown_s, sflux + 3 * i,
+                element_update<NONLIN, CACHED == 1 ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, u[j], shi[j],
+                                       CACHED == 2 ? s_slo[i] : slo[j], i < nown_s, sflux + 3 * i,
                                        a.theta, one_p_theta, dt, a.g);
             }
         }
@@ -186,11 +191,13 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
 #pragma unroll
         for (int q = 1; q < SPT; q++)
             if (q == j) { uu = u[q]; sh = shi[q]; sl = slo[q]; }
+        if (CACHED == 2) sl = s_slo[i];
         element_update<NONLIN, CACHED == 1 ? 1 : kUncachedPacked>(e0, e1, e2, g, coef, r, uu, sh, sl, i < nown_s, sflux + 3 * i, a.theta,
                                one_p_theta, dt, a.g);
 #pragma unroll
         for (int q = 0; q < SPT; q++)
             if (q == j) { u[q] = uu; shi[q] = sh; slo[q] = sl; }
+        if (CACHED == 2) s_slo[i] = sl;
     };
 
     // Slots updated first: whole rounds of interior slots (one per thread each), so that
@@ -328,7 +335,8 @@ __device__ __forceinline__ void persistent_patch(const PArgs &P, const int p, co
             P.U[s0 + i] = u[j];
             if (i < nown_s) {
                 const int w = P.sv[s0 + i].w;
-                P.Umean[w] = make_float2((shi[j].x + slo[j].x) * a.inv_M, (shi[j].y + slo[j].y) * a.inv_M);
+                const float2 lo = CACHED == 2 ? s_slo[i] : slo[j];
+                P.Umean[w] = make_float2((shi[j].x + lo.x) * a.inv_M, (shi[j].y + lo.y) * a.inv_M);
             }
         }
     }
@@ -437,10 +445,14 @@ PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
     if (m.csr < 65536 && 3 * (size_t)m.slots < 65536) {
         if (spt <= 4 && L.total_cached <= budget && m.slots < 16384)
             cached = 1;
-        else if (spt >= 4 && L.total_vcached <= budget && persistent_kernel(spt, 0, 2, 0))
+        else if (spt >= 4 && L.total_vcached + sizeof(float2) * (size_t)m.slots <= budget &&
+                 persistent_kernel(spt, 0, 2, 0))
             cached = 2;
     }
-    const size_t smem = cached == 1 ? L.total_cached : cached == 2 ? L.total_vcached : L.total_plain;
+    // cached = 2 keeps the low parts of the slots' compensated sums where the static data would go
+    const size_t smem = cached == 1   ? L.total_cached
+                        : cached == 2 ? L.total_vcached + sizeof(float2) * (size_t)m.slots
+                                      : L.total_plain;
     if (smem > budget) return plan;
     // every variant the plan may launch must reach blocks_per_sm resident blocks
     for (int nonlin = 0; nonlin < 2; nonlin++)
