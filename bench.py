@@ -48,6 +48,9 @@ def parse(argv=None):
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["auto", "graph", "persistent"], default="auto")
+    ap.add_argument("--persistent-form", choices=["auto", "registers", "stream", "stream-uncached"], default="auto",
+                    help="channel and sphere: kernel form of the persistent mode (auto: registers unless a "
+                         "patch needs 8 or more slots per thread)")
     ap.add_argument("--scheme", choices=["se", "sesm"], default="se",
                     help="se: dissipative forward-backward (Eq. 4.10); sesm: AB3-AM4 (Eqs. 4.7-4.8)")
     ap.add_argument("--visc", type=str, default=None, metavar="A_BG,C_V",
@@ -763,6 +766,9 @@ def run_ours(args, world, rank, local):
     sim = S.Subcycle(local, stream=stream)
     sim.sesw_set_mode({"auto": S.SESW_MODE_AUTO, "graph": S.SESW_MODE_GRAPH,
                        "persistent": S.SESW_MODE_PERSISTENT}[args.mode])
+    sim.sesw_set_persistent_form({"auto": S.SESW_FORM_AUTO, "registers": S.SESW_FORM_REGISTERS,
+                                  "stream": S.SESW_FORM_STREAM,
+                                  "stream-uncached": S.SESW_FORM_STREAM_UNCACHED}[args.persistent_form])
     pv = args.patch_vertices
     if pv is None:
         if args.visc:

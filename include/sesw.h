@@ -277,7 +277,10 @@ int sesw_set_persistent_form(sesw_ctx *ctx, int32_t form);
 int sesw_set_large_basins(sesw_ctx *ctx, int32_t blocks_per_sm, int32_t form);
 
 /* Persistent mode: resident blocks (patches) per SM, 1 to 4; 0 (default) tries 2
- * and falls back to 1. Takes effect at the next mesh upload. */
+ * and falls back to 1. With 0, a single mesh whose patches at 2 blocks per SM do not keep all
+ * their data on chip takes 1 block per SM when every patch then runs the register kernel (the
+ * choice is made for the SE scheme: the SESM streaming kernel on such a mesh, e.g. the level-8
+ * sphere, is faster at 2). Takes effect at the next mesh upload. */
 int sesw_set_blocks_per_sm(sesw_ctx *ctx, int32_t blocks_per_sm);
 
 /* Threads per block of the substep kernel (a multiple of 32 in [32, 1024]);

@@ -25,11 +25,13 @@ def _ensemble(n=6, scale=0.02, seed=20231118):
     return I.ensemble_cases(nbasins=n, scale=scale, seed=seed, nsteps=3)
 
 
-def _run_batch(S, cases, mode, nsteps, patch_vertices=None):
+def _run_batch(S, cases, mode, nsteps, patch_vertices=None, large_form=None):
     with S.Subcycle() as s:
         s.sesw_set_mode(mode)
         if patch_vertices:
             s.sesw_set_patch_vertices(patch_vertices)
+        if large_form is not None:
+            s.sesw_set_large_basins(0, large_form)
         s.sesw_mesh_upload_batch([c.mesh for c in cases])
         s.sesw_set_params_batch([c.params for c in cases])
         s.sesw_set_forcing(np.concatenate([c.R for c in cases]))
@@ -143,17 +145,13 @@ def test_full_size_ensemble_matches_oracle(S, full_ensemble, bps):
 
 
 def test_batch_mixes_streamed_and_cached_packs(S):
-    """One step launching different kernels per pack: the level-8 sphere (too large for the register
-    kernel, so its pack streams its state from L2) batched with small basins (cached packs). Every
-    basin against the oracle."""
+    """One step launching different kernels per pack: the level-8 sphere (a large basin whose pack
+    streams its state from L2) batched with small basins (cached packs). Every basin against the
+    oracle."""
     sphere = I.sphere_case(level=8, nsteps=2)
     small = I.ensemble_cases(nbasins=3, vmin=5000, vmax=20000, M=sphere.params.M, nsteps=2, seed=5)
-    with S.Subcycle() as s:
-        s.sesw_set_mode(PERSISTENT)
-        s.sesw_mesh_upload(sphere.mesh)
-        assert s.sesw_get_info()["streamed"] == 1
     cases = small + [sphere]
-    (eta, U, Um), info, _ = _run_batch(S, cases, PERSISTENT, 2)
+    (eta, U, Um), info, _ = _run_batch(S, cases, PERSISTENT, 2, large_form=S.SESW_FORM_STREAM)
     assert info["mode"] == PERSISTENT and info["npack"] >= 2, info
     assert info["streamed"] == 0 and info["cached"] == 1, info     # the first pack: the small basins
     for c, e, u, um in zip(cases, _split(cases, eta, "v"), _split(cases, U, "e"), _split(cases, Um, "e")):

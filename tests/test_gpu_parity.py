@@ -315,12 +315,14 @@ def test_persistent_tags_continue_across_launches_with_changing_substep_counts(s
 
 
 def test_streaming_layout_with_freshwater_and_step_mean(sesw):
-    """Patches too large for the register kernel (the level-8 sphere in automatic mode) stream their
-    transport, sums and static data from L2. Its variant with the per-vertex terms: the freshwater
-    flux over 2 steps against the oracle, and the step-mean elevation of one step."""
+    """The streaming kernel (the level-8 sphere's patches at two blocks per SM, form streamed): the
+    transport, sums and static data stream from L2. Its variant with the per-vertex terms: the
+    freshwater flux over 2 steps against the oracle, and the step-mean elevation of one step."""
     case = I.sphere_case(level=8, nsteps=2)
     W = 2e-6 * (0.3 + np.random.default_rng(31).standard_normal(case.mesh.nv))
     with sesw.Subcycle() as s:
+        s.sesw_set_blocks_per_sm(2)
+        s.sesw_set_persistent_form(sesw.SESW_FORM_STREAM)
         s.sesw_mesh_upload(case.mesh)
         info = s.sesw_get_info()
         assert info["mode"] == PERSISTENT and info["streamed"] == 1, info

@@ -33,9 +33,11 @@ def _sesm(case, theta=0.14):
     return closed.sesm_params(theta / 2.0)
 
 
-def _run(S, case, nsteps, mode=GRAPH):
+def _run(S, case, nsteps, mode=GRAPH, bps=None):
     with S.Subcycle() as s:
         s.sesw_set_mode(mode)
+        if bps:
+            s.sesw_set_blocks_per_sm(bps)
         s.sesw_mesh_upload(case.mesh)
         s.sesw_set_params(case.params)
         s.sesw_set_forcing(case.R)
@@ -171,7 +173,7 @@ def test_sesm_streamed_on_the_sphere_matches_oracle(S):
     persistent layout streams the transport levels and sums from L2; 2 steps against the oracle."""
     case = I.sphere_case(level=8, nsteps=2)
     coef = _sesm(case)
-    (got, info) = _run(S, case, 2, PERSISTENT)
+    (got, info) = _run(S, case, 2, PERSISTENT, bps=2)
     assert info["mode"] == PERSISTENT and info["streamed"] == 1, info
     _check(case, coef, got, 2, "sphere8 SESM streamed")
 
