@@ -386,6 +386,7 @@ void *persistent_kernel(int spt, int nonlin, int cached, int extra)
         switch (spt) {
         case 4: return persistent_fn<4, 2>(nonlin, extra);
         case 6: return persistent_fn<6, 2>(nonlin, extra);
+        case 7: return persistent_fn<7, 2>(nonlin, extra);
         case 8: return persistent_fn<8, 2>(nonlin, extra);
         default: return nullptr;
         }
@@ -419,18 +420,6 @@ PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
     const int max_threads = 1024 / blocks_per_sm;
     // fewest slots per thread such that one block of at most max_threads covers the
     // largest patch; the block is then sized to that patch (multiple of 32)
-    static const int spts[] = {1, 2, 3, 4, 6, 8};
-    int spt = 0, t = 0;
-    for (int cand : spts) {
-        const int need = (m.slots + cand - 1) / cand;
-        const int tt = ((need + 31) / 32) * 32;
-        if (tt <= max_threads) {
-            spt = cand;
-            t = tt < 32 ? 32 : tt;
-            break;
-        }
-    }
-    if (!spt) return plan;
     const SmemLayout L = smem_layout(m);
     // per block: the opt-in limit, and the SM's capacity shared by blocks_per_sm blocks
     // (1 KB of each block's share is reserved by the system, plus the kernel's static shared)
@@ -438,6 +427,21 @@ PersistentPlan persistent_plan(const PatchMax &m, int blocks_per_sm)
     const size_t share = (size_t)smem_sm / (size_t)blocks_per_sm;
     if (share < 2048) return plan;
     budget = std::min(budget, share - 2048);
+    // 7 slots per thread exist only with the vertices' data in shared memory (cached = 2)
+    const bool vcached_fits = m.csr < 65536 && 3 * (size_t)m.slots < 65536 &&
+                              L.total_vcached + sizeof(float2) * (size_t)m.slots <= budget;
+    static const int spts[] = {1, 2, 3, 4, 6, 7, 8};
+    int spt = 0, t = 0;
+    for (int cand : spts) {
+        const int need = (m.slots + cand - 1) / cand;
+        const int tt = ((need + 31) / 32) * 32;
+        if (tt <= max_threads && (cand != 7 || vcached_fits)) {
+            spt = cand;
+            t = tt < 32 ? 32 : tt;
+            break;
+        }
+    }
+    if (!spt) return plan;
     // the cached variants index incidence entries and offsets with 16 bits; the slots' static
     // data join the vertices' data in shared memory when they fit (cached = 1), else only the
     // vertices' data (cached = 2, with 4 or more slots per thread)

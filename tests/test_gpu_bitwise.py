@@ -154,13 +154,13 @@ def test_batch_with_large_basins_on_their_own_residency(S):
 
 
 def test_sphere_register_and_streamed_layouts_are_bitwise_the_same(S):
-    """The level-8 sphere in automatic mode runs the register kernel at one block per SM with 8
+    """The level-8 sphere in automatic mode runs the register kernel at one block per SM with 7
     slots per thread, its vertices' data and compensation terms in shared memory; the streaming
     kernel at two blocks per SM gives bitwise the same 3 steps."""
     case = I.sphere_case(level=8, nsteps=3)
     got, info = _run(S, case, 3, PERSISTENT)
     assert info["mode"] == PERSISTENT and info["streamed"] == 0 and info["cached"] == 2, info
-    assert info["blocks_per_sm"] == 1 and info["slots_per_thread"] == 8, info
+    assert info["blocks_per_sm"] == 1 and info["slots_per_thread"] == 7, info
     ref, info2 = _run(S, case, 3, PERSISTENT, form=2, bps=2)
     assert info2["streamed"] == 1, info2
     _same(ref, got, "sphere8 registers vs streamed")
