@@ -717,6 +717,19 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
     TRY(upload(c, &d.h0_e, hm.h0_e, "h0_e"));
     TRY(upload(c, &d.vperm, hm.vperm, "vperm"));
     TRY(upload(c, &d.eperm, hm.eperm, "eperm"));
+    // caller-order maps, so that the state transfers read and write the caller's arrays in order
+    std::vector<int> slot_e(hm.nslot), einv(hm.ne), eown(hm.ne), vinv(hm.nv);
+    for (int s = 0; s < hm.nslot; s++) {
+        const int w = hm.slot_v[s].w;
+        slot_e[s] = hm.eperm[w >= 0 ? w : -1 - w];
+        if (w >= 0) eown[hm.eperm[w]] = s;
+    }
+    for (int w = 0; w < hm.ne; w++) einv[hm.eperm[w]] = w;
+    for (int v = 0; v < hm.nv; v++) vinv[hm.vperm[v]] = v;
+    TRY(upload(c, &d.slot_e, slot_e, "slot_e"));
+    TRY(upload(c, &d.einv, einv, "einv"));
+    TRY(upload(c, &d.eown, eown, "eown"));
+    TRY(upload(c, &d.vinv, vinv, "vinv"));
     TRY(zalloc(c, &d.patch_dt, hm.npatch, "patch_dt"));
     TRY(zalloc(c, &d.slot_k, hm.nslot, "slot_k"));
     if (mode == SESW_MODE_PERSISTENT) {

@@ -112,6 +112,11 @@ struct DevMesh {
     int *vperm = nullptr;
     int *eperm = nullptr;
     int *elem_slot = nullptr;      // new element -> owner slot
+    // caller-order maps of the state transfers
+    int *slot_e = nullptr;         // [nslot] caller element of each slot (owner and guest copies)
+    int *einv = nullptr;           // [ne] caller element -> new element
+    int *eown = nullptr;           // [ne] caller element -> its owner slot
+    int *vinv = nullptr;           // [nv] caller vertex -> new vertex
     float *patch_dt = nullptr;     // [npatch] substep length tau/M of the patch's basin
     float4 *slot_k = nullptr;      // [nslot] the persistent kernels' step coefficients of each slot,
                                    // (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)), set with the parameters

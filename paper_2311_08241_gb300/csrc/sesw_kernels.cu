@@ -304,14 +304,14 @@ __global__ void k_scatter_eta(const int *__restrict__ vperm, const double *__res
         eta[v] = (float)in[vperm[v]];
 }
 
-// Copy a caller-order [ne][2] field into every slot (owner and guest copies alike).
-__global__ void k_scatter_slots(const int4 *__restrict__ sv, const int *__restrict__ eperm,
-                                const double *__restrict__ in, float2 *__restrict__ out, int nslot)
+// Copy a caller-order [ne][2] field into every slot (owner and guest copies alike); slot_e
+// holds each slot's caller element.
+__global__ void k_scatter_slots(const int *__restrict__ slot_e, const double *__restrict__ in,
+                                float2 *__restrict__ out, int nslot)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < nslot; s += gridDim.x * blockDim.x) {
-        const int w = sv[s].w;
-        const int e = eperm[w >= 0 ? w : -1 - w];
-        out[s] = make_float2((float)in[2 * (size_t)e], (float)in[2 * (size_t)e + 1]);
+        const size_t e = (size_t)slot_e[s];
+        out[s] = make_float2((float)in[2 * e], (float)in[2 * e + 1]);
     }
 }
 
@@ -322,26 +322,25 @@ __global__ void k_gather_scaled(const int *__restrict__ vperm, const float *__re
         out[vperm[v]] = (double)x[v] * scale;
 }
 
-__global__ void k_gather(const int4 *__restrict__ sv, const int *__restrict__ vperm, const int *__restrict__ eperm,
+// The state in caller order, written in order (the reads follow the inverse maps): eta of caller
+// vertex v, U from the owner slot and <<U>> of caller element e.
+__global__ void k_gather(const int *__restrict__ vinv, const int *__restrict__ einv, const int *__restrict__ eown,
                          const float *__restrict__ eta, const float2 *__restrict__ U,
                          const float2 *__restrict__ Umean, double *__restrict__ eta_out,
-                         double *__restrict__ U_out, double *__restrict__ Um_out, int nv, int nslot)
+                         double *__restrict__ U_out, double *__restrict__ Um_out, int nv, int ne)
 {
     const int stride = gridDim.x * blockDim.x;
     const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
     if (eta_out)
-        for (int v = t0; v < nv; v += stride) eta_out[vperm[v]] = (double)eta[v];
-    for (int s = t0; s < nslot; s += stride) {
-        const int w = sv[s].w;
-        if (w < 0) continue;
-        const int e = eperm[w];
+        for (int v = t0; v < nv; v += stride) eta_out[v] = (double)eta[vinv[v]];
+    for (int e = t0; e < ne; e += stride) {
         if (U_out) {
-            const float2 u = U[s];
+            const float2 u = U[eown[e]];
             U_out[2 * (size_t)e] = (double)u.x;
             U_out[2 * (size_t)e + 1] = (double)u.y;
         }
         if (Um_out) {
-            const float2 u = Umean[w];
+            const float2 u = Umean[einv[e]];
             Um_out[2 * (size_t)e] = (double)u.x;
             Um_out[2 * (size_t)e + 1] = (double)u.y;
         }
@@ -590,15 +589,13 @@ cudaError_t launch_scatter_state(const DevMesh &m, const DevState &s, const doub
     if (eta)
         k_scatter_eta<<<grid_for(m.nv, kAuxThreads), kAuxThreads, 0, stream>>>(m.vperm, eta, s.eta[parity], m.nv);
     if (U)
-        k_scatter_slots<<<grid_for(m.nslot, kAuxThreads), kAuxThreads, 0, stream>>>(m.slot_v, m.eperm, U, s.U,
-                                                                                      m.nslot);
+        k_scatter_slots<<<grid_for(m.nslot, kAuxThreads), kAuxThreads, 0, stream>>>(m.slot_e, U, s.U, m.nslot);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scatter_forcing(const DevMesh &m, const DevState &s, const double *R, cudaStream_t stream)
 {
-    k_scatter_slots<<<grid_for(m.nslot, kAuxThreads), kAuxThreads, 0, stream>>>(m.slot_v, m.eperm, R, s.R,
-                                                                                  m.nslot);
+    k_scatter_slots<<<grid_for(m.nslot, kAuxThreads), kAuxThreads, 0, stream>>>(m.slot_e, R, s.R, m.nslot);
     return cudaGetLastError();
 }
 
@@ -611,8 +608,8 @@ cudaError_t launch_gather_scaled(const DevMesh &m, const float *x, double scale,
 cudaError_t launch_gather_state(const DevMesh &m, const DevState &s, int parity, double *eta, double *U,
                                 double *Umean, cudaStream_t stream)
 {
-    k_gather<<<grid_for(m.nv > m.nslot ? m.nv : m.nslot, kAuxThreads), kAuxThreads, 0, stream>>>(
-        m.slot_v, m.vperm, m.eperm, s.eta[parity], s.U, s.Umean, eta, U, Umean, m.nv, m.nslot);
+    k_gather<<<grid_for(m.nv > m.ne ? m.nv : m.ne, kAuxThreads), kAuxThreads, 0, stream>>>(
+        m.vinv, m.einv, m.eown, s.eta[parity], s.U, s.Umean, eta, U, Umean, m.nv, m.ne);
     return cudaGetLastError();
 }
 
