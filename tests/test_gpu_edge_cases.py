@@ -126,3 +126,39 @@ def test_upload_with_caller_edges_and_areas(S, mode):
     for k in range(3):
         assert np.array_equal(out[0][k], out[1][k])
     _assert_close(case, out[1], f"basin with caller tables mode={mode}")
+
+
+@MODES
+def test_parameters_changed_between_steps(S, mode):
+    """The step coefficients follow every sesw_set_params: the channel advances 3 steps, then 2 with
+    another tau (hence dt) and g, then 2 with a third M; against the oracle run through the same
+    sequence, within twice the FP32 oracle's drift."""
+    import dataclasses
+
+    from parity_util import ENVELOPE_FACTOR, ULP_FLOOR, _maxabs
+
+    case = I.channel_case(nsteps=3)
+    p0 = case.params
+    seq = [(p0, 3), (dataclasses.replace(p0, tau=0.75 * p0.tau, g=9.7), 2),
+           (dataclasses.replace(p0, tau=0.75 * p0.tau, g=9.7, M=30), 2)]
+    with S.Subcycle() as s:
+        s.sesw_set_mode(mode)
+        s.sesw_mesh_upload(case.mesh)
+        s.sesw_set_forcing(case.R)
+        for k, (p, n) in enumerate(seq):
+            s.sesw_set_params(p)
+            if k == 0:
+                s.sesw_set_state(case.eta0, case.U0)
+            s.sesw_advance(n)
+        got = s.sesw_get_state()
+    refs = []
+    for L in (None, orc.lib_fp32()):
+        om = orc.OracleMesh(case.mesh, L) if L is not None else orc.OracleMesh(case.mesh)
+        eta, U = case.eta0, case.U0
+        for p, n in seq:
+            eta, U, Um, _ = om.advance(case.R, p, n, eta, U)
+        refs.append((eta, U, Um))
+    ref, r32 = refs
+    for k, name in enumerate(("eta", "U", "<<U>>")):
+        tol = ENVELOPE_FACTOR * _maxabs(r32[k] - ref[k]) + ULP_FLOOR * _maxabs(ref[k])
+        assert _maxabs(got[k] - ref[k]) <= tol, f"{name}: {_maxabs(got[k] - ref[k]):.3e} > {tol:.3e}"
