@@ -308,8 +308,8 @@ cudaError_t pack_linear_tc(int K, const __nv_bfloat16 *W, __nv_bfloat16 *packed,
 // The inputs of a message layer, formed inside the tensor-core layer from the hidden states:
 // kind 0, element rows, Z_e = [h_e, L sum_k dphi_k/dx h_vk, L sum_k dphi_k/dy h_vk] (K = 192);
 // kind 1, vertex rows, Z_v = [h_v, sum A_e h_e / sum A_e over the vertex's triangles] (K = 128).
-// The layer writes Y = tanh(Z W + b) and h_next = h + Y ([N][64] each; h_next must not alias
-// the inputs).
+// The layer writes Y = tanh(Z W + b) (unless Y is null) and h_next = h + Y ([N][64] each; h_next
+// must not alias the inputs).
 struct MsgLayerArgs {
     int kind;                   // 0 element rows, 1 vertex rows
     int N;                      // rows

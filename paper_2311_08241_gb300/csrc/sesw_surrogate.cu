@@ -729,8 +729,9 @@ cudaError_t dgrad(Surrogate &S, cudaStream_t st, const Layer &ly, int N, const f
     return mm(S, st, N, ly.C, ly.K, dA, S.w16 + ly.w, 1, nullptr, 0, nullptr, dZ);
 }
 
-// forward of one sample whose features are in S.xv, S.xe
-cudaError_t forward(Surrogate &S, cudaStream_t st)
+// forward of one sample whose features are in S.xv, S.xe; keep_y keeps each message layer's
+// activation Y for the backward pass (inference does without it)
+cudaError_t forward(Surrogate &S, cudaStream_t st, bool keep_y = true)
 {
     cudaError_t e;
     const Layer &lv0 = S.L[0], &le0 = S.L[1];
@@ -739,8 +740,11 @@ cudaError_t forward(Surrogate &S, cudaStream_t st)
     for (int l = 0; l < NL; l++) {
         const Layer &le = S.L[2 + 2 * l], &lv = S.L[3 + 2 * l];
         // h_e(l+1) = h_e(l) + y_e(l), then h_v(l+1) = h_v(l) + y_v(l) from h_e(l+1)
-        if ((e = msg_layer(S, st, le, 0, S.he[l], S.hv[l], S.ye[l], S.he[l + 1])) != cudaSuccess) return e;
-        if ((e = msg_layer(S, st, lv, 1, S.hv[l], S.he[l + 1], S.yv[l], S.hv[l + 1])) != cudaSuccess) return e;
+        if ((e = msg_layer(S, st, le, 0, S.he[l], S.hv[l], keep_y ? S.ye[l] : nullptr, S.he[l + 1])) != cudaSuccess)
+            return e;
+        if ((e = msg_layer(S, st, lv, 1, S.hv[l], S.he[l + 1], keep_y ? S.yv[l] : nullptr, S.hv[l + 1])) !=
+            cudaSuccess)
+            return e;
     }
     const Layer &leo = S.L[2 + 2 * NL], &lvo = S.L[3 + 2 * NL];
     if ((e = mm(S, st, S.E, HC, 4, S.he[NL], S.w16 + leo.w, 0, S.w32 + leo.b, 0, nullptr, S.oe)) != cudaSuccess) return e;
@@ -1227,7 +1231,7 @@ int sesw_surrogate_advance(sesw_ctx *c, int32_t nsteps, double resid_tol, int32_
         SCK(cudaMemcpyAsync(S.save_U, c->ds.U, sizeof(float2) * c->dm.nslot, cudaMemcpyDeviceToDevice, c->stream));
         sesw::k_features<<<sesw::grid1(std::max(S.V, S.E)), 256, 0, c->stream>>>(
             S.V, S.E, S.cur_eta, S.cur_U, S.cur_R, c->dm.h0_v, S.eH0, S.ef, S.scales, S.xv, S.xe);
-        SCK(sesw::forward(S, c->stream));
+        SCK(sesw::forward(S, c->stream, false));
         sesw::k_apply_elems<<<sesw::grid1(c->dm.nslot), 256, 0, c->stream>>>(S.E, c->dm.nslot, c->dm.slot_v, S.oe,
                                                                               S.scales, S.cur_U, c->ds.U, c->ds.Umean);
         float *eta1 = c->ds.eta[c->parity ^ 1];

@@ -328,7 +328,7 @@ k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *
             float acc[16];
             tmem_ld16(taddr + q * 16, acc);
             if (n < N) {
-                float4 *dy = reinterpret_cast<float4 *>(a.Y + (size_t)n * TC_N + q * 16);
+                float4 *dy = a.Y ? reinterpret_cast<float4 *>(a.Y + (size_t)n * TC_N + q * 16) : nullptr;
                 float4 *dh = reinterpret_cast<float4 *>(a.hnext + (size_t)n * TC_N + q * 16);
 #pragma unroll
                 for (int t = 0; t < 16; t += 4) {
@@ -336,7 +336,7 @@ k_msg_layer_tc(const MsgLayerArgs a, const uint4 *__restrict__ Wp, const float *
 #pragma unroll
                     for (int u = 0; u < 4; u++) y[u] = tanhf(__fadd_rn(acc[t + u], bias[q * 16 + t + u]));
                     const float4 h = hres[(q - 2 * half) * 4 + t / 4];
-                    dy[t / 4] = make_float4(y[0], y[1], y[2], y[3]);
+                    if (dy) dy[t / 4] = make_float4(y[0], y[1], y[2], y[3]);
                     dh[t / 4] = make_float4(__fadd_rn(h.x, y[0]), __fadd_rn(h.y, y[1]), __fadd_rn(h.z, y[2]),
                                             __fadd_rn(h.w, y[3]));
                 }
