@@ -19,12 +19,17 @@ namespace {
 // Substep m: update the interior slots (corners all own vertices); update the other
 // slots, reading the halo elevation from the exchange buffer of parity m; vertex pass;
 // write the own vertices' new elevation to the exchange buffer of parity m+1 (the
-// exchange protocol is described in sesw_persistent.cuh).
+// exchange protocol is described in sesw_persistent.cuh). In the cached forms one thread
+// per halo vertex fetches the halo elevation into shared memory during the interior rounds.
 //
 // Vertex order. Mesh preparation puts the vertices that other patches read first in
-// each patch, so the vertex pass publishes them in its first round; the halo words of a
-// thread's last-round slot are then requested right after its first element round and
-// have usually arrived by the time the slot is updated.
+// each patch, so the vertex pass publishes them in its first round; where a patch has more
+// halo vertices than threads, the halo words of a thread's last-round slot are requested
+// right after its first element round and have usually arrived by the time the slot is
+// updated.
+//
+// The slots' step coefficients come from DevMesh::slot_k (formed once per parameter change);
+// with CACHED = 2 the low parts of the compensated sums live in shared memory.
 
 // Element update of one slot (Eq. 4.10, first row, and the theta-weighted flux);
 // coef = (dt A_e, g H0_e, f dt / 2, 1 / (1 + (f dt / 2)^2)).
