@@ -111,7 +111,6 @@ struct DevMesh {
     double *h0_e = nullptr;        // FP64 diagnostics
     int *vperm = nullptr;
     int *eperm = nullptr;
-    int *elem_slot = nullptr;      // new element -> owner slot
     // caller-order maps of the state transfers
     int *slot_e = nullptr;         // [nslot] caller element of each slot (owner and guest copies)
     int *einv = nullptr;           // [ne] caller element -> new element
