@@ -185,9 +185,10 @@ typedef struct sesw_info {
     int32_t slots_per_thread;/* persistent mode: element slots per thread (held in registers,
                                 or slot-loop rounds when streamed) */
     int32_t cached;          /* persistent mode, register kernels: 1 when the static slot data lives in
-                                shared memory, 2 when the vertices' data does and the static data of
-                                the first rounds of slots (large patches); streaming kernels
-                                (streamed != 0): 1 when the vertices' data lives in shared memory */
+                                shared memory, 2 when the vertices' data and the low parts of the
+                                compensated sums do and the static slot data are read from L2
+                                (large patches); streaming kernels (streamed != 0): 1 when the
+                                vertices' data lives in shared memory */
     int32_t nbasin;          /* meshes in the uploaded batch (1 for sesw_mesh_upload) */
     double courant_max;      /* estimated largest substep Courant number sqrt(gH kappa^2) dt
                                 (0 until parameters are set) */
@@ -248,10 +249,12 @@ int sesw_set_patch_vertices(sesw_ctx *ctx, int32_t patch_vertices);
 int sesw_set_mode(sesw_ctx *ctx, int32_t mode);
 
 /* Persistent mode: which kernel form each pack (one cooperative launch) runs.
- *   SESW_FORM_AUTO             the register form where a thread holds at most 6 slots, else
- *                              the streaming form (default)
+ *   SESW_FORM_AUTO             the register form where a thread holds at most 6 slots, or 7 or
+ *                              8 with the vertices' data and compensation terms in shared
+ *                              memory; else the streaming form (default)
  *   SESW_FORM_REGISTERS        transports and sums in registers, static slot data in shared
- *                              memory when it fits (sesw_info.streamed = 0)
+ *                              memory when it fits, else the vertices' data and the low parts of
+ *                              the compensated sums (sesw_info.streamed = 0)
  *   SESW_FORM_STREAM           transports, sums and static data read from L2 slot by slot,
  *                              corner indices in shared memory when they fit (streamed = 1, else 2)
  *   SESW_FORM_STREAM_UNCACHED  the streaming form with the corner indices read from L2 too
