@@ -234,3 +234,31 @@ def test_bench_variants_run_on_the_channel():
     assert bench.parse(["--freshwater", "2e-6", "--workload", "sphere"]).workload == "sphere"
     with pytest.raises(SystemExit):
         bench.parse(["--scheme", "sesm", "--workload", "ensemble"])
+
+
+def test_bench_issue_roofline_and_profile_figures(tmp_path, monkeypatch):
+    """The issue-bound roofline divides warp instructions by time against SMs x 4 x clock, and
+    the committed kernel summaries are read only when their source hash matches, per layout."""
+    import bench
+
+    r = bench.roofline_issue("k", 2e-3, 1.2e9, 4e8, 3e10, 152, 2070.0, per="step")
+    peak = 152 * 4 * 2070e6
+    assert r["bound"] == "issue" and abs(r["peak"] - peak) < 1.0
+    assert abs(r["achieved"] - 6e11) < 1.0 and abs(r["frac"] - 6e11 / peak) < 1e-12
+    assert abs(r["dram"]["achieved_gbs"] - 200.0) < 1e-9
+    assert abs(r["algorithmic"]["gbs"] - 15000.0) < 1e-6
+    assert bench.roofline_issue("k", 1e-3, None, None, 1e9, 152, 2070.0)["frac"] is None
+
+    h = bench.kernel_source_hash(("k_persistent",))
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "x.md").write_text(f"kernel_source_sha256_16: {h}\n\nlayout: a\nwarp_instructions_per_step: 5\n"
+                               "dram_bytes_per_step: 7\n\nlayout: b\nwarp_instructions_per_step: 11\n")
+    (prof / "stale.md").write_text("kernel_source_sha256_16: 0000000000000000\nwarp_instructions_per_launch: 3\n")
+    real_join = bench.os.path.join
+    monkeypatch.setattr(bench.os.path, "join",
+                        lambda *a: str(prof / a[-1]) if len(a) == 3 and a[1] == "profiles" else real_join(*a))
+    assert bench.profile_figures("x", ("k_persistent",), layout="a")["warp_instructions_per_step"] == 5.0
+    assert bench.profile_figures("x", ("k_persistent",), layout="b")["warp_instructions_per_step"] == 11.0
+    assert bench.profile_figures("x", ("k_persistent",), layout="c") is None
+    assert bench.profile_figures("stale", ("k_persistent",)) is None
