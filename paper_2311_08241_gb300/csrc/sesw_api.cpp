@@ -641,7 +641,11 @@ static int upload_batch(sesw_ctx *c, const sesw_mesh *meshes, int n)
                 std::vector<sesw::PackPlan> packs_try;
                 std::vector<std::vector<int>> basins_try;
                 rc = prepare_parts(c, meshes, n, pv, hm_try, err);
-                if (rc != SESW_OK) return fail(c, rc, err);
+                if (rc != SESW_OK) {
+                    // a layout already found stands; otherwise the mesh itself is at fault
+                    if (!packs.empty()) continue;
+                    return fail(c, rc, err);
+                }
                 if (sesw::build_halos(hm_try, err) == SESW_OK)
                     make_packs(hm_try, large, nblk, bps, c->form, nblk_large, bps_large, form_large, packs_try,
                                basins_try);
