@@ -262,3 +262,21 @@ def test_bench_issue_roofline_and_profile_figures(tmp_path, monkeypatch):
     assert bench.profile_figures("x", ("k_persistent",), layout="b")["warp_instructions_per_step"] == 11.0
     assert bench.profile_figures("x", ("k_persistent",), layout="c") is None
     assert bench.profile_figures("stale", ("k_persistent",)) is None
+
+
+def test_bench_reference_arm_on_a_small_ensemble():
+    """`bench.py --impl reference` times the oracle on the host cores and prints one JSON line with
+    the reference keys (a tiny ensemble of the default recipe, one step)."""
+    import json
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--ensemble-basins",
+                          "3", "--ensemble-scale", "0.03", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads([l for l in out.stdout.splitlines() if l.startswith("{")][-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == line["metric"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"]["value"] == line["value"] and line["e2e"]["h2d_bytes_per_step"] == 0
